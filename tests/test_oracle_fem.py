@@ -1,0 +1,168 @@
+"""Pins of the oracle's Q1/Q1-LPS operator, right-hand side and transfer
+against closed forms, a manufactured solution, finite differences and the
+Galerkin identities of nested spaces."""
+import numpy as np
+import pytest
+
+import mms
+from paper_2307_14837_gb300 import inputs as I
+from oracle import dnnmg, fem, mesh, solve, transfer
+
+
+def _fine(n, jitter=0.0, seed=0):
+    m = I.cavity_mesh(n, jitter=jitter, seed=seed)
+    h = mesh.Hierarchy(m["xyz"], m["cells"], m["vertex_bc"])
+    return m, h, dnnmg.fine_level(h)
+
+
+PRM0 = dict(m=0.0, theta=1.0, nu=0.0, alpha0=0.02, delta0=0.1, lps=False)
+
+
+def _op(lev, x, **kw):
+    return lev.operator(x, dict(PRM0, **kw))
+
+
+def _interior(lev):
+    x = lev.xyz
+    return ~np.any((np.abs(x) < 1e-12) | (np.abs(x - 1) < 1e-12), axis=1)
+
+
+@pytest.mark.parametrize("jitter", [0.0, 0.25])
+def test_mass_rows_sum_to_volume(jitter):
+    _, _, lev = _fine(2, jitter, seed=5)
+    x = np.zeros((lev.n, 4))
+    x[:, 0] = 1.0
+    R = _op(lev, x, m=1.0)
+    assert abs(R[:, 0].sum() - 1.0) < 1e-13          # unit cube
+    assert np.allclose(R[:, 0], lev.lumped_mass(), rtol=0, atol=1e-15)
+    assert np.abs(R[:, 1:]).max() < 1e-15
+
+
+@pytest.mark.parametrize("jitter", [0.0, 0.25])
+def test_divergence_of_linear_fields(jitter):
+    _, _, lev = _fine(2, jitter, seed=6)
+    A = np.array([[1.0, 2.0, -1.0], [0.5, -3.0, 2.0], [1.5, 0.25, 2.0]])   # trace 0
+    x = np.zeros((lev.n, 4))
+    x[:, 0:3] = lev.xyz @ A.T
+    R = _op(lev, x)
+    assert np.abs(R[:, 3]).max() < 1e-14
+    x[:, 0:3] = lev.xyz @ np.diag([1.0, 0.0, 0.0]).T     # div = 1
+    R = _op(lev, x)
+    assert np.allclose(R[:, 3], lev.lumped_mass(), rtol=0, atol=1e-15)
+
+
+def test_viscous_and_pressure_terms_on_linear_fields():
+    _, _, lev = _fine(2)
+    inner = _interior(lev)
+    A = np.array([[1.0, 2.0, -1.0], [0.5, -3.0, 2.0], [1.5, 0.25, 2.0]])
+    x = np.zeros((lev.n, 4))
+    x[:, 0:3] = lev.xyz @ A.T
+    R = _op(lev, x, nu=0.7) - _op(lev, x, nu=0.0)     # the viscous term alone
+    assert np.abs(R[inner, 0:3]).max() < 1e-14         # -nu Lap(linear) = 0
+    assert np.abs(R[~inner, 0:3]).max() > 1e-3
+    g = np.array([0.3, -1.2, 2.0])
+    x = np.zeros((lev.n, 4))
+    x[:, 3] = lev.xyz @ g + 0.7
+    R = _op(lev, x)
+    # -(p, d_c phi_j) = (d_c p, phi_j) for interior j
+    assert np.allclose(R[inner, 0:3], lev.lumped_mass()[inner, None] * g[None, :], rtol=0, atol=1e-14)
+    # constant pressure: no force on interior nodes; all rows sum to zero
+    x[:, 3] = 2.5
+    R = _op(lev, x)
+    assert np.abs(R[inner, 0:3]).max() < 1e-14
+    assert np.abs(R[:, 0:3].sum(axis=0)).max() < 1e-13
+
+
+def test_convection_equals_mass_of_advected_field():
+    # v = A x  =>  (v.grad) v = A A x, linear, so (conv, phi_j) = (A A x, phi_j)
+    _, _, lev = _fine(2)
+    A = np.array([[0.4, -1.0, 0.3], [0.7, 0.2, -0.5], [-0.2, 0.9, 0.1]])
+    x = np.zeros((lev.n, 4))
+    x[:, 0:3] = lev.xyz @ A.T
+    Rc = _op(lev, x)
+    y = np.zeros((lev.n, 4))
+    y[:, 0:3] = lev.xyz @ (A @ A).T
+    Rm = _op(lev, y, m=1.0) - _op(lev, y, m=0.0)      # the mass term alone
+    assert np.allclose(Rc[:, 0:3], Rm[:, 0:3], rtol=0, atol=1e-15)
+    assert np.allclose(Rc[:, 0:3].sum(axis=0), A @ A @ np.full(3, 0.5), rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("theta", [1.0, 0.5])
+def test_restriction_of_fine_rhs_equals_coarse_rhs(theta):
+    # nested spaces + exact quadrature on affine cells: P^T b_{L+1}(P v) = b_L(v)
+    m, h, lev = _fine(4)
+    coarse = fem.Level(m["xyz"], m["cells"], m["vertex_bc"], True)
+    prm = dict(m=100.0, theta=theta, nu=0.01)
+    v = I.coarse_state(m, 1)[:, 0:3]
+    bc = coarse.rhs(v, prm)
+    bc[h.dirichlet_coarse(), 0:3] = 0.0
+    br = transfer.restrict(h, lev.rhs(transfer.prolongate(h, v), prm))
+    assert np.abs(br - bc).max() <= 1e-13 * np.abs(bc).max()
+
+
+def test_prolongation_exact_for_trilinear_and_adjoint():
+    m, h, _ = _fine(4, jitter=0.2, seed=2)
+    X = m["xyz"][m["cells"]]
+    g = I.coarse_state(m, 4)
+    xf = transfer.prolongate(h, g)
+    for iota in range(27):
+        expect = np.einsum("k,nkc->nc", mesh.corner_weights(iota), g[m["cells"]])
+        assert np.allclose(xf[h.patch_map[:, iota]], expect, rtol=0, atol=1e-14)
+    # on a dyadic mesh a trilinear field is reproduced bit for bit
+    m2, h2, _ = _fine(4)
+    f = lambda p: 1.0 + 2.0 * p[:, 0] - 0.5 * p[:, 1] + 0.25 * p[:, 2] + p[:, 0] * p[:, 1] * p[:, 2]
+    assert np.array_equal(transfer.prolongate(h2, f(m2["xyz"])), f(h2.xyz_f))
+    # adjointness
+    rng = np.random.default_rng(0)
+    a = rng.standard_normal(h.n_coarse_vertices)
+    b = rng.standard_normal(h.n_fine)
+    P = transfer.prolongation_matrix(h)
+    assert abs(np.dot(transfer.prolongate(h, a), b) - np.dot(a, P.T @ b)) < 1e-12
+
+
+def test_lps_vanishes_on_prolongated_fields_only():
+    m, h, lev = _fine(4, jitter=0.2, seed=7)
+    xf = transfer.prolongate(h, I.coarse_state(m, 0))
+    Xg, Ug = lev.xyz[lev.groups], xf[lev.groups]
+    L = fem.group_lps(Xg, Ug, 100.0, 0.01, 0.02, 0.1)
+    assert np.abs(L).max() == 0.0
+    rng = np.random.default_rng(1)
+    Ur = Ug + 0.1 * rng.standard_normal(Ug.shape)
+    assert np.abs(fem.group_lps(Xg, Ur, 100.0, 0.01, 0.02, 0.1)).max() > 1e-6
+
+
+def test_complex_step_jacobian_matches_finite_differences():
+    m, h, lev = _fine(2, jitter=0.2, seed=9)
+    prm = dict(m=20.0, theta=0.5, nu=0.05, alpha0=0.02, delta0=0.1)
+    rng = np.random.default_rng(3)
+    x = I.coarse_state(dict(m, xyz=lev.xyz, vertex_bc=lev.bc), 2) + 0.05 * rng.standard_normal((lev.n, 4))
+    J = lev.jacobian(x, prm).toarray()
+    frozen = dict(prm, vref=x)            # parameters frozen, as in the Jacobian
+    eps = 1e-6
+    Jfd = np.empty_like(J)
+    for k in range(4 * lev.n):
+        dx = np.zeros(4 * lev.n)
+        dx[k] = eps
+        Jfd[:, k] = (lev.operator(x + dx.reshape(-1, 4), frozen).ravel()
+                     - lev.operator(x - dx.reshape(-1, 4), frozen).ravel()) / (2 * eps)
+    assert np.abs(J - Jfd).max() <= 1e-7 * np.abs(J).max()
+
+
+def test_manufactured_solution_convergence():
+    nu = 0.1
+    errs = []
+    for n in (2, 4):
+        m, h, lev = _fine(n)
+        prm = dict(m=10.0, theta=0.5, nu=nu, alpha0=0.02, delta0=0.1)
+        v, _ = mms.exact(lev.xyz)
+        f = mms.force(lev.xyz, nu)
+        F = lev.rhs(v, prm, f_new=f, f_old=f)
+        x0 = np.zeros((lev.n, 4))
+        x0[lev.dirichlet, 0:3] = v[lev.dirichlet]
+        x, info = solve.newton(lev, x0, F, prm)
+        assert info["residuals"][-1] < 1e-10
+        errs.append(mms.errors(lev, x))
+    rates = np.log2(np.array(errs[0]) / np.array(errs[1]))
+    assert rates[0] > 1.8, rates      # velocity L2 ~ h^2
+    assert rates[1] > 0.95, rates     # velocity H1 ~ h
+    assert rates[2] > 1.5, rates      # pressure L2 (LPS: at least h)

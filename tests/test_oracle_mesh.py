@@ -1,0 +1,118 @@
+"""Pins of the oracle's mesh hierarchy (refinement, patch map, valences,
+boundary kinds) against closed forms and brute force."""
+import os
+
+import numpy as np
+import pytest
+
+from paper_2307_14837_gb300 import inputs as I
+from oracle import fem, mesh
+
+
+def _hier(m):
+    return mesh.Hierarchy(m["xyz"], m["cells"], m["vertex_bc"])
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4])
+def test_counts_closed_form(n):
+    m = I.cavity_mesh(n, grouped=False)
+    h = _hier(m)
+    # (2n+1)^3 fine nodes; 3 n^2 (n+1) edges; 3 n (n+1)^2 faces
+    assert h.n_fine == (2 * n + 1) ** 3
+    assert h.n_edges == 3 * n * (n + 1) ** 2
+    assert h.n_faces == 3 * n * n * (n + 1)
+    assert h.mult.sum() == 27 * h.n_patches
+
+
+@pytest.mark.parametrize("n", [2, 3])
+def test_valence_closed_form_and_brute_force(n):
+    m = I.cavity_mesh(n, grouped=False)
+    h = _hier(m)
+    ijk = np.rint(h.xyz_f * 2 * n).astype(int)          # fine grid index 0..2n
+
+    def m1(i):
+        return np.where(i % 2 == 1, 1, np.where((i == 0) | (i == 2 * n), 1, 2))
+    closed = m1(ijk[:, 0]) * m1(ijk[:, 1]) * m1(ijk[:, 2])
+    assert np.array_equal(h.mult, closed)
+    # brute force: count coarse cells whose closed box contains the node
+    lo = m["xyz"][m["cells"][:, 0]]
+    hi = m["xyz"][m["cells"][:, 7]]
+    brute = np.array([np.sum(np.all((p >= lo - 1e-12) & (p <= hi + 1e-12), axis=1)) for p in h.xyz_f])
+    assert np.array_equal(h.mult, brute)
+
+
+@pytest.mark.parametrize("jitter", [0.0, 0.2])
+def test_patch_map_points_at_trilinear_positions(jitter):
+    m = I.cavity_mesh(4, jitter=jitter, seed=3)
+    h = _hier(m)
+    X = m["xyz"][m["cells"]]                              # [Nc, 8, 3]
+    for iota in range(27):
+        w = mesh.corner_weights(iota)
+        expect = np.einsum("k,nkd->nd", w, X)
+        got = h.xyz_f[h.patch_map[:, iota]]
+        assert np.allclose(got, expect, rtol=0, atol=1e-15)
+    # every patch has 27 distinct nodes
+    assert all(len(set(r)) == 27 for r in h.patch_map.tolist())
+
+
+def test_hierarchical_numbering():
+    m = I.cavity_mesh(2, grouped=False)
+    h = _hier(m)
+    nv = m["xyz"].shape[0]
+    # coarse vertices keep their numbers, cell centres come last in cell order
+    assert np.array_equal(h.patch_map[:, [0, 2, 6, 8, 18, 20, 24, 26]], m["cells"])
+    assert np.array_equal(h.patch_map[:, 13], nv + h.n_edges + h.n_faces + np.arange(8))
+    # first cell's 12 edges are numbered first, in local edge order
+    e_iota = [1, 7, 19, 25, 3, 5, 21, 23, 9, 11, 15, 17]
+    assert np.array_equal(h.patch_map[0, e_iota], nv + np.arange(12))
+
+
+def test_cavity_fine_boundary_kinds():
+    m = I.cavity_mesh(4)
+    h = _hier(m)
+    x = h.xyz_f
+    on_b = np.any((np.abs(x) < 1e-14) | (np.abs(x - 1) < 1e-14), axis=1)
+    lid = np.abs(x[:, 2] - 1) < 1e-14
+    expect = np.where(lid, 2, np.where(on_b, 1, 0))
+    assert np.array_equal(h.bc_f, expect)
+
+
+def test_channel_kinds_and_positive_jacobians():
+    m = I.channel_mesh(4, seed=1)
+    h = _hier(m)
+    x = h.xyz_f
+    H, Lx = I.CHANNEL_HEIGHT, I.CHANNEL_LENGTH
+    inflow = np.abs(x[:, 0]) < 1e-12
+    out = np.abs(x[:, 0] - Lx) < 1e-12
+    walls = (np.abs(x[:, 1]) < 1e-12) | (np.abs(x[:, 1] - H) < 1e-12) | \
+        (np.abs(x[:, 2]) < 1e-12) | (np.abs(x[:, 2] - H) < 1e-12)
+    assert np.all(h.bc_f[inflow] == 2)
+    assert np.all(h.bc_f[out & ~walls] == 3)
+    assert np.all(h.bc_f[out & walls] == 1)
+    assert np.all(h.bc_f[walls & ~inflow] == 1)
+    # every fine cell is a valid (positively oriented) hexahedron
+    det, _ = fem.cell_geometry(h.xyz_f[h.cells_f])
+    assert det.min() > 0
+
+
+def test_edge_lengths_cube():
+    m = I.cavity_mesh(4)
+    h = _hier(m)
+    assert np.allclose(h.edge_lengths(), 0.25, rtol=0, atol=1e-15)
+    # order: xi-edges measure along x
+    m2 = dict(m)
+    xyz = m["xyz"] * np.array([1.0, 2.0, 3.0])
+    h2 = mesh.Hierarchy(xyz, m["cells"], m["vertex_bc"])
+    e = h2.edge_lengths()
+    assert np.allclose(e[:, 0:4], 0.25) and np.allclose(e[:, 4:8], 0.5) and np.allclose(e[:, 8:12], 0.75)
+
+
+def test_golden_patch_sizes():
+    path = os.path.join(os.path.dirname(__file__), "golden", "patch_sizes.txt")
+    rows = [list(map(int, l.split())) for l in open(path) if l.strip() and not l.startswith("#")]
+    J1 = rows[0]
+    assert J1[1] == 27 and J1[2] == 4 * 27 and J1[4] == 2 * J1[2] + J1[3] and J1[5] == 3 * 27
+    # the build's patch: 27 nodes per coarse cell
+    m = I.cavity_mesh(2)
+    h = _hier(m)
+    assert h.patch_map.shape[1] == J1[1]
