@@ -1,0 +1,343 @@
+"""Benchmark of the DNN-MG patch-correction step on GB300.
+
+A step is one pass of the whole patch path (prolongation, fine residual,
+local restriction, patch network, extension, corrected rhs and restriction)
+over one coarse solution of the channel workload: ~314k coarse hexahedra
+(channel 2.5 x 0.41 x 0.41 with a seeded cylinder, nz = 37), ~2.5M fine cells,
+one patch per coarse cell, BF16 network 228-1024x4-81 with FP32 accumulation,
+FP32 fields, Crank-Nicolson dt = 0.005, Re = 200.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun) every rank runs an independent replica (weak scaling;
+the path has no data exchange between simulations); the time is the max over
+ranks.  --impl reference times the FP64 CPU oracle on a bounded sample of the
+same workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DNN-MG time steps/sec and patches/sec (BF16 batched vs plain FP64, same GPU, equal error)"
+UNIT = "steps/s"
+WIDTHS = (228, 1024, 1024, 1024, 1024, 81)
+NZ = 37
+DT, THETA = 0.005, 0.5
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def network_flops_per_patch(widths=WIDTHS):
+    return sum(2 * widths[i] * widths[i + 1] for i in range(len(widths) - 1))
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+
+    def summary(self):
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def build_workload(seed=0):
+    from paper_2307_14837_gb300 import inputs as I
+    m = I.channel_mesh(NZ, seed=seed)
+    nu = m["meta"]["D"] / 200.0          # Re = mean inflow * D / nu = 200
+    return m, nu
+
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    from paper_2307_14837_gb300 import capi, inputs as I
+    from paper_2307_14837_gb300.path import PatchPath
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    m, nu = build_workload(seed=rank)
+    stream = torch.cuda.Stream(dev)
+    p = PatchPath(m, nu, DT, THETA, "bf16", device=dev, stream=stream)
+    Ws, ss, ts = I.network_weights(WIDTHS, seed=0)
+    p.set_network(WIDTHS, Ws, ss, ts, skip=True)
+    nc, nf, nv = p.n_patches, p.n_fine, p.n_coarse
+    xc_h = I.coarse_state(m, seed=rank).astype(np.float32)
+    F_h = I.fine_rhs(nf, seed=rank, scale=(1 / DT) * 0.42 / (8 * nc)).astype(np.float32)
+    xc = p.to_device(xc_h)
+    Fa = p.to_device(F_h)
+    Fb = torch.empty_like(Fa)
+    bc = p.field(nv, 4)
+    r = p.field(nf, 4)
+    X = p.field(nc, 256, torch.bfloat16)
+    Y = p.field(nc, 81)
+    d = p.field(nf, 3)
+    ctx = p.ctx
+
+    def step(F_in, F_out, ev=None):
+        # the stages of dnnmg_patch_step, called one by one so that the
+        # network stage can be timed on its own (same kernels, same order)
+        capi.dnnmg_residual(ctx, xc, F_in, r)
+        capi.dnnmg_local_restrict(ctx, xc, r, X)
+        if ev:
+            ev[0].record(stream)
+        capi.dnnmg_network(ctx, X, Y, nc)
+        if ev:
+            ev[1].record(stream)
+        capi.dnnmg_extend(ctx, Y, d)
+        capi.dnnmg_rhs_restrict(ctx, xc, d, F_out, bc)
+
+    with torch.cuda.stream(stream):
+        for i in range(args.warmup):
+            step(Fa, Fb)
+            Fa, Fb = Fb, Fa
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+        n0 = capi.dnnmg_launch_count(ctx)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        with Clocks(local_rank) as clk:
+            t0.record(stream)
+            for i in range(args.steps):
+                step(Fa, Fb, evs[i])
+                Fa, Fb = Fb, Fa
+            t1.record(stream)
+            torch.cuda.synchronize(dev)
+        launches = capi.dnnmg_launch_count(ctx) - n0
+        if world > 1:
+            torch.distributed.barrier()
+        elapsed_ms = t0.elapsed_time(t1)
+        net_ms = [a.elapsed_time(b) for a, b in evs]
+
+    # end to end through the C ABI with host buffers (pinned)
+    xc_p = torch.from_numpy(xc_h).pin_memory()
+    F_p = torch.from_numpy(F_h).pin_memory()
+    bf_p = torch.empty((nf, 4), dtype=torch.float32).pin_memory()
+    bc_p = torch.empty((nv, 4), dtype=torch.float32).pin_memory()
+    capi.dnnmg_set_stream(ctx, stream)
+    for _ in range(max(1, args.warmup // 2)):
+        capi.dnnmg_patch_step_host(ctx, xc_p, F_p, bf_p, bc_p)
+    torch.cuda.synchronize(dev)
+    te0 = time.perf_counter()
+    for _ in range(args.steps):
+        capi.dnnmg_patch_step_host(ctx, xc_p, F_p, bf_p, bc_p)
+    e2e_s = time.perf_counter() - te0
+
+    # the plain FP64 form of the same step on the same GPU
+    fp64 = None
+    if not args.no_fp64 and rank == 0:
+        q = PatchPath(m, nu, DT, THETA, "fp64", device=dev, stream=stream)
+        q.set_network(WIDTHS, Ws, ss, ts, skip=True)
+        xq, Fq = q.to_device(xc_h.astype(np.float64)), q.to_device(F_h.astype(np.float64))
+        bfq, bcq = q.field(nf, 4), q.field(nv, 4)
+        with torch.cuda.stream(stream):
+            q.step(xq, Fq, bfq, bcq)
+            torch.cuda.synchronize(dev)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            q.step(xq, Fq, bfq, bcq)
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+        ms = a.elapsed_time(b)
+        fp64 = {"ms_per_step": round(ms, 3), "steps_per_s": round(1000.0 / ms, 4),
+                "patches_per_s": round(nc * 1000.0 / ms, 1), "timed_steps": 1}
+        q.close()
+
+    res = dict(elapsed_ms=elapsed_ms, net_ms=net_ms, launches=launches, clocks=clk.summary(),
+               e2e_s=e2e_s, nc=nc, nf=nf, nv=nv, fp64=fp64)
+    p.close()
+    return res
+
+
+def oracle_sample(seconds_target=15.0):
+    """Time the FP64 oracle's patch step on a sample of the channel workload:
+    the same channel family and network at nz = 10 (~6.3k patches).  Returns
+    (patches per second, description, threads)."""
+    import numpy as np
+
+    from paper_2307_14837_gb300 import inputs as I
+    from oracle import dnnmg as odnnmg, mesh as omesh
+    m = I.channel_mesh(10, seed=0)
+    nu = m["meta"]["D"] / 200.0
+    h = omesh.Hierarchy(m["xyz"], m["cells"], m["vertex_bc"])
+    lev = odnnmg.fine_level(h)
+    xc = I.coarse_state(m, 0)
+    F = I.fine_rhs(h.n_fine, 0, scale=(1 / DT) * 0.42 / (8 * h.n_patches))
+    Ws, ss, ts = I.network_weights(WIDTHS, seed=0)
+    prm = dict(m=1 / DT, theta=THETA, nu=nu, alpha0=0.02, delta0=0.1)
+    t = time.perf_counter()
+    n = 0
+    while True:
+        odnnmg.hot_path_step(h, (Ws, ss, ts, True), xc, F, prm, level=lev)
+        n += 1
+        if time.perf_counter() - t > seconds_target or n >= 3:
+            break
+    dt = time.perf_counter() - t
+    threads = os.cpu_count()
+    try:
+        import threadpoolctl
+        info = threadpoolctl.threadpool_info()
+        threads = max((i.get("num_threads", 1) for i in info), default=threads)
+    except Exception:
+        pass
+    desc = (f"oracle patch step (FP64 numpy) on the channel family at nz=10: {h.n_patches} patches, "
+            f"{h.n_fine} fine nodes, {n} step(s); patches/s scaled to the {WIDTHS} network workload")
+    return h.n_patches * n / dt, desc, threads
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    n_patches_full = 314389
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        t0 = time.perf_counter()
+        vals = []
+        for _ in range(args.warmup):
+            oracle_sample(seconds_target=0.0)
+        for _ in range(args.steps):
+            pps, desc, threads = oracle_sample(seconds_target=0.0)
+            vals.append(pps)
+        pps = statistics.median(vals)
+        v = pps / n_patches_full
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / v,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic",
+                "config": {"workload": "channel nz=37 (314389 patches), CN dt=0.005, Re=200, "
+                                       "network 228-1024x4-81; oracle timed on a sample", "sample": desc},
+                "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc},
+                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+                "patches_per_s": pps, "wall_s": time.perf_counter() - t0}
+        print(json.dumps(line))
+        return
+
+    import torch
+    if world > 1:
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    res = run_ours(args, rank, world, local_rank)
+    # max over ranks of the timed region
+    el = res["elapsed_ms"]
+    if world > 1:
+        t = torch.tensor([el], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        el = float(t.item())
+    if rank != 0:
+        torch.distributed.destroy_process_group()
+        return
+    K = args.steps
+    ms = el / K
+    value = world * K / (el / 1000.0)
+    nc, nf, nv = res["nc"], res["nf"], res["nv"]
+    peaks, peak_src = _peaks()
+    net_ms = statistics.mean(res["net_ms"])
+    flops = network_flops_per_patch() * nc
+    achieved = flops / (net_ms / 1000.0) / 1e12
+    peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+        "data": "synthetic",
+        "config": {"workload": f"channel 2.5x0.41x0.41 with seeded cylinder, nz={NZ}: {nc} patches "
+                               f"(coarse hex), {nf} fine nodes; BF16 network {'-'.join(map(str, WIDTHS))}, "
+                               f"FP32 fields, CN dt={DT}, Re=200",
+                   "patches_per_step": nc, "l2": "working set > L2 (activations 644 MB per layer)",
+                   "parallelism": f"replicas x{world}"},
+        "patches_per_s": value * nc,
+        "roofline": {"bound": "tensor", "kernel": "network layers (BF16 GEMM chain)",
+                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "peak_source": f"{peak_src} bf16 sustained", "traffic": None,
+                     "network_ms_per_step": net_ms, "network_share": net_ms / ms},
+        "e2e": {"value": world * K / res["e2e_s"] if res["e2e_s"] > 0 else None, "unit": UNIT,
+                "h2d_bytes_per_step": (nv + nf) * 16, "d2h_bytes_per_step": (nf + nv) * 16},
+        "gpu_launches": res["launches"],
+        "clocks": res["clocks"],
+        "fp64_plain": res["fp64"],
+    }
+    if not args.no_cpu_baseline:
+        pps, desc, threads = oracle_sample()
+        line["cpu_baseline"] = {"value": pps / nc, "unit": UNIT, "cores": threads, "kind": "oracle",
+                                "sample": desc, "patches_per_s": pps}
+    print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,244 @@
+/*
+ * dnnmg.h -- C ABI of libdnnmg, the GB300 (sm_103a) patch-correction path of
+ * the Deep Neural Network Multigrid method (DNN-MG).
+ *
+ * One DNN-MG time step (Sec. 5.1, Alg. 1) solves the coarse system on level L
+ * and then runs the patch correction on level L+1:
+ *
+ *   x~   = P x^L                          prolongation           dnnmg_prolongate
+ *   r    = F - A_{L+1}(x~)                fine residual, Eq. (9) dnnmg_residual
+ *   X    = [Q(x~) | Q(r) | h^c]           local restriction,     dnnmg_local_restrict
+ *                                         Eqs. (13)-(14) + the 12 edge lengths
+ *   Y    = N(X)                           patch network, Sec. 4  dnnmg_network
+ *   d    = L(Y) = mu . sum_P L(Y_P, P)    extension, Eq. (15)    dnnmg_extend
+ *   b    = Rhs(v~ + d), b^L = R b         rhs of Eq. (6) on L+1, dnnmg_rhs_restrict
+ *                                         restricted to level L
+ *
+ * dnnmg_patch_step runs all six in order on one CUDA stream.
+ *
+ * Conventions shared by every entry point
+ *   - Every call returns a dnnmg_status; nothing throws across the ABI.
+ *   - A context owns the mesh hierarchy (on the host and on the device), the
+ *     network and its scratch buffers.  It is bound to the CUDA device that
+ *     was current at dnnmg_create and to one stream; calls on one context
+ *     must not overlap (the context is not thread-safe).
+ *   - Field pointers named *_dev are device pointers owned by the caller and
+ *     only borrowed for the call; *_host pointers are host memory.  Kernels
+ *     are enqueued on the context's stream and the call returns without
+ *     waiting, except where a function says it synchronises.
+ *   - Field element type follows the context's precision:
+ *       DNNMG_FP64: double fields, double network;
+ *       DNNMG_FP32: float fields, float network;
+ *       DNNMG_BF16: float fields, network input/activations bf16 with fp32
+ *                   accumulation, network output float.
+ *   - Layouts (row-major, node-major):
+ *       x_coarse  [n_coarse_vertices][4]  (u, v, w, p) on level L
+ *       x_fine, F, r, b_fine  [n_fine_nodes][4]
+ *       d         [n_fine_nodes][3]       velocity correction
+ *       b_coarse  [n_coarse_vertices][4]
+ *       X         [n_patches][n_in_padded]: columns 0..107 x~ at the 27 patch
+ *                 nodes (u,v,w,p), 108..215 r likewise, 216..227 edge
+ *                 lengths, 228.. zero
+ *       Y         [n_patches][81]: 27 x (u, v, w)
+ *     Patch node iota = a + 3b + 9c, (a,b,c) in {0,1,2}^3 along the coarse
+ *     cell's reference axes.
+ *   - Dirichlet velocity rows (fine node kinds 1 and 2) of r, d and b_fine,
+ *     and coarse Dirichlet velocity rows of b_coarse are zero; pressure rows
+ *     of b_fine and b_coarse are zero.
+ *   - Errors: DNNMG_EINVAL for null or inconsistent arguments (nothing is
+ *     launched), DNNMG_ECUDA when a CUDA call fails (dnnmg_last_error has the
+ *     CUDA message), DNNMG_ESTATE for calls out of order (e.g. dnnmg_network
+ *     before dnnmg_set_network).
+ */
+#ifndef DNNMG_H
+#define DNNMG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DNNMG_ABI_VERSION 1
+
+typedef struct dnnmg_ctx dnnmg_ctx;
+
+typedef enum {
+    DNNMG_OK = 0,
+    DNNMG_EINVAL = -1,
+    DNNMG_ENOMEM = -2,
+    DNNMG_ECUDA = -3,
+    DNNMG_ENOCONV = -4,
+    DNNMG_ENAN = -5,
+    DNNMG_ETIMEOUT = -6,
+    DNNMG_ESTATE = -7,
+    DNNMG_EUNSUPPORTED = -8
+} dnnmg_status;
+
+typedef enum { DNNMG_FP64 = 0, DNNMG_FP32 = 1, DNNMG_BF16 = 2 } dnnmg_precision;
+
+/* Coarse mesh (level L).  Hexahedra with vertices in lexicographic order:
+ * local vertex k sits at reference corner (k&1, (k>>1)&1, (k>>2)&1).
+ * vertex_bc: 0 interior, 1 no-slip wall, 2 driven Dirichlet (lid/inflow),
+ * 3 do-nothing outflow.  All arrays are copied by dnnmg_create. */
+typedef struct {
+    int32_t n_vertices;
+    const double* xyz;             /* [n_vertices][3] */
+    int32_t n_cells;
+    const int32_t* cell_vertices;  /* [n_cells][8] */
+    const int32_t* vertex_bc;      /* [n_vertices] */
+} dnnmg_mesh_desc;
+
+/* Time discretisation of Eq. (6) as a theta-scheme (theta = 1/2 is the
+ * paper's Crank-Nicolson, theta = 1 backward Euler). */
+typedef struct {
+    double nu;          /* kinematic viscosity */
+    double dt;          /* time step k */
+    double theta;
+    int32_t precision;  /* dnnmg_precision */
+    int32_t reserved;   /* must be 0 */
+} dnnmg_params;
+
+/* Patch network of Sec. 4 in inference form: layer i computes
+ * z = scale_i . (W_i h) + shift_i; hidden layers apply ReLU and, when
+ * skip != 0 and i >= 1 (0-based) and widths match, add their input. */
+typedef struct {
+    int32_t n_layers;        /* number of weight matrices, >= 1 */
+    const int32_t* widths;   /* n_layers + 1 entries; widths[0] == 228, widths[n_layers] == 81 */
+    int32_t skip;
+} dnnmg_net_desc;
+
+typedef struct {
+    int64_t n_coarse_vertices;
+    int64_t n_patches;         /* = number of coarse cells */
+    int64_t n_fine_nodes;
+    int64_t n_coarse_edges;
+    int64_t n_coarse_faces;
+    int32_t n_in;              /* 228 */
+    int32_t n_in_padded;       /* row stride of X */
+    int32_t n_out;             /* 81 */
+    int32_t precision;
+} dnnmg_sizes;
+
+/* Mesh data a caller can read back (dnnmg_get_mesh_data). */
+typedef enum {
+    DNNMG_PATCH_MAP = 0,    /* int32 [n_patches][27]: dof(P, iota) of Sec. 5.2 */
+    DNNMG_VALENCE = 1,      /* int32 [n_fine_nodes]: patches containing each node (1/mu) */
+    DNNMG_FINE_KIND = 2,    /* int32 [n_fine_nodes]: boundary kind 0..3 */
+    DNNMG_FINE_XYZ = 3,     /* double [n_fine_nodes][3] */
+    DNNMG_EDGE_LENGTHS = 4  /* double [n_patches][12] */
+} dnnmg_mesh_item;
+
+/* Build the level-(L+1) hierarchy of a coarse mesh on the host, upload it to
+ * the current CUDA device and bind the context to `cuda_stream` (a
+ * cudaStream_t; NULL = legacy default stream).  Fine nodes are numbered
+ * hierarchically: coarse vertices, then one node per coarse edge, face and
+ * cell in order of first appearance (cells in order; edges and faces in the
+ * local order xi-, eta-, zeta-edges / xi=0, xi=1, eta=0, eta=1, zeta=0,
+ * zeta=1 faces).  A coarse boundary face takes the lowest-priority kind of
+ * its vertices (priority 3 < 1 < 2); a fine node on a boundary edge the
+ * highest-priority kind of the boundary faces through it.
+ * Errors: EINVAL (bad sizes, vertex index out of range, a boundary face with
+ * an interior-marked vertex), ENOMEM, ECUDA.  On error *out is NULL. */
+dnnmg_status dnnmg_create(const dnnmg_mesh_desc* mesh, const dnnmg_params* params,
+                          void* cuda_stream, dnnmg_ctx** out);
+
+/* Free every host and device resource of the context (NULL is a no-op).
+ * Waits for the context's stream first. */
+void dnnmg_destroy(dnnmg_ctx* ctx);
+
+const char* dnnmg_strerror(dnnmg_status status);
+/* Message of the last failing call on this context (static "" if none). */
+const char* dnnmg_last_error(const dnnmg_ctx* ctx);
+
+dnnmg_status dnnmg_get_sizes(const dnnmg_ctx* ctx, dnnmg_sizes* out);
+
+/* Copy mesh data to host memory `host_buf` of `bytes` bytes (EINVAL if too
+ * small). */
+dnnmg_status dnnmg_get_mesh_data(const dnnmg_ctx* ctx, int32_t item, void* host_buf, size_t bytes);
+
+dnnmg_status dnnmg_set_stream(dnnmg_ctx* ctx, void* cuda_stream);
+
+/* Load the patch network (Sec. 4).  W[i] points to widths[i+1] x widths[i]
+ * doubles (row-major), scale[i] / shift[i] to widths[i+1] doubles (NULL =
+ * 1 / 0).  Host memory; copied and converted to the context's precision.
+ * Synchronises the stream.  Errors: EINVAL (widths[0] != 228,
+ * widths[n_layers] != 81, width > 4096 or not a multiple of 16 for hidden
+ * layers in the BF16 form), ENOMEM, ECUDA. */
+dnnmg_status dnnmg_set_network(dnnmg_ctx* ctx, const dnnmg_net_desc* net,
+                               const double* const* W, const double* const* scale,
+                               const double* const* shift);
+
+/* Prolongation x~ = P x^L (Alg. 1): every fine node takes the mean of the
+ * coarse vertex values of the entity it refines.
+ * x_coarse_dev [n_coarse_vertices][4] -> x_fine_dev [n_fine_nodes][4]. */
+dnnmg_status dnnmg_prolongate(dnnmg_ctx* ctx, const void* x_coarse_dev, void* x_fine_dev);
+
+/* Fine residual r = F - A_{L+1}(P x^L) of Eq. (9), the Q1/Q1 Galerkin form
+ * of Eq. (6) with 2x2x2 Gauss quadrature on every fine cell (fused with the
+ * prolongation; the local projection terms vanish on prolongated fields and
+ * are not evaluated).  Velocity rows at Dirichlet nodes are 0.
+ * Deterministic: per-patch partial sums are reduced per node in patch
+ * order.  Uses context scratch of n_patches*27*4 elements. */
+dnnmg_status dnnmg_residual(dnnmg_ctx* ctx, const void* x_coarse_dev, const void* F_dev,
+                            void* r_dev);
+
+/* Network input rows X = [Q(P x^L) | Q(r) | h^c] (Eqs. (13)-(14) and the
+ * edge-length features of Sec. 5.2).  X_dev element type: double (FP64),
+ * float (FP32), bf16 (BF16); row stride n_in_padded. */
+dnnmg_status dnnmg_local_restrict(dnnmg_ctx* ctx, const void* x_coarse_dev, const void* r_dev,
+                                  void* X_dev);
+
+/* Y = N(X) for n_rows rows (Sec. 4).  X_dev as produced by
+ * dnnmg_local_restrict, Y_dev [n_rows][81] double (FP64) or float.
+ * Errors: ESTATE before dnnmg_set_network, EINVAL if n_rows exceeds the
+ * capacity fixed at dnnmg_set_network (max(n_patches, 1)). */
+dnnmg_status dnnmg_network(dnnmg_ctx* ctx, const void* X_dev, void* Y_dev, int64_t n_rows);
+
+/* Extension d = mu . sum_P L(Y_P, P) of Eq. (15), mu = 1 / valence, summed
+ * in patch order (deterministic, no atomics).  d_dev [n_fine_nodes][3];
+ * zero at Dirichlet velocity nodes. */
+dnnmg_status dnnmg_extend(dnnmg_ctx* ctx, const void* Y_dev, void* d_dev);
+
+/* Right-hand side of Eq. (6) for the next step on level L+1 with the
+ * corrected velocity P x^L + d (no force), and its restriction
+ * b^L = P^T b to level L.  b_fine_dev [n_fine_nodes][4],
+ * b_coarse_dev [n_coarse_vertices][4] (either may be NULL to skip it). */
+dnnmg_status dnnmg_rhs_restrict(dnnmg_ctx* ctx, const void* x_coarse_dev, const void* d_dev,
+                                void* b_fine_dev, void* b_coarse_dev);
+
+/* The whole patch correction of one time step: prolongate, residual with
+ * F_dev, local restriction, network, extension, rhs and restriction.  r, X,
+ * Y and d live in context buffers (readable with dnnmg_get_buffer).
+ * b_fine_dev may alias F_dev (the step reads F before writing b). */
+dnnmg_status dnnmg_patch_step(dnnmg_ctx* ctx, const void* x_coarse_dev, const void* F_dev,
+                              void* b_fine_dev, void* b_coarse_dev);
+
+/* dnnmg_patch_step on host buffers: copies x_coarse and F to the device,
+ * runs the step, copies b_fine and b_coarse back, and synchronises.  For
+ * pinned host memory the copies are asynchronous on the context's stream. */
+dnnmg_status dnnmg_patch_step_host(dnnmg_ctx* ctx, const void* x_coarse_host, const void* F_host,
+                                   void* b_fine_host, void* b_coarse_host);
+
+typedef enum {
+    DNNMG_BUF_R = 0,   /* [n_fine_nodes][4] residual of the last step */
+    DNNMG_BUF_X = 1,   /* [n_patches][n_in_padded] network input */
+    DNNMG_BUF_Y = 2,   /* [n_patches][81] network output */
+    DNNMG_BUF_D = 3    /* [n_fine_nodes][3] correction */
+} dnnmg_buffer;
+
+/* Device pointer of a context buffer (valid until dnnmg_destroy). */
+dnnmg_status dnnmg_get_buffer(dnnmg_ctx* ctx, int32_t which, void** dev_ptr);
+
+/* Wait for the context's stream, polling at most timeout_us microseconds
+ * (< 0: no limit).  ETIMEOUT if work is still pending then. */
+dnnmg_status dnnmg_sync(dnnmg_ctx* ctx, int64_t timeout_us);
+
+/* Number of kernel launches this context has issued (for accounting). */
+int64_t dnnmg_launch_count(const dnnmg_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DNNMG_H */

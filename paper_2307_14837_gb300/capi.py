@@ -1,0 +1,220 @@
+"""ctypes binding of libdnnmg (include/dnnmg.h): argument marshalling only.
+
+Each ``dnnmg_*`` function here calls the C entry point of the same name and
+raises ``DnnmgError`` on a non-zero status.  Device buffers are passed as
+torch CUDA tensors (their data pointers are borrowed for the call); every
+step of the path runs in the library's CUDA kernels.  There is no fallback:
+if the library is not built, loading it raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+FP64, FP32, BF16 = 0, 1, 2
+PATCH_MAP, VALENCE, FINE_KIND, FINE_XYZ, EDGE_LENGTHS = 0, 1, 2, 3, 4
+BUF_R, BUF_X, BUF_Y, BUF_D = 0, 1, 2, 3
+N_IN, N_OUT = 228, 81
+
+
+class DnnmgError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"libdnnmg status {status}: {msg}")
+        self.status = status
+
+
+class MeshDesc(ctypes.Structure):
+    _fields_ = [("n_vertices", ctypes.c_int32), ("xyz", ctypes.POINTER(ctypes.c_double)),
+                ("n_cells", ctypes.c_int32), ("cell_vertices", ctypes.POINTER(ctypes.c_int32)),
+                ("vertex_bc", ctypes.POINTER(ctypes.c_int32))]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("nu", ctypes.c_double), ("dt", ctypes.c_double), ("theta", ctypes.c_double),
+                ("precision", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class NetDesc(ctypes.Structure):
+    _fields_ = [("n_layers", ctypes.c_int32), ("widths", ctypes.POINTER(ctypes.c_int32)),
+                ("skip", ctypes.c_int32)]
+
+
+class Sizes(ctypes.Structure):
+    _fields_ = [("n_coarse_vertices", ctypes.c_int64), ("n_patches", ctypes.c_int64),
+                ("n_fine_nodes", ctypes.c_int64), ("n_coarse_edges", ctypes.c_int64),
+                ("n_coarse_faces", ctypes.c_int64), ("n_in", ctypes.c_int32),
+                ("n_in_padded", ctypes.c_int32), ("n_out", ctypes.c_int32), ("precision", ctypes.c_int32)]
+
+
+_VP = ctypes.c_void_p
+_SIGS = {
+    "dnnmg_create": ([ctypes.POINTER(MeshDesc), ctypes.POINTER(Params), _VP, ctypes.POINTER(_VP)], ctypes.c_int),
+    "dnnmg_destroy": ([_VP], None),
+    "dnnmg_strerror": ([ctypes.c_int], ctypes.c_char_p),
+    "dnnmg_last_error": ([_VP], ctypes.c_char_p),
+    "dnnmg_get_sizes": ([_VP, ctypes.POINTER(Sizes)], ctypes.c_int),
+    "dnnmg_get_mesh_data": ([_VP, ctypes.c_int32, _VP, ctypes.c_size_t], ctypes.c_int),
+    "dnnmg_set_stream": ([_VP, _VP], ctypes.c_int),
+    "dnnmg_set_network": ([_VP, ctypes.POINTER(NetDesc), ctypes.POINTER(_VP), ctypes.POINTER(_VP),
+                           ctypes.POINTER(_VP)], ctypes.c_int),
+    "dnnmg_prolongate": ([_VP, _VP, _VP], ctypes.c_int),
+    "dnnmg_residual": ([_VP, _VP, _VP, _VP], ctypes.c_int),
+    "dnnmg_local_restrict": ([_VP, _VP, _VP, _VP], ctypes.c_int),
+    "dnnmg_network": ([_VP, _VP, _VP, ctypes.c_int64], ctypes.c_int),
+    "dnnmg_extend": ([_VP, _VP, _VP], ctypes.c_int),
+    "dnnmg_rhs_restrict": ([_VP, _VP, _VP, _VP, _VP], ctypes.c_int),
+    "dnnmg_patch_step": ([_VP, _VP, _VP, _VP, _VP], ctypes.c_int),
+    "dnnmg_patch_step_host": ([_VP, _VP, _VP, _VP, _VP], ctypes.c_int),
+    "dnnmg_get_buffer": ([_VP, ctypes.c_int32, ctypes.POINTER(_VP)], ctypes.c_int),
+    "dnnmg_sync": ([_VP, ctypes.c_int64], ctypes.c_int),
+    "dnnmg_launch_count": ([_VP], ctypes.c_int64),
+}
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libdnnmg.so (built by paper_2307_14837_gb300.build.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"libdnnmg is not built ({path} missing): run paper_2307_14837_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    for name, (args, res) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _ptr(t):
+    """Device (or host) address of a tensor / numpy array / int / None."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+def _check(ctx, status):
+    if status != 0:
+        lib = load()
+        msg = lib.dnnmg_strerror(status).decode()
+        if ctx:
+            extra = lib.dnnmg_last_error(ctx).decode()
+            if extra:
+                msg += f" ({extra})"
+        raise DnnmgError(status, msg)
+
+
+# -- thin wrappers with the C names ------------------------------------------
+
+def dnnmg_create(mesh, nu, dt, theta, precision, stream=None):
+    """mesh: dict with xyz [nv,3] float64, cells [nc,8] int32, vertex_bc [nv] int32.
+    stream: a torch.cuda.Stream, an int handle, or None (default stream)."""
+    lib = load()
+    xyz = np.ascontiguousarray(mesh["xyz"], dtype=np.float64)
+    cells = np.ascontiguousarray(mesh["cells"], dtype=np.int32)
+    bc = np.ascontiguousarray(mesh["vertex_bc"], dtype=np.int32)
+    desc = MeshDesc(int(xyz.shape[0]), xyz.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                    int(cells.shape[0]), cells.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                    bc.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+    prm = Params(float(nu), float(dt), float(theta), int(precision), 0)
+    handle = _VP()
+    s = getattr(stream, "cuda_stream", stream)
+    _check(None, lib.dnnmg_create(ctypes.byref(desc), ctypes.byref(prm), s, ctypes.byref(handle)))
+    return handle.value
+
+
+def dnnmg_destroy(ctx):
+    load().dnnmg_destroy(ctx)
+
+
+def dnnmg_get_sizes(ctx) -> dict:
+    s = Sizes()
+    _check(ctx, load().dnnmg_get_sizes(ctx, ctypes.byref(s)))
+    return {k: getattr(s, k) for k, _ in Sizes._fields_}
+
+
+def dnnmg_get_mesh_data(ctx, item):
+    sz = dnnmg_get_sizes(ctx)
+    shape, dt = {PATCH_MAP: ((sz["n_patches"], 27), np.int32), VALENCE: ((sz["n_fine_nodes"],), np.int32),
+                 FINE_KIND: ((sz["n_fine_nodes"],), np.int32), FINE_XYZ: ((sz["n_fine_nodes"], 3), np.float64),
+                 EDGE_LENGTHS: ((sz["n_patches"], 12), np.float64)}[item]
+    out = np.empty(shape, dtype=dt)
+    _check(ctx, load().dnnmg_get_mesh_data(ctx, item, out.ctypes.data, out.nbytes))
+    return out
+
+
+def dnnmg_set_stream(ctx, stream):
+    _check(ctx, load().dnnmg_set_stream(ctx, getattr(stream, "cuda_stream", stream)))
+
+
+def dnnmg_set_network(ctx, widths, Ws, scales=None, shifts=None, skip=True):
+    L = len(Ws)
+    w = np.ascontiguousarray(widths, dtype=np.int32)
+    keep = [np.ascontiguousarray(W, dtype=np.float64) for W in Ws]
+    ks = [np.ascontiguousarray(s, dtype=np.float64) for s in scales] if scales is not None else None
+    kt = [np.ascontiguousarray(t, dtype=np.float64) for t in shifts] if shifts is not None else None
+    arr = lambda lst: (_VP * L)(*[a.ctypes.data for a in lst]) if lst is not None else None
+    desc = NetDesc(L, w.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), 1 if skip else 0)
+    _check(ctx, load().dnnmg_set_network(ctx, ctypes.byref(desc), arr(keep), arr(ks), arr(kt)))
+
+
+def dnnmg_prolongate(ctx, x_coarse, x_fine):
+    _check(ctx, load().dnnmg_prolongate(ctx, _ptr(x_coarse), _ptr(x_fine)))
+
+
+def dnnmg_residual(ctx, x_coarse, F, r):
+    _check(ctx, load().dnnmg_residual(ctx, _ptr(x_coarse), _ptr(F), _ptr(r)))
+
+
+def dnnmg_local_restrict(ctx, x_coarse, r, X):
+    _check(ctx, load().dnnmg_local_restrict(ctx, _ptr(x_coarse), _ptr(r), _ptr(X)))
+
+
+def dnnmg_network(ctx, X, Y, n_rows):
+    _check(ctx, load().dnnmg_network(ctx, _ptr(X), _ptr(Y), int(n_rows)))
+
+
+def dnnmg_extend(ctx, Y, d):
+    _check(ctx, load().dnnmg_extend(ctx, _ptr(Y), _ptr(d)))
+
+
+def dnnmg_rhs_restrict(ctx, x_coarse, d, b_fine, b_coarse):
+    _check(ctx, load().dnnmg_rhs_restrict(ctx, _ptr(x_coarse), _ptr(d), _ptr(b_fine), _ptr(b_coarse)))
+
+
+def dnnmg_patch_step(ctx, x_coarse, F, b_fine, b_coarse):
+    _check(ctx, load().dnnmg_patch_step(ctx, _ptr(x_coarse), _ptr(F), _ptr(b_fine), _ptr(b_coarse)))
+
+
+def dnnmg_patch_step_host(ctx, x_coarse, F, b_fine, b_coarse):
+    _check(ctx, load().dnnmg_patch_step_host(ctx, _ptr(x_coarse), _ptr(F), _ptr(b_fine), _ptr(b_coarse)))
+
+
+def dnnmg_get_buffer(ctx, which) -> int:
+    p = _VP()
+    _check(ctx, load().dnnmg_get_buffer(ctx, int(which), ctypes.byref(p)))
+    return p.value
+
+
+def dnnmg_sync(ctx, timeout_us=-1):
+    _check(ctx, load().dnnmg_sync(ctx, int(timeout_us)))
+
+
+def dnnmg_launch_count(ctx) -> int:
+    return int(load().dnnmg_launch_count(ctx))

@@ -1,0 +1,462 @@
+// extern "C" entry points of libdnnmg (declared in include/dnnmg.h).
+#include <chrono>
+#include <cstring>
+#include <new>
+#include <thread>
+
+#include "internal.h"
+
+using namespace dnnmg;
+
+namespace {
+
+const char* kStatusText[] = {"ok", "invalid argument", "out of memory", "CUDA error", "no convergence",
+                             "NaN or Inf", "timeout", "call out of order", "unsupported"};
+
+dnnmg_status fail(dnnmg_ctx* ctx, dnnmg_status st, const std::string& msg) {
+    if (ctx) ctx->last_error = msg;
+    return st;
+}
+
+dnnmg_status cuda_fail(dnnmg_ctx* ctx, cudaError_t e, const char* where) {
+    if (ctx) ctx->last_error = std::string(where) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? DNNMG_ENOMEM : DNNMG_ECUDA;
+}
+
+#define CK(ctx, call)                                        \
+    do {                                                     \
+        cudaError_t e_ = (call);                             \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+    } while (0)
+
+template <typename T>
+dnnmg_status upload(dnnmg_ctx* ctx, const T* host, size_t n, T** dev) {
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, n * sizeof(T) > 0 ? n * sizeof(T) : 1);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc");
+    ctx->allocations.push_back(p);
+    if (n) {
+        e = cudaMemcpy(p, host, n * sizeof(T), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemcpy");
+    }
+    *dev = static_cast<T*>(p);
+    return DNNMG_OK;
+}
+
+dnnmg_status alloc(dnnmg_ctx* ctx, size_t bytes, void** dev) {
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes > 0 ? bytes : 1);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc");
+    ctx->allocations.push_back(p);
+    *dev = p;
+    return DNNMG_OK;
+}
+
+size_t field_elem(int precision) { return precision == DNNMG_FP64 ? sizeof(double) : sizeof(float); }
+
+bool is_fp64(const dnnmg_ctx* c) { return c->precision == DNNMG_FP64; }
+
+}  // namespace
+
+extern "C" {
+
+const char* dnnmg_strerror(dnnmg_status s) {
+    const int i = -int(s);
+    if (i < 0 || i >= int(sizeof(kStatusText) / sizeof(kStatusText[0]))) return "unknown status";
+    return kStatusText[i];
+}
+
+const char* dnnmg_last_error(const dnnmg_ctx* ctx) { return ctx ? ctx->last_error.c_str() : ""; }
+
+int64_t dnnmg_launch_count(const dnnmg_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+void dnnmg_destroy(dnnmg_ctx* ctx) {
+    if (!ctx) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    for (void* p : ctx->allocations) cudaFree(p);
+    cudaSetDevice(cur);
+    delete ctx;
+}
+
+dnnmg_status dnnmg_create(const dnnmg_mesh_desc* mesh, const dnnmg_params* params, void* cuda_stream,
+                          dnnmg_ctx** out) {
+    if (!out) return DNNMG_EINVAL;
+    *out = nullptr;
+    if (!mesh || !params) return DNNMG_EINVAL;
+    if (params->precision < DNNMG_FP64 || params->precision > DNNMG_BF16 || params->reserved != 0 ||
+        !(params->dt > 0.0) || !(params->nu >= 0.0) || !(params->theta >= 0.0 && params->theta <= 1.0))
+        return DNNMG_EINVAL;
+    dnnmg_ctx* ctx = new (std::nothrow) dnnmg_ctx();
+    if (!ctx) return DNNMG_ENOMEM;
+    std::string err;
+    dnnmg_status st = build_hierarchy(mesh, &ctx->host, &err);
+    if (st != DNNMG_OK) {
+        delete ctx;
+        return st;
+    }
+    ctx->precision = params->precision;
+    ctx->op = OpParams{1.0 / params->dt, params->theta, params->nu};
+    ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+    if (cudaGetDevice(&ctx->device) != cudaSuccess) {
+        delete ctx;
+        return DNNMG_ECUDA;
+    }
+    const HostHierarchy& h = ctx->host;
+    DeviceMesh& dm = ctx->dm;
+    dm.nv = h.nv;
+    dm.nc = h.nc;
+    dm.n_fine = h.n_fine;
+    auto done = [&](dnnmg_status s) {
+        if (s != DNNMG_OK) {
+            dnnmg_destroy(ctx);
+            return s;
+        }
+        *out = ctx;
+        return DNNMG_OK;
+    };
+    int32_t* p;
+#define UP(vec, field)                                                           \
+    do {                                                                         \
+        st = upload(ctx, vec.data(), vec.size(), &p);                            \
+        if (st != DNNMG_OK) return done(st);                                     \
+        dm.field = p;                                                            \
+    } while (0)
+    UP(h.cells, cells);
+    UP(h.patch_map, patch_map);
+    UP(h.node_ptr, node_ptr);
+    UP(h.node_idx, node_idx);
+    UP(h.vert_ptr, vert_ptr);
+    UP(h.vert_idx, vert_idx);
+#undef UP
+    std::vector<uint8_t> fd(size_t(h.n_fine)), cd(size_t(h.nv));
+    for (int64_t j = 0; j < h.n_fine; ++j) fd[j] = (h.kind_f[j] == 1 || h.kind_f[j] == 2) ? 1 : 0;
+    for (int64_t v = 0; v < h.nv; ++v) cd[v] = (h.bc_c[v] == 1 || h.bc_c[v] == 2) ? 1 : 0;
+    uint8_t* pu;
+    if ((st = upload(ctx, fd.data(), fd.size(), &pu)) != DNNMG_OK) return done(st);
+    dm.fine_dir = pu;
+    if ((st = upload(ctx, cd.data(), cd.size(), &pu)) != DNNMG_OK) return done(st);
+    dm.coarse_dir = pu;
+    if (is_fp64(ctx)) {
+        double* pd;
+        if ((st = upload(ctx, h.xyz_c.data(), h.xyz_c.size(), &pd)) != DNNMG_OK) return done(st);
+        dm.xyz_d = pd;
+        if ((st = upload(ctx, h.edge_len.data(), h.edge_len.size(), &pd)) != DNNMG_OK) return done(st);
+        dm.edge_d = pd;
+    } else {
+        std::vector<float> xf(h.xyz_c.begin(), h.xyz_c.end()), ef(h.edge_len.begin(), h.edge_len.end());
+        float* pf;
+        if ((st = upload(ctx, xf.data(), xf.size(), &pf)) != DNNMG_OK) return done(st);
+        dm.xyz_f = pf;
+        if ((st = upload(ctx, ef.data(), ef.size(), &pf)) != DNNMG_OK) return done(st);
+        dm.edge_f = pf;
+    }
+    const size_t fe = field_elem(ctx->precision);
+    const size_t xe = ctx->precision == DNNMG_BF16 ? 2 : fe;
+    const size_t nc = size_t(h.nc), nf = size_t(h.n_fine), nv = size_t(h.nv);
+    if ((st = alloc(ctx, nc * 27 * 4 * fe, &ctx->partial)) != DNNMG_OK) return done(st);
+    if ((st = alloc(ctx, nc * 8 * 4 * fe, &ctx->partial_c)) != DNNMG_OK) return done(st);
+    if ((st = alloc(ctx, nf * 4 * fe, &ctx->buf_r)) != DNNMG_OK) return done(st);
+    if ((st = alloc(ctx, nc * kNInPad * xe, &ctx->buf_X)) != DNNMG_OK) return done(st);
+    if ((st = alloc(ctx, nc * kNOut * fe, &ctx->buf_Y)) != DNNMG_OK) return done(st);
+    if ((st = alloc(ctx, nf * 3 * fe, &ctx->buf_d)) != DNNMG_OK) return done(st);
+    if ((st = alloc(ctx, nv * 4 * fe, &ctx->buf_xc)) != DNNMG_OK) return done(st);
+    if ((st = alloc(ctx, nf * 4 * fe, &ctx->buf_F)) != DNNMG_OK) return done(st);
+    if ((st = alloc(ctx, nv * 4 * fe, &ctx->buf_bc)) != DNNMG_OK) return done(st);
+    return done(DNNMG_OK);
+}
+
+dnnmg_status dnnmg_get_sizes(const dnnmg_ctx* ctx, dnnmg_sizes* out) {
+    if (!ctx || !out) return DNNMG_EINVAL;
+    out->n_coarse_vertices = ctx->host.nv;
+    out->n_patches = ctx->host.nc;
+    out->n_fine_nodes = ctx->host.n_fine;
+    out->n_coarse_edges = ctx->host.ne;
+    out->n_coarse_faces = ctx->host.nf;
+    out->n_in = kNIn;
+    out->n_in_padded = kNInPad;
+    out->n_out = kNOut;
+    out->precision = ctx->precision;
+    return DNNMG_OK;
+}
+
+dnnmg_status dnnmg_get_mesh_data(const dnnmg_ctx* ctx, int32_t item, void* host_buf, size_t bytes) {
+    if (!ctx || !host_buf) return DNNMG_EINVAL;
+    const HostHierarchy& h = ctx->host;
+    const void* src = nullptr;
+    size_t n = 0;
+    switch (item) {
+        case DNNMG_PATCH_MAP: src = h.patch_map.data(); n = h.patch_map.size() * 4; break;
+        case DNNMG_VALENCE: src = h.valence.data(); n = h.valence.size() * 4; break;
+        case DNNMG_FINE_KIND: src = h.kind_f.data(); n = h.kind_f.size() * 4; break;
+        case DNNMG_FINE_XYZ: src = h.xyz_f.data(); n = h.xyz_f.size() * 8; break;
+        case DNNMG_EDGE_LENGTHS: src = h.edge_len.data(); n = h.edge_len.size() * 8; break;
+        default: return DNNMG_EINVAL;
+    }
+    if (bytes < n) return DNNMG_EINVAL;
+    std::memcpy(host_buf, src, n);
+    return DNNMG_OK;
+}
+
+dnnmg_status dnnmg_set_stream(dnnmg_ctx* ctx, void* cuda_stream) {
+    if (!ctx) return DNNMG_EINVAL;
+    ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+    return DNNMG_OK;
+}
+
+dnnmg_status dnnmg_set_network(dnnmg_ctx* ctx, const dnnmg_net_desc* net, const double* const* W,
+                               const double* const* scale, const double* const* shift) {
+    if (!ctx || !net || !W || !net->widths || net->n_layers < 1 || net->n_layers > 64) return DNNMG_EINVAL;
+    const int L = net->n_layers;
+    if (net->widths[0] != kNIn || net->widths[L] != kNOut)
+        return fail(ctx, DNNMG_EINVAL, "network widths must start at 228 and end at 81");
+    for (int i = 1; i < L; ++i) {
+        const int w = net->widths[i];
+        if (w < 16 || w > 4096 || w % 16)
+            return fail(ctx, DNNMG_EINVAL, "hidden widths must be multiples of 16 in [16, 4096]");
+    }
+    for (int i = 0; i < L; ++i)
+        if (!W[i]) return DNNMG_EINVAL;
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    // release a previous network's memory
+    auto drop = [&](void* p) {
+        if (!p) return;
+        for (auto& a : ctx->allocations)
+            if (a == p) {
+                cudaFree(a);
+                a = nullptr;
+            }
+    };
+    for (void* p : ctx->W) drop(p);
+    for (void* p : ctx->scale) drop(p);
+    for (void* p : ctx->shift) drop(p);
+    drop(ctx->act[0]);
+    drop(ctx->act[1]);
+    ctx->W.clear();
+    ctx->scale.clear();
+    ctx->shift.clear();
+    ctx->has_net = false;
+    ctx->n_layers = L;
+    ctx->skip = net->skip;
+    ctx->widths.assign(net->widths, net->widths + L + 1);
+    ctx->kpad.resize(L);
+    ctx->npad.resize(L);
+    int maxw = 16;
+    for (int i = 0; i < L; ++i) {
+        ctx->kpad[i] = i == 0 ? kNInPad : ctx->widths[i];
+        ctx->npad[i] = ctx->widths[i + 1];
+        if (i < L - 1) maxw = std::max(maxw, ctx->widths[i + 1]);
+    }
+    dnnmg_status st;
+    for (int i = 0; i < L; ++i) {
+        const int N = ctx->npad[i], K = ctx->kpad[i], n_true = ctx->widths[i + 1], k_true = ctx->widths[i];
+        std::vector<double> w(size_t(N) * K, 0.0), s(size_t(N), 0.0), t(size_t(N), 0.0);
+        for (int n = 0; n < n_true; ++n) {
+            for (int k = 0; k < k_true; ++k) w[size_t(n) * K + k] = W[i][size_t(n) * k_true + k];
+            s[n] = scale && scale[i] ? scale[i][n] : 1.0;
+            t[n] = shift && shift[i] ? shift[i][n] : 0.0;
+        }
+        void* dw;
+        void* ds;
+        void* dt;
+        if (ctx->precision == DNNMG_FP64) {
+            double* p;
+            if ((st = upload(ctx, w.data(), w.size(), &p)) != DNNMG_OK) return st;
+            dw = p;
+            if ((st = upload(ctx, s.data(), s.size(), &p)) != DNNMG_OK) return st;
+            ds = p;
+            if ((st = upload(ctx, t.data(), t.size(), &p)) != DNNMG_OK) return st;
+            dt = p;
+        } else {
+            std::vector<float> sf(s.begin(), s.end()), tf(t.begin(), t.end());
+            float* p;
+            if (ctx->precision == DNNMG_FP32) {
+                std::vector<float> wf(w.begin(), w.end());
+                if ((st = upload(ctx, wf.data(), wf.size(), &p)) != DNNMG_OK) return st;
+                dw = p;
+            } else {
+                std::vector<__nv_bfloat16> wb(w.size());
+                for (size_t e = 0; e < w.size(); ++e) wb[e] = __float2bfloat16_rn(float(w[e]));
+                __nv_bfloat16* pb;
+                if ((st = upload(ctx, wb.data(), wb.size(), &pb)) != DNNMG_OK) return st;
+                dw = pb;
+            }
+            if ((st = upload(ctx, sf.data(), sf.size(), &p)) != DNNMG_OK) return st;
+            ds = p;
+            if ((st = upload(ctx, tf.data(), tf.size(), &p)) != DNNMG_OK) return st;
+            dt = p;
+        }
+        ctx->W.push_back(dw);
+        ctx->scale.push_back(ds);
+        ctx->shift.push_back(dt);
+    }
+    ctx->act_rows = std::max<int64_t>(ctx->host.nc, 1);
+    ctx->act_ld = maxw;
+    const size_t ae = ctx->precision == DNNMG_FP64 ? 8 : (ctx->precision == DNNMG_FP32 ? 4 : 2);
+    for (int b = 0; b < 2; ++b)
+        if ((st = alloc(ctx, size_t(ctx->act_rows) * maxw * ae, &ctx->act[b])) != DNNMG_OK) return st;
+    ctx->has_net = true;
+    return DNNMG_OK;
+}
+
+dnnmg_status dnnmg_prolongate(dnnmg_ctx* ctx, const void* x_coarse_dev, void* x_fine_dev) {
+    if (!ctx || !x_coarse_dev || !x_fine_dev) return DNNMG_EINVAL;
+    cudaError_t e = is_fp64(ctx) ? launch_prolongate(ctx->dm, (const double*)x_coarse_dev, (double*)x_fine_dev, ctx->stream)
+                                 : launch_prolongate(ctx->dm, (const float*)x_coarse_dev, (float*)x_fine_dev, ctx->stream);
+    ctx->launches += 1;
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "prolongate");
+    return DNNMG_OK;
+}
+
+dnnmg_status dnnmg_residual(dnnmg_ctx* ctx, const void* x_coarse_dev, const void* F_dev, void* r_dev) {
+    if (!ctx || !x_coarse_dev || !F_dev || !r_dev) return DNNMG_EINVAL;
+    int launches = 0;
+    cudaError_t e = is_fp64(ctx)
+                        ? launch_residual(ctx->dm, ctx->op, (const double*)x_coarse_dev, (const double*)F_dev,
+                                          (double*)r_dev, (double*)ctx->partial, ctx->stream, &launches)
+                        : launch_residual(ctx->dm, ctx->op, (const float*)x_coarse_dev, (const float*)F_dev,
+                                          (float*)r_dev, (float*)ctx->partial, ctx->stream, &launches);
+    ctx->launches += launches;
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "residual");
+    return DNNMG_OK;
+}
+
+dnnmg_status dnnmg_local_restrict(dnnmg_ctx* ctx, const void* x_coarse_dev, const void* r_dev, void* X_dev) {
+    if (!ctx || !x_coarse_dev || !r_dev || !X_dev) return DNNMG_EINVAL;
+    cudaError_t e;
+    if (ctx->precision == DNNMG_FP64)
+        e = launch_local_restrict(ctx->dm, (const double*)x_coarse_dev, (const double*)r_dev, (double*)X_dev, ctx->stream);
+    else if (ctx->precision == DNNMG_FP32)
+        e = launch_local_restrict(ctx->dm, (const float*)x_coarse_dev, (const float*)r_dev, (float*)X_dev, ctx->stream);
+    else
+        e = launch_local_restrict(ctx->dm, (const float*)x_coarse_dev, (const float*)r_dev, (__nv_bfloat16*)X_dev,
+                                  ctx->stream);
+    ctx->launches += 1;
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "local_restrict");
+    return DNNMG_OK;
+}
+
+dnnmg_status dnnmg_network(dnnmg_ctx* ctx, const void* X_dev, void* Y_dev, int64_t n_rows) {
+    if (!ctx || !X_dev || !Y_dev || n_rows < 0) return DNNMG_EINVAL;
+    if (!ctx->has_net) return fail(ctx, DNNMG_ESTATE, "dnnmg_network before dnnmg_set_network");
+    if (n_rows > ctx->act_rows) return fail(ctx, DNNMG_EINVAL, "n_rows exceeds the activation capacity");
+    const int L = ctx->n_layers;
+    for (int i = 0; i < L; ++i) {
+        const bool last = i == L - 1;
+        const void* A = i == 0 ? X_dev : ctx->act[(i - 1) & 1];
+        const int64_t lda = i == 0 ? kNInPad : ctx->act_ld;
+        void* C = last ? Y_dev : ctx->act[i & 1];
+        const int64_t ldc = last ? kNOut : ctx->act_ld;
+        const bool skip = ctx->skip && i >= 1 && !last && ctx->widths[i] == ctx->widths[i + 1];
+        const void* R = skip ? A : nullptr;
+        const int N = ctx->npad[i], K = ctx->kpad[i];
+        cudaError_t e;
+        if (ctx->precision == DNNMG_FP64) {
+            e = launch_layer_simt((const double*)A, lda, (const double*)ctx->W[i], K, (const double*)ctx->scale[i],
+                                  (const double*)ctx->shift[i], (double*)C, ldc, (const double*)R, lda, n_rows, N, K,
+                                  !last, ctx->stream);
+        } else if (ctx->precision == DNNMG_FP32) {
+            e = launch_layer_simt((const float*)A, lda, (const float*)ctx->W[i], K, (const float*)ctx->scale[i],
+                                  (const float*)ctx->shift[i], (float*)C, ldc, (const float*)R, lda, n_rows, N, K,
+                                  !last, ctx->stream);
+        } else if (!last) {
+            e = launch_layer_simt((const __nv_bfloat16*)A, lda, (const __nv_bfloat16*)ctx->W[i], K,
+                                  (const float*)ctx->scale[i], (const float*)ctx->shift[i], (__nv_bfloat16*)C, ldc,
+                                  (const __nv_bfloat16*)R, lda, n_rows, N, K, true, ctx->stream);
+        } else {
+            e = launch_layer_simt((const __nv_bfloat16*)A, lda, (const __nv_bfloat16*)ctx->W[i], K,
+                                  (const float*)ctx->scale[i], (const float*)ctx->shift[i], (float*)C, ldc,
+                                  (const __nv_bfloat16*)nullptr, lda, n_rows, N, K, false, ctx->stream);
+        }
+        ctx->launches += 1;
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "network layer");
+    }
+    return DNNMG_OK;
+}
+
+dnnmg_status dnnmg_extend(dnnmg_ctx* ctx, const void* Y_dev, void* d_dev) {
+    if (!ctx || !Y_dev || !d_dev) return DNNMG_EINVAL;
+    cudaError_t e = is_fp64(ctx) ? launch_extend(ctx->dm, (const double*)Y_dev, (double*)d_dev, ctx->stream)
+                                 : launch_extend(ctx->dm, (const float*)Y_dev, (float*)d_dev, ctx->stream);
+    ctx->launches += 1;
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "extend");
+    return DNNMG_OK;
+}
+
+dnnmg_status dnnmg_rhs_restrict(dnnmg_ctx* ctx, const void* x_coarse_dev, const void* d_dev, void* b_fine_dev,
+                                void* b_coarse_dev) {
+    if (!ctx || !x_coarse_dev || !d_dev) return DNNMG_EINVAL;
+    int launches = 0;
+    cudaError_t e =
+        is_fp64(ctx)
+            ? launch_rhs_restrict(ctx->dm, ctx->op, (const double*)x_coarse_dev, (const double*)d_dev,
+                                  (double*)b_fine_dev, (double*)b_coarse_dev, (double*)ctx->partial,
+                                  (double*)ctx->partial_c, ctx->stream, &launches)
+            : launch_rhs_restrict(ctx->dm, ctx->op, (const float*)x_coarse_dev, (const float*)d_dev,
+                                  (float*)b_fine_dev, (float*)b_coarse_dev, (float*)ctx->partial,
+                                  (float*)ctx->partial_c, ctx->stream, &launches);
+    ctx->launches += launches;
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "rhs_restrict");
+    return DNNMG_OK;
+}
+
+dnnmg_status dnnmg_patch_step(dnnmg_ctx* ctx, const void* x_coarse_dev, const void* F_dev, void* b_fine_dev,
+                              void* b_coarse_dev) {
+    if (!ctx || !x_coarse_dev || !F_dev) return DNNMG_EINVAL;
+    if (!ctx->has_net) return fail(ctx, DNNMG_ESTATE, "dnnmg_patch_step before dnnmg_set_network");
+    dnnmg_status st;
+    if ((st = dnnmg_residual(ctx, x_coarse_dev, F_dev, ctx->buf_r)) != DNNMG_OK) return st;
+    if ((st = dnnmg_local_restrict(ctx, x_coarse_dev, ctx->buf_r, ctx->buf_X)) != DNNMG_OK) return st;
+    if ((st = dnnmg_network(ctx, ctx->buf_X, ctx->buf_Y, ctx->host.nc)) != DNNMG_OK) return st;
+    if ((st = dnnmg_extend(ctx, ctx->buf_Y, ctx->buf_d)) != DNNMG_OK) return st;
+    return dnnmg_rhs_restrict(ctx, x_coarse_dev, ctx->buf_d, b_fine_dev, b_coarse_dev);
+}
+
+dnnmg_status dnnmg_patch_step_host(dnnmg_ctx* ctx, const void* x_coarse_host, const void* F_host,
+                                   void* b_fine_host, void* b_coarse_host) {
+    if (!ctx || !x_coarse_host || !F_host) return DNNMG_EINVAL;
+    const size_t fe = field_elem(ctx->precision);
+    const size_t nv = size_t(ctx->host.nv), nf = size_t(ctx->host.n_fine);
+    CK(ctx, cudaMemcpyAsync(ctx->buf_xc, x_coarse_host, nv * 4 * fe, cudaMemcpyHostToDevice, ctx->stream));
+    CK(ctx, cudaMemcpyAsync(ctx->buf_F, F_host, nf * 4 * fe, cudaMemcpyHostToDevice, ctx->stream));
+    dnnmg_status st = dnnmg_patch_step(ctx, ctx->buf_xc, ctx->buf_F, ctx->buf_F, ctx->buf_bc);
+    if (st != DNNMG_OK) return st;
+    if (b_fine_host)
+        CK(ctx, cudaMemcpyAsync(b_fine_host, ctx->buf_F, nf * 4 * fe, cudaMemcpyDeviceToHost, ctx->stream));
+    if (b_coarse_host)
+        CK(ctx, cudaMemcpyAsync(b_coarse_host, ctx->buf_bc, nv * 4 * fe, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return DNNMG_OK;
+}
+
+dnnmg_status dnnmg_get_buffer(dnnmg_ctx* ctx, int32_t which, void** dev_ptr) {
+    if (!ctx || !dev_ptr) return DNNMG_EINVAL;
+    switch (which) {
+        case DNNMG_BUF_R: *dev_ptr = ctx->buf_r; break;
+        case DNNMG_BUF_X: *dev_ptr = ctx->buf_X; break;
+        case DNNMG_BUF_Y: *dev_ptr = ctx->buf_Y; break;
+        case DNNMG_BUF_D: *dev_ptr = ctx->buf_d; break;
+        default: return DNNMG_EINVAL;
+    }
+    return DNNMG_OK;
+}
+
+dnnmg_status dnnmg_sync(dnnmg_ctx* ctx, int64_t timeout_us) {
+    if (!ctx) return DNNMG_EINVAL;
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t e = cudaStreamQuery(ctx->stream);
+        if (e == cudaSuccess) return DNNMG_OK;
+        if (e != cudaErrorNotReady) return cuda_fail(ctx, e, "cudaStreamQuery");
+        if (timeout_us >= 0) {
+            const auto us = std::chrono::duration_cast<std::chrono::microseconds>(
+                                std::chrono::steady_clock::now() - t0).count();
+            if (us > timeout_us) return fail(ctx, DNNMG_ETIMEOUT, "dnnmg_sync: timeout");
+        }
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,293 @@
+// Host construction of level L+1 and the DNN-MG patch data (Sec. 5.2).
+//
+// A patch is one coarse cell with the 27 nodes of its uniform refinement;
+// dof(P, iota) of Sec. 5.2 is patch_map[P][iota] with iota = a + 3b + 9c.
+// Fine nodes: coarse vertices keep their numbers, then one node per coarse
+// edge, face and cell, numbered by first appearance (cells in order, local
+// edges / faces in the order of kEdges / kFaces).  The valence of a node is
+// the number of patches that contain it (mu = 1 / valence in Eq. (15)).
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstring>
+#include <unordered_map>
+
+#include "internal.h"
+
+namespace dnnmg {
+namespace {
+
+// local edges: xi-edges, eta-edges, zeta-edges
+const int kEdges[12][2] = {{0, 1}, {2, 3}, {4, 5}, {6, 7}, {0, 2}, {1, 3},
+                           {4, 6}, {5, 7}, {0, 4}, {1, 5}, {2, 6}, {3, 7}};
+// local faces xi=0, xi=1, eta=0, eta=1, zeta=0, zeta=1; vertices listed
+// lexicographically in the face's two free coordinates
+const int kFaces[6][4] = {{0, 2, 4, 6}, {1, 3, 5, 7}, {0, 1, 4, 5},
+                          {2, 3, 6, 7}, {0, 1, 2, 3}, {4, 5, 6, 7}};
+
+struct FaceKey {
+    uint64_t lo, hi;
+    bool operator==(const FaceKey& o) const { return lo == o.lo && hi == o.hi; }
+};
+struct FaceHash {
+    size_t operator()(const FaceKey& k) const {
+        uint64_t x = k.lo * 0x9E3779B97F4A7C15ull ^ (k.hi + 0x632BE59BD9B4E019ull + (k.lo << 6));
+        x ^= x >> 31;
+        return static_cast<size_t>(x * 0xBF58476D1CE4E5B9ull);
+    }
+};
+struct EdgeHash {
+    size_t operator()(uint64_t k) const {
+        k ^= k >> 33;
+        k *= 0xFF51AFD7ED558CCDull;
+        k ^= k >> 33;
+        return static_cast<size_t>(k);
+    }
+};
+
+FaceKey face_key(const int32_t* cv, int f) {
+    std::array<uint32_t, 4> v;
+    for (int i = 0; i < 4; ++i) v[i] = static_cast<uint32_t>(cv[kFaces[f][i]]);
+    std::sort(v.begin(), v.end());
+    return FaceKey{(uint64_t(v[0]) << 32) | v[1], (uint64_t(v[2]) << 32) | v[3]};
+}
+
+uint64_t edge_key(int32_t a, int32_t b) {
+    if (a > b) std::swap(a, b);
+    return (uint64_t(uint32_t(a)) << 32) | uint32_t(b);
+}
+
+// priority of boundary kinds: outflow (3) < wall (1) < driven (2)
+int prio(int kind) { return kind == 3 ? 0 : kind == 1 ? 1 : kind == 2 ? 2 : -1; }
+int kind_of_prio(int p) { return p == 0 ? 3 : p == 1 ? 1 : 2; }
+
+// What patch node iota refines: 0 vertex, 1 edge, 2 face, 3 cell; and which one.
+struct LocalEntity {
+    int type, index;
+};
+LocalEntity local_entity(int iota) {
+    const int a = iota % 3, b = (iota / 3) % 3, c = iota / 9;
+    const int mids = (a == 1) + (b == 1) + (c == 1);
+    if (mids == 0) return {0, a / 2 + 2 * (b / 2) + 4 * (c / 2)};
+    if (mids == 1) {
+        if (a == 1) return {1, b / 2 + 2 * (c / 2)};
+        if (b == 1) return {1, 4 + a / 2 + 2 * (c / 2)};
+        return {1, 8 + a / 2 + 2 * (b / 2)};
+    }
+    if (mids == 2) {
+        if (a != 1) return {2, a / 2};
+        if (b != 1) return {2, 2 + b / 2};
+        return {2, 4 + c / 2};
+    }
+    return {3, 0};
+}
+
+}  // namespace
+
+dnnmg_status build_hierarchy(const dnnmg_mesh_desc* mesh, HostHierarchy* h, std::string* err) {
+    if (!mesh || !mesh->xyz || !mesh->cell_vertices || !mesh->vertex_bc || mesh->n_vertices <= 0 ||
+        mesh->n_cells <= 0) {
+        *err = "mesh: null array or non-positive size";
+        return DNNMG_EINVAL;
+    }
+    const int64_t nv = mesh->n_vertices, nc = mesh->n_cells;
+    // 27 nc node references must fit int32 CSR entries
+    if (nc > (int64_t(1) << 31) / 32) {
+        *err = "mesh: too many cells";
+        return DNNMG_EINVAL;
+    }
+    h->nv = nv;
+    h->nc = nc;
+    h->xyz_c.assign(mesh->xyz, mesh->xyz + 3 * nv);
+    h->cells.assign(mesh->cell_vertices, mesh->cell_vertices + 8 * nc);
+    h->bc_c.assign(mesh->vertex_bc, mesh->vertex_bc + nv);
+    for (int64_t v = 0; v < nv; ++v) {
+        if (h->bc_c[v] < 0 || h->bc_c[v] > 3) {
+            *err = "mesh: vertex_bc outside 0..3";
+            return DNNMG_EINVAL;
+        }
+    }
+    for (int64_t c = 0; c < nc; ++c) {
+        const int32_t* cv = &h->cells[8 * c];
+        for (int k = 0; k < 8; ++k) {
+            if (cv[k] < 0 || cv[k] >= nv) {
+                *err = "mesh: cell vertex index out of range";
+                return DNNMG_EINVAL;
+            }
+            for (int l = 0; l < k; ++l)
+                if (cv[l] == cv[k]) {
+                    *err = "mesh: cell with a repeated vertex";
+                    return DNNMG_EINVAL;
+                }
+        }
+    }
+
+    // ---- boundary faces and their kinds
+    std::unordered_map<FaceKey, int32_t, FaceHash> face_count;
+    face_count.reserve(size_t(4 * nc));
+    for (int64_t c = 0; c < nc; ++c)
+        for (int f = 0; f < 6; ++f) face_count[face_key(&h->cells[8 * c], f)]++;
+    std::unordered_map<FaceKey, int32_t, FaceHash> bface_kind;
+    for (const auto& kv : face_count) {
+        if (kv.second != 1) continue;
+        const uint32_t v[4] = {uint32_t(kv.first.lo >> 32), uint32_t(kv.first.lo),
+                               uint32_t(kv.first.hi >> 32), uint32_t(kv.first.hi)};
+        int p = 3;
+        for (int i = 0; i < 4; ++i) {
+            const int k = h->bc_c[v[i]];
+            if (k == 0) {
+                *err = "mesh: boundary face with an interior-marked vertex";
+                return DNNMG_EINVAL;
+            }
+            p = std::min(p, prio(k));
+        }
+        bface_kind[kv.first] = kind_of_prio(p);
+    }
+    std::unordered_map<uint64_t, int32_t, EdgeHash> bedge_prio;
+    for (int64_t c = 0; c < nc; ++c) {
+        const int32_t* cv = &h->cells[8 * c];
+        for (int f = 0; f < 6; ++f) {
+            auto it = bface_kind.find(face_key(cv, f));
+            if (it == bface_kind.end()) continue;
+            const int p = prio(it->second);
+            const int32_t* fv = kFaces[f];
+            const int pairs[4][2] = {{0, 1}, {2, 3}, {0, 2}, {1, 3}};
+            for (auto& pr : pairs) {
+                const uint64_t k = edge_key(cv[fv[pr[0]]], cv[fv[pr[1]]]);
+                auto e = bedge_prio.find(k);
+                if (e == bedge_prio.end())
+                    bedge_prio[k] = p;
+                else
+                    e->second = std::max(e->second, p);
+            }
+        }
+    }
+
+    // ---- number edges and faces by first appearance
+    std::unordered_map<uint64_t, int32_t, EdgeHash> edge_id;
+    edge_id.reserve(size_t(4 * nc));
+    std::vector<std::array<int32_t, 2>> edge_par;
+    for (int64_t c = 0; c < nc; ++c) {
+        const int32_t* cv = &h->cells[8 * c];
+        for (int e = 0; e < 12; ++e) {
+            const int32_t a = cv[kEdges[e][0]], b = cv[kEdges[e][1]];
+            auto ins = edge_id.emplace(edge_key(a, b), int32_t(nv + edge_par.size()));
+            if (ins.second) edge_par.push_back({a, b});
+        }
+    }
+    const int64_t ne = int64_t(edge_par.size());
+    std::unordered_map<FaceKey, int32_t, FaceHash> face_id;
+    face_id.reserve(size_t(4 * nc));
+    std::vector<std::array<int32_t, 4>> face_par;
+    for (int64_t c = 0; c < nc; ++c) {
+        const int32_t* cv = &h->cells[8 * c];
+        for (int f = 0; f < 6; ++f) {
+            auto ins = face_id.emplace(face_key(cv, f), int32_t(nv + ne + face_par.size()));
+            if (ins.second)
+                face_par.push_back({cv[kFaces[f][0]], cv[kFaces[f][1]], cv[kFaces[f][2]], cv[kFaces[f][3]]});
+        }
+    }
+    const int64_t nf = int64_t(face_par.size());
+    const int64_t n_fine = nv + ne + nf + nc;
+    if (n_fine >= (int64_t(1) << 31)) {
+        *err = "mesh: too many fine nodes for int32 indices";
+        return DNNMG_EINVAL;
+    }
+    h->ne = ne;
+    h->nf = nf;
+    h->n_fine = n_fine;
+
+    // ---- patch map
+    h->patch_map.resize(size_t(27 * nc));
+    for (int64_t c = 0; c < nc; ++c) {
+        const int32_t* cv = &h->cells[8 * c];
+        for (int iota = 0; iota < 27; ++iota) {
+            const LocalEntity le = local_entity(iota);
+            int32_t id;
+            if (le.type == 0)
+                id = cv[le.index];
+            else if (le.type == 1)
+                id = edge_id.at(edge_key(cv[kEdges[le.index][0]], cv[kEdges[le.index][1]]));
+            else if (le.type == 2)
+                id = face_id.at(face_key(cv, le.index));
+            else
+                id = int32_t(nv + ne + nf + c);
+            h->patch_map[size_t(27 * c + iota)] = id;
+        }
+    }
+
+    // ---- kinds, coordinates
+    h->kind_f.assign(size_t(n_fine), 0);
+    h->xyz_f.assign(size_t(3 * n_fine), 0.0);
+    for (int64_t v = 0; v < nv; ++v) {
+        h->kind_f[v] = h->bc_c[v];
+        for (int d = 0; d < 3; ++d) h->xyz_f[3 * v + d] = h->xyz_c[3 * v + d];
+    }
+    for (int64_t i = 0; i < ne; ++i) {
+        const auto& e = edge_par[i];
+        auto it = bedge_prio.find(edge_key(e[0], e[1]));
+        h->kind_f[nv + i] = it == bedge_prio.end() ? 0 : kind_of_prio(it->second);
+        for (int d = 0; d < 3; ++d)
+            h->xyz_f[3 * (nv + i) + d] = (h->xyz_c[3 * e[0] + d] + h->xyz_c[3 * e[1] + d]) / 2.0;
+    }
+    for (int64_t i = 0; i < nf; ++i) {
+        const auto& f = face_par[i];
+        FaceKey key;
+        {
+            std::array<uint32_t, 4> v = {uint32_t(f[0]), uint32_t(f[1]), uint32_t(f[2]), uint32_t(f[3])};
+            std::sort(v.begin(), v.end());
+            key = FaceKey{(uint64_t(v[0]) << 32) | v[1], (uint64_t(v[2]) << 32) | v[3]};
+        }
+        auto it = bface_kind.find(key);
+        h->kind_f[nv + ne + i] = it == bface_kind.end() ? 0 : it->second;
+        for (int d = 0; d < 3; ++d) {
+            double s = 0.0;
+            for (int k = 0; k < 4; ++k) s += h->xyz_c[3 * f[k] + d];
+            h->xyz_f[3 * (nv + ne + i) + d] = s / 4.0;
+        }
+    }
+    for (int64_t c = 0; c < nc; ++c) {
+        for (int d = 0; d < 3; ++d) {
+            double s = 0.0;
+            for (int k = 0; k < 8; ++k) s += h->xyz_c[3 * h->cells[8 * c + k] + d];
+            h->xyz_f[3 * (nv + ne + nf + c) + d] = s / 8.0;
+        }
+    }
+
+    // ---- valences and the node -> (patch, iota) CSR in patch order
+    h->valence.assign(size_t(n_fine), 0);
+    for (int64_t e = 0; e < 27 * nc; ++e) h->valence[h->patch_map[e]]++;
+    h->node_ptr.assign(size_t(n_fine + 1), 0);
+    for (int64_t j = 0; j < n_fine; ++j) h->node_ptr[j + 1] = h->node_ptr[j] + h->valence[j];
+    h->node_idx.assign(size_t(27 * nc), 0);
+    {
+        std::vector<int32_t> fill(h->node_ptr.begin(), h->node_ptr.end() - 1);
+        for (int64_t e = 0; e < 27 * nc; ++e) h->node_idx[fill[h->patch_map[e]]++] = int32_t(e);
+    }
+    // coarse vertex -> (patch, local vertex) CSR in patch order
+    h->vert_ptr.assign(size_t(nv + 1), 0);
+    for (int64_t e = 0; e < 8 * nc; ++e) h->vert_ptr[h->cells[e] + 1]++;
+    for (int64_t v = 0; v < nv; ++v) h->vert_ptr[v + 1] += h->vert_ptr[v];
+    h->vert_idx.assign(size_t(8 * nc), 0);
+    {
+        std::vector<int32_t> fill(h->vert_ptr.begin(), h->vert_ptr.end() - 1);
+        for (int64_t e = 0; e < 8 * nc; ++e) h->vert_idx[fill[h->cells[e]]++] = int32_t(e);
+    }
+
+    // ---- geometry features: the 12 edge lengths of each coarse cell
+    h->edge_len.resize(size_t(12 * nc));
+    for (int64_t c = 0; c < nc; ++c) {
+        const int32_t* cv = &h->cells[8 * c];
+        for (int e = 0; e < 12; ++e) {
+            double s = 0.0;
+            for (int d = 0; d < 3; ++d) {
+                const double t = h->xyz_c[3 * cv[kEdges[e][1]] + d] - h->xyz_c[3 * cv[kEdges[e][0]] + d];
+                s += t * t;
+            }
+            h->edge_len[size_t(12 * c + e)] = std::sqrt(s);
+        }
+    }
+    return DNNMG_OK;
+}
+
+}  // namespace dnnmg

@@ -1,0 +1,122 @@
+// Internal declarations of libdnnmg (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "dnnmg.h"
+
+namespace dnnmg {
+
+constexpr int kNodes = 27;     // fine nodes per patch
+constexpr int kNIn = 228;      // network inputs per patch
+constexpr int kNInPad = 256;   // row stride of X
+constexpr int kNOut = 81;      // network outputs per patch
+
+// Level L+1 of a coarse mesh and the patch data, built on the host.
+struct HostHierarchy {
+    int64_t nv = 0, nc = 0, ne = 0, nf = 0, n_fine = 0;
+    std::vector<double> xyz_c;       // [nv][3]
+    std::vector<int32_t> cells;      // [nc][8]
+    std::vector<int32_t> bc_c;       // [nv]
+    std::vector<int32_t> patch_map;  // [nc][27]
+    std::vector<int32_t> kind_f;     // [n_fine]
+    std::vector<int32_t> valence;    // [n_fine]
+    std::vector<double> xyz_f;       // [n_fine][3]
+    std::vector<double> edge_len;    // [nc][12]
+    std::vector<int32_t> node_ptr, node_idx;   // fine node -> P*27+iota, patch order
+    std::vector<int32_t> vert_ptr, vert_idx;   // coarse vertex -> P*8+k, patch order
+};
+
+dnnmg_status build_hierarchy(const dnnmg_mesh_desc* mesh, HostHierarchy* h, std::string* err);
+
+// Device copy of the mesh data the kernels read.
+struct DeviceMesh {
+    int64_t nv = 0, nc = 0, n_fine = 0;
+    const int32_t* cells = nullptr;      // [nc][8]
+    const int32_t* patch_map = nullptr;  // [nc][27]
+    const int32_t* node_ptr = nullptr;   // [n_fine+1]
+    const int32_t* node_idx = nullptr;   // [27 nc]
+    const int32_t* vert_ptr = nullptr;   // [nv+1]
+    const int32_t* vert_idx = nullptr;   // [8 nc]
+    const uint8_t* fine_dir = nullptr;   // [n_fine] 1 = Dirichlet velocity
+    const uint8_t* coarse_dir = nullptr; // [nv]
+    const double* xyz_d = nullptr;       // [nv][3] double
+    const float* xyz_f = nullptr;        // [nv][3] float
+    const double* edge_d = nullptr;      // [nc][12]
+    const float* edge_f = nullptr;       // [nc][12]
+};
+
+struct OpParams {
+    double m;      // 1 / dt
+    double theta;
+    double nu;
+};
+
+// ---- patch kernels (kernels.cu); T = double or float -------------------
+template <typename T>
+cudaError_t launch_prolongate(const DeviceMesh& dm, const T* xc, T* xf, cudaStream_t s);
+template <typename T>
+cudaError_t launch_residual(const DeviceMesh& dm, OpParams p, const T* xc, const T* F, T* r,
+                            T* partial, cudaStream_t s, int* launches);
+template <typename T, typename TX>
+cudaError_t launch_local_restrict(const DeviceMesh& dm, const T* xc, const T* r, TX* X,
+                                  cudaStream_t s);
+template <typename T>
+cudaError_t launch_extend(const DeviceMesh& dm, const T* Y, T* d, cudaStream_t s);
+template <typename T>
+cudaError_t launch_rhs_restrict(const DeviceMesh& dm, OpParams p, const T* xc, const T* d,
+                                T* b_fine, T* b_coarse, T* partial, T* partial_c,
+                                cudaStream_t s, int* launches);
+
+// ---- network layers -------------------------------------------------------
+// C[M][N] (row stride ldc) = epilogue(A[M][K] (lda) * W[N][K]^T):
+//   z = scale[n] * acc + shift[n]; relu if `relu`; + R[m][n] (ldr) if R != null.
+template <typename TA, typename TW, typename TC, typename TS>
+cudaError_t launch_layer_simt(const TA* A, int64_t lda, const TW* W, int64_t ldw,
+                              const TS* scale, const TS* shift, TC* C, int64_t ldc,
+                              const TA* R, int64_t ldr, int64_t M, int N, int K, bool relu,
+                              cudaStream_t s);
+
+}  // namespace dnnmg
+
+// The context behind the opaque handle.
+struct dnnmg_ctx {
+    dnnmg::HostHierarchy host;
+    dnnmg::DeviceMesh dm;
+    int device = 0;
+    int precision = DNNMG_FP64;
+    dnnmg::OpParams op{};
+    cudaStream_t stream = nullptr;
+    std::string last_error;
+    int64_t launches = 0;
+    std::vector<void*> allocations;   // freed at destroy
+
+    // scratch and step buffers (element type by precision)
+    void* partial = nullptr;     // [nc][27][4]
+    void* partial_c = nullptr;   // [nc][8][4]
+    void* buf_r = nullptr;       // [n_fine][4]
+    void* buf_X = nullptr;       // [nc][kNInPad]
+    void* buf_Y = nullptr;       // [nc][81]
+    void* buf_d = nullptr;       // [n_fine][3]
+    void* buf_xc = nullptr;      // [nv][4]  (host-buffer step)
+    void* buf_F = nullptr;       // [n_fine][4]
+    void* buf_bc = nullptr;      // [nv][4]
+
+    // network
+    bool has_net = false;
+    int n_layers = 0;
+    int skip = 0;
+    std::vector<int> widths;     // true widths
+    std::vector<int> kpad;       // padded K per layer (input width as stored)
+    std::vector<int> npad;       // padded N per layer (rows of stored W)
+    std::vector<void*> W;        // per layer [npad][kpad] in the weight dtype
+    std::vector<void*> scale, shift;  // per layer [npad] (double for FP64 else float)
+    void* act[2] = {nullptr, nullptr};  // [nc][max width] activations
+    int64_t act_rows = 0;
+    int act_ld = 0;
+};

@@ -1,0 +1,675 @@
+// Patch kernels of the DNN-MG correction (Sec. 5.1-5.2) for sm_103a.
+//
+// Data flow of one step (all device memory, one stream):
+//   patch_operator<RES>  coarse x^L -> per-patch partial A(P x^L) [nc][27][4]
+//   node_reduce<RES>     r_j = F_j - sum over patches containing j (patch order)
+//   local_restrict       X[P] = [x~(27x4) | r(27x4) | 12 edge lengths | 0 pad]
+//   (network layers)     Y = N(X)
+//   extend               d_j = mu_j * sum_P Y[P][iota]  (patch order)
+//   patch_operator<RHS>  per-patch partial b(x~ + d) [nc][27][4] and its
+//                        restriction to the 8 corners [nc][8][4]
+//   node_reduce<RHS>     b_j = sum of partials; vertex_reduce: b^L_v likewise
+//
+// Every reduction is a gather over a CSR list sorted by patch index, so the
+// results are bitwise reproducible run to run (no floating-point atomics).
+#include <cstdio>
+
+#include "internal.h"
+
+namespace dnnmg {
+namespace {
+
+// 0.5 / sqrt(3): the 2-point Gauss points on [0, 1] are 0.5 -+ this.
+constexpr double kGaussOff = 0.28867513459481288225457439025098;
+
+template <typename T>
+struct V4 {};
+template <>
+struct alignas(16) V4<float> {
+    float x, y, z, w;
+};
+template <>
+struct alignas(32) V4<double> {
+    double x, y, z, w;
+};
+
+template <typename T>
+__device__ __forceinline__ V4<T> ld4(const T* p) {
+    return *reinterpret_cast<const V4<T>*>(p);
+}
+template <typename T>
+__device__ __forceinline__ void st4(T* p, V4<T> v) {
+    *reinterpret_cast<V4<T>*>(p) = v;
+}
+
+// Interpolate corner values c[8] (corner k at (k&1, (k>>1)&1, (k>>2)&1)) to
+// the patch node with grid coordinates (a, b, cz) in {0,1,2}^3: along each
+// axis coordinate 0 takes corner 0, 2 corner 1, 1 the mean of both.
+template <typename T>
+__device__ __forceinline__ T lerp_axis(int a, T c0, T c1) {
+    return a == 0 ? c0 : (a == 2 ? c1 : T(0.5) * (c0 + c1));
+}
+template <typename T, int STRIDE>
+__device__ __forceinline__ T interp27(const T* c, int comp, int a, int b, int cz) {
+    T e00 = lerp_axis(a, c[0 * STRIDE + comp], c[1 * STRIDE + comp]);
+    T e10 = lerp_axis(a, c[2 * STRIDE + comp], c[3 * STRIDE + comp]);
+    T e01 = lerp_axis(a, c[4 * STRIDE + comp], c[5 * STRIDE + comp]);
+    T e11 = lerp_axis(a, c[6 * STRIDE + comp], c[7 * STRIDE + comp]);
+    T f0 = lerp_axis(b, e00, e10);
+    T f1 = lerp_axis(b, e01, e11);
+    return lerp_axis(cz, f0, f1);
+}
+
+// Q1 basis on [0,1]^3 at 2x2x2 Gauss point q = qa + 2 qb + 4 qc.
+template <typename T>
+__device__ __forceinline__ T gpt(int i) {
+    return i ? T(0.5 + kGaussOff) : T(0.5 - kGaussOff);
+}
+template <typename T>
+__device__ __forceinline__ T basis(int k, int q) {
+    T r = T(1);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const T xi = gpt<T>((q >> d) & 1);
+        r *= ((k >> d) & 1) ? xi : T(1) - xi;
+    }
+    return r;
+}
+template <typename T>
+__device__ __forceinline__ T dbasis(int k, int q, int e) {
+    T r = T(1);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const T xi = gpt<T>((q >> d) & 1);
+        if (d == e)
+            r *= ((k >> d) & 1) ? T(1) : T(-1);
+        else
+            r *= ((k >> d) & 1) ? xi : T(1) - xi;
+    }
+    return r;
+}
+
+enum { MODE_RESIDUAL = 0, MODE_RHS = 1 };
+
+// Element integrals of one fine cell with vertex coordinates x[k] and nodal
+// values u[k] (smem pointers with per-vertex strides 3 and 4), accumulated
+// into R[8][4].
+//   MODE_RESIDUAL: Galerkin part of A_h (Eq. (6) left-hand side):
+//     R_kc += w [ (m v_c + th conv_c) N_k + th nu Dv_c . g_k - p (g_k)_c ]
+//     R_k3 += w div(v) N_k
+//   MODE_RHS: right-hand side of Eq. (6) without force:
+//     R_kc += w [ (m v_c - (1-th) conv_c) N_k - (1-th) nu Dv_c . g_k ]
+// with g_k = J^{-T} grad_ref N_k and w = det J / 8.  The gradient terms are
+// applied in reference coordinates: Dv_c . g_k - p (g_k)_c =
+// sum_e dN_k/dxi_e * Fhat_ce with Fhat_ce = sum_d Jinv_ed (coef Dv_cd - p delta_cd).
+template <typename T, int MODE>
+__device__ __forceinline__ void element(const T* const (&xs)[8], const T* const (&us)[8], T (&R)[8][4],
+                                        T m, T th, T nu) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        T J[3][3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+#pragma unroll
+            for (int e = 0; e < 3; ++e) {
+                T s = T(0);
+#pragma unroll
+                for (int k = 0; k < 8; ++k) s += xs[k][d] * dbasis<T>(k, q, e);
+                J[d][e] = s;
+            }
+        const T c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+        const T c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+        const T c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+        const T det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+        const T idet = T(1) / det;
+        // Jinv[e][d] = d xi_e / d x_d
+        T Ji[3][3];
+        Ji[0][0] = c00 * idet;
+        Ji[1][0] = c01 * idet;
+        Ji[2][0] = c02 * idet;
+        Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) * idet;
+        Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) * idet;
+        Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) * idet;
+        Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) * idet;
+        Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) * idet;
+        Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) * idet;
+        const T w = det * T(0.125);
+
+        T v[3] = {T(0), T(0), T(0)}, p = T(0);
+        T Dr[3][3];   // d v_c / d xi_e
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int e = 0; e < 3; ++e) Dr[c][e] = T(0);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const T Nk = basis<T>(k, q);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const T uk = us[k][c];
+                v[c] += Nk * uk;
+#pragma unroll
+                for (int e = 0; e < 3; ++e) Dr[c][e] += uk * dbasis<T>(k, q, e);
+            }
+            if (MODE == MODE_RESIDUAL) p += Nk * us[k][3];
+        }
+        T Dv[3][3];   // d v_c / d x_d
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) Dv[c][d] = Dr[c][0] * Ji[0][d] + Dr[c][1] * Ji[1][d] + Dr[c][2] * Ji[2][d];
+        T a[3], F[3][3];
+        const T visc = (MODE == MODE_RESIDUAL ? th : th - T(1)) * nu * w;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const T conv = v[0] * Dv[c][0] + v[1] * Dv[c][1] + v[2] * Dv[c][2];
+            a[c] = w * (m * v[c] + (MODE == MODE_RESIDUAL ? th : th - T(1)) * conv);
+            T G[3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) G[d] = visc * Dv[c][d] - (MODE == MODE_RESIDUAL && d == c ? w * p : T(0));
+#pragma unroll
+            for (int e = 0; e < 3; ++e) F[c][e] = Ji[e][0] * G[0] + Ji[e][1] * G[1] + Ji[e][2] * G[2];
+        }
+        const T wdiv = w * (Dv[0][0] + Dv[1][1] + Dv[2][2]);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const T Nk = basis<T>(k, q);
+            const T d0 = dbasis<T>(k, q, 0), d1 = dbasis<T>(k, q, 1), d2 = dbasis<T>(k, q, 2);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) R[k][c] += a[c] * Nk + F[c][0] * d0 + F[c][1] * d1 + F[c][2] * d2;
+            if (MODE == MODE_RESIDUAL) R[k][3] += wdiv * Nk;
+        }
+    }
+}
+
+constexpr int kPatchesPerBlock = 8;   // 8 fine cells each -> 64 threads
+
+// One thread per fine cell; 8 consecutive threads form a patch.
+template <typename T, int MODE>
+__global__ void __launch_bounds__(64) patch_operator_kernel(
+    int64_t nc, const int32_t* __restrict__ cells, const int32_t* __restrict__ patch_map,
+    const T* __restrict__ xyz, const T* __restrict__ xc, const T* __restrict__ dfine, T m, T th, T nu,
+    T* __restrict__ partial, T* __restrict__ partial_c) {
+    __shared__ T s_cx[kPatchesPerBlock][8][3];    // corner coordinates
+    __shared__ T s_cu[kPatchesPerBlock][8][4];    // corner values
+    __shared__ T s_nx[kPatchesPerBlock][27][3];   // patch node coordinates
+    __shared__ T s_nu[kPatchesPerBlock][27][4];   // patch node values
+    __shared__ T s_R[kPatchesPerBlock][8][8][4];  // per-cell contributions
+
+    const int lp = threadIdx.x >> 3;   // patch within block
+    const int t = threadIdx.x & 7;     // child cell / corner
+    const int64_t P = int64_t(blockIdx.x) * kPatchesPerBlock + lp;
+    const bool active = P < nc;
+
+    if (active) {
+        const int32_t v = cells[8 * P + t];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) s_cx[lp][t][d] = xyz[3 * int64_t(v) + d];
+        const V4<T> u = ld4(xc + 4 * int64_t(v));
+        s_cu[lp][t][0] = u.x;
+        s_cu[lp][t][1] = u.y;
+        s_cu[lp][t][2] = u.z;
+        s_cu[lp][t][3] = u.w;
+    }
+    __syncthreads();
+    if (active) {
+        for (int iota = t; iota < 27; iota += 8) {
+            const int a = iota % 3, b = (iota / 3) % 3, c = iota / 9;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) s_nx[lp][iota][d] = interp27<T, 3>(&s_cx[lp][0][0], d, a, b, c);
+#pragma unroll
+            for (int d = 0; d < 4; ++d) s_nu[lp][iota][d] = interp27<T, 4>(&s_cu[lp][0][0], d, a, b, c);
+            if (MODE == MODE_RHS) {   // corrected velocity x~ + d
+                const int64_t j = patch_map[27 * P + iota];
+#pragma unroll
+                for (int d = 0; d < 3; ++d) s_nu[lp][iota][d] += dfine[3 * j + d];
+            }
+        }
+    }
+    __syncthreads();
+    if (active) {
+        const int ci = t & 1, cj = (t >> 1) & 1, ck = (t >> 2) & 1;
+        const T* xs[8];
+        const T* us[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int node = (ci + (k & 1)) + 3 * (cj + ((k >> 1) & 1)) + 9 * (ck + ((k >> 2) & 1));
+            xs[k] = &s_nx[lp][node][0];
+            us[k] = &s_nu[lp][node][0];
+        }
+        T R[8][4];
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) R[k][c] = T(0);
+        element<T, MODE>(xs, us, R, m, th, nu);
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) s_R[lp][t][k][c] = R[k][c];
+    }
+    __syncthreads();
+    // sum the children's contributions at each patch node, children in order
+    for (int iota = t; active && iota < 27; iota += 8) {
+        const int a = iota % 3, b = (iota / 3) % 3, c = iota / 9;
+        T acc[4] = {T(0), T(0), T(0), T(0)};
+        for (int k2 = 0; k2 < 2; ++k2) {
+            const int ck = c - k2;
+            if (ck < 0 || ck > 1) continue;
+            for (int j2 = 0; j2 < 2; ++j2) {
+                const int cj = b - j2;
+                if (cj < 0 || cj > 1) continue;
+                for (int i2 = 0; i2 < 2; ++i2) {
+                    const int ci = a - i2;
+                    if (ci < 0 || ci > 1) continue;
+                    const int child = ci + 2 * cj + 4 * ck;
+                    const int vert = i2 + 2 * j2 + 4 * k2;
+#pragma unroll
+                    for (int d = 0; d < 4; ++d) acc[d] += s_R[lp][child][vert][d];
+                }
+            }
+        }
+        if (MODE == MODE_RHS) acc[3] = T(0);
+        st4(partial + (27 * P + iota) * 4, V4<T>{acc[0], acc[1], acc[2], acc[3]});
+        if (MODE == MODE_RHS) {
+            // keep the node sums for the restriction below
+#pragma unroll
+            for (int d = 0; d < 4; ++d) s_nu[lp][iota][d] = acc[d];
+        }
+    }
+    if (MODE == MODE_RHS) {
+        __syncthreads();
+        if (!active) return;
+        // restriction P^T of the patch's partial rhs onto its 8 corners:
+        // corner k collects node iota with the trilinear weight of k at iota
+        const int k = t;
+        const int kx = k & 1, ky = (k >> 1) & 1, kz = (k >> 2) & 1;
+        T acc[3] = {T(0), T(0), T(0)};
+        for (int iota = 0; iota < 27; ++iota) {
+            const int a = iota % 3, b = (iota / 3) % 3, c = iota / 9;
+            const T wx = a == 1 ? T(0.5) : ((a == 2) == (kx == 1) ? T(1) : T(0));
+            const T wy = b == 1 ? T(0.5) : ((b == 2) == (ky == 1) ? T(1) : T(0));
+            const T wz = c == 1 ? T(0.5) : ((c == 2) == (kz == 1) ? T(1) : T(0));
+            const T wgt = wx * wy * wz;
+            if (wgt != T(0)) {
+#pragma unroll
+                for (int d = 0; d < 3; ++d) acc[d] += wgt * s_nu[lp][iota][d];
+            }
+        }
+        st4(partial_c + (8 * P + k) * 4, V4<T>{acc[0], acc[1], acc[2], T(0)});
+    }
+}
+
+// r_j = F_j - sum_{(P,iota) in j} partial[P][iota]  (RESIDUAL)
+// b_j = sum partial (pressure row 0)                   (RHS)
+// Velocity rows of Dirichlet nodes are 0.
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256) node_reduce_kernel(
+    int64_t n, const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
+    const T* __restrict__ partial, const uint8_t* __restrict__ dir, const T* __restrict__ F,
+    T* __restrict__ out) {
+    const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    T acc[4] = {T(0), T(0), T(0), T(0)};
+    const int32_t e1 = ptr[j + 1];
+    for (int32_t e = ptr[j]; e < e1; ++e) {
+        const V4<T> pv = ld4(partial + 4 * int64_t(idx[e]));
+        acc[0] += pv.x;
+        acc[1] += pv.y;
+        acc[2] += pv.z;
+        acc[3] += pv.w;
+    }
+    V4<T> o;
+    if (MODE == MODE_RESIDUAL) {
+        const V4<T> f = ld4(F + 4 * j);
+        o = V4<T>{f.x - acc[0], f.y - acc[1], f.z - acc[2], f.w - acc[3]};
+    } else {
+        o = V4<T>{acc[0], acc[1], acc[2], T(0)};
+    }
+    if (dir[j]) {
+        o.x = T(0);
+        o.y = T(0);
+        o.z = T(0);
+    }
+    st4(out + 4 * j, o);
+}
+
+// b^L_v = sum over (P, k) with cells[P][k] = v of partial_c[P][k]; Dirichlet
+// velocity rows and the pressure row are 0.
+template <typename T>
+__global__ void __launch_bounds__(256) vertex_reduce_kernel(
+    int64_t n, const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
+    const T* __restrict__ partial_c, const uint8_t* __restrict__ dir, T* __restrict__ out) {
+    const int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    T acc[3] = {T(0), T(0), T(0)};
+    const int32_t e1 = ptr[v + 1];
+    for (int32_t e = ptr[v]; e < e1; ++e) {
+        const V4<T> pv = ld4(partial_c + 4 * int64_t(idx[e]));
+        acc[0] += pv.x;
+        acc[1] += pv.y;
+        acc[2] += pv.z;
+    }
+    if (dir[v]) acc[0] = acc[1] = acc[2] = T(0);
+    st4(out + 4 * v, V4<T>{acc[0], acc[1], acc[2], T(0)});
+}
+
+// x_fine[j] from the first patch containing j (deterministic).
+template <typename T>
+__global__ void __launch_bounds__(256) prolongate_kernel(
+    int64_t n, const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
+    const int32_t* __restrict__ cells, const T* __restrict__ xc, T* __restrict__ xf) {
+    const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const int32_t e = idx[ptr[j]];
+    const int64_t P = e / 27;
+    const int iota = e % 27;
+    const int a = iota % 3, b = (iota / 3) % 3, c = iota / 9;
+    T cu[8][4];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const V4<T> u = ld4(xc + 4 * int64_t(cells[8 * P + k]));
+        cu[k][0] = u.x;
+        cu[k][1] = u.y;
+        cu[k][2] = u.z;
+        cu[k][3] = u.w;
+    }
+    V4<T> o;
+    o.x = interp27<T, 4>(&cu[0][0], 0, a, b, c);
+    o.y = interp27<T, 4>(&cu[0][0], 1, a, b, c);
+    o.z = interp27<T, 4>(&cu[0][0], 2, a, b, c);
+    o.w = interp27<T, 4>(&cu[0][0], 3, a, b, c);
+    st4(xf + 4 * j, o);
+}
+
+template <typename TX>
+__device__ __forceinline__ TX cvt(float v);
+template <>
+__device__ __forceinline__ float cvt<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 cvt<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+template <typename TX>
+__device__ __forceinline__ TX cvtd(double v);
+template <>
+__device__ __forceinline__ double cvtd<double>(double v) { return v; }
+
+template <typename T, typename TX>
+__device__ __forceinline__ TX to_x(T v) {
+    if constexpr (sizeof(T) == 8)
+        return cvtd<TX>(v);
+    else
+        return cvt<TX>(v);
+}
+
+// One warp per patch: X[P] = [x~ at 27 nodes | r at 27 nodes | h^c | 0].
+template <typename T, typename TX>
+__global__ void __launch_bounds__(256) local_restrict_kernel(
+    int64_t nc, const int32_t* __restrict__ cells, const int32_t* __restrict__ patch_map,
+    const T* __restrict__ xc, const T* __restrict__ r, const T* __restrict__ edge_len,
+    TX* __restrict__ X) {
+    const int lane = threadIdx.x & 31;
+    const int64_t P = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    if (P >= nc) return;
+    T cu[4] = {T(0), T(0), T(0), T(0)};
+    if (lane < 8) {
+        const V4<T> u = ld4(xc + 4 * int64_t(cells[8 * P + lane]));
+        cu[0] = u.x;
+        cu[1] = u.y;
+        cu[2] = u.z;
+        cu[3] = u.w;
+    }
+    T corner[8][4];
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+#pragma unroll
+        for (int d = 0; d < 4; ++d) corner[k][d] = __shfl_sync(0xffffffffu, cu[d], k);
+    TX* row = X + P * kNInPad;
+    if (lane < 27) {
+        const int a = lane % 3, b = (lane / 3) % 3, c = lane / 9;
+#pragma unroll
+        for (int d = 0; d < 4; ++d) row[4 * lane + d] = to_x<T, TX>(interp27<T, 4>(&corner[0][0], d, a, b, c));
+        const int64_t j = patch_map[27 * P + lane];
+        const V4<T> rv = ld4(r + 4 * j);
+        row[108 + 4 * lane + 0] = to_x<T, TX>(rv.x);
+        row[108 + 4 * lane + 1] = to_x<T, TX>(rv.y);
+        row[108 + 4 * lane + 2] = to_x<T, TX>(rv.z);
+        row[108 + 4 * lane + 3] = to_x<T, TX>(rv.w);
+    }
+    if (lane < 12) row[216 + lane] = to_x<T, TX>(edge_len[12 * P + lane]);
+    if (lane < kNInPad - kNIn) row[kNIn + lane] = to_x<T, TX>(T(0));
+}
+
+// d_j = mu_j * sum_{(P,iota) in j} Y[P][3 iota + c], mu_j = 1 / valence.
+template <typename T>
+__global__ void __launch_bounds__(256) extend_kernel(
+    int64_t n, const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
+    const T* __restrict__ Y, const uint8_t* __restrict__ dir, T* __restrict__ d) {
+    const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    T acc[3] = {T(0), T(0), T(0)};
+    const int32_t e0 = ptr[j], e1 = ptr[j + 1];
+    for (int32_t e = e0; e < e1; ++e) {
+        const int32_t pe = idx[e];
+        const int64_t P = pe / 27;
+        const int iota = pe - int32_t(P) * 27;
+        const T* y = Y + P * kNOut + 3 * iota;
+        acc[0] += y[0];
+        acc[1] += y[1];
+        acc[2] += y[2];
+    }
+    const T mu = T(1) / T(e1 - e0);
+    const bool dj = dir[j] != 0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) d[3 * j + c] = dj ? T(0) : acc[c] * mu;
+}
+
+// ---- SIMT network layer ----------------------------------------------------
+template <typename T>
+struct AccOf {
+    using type = float;
+};
+template <>
+struct AccOf<double> {
+    using type = double;
+};
+
+template <typename T>
+__device__ __forceinline__ float tof(T v) {
+    return float(v);
+}
+template <>
+__device__ __forceinline__ float tof<__nv_bfloat16>(__nv_bfloat16 v) {
+    return __bfloat162float(v);
+}
+template <typename TACC, typename T>
+__device__ __forceinline__ TACC toacc(T v) {
+    if constexpr (sizeof(TACC) == 8)
+        return TACC(v);
+    else
+        return tof<T>(v);
+}
+template <typename TC, typename TACC>
+__device__ __forceinline__ TC fromacc(TACC v) {
+    if constexpr (sizeof(TC) == 2)
+        return __float2bfloat16_rn(float(v));
+    else
+        return TC(v);
+}
+
+// 64 x 64 output tile per block of 256 threads, 4 x 4 per thread, K step 16.
+template <typename TA, typename TW, typename TC, typename TS, typename TACC>
+__global__ void __launch_bounds__(256) layer_simt_kernel(
+    const TA* __restrict__ A, int64_t lda, const TW* __restrict__ W, int64_t ldw,
+    const TS* __restrict__ scale, const TS* __restrict__ shift, TC* __restrict__ C, int64_t ldc,
+    const TA* __restrict__ R, int64_t ldr, int64_t M, int N, int K, int relu) {
+    __shared__ TACC sA[16][64 + 1];
+    __shared__ TACC sW[16][64 + 1];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int64_t m0 = int64_t(blockIdx.x) * 64;
+    const int n0 = blockIdx.y * 64;
+    TACC acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = TACC(0);
+    for (int k0 = 0; k0 < K; k0 += 16) {
+        // load 64 x 16 of A and of W (each thread 4 elements of each)
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+            const int e = threadIdx.x + 256 * l;   // 0..1023
+            const int row = e >> 4, kk = e & 15;
+            const int64_t gm = m0 + row;
+            const int gn = n0 + row;
+            sA[kk][row] = gm < M ? toacc<TACC>(A[gm * lda + k0 + kk]) : TACC(0);
+            sW[kk][row] = gn < N ? toacc<TACC>(W[int64_t(gn) * ldw + k0 + kk]) : TACC(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+            TACC a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = sA[kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = sW[kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int64_t gm = m0 + ty + 16 * i;
+        if (gm >= M) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int gn = n0 + tx + 16 * j;
+            if (gn >= N) continue;
+            TACC z = toacc<TACC>(scale[gn]) * acc[i][j] + toacc<TACC>(shift[gn]);
+            if (relu) z = z > TACC(0) ? z : TACC(0);
+            if (R) z += toacc<TACC>(R[gm * ldr + gn]);
+            C[gm * ldc + gn] = fromacc<TC, TACC>(z);
+        }
+    }
+}
+
+inline unsigned blocks_for(int64_t n, int per) { return unsigned((n + per - 1) / per); }
+
+}  // namespace
+
+// ---- launchers ---------------------------------------------------------------
+template <typename T>
+static const T* xyz_of(const DeviceMesh& dm);
+template <>
+const double* xyz_of<double>(const DeviceMesh& dm) { return dm.xyz_d; }
+template <>
+const float* xyz_of<float>(const DeviceMesh& dm) { return dm.xyz_f; }
+template <typename T>
+static const T* edge_of(const DeviceMesh& dm);
+template <>
+const double* edge_of<double>(const DeviceMesh& dm) { return dm.edge_d; }
+template <>
+const float* edge_of<float>(const DeviceMesh& dm) { return dm.edge_f; }
+
+template <typename T>
+cudaError_t launch_prolongate(const DeviceMesh& dm, const T* xc, T* xf, cudaStream_t s) {
+    prolongate_kernel<T><<<blocks_for(dm.n_fine, 256), 256, 0, s>>>(dm.n_fine, dm.node_ptr, dm.node_idx,
+                                                                     dm.cells, xc, xf);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_residual(const DeviceMesh& dm, OpParams p, const T* xc, const T* F, T* r, T* partial,
+                            cudaStream_t s, int* launches) {
+    patch_operator_kernel<T, MODE_RESIDUAL><<<blocks_for(dm.nc, kPatchesPerBlock), 64, 0, s>>>(
+        dm.nc, dm.cells, dm.patch_map, xyz_of<T>(dm), xc, nullptr, T(p.m), T(p.theta), T(p.nu), partial,
+        nullptr);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    node_reduce_kernel<T, MODE_RESIDUAL><<<blocks_for(dm.n_fine, 256), 256, 0, s>>>(
+        dm.n_fine, dm.node_ptr, dm.node_idx, partial, dm.fine_dir, F, r);
+    *launches += 2;
+    return cudaGetLastError();
+}
+
+template <typename T, typename TX>
+cudaError_t launch_local_restrict(const DeviceMesh& dm, const T* xc, const T* r, TX* X, cudaStream_t s) {
+    local_restrict_kernel<T, TX><<<blocks_for(dm.nc * 32, 256), 256, 0, s>>>(
+        dm.nc, dm.cells, dm.patch_map, xc, r, edge_of<T>(dm), X);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_extend(const DeviceMesh& dm, const T* Y, T* d, cudaStream_t s) {
+    extend_kernel<T><<<blocks_for(dm.n_fine, 256), 256, 0, s>>>(dm.n_fine, dm.node_ptr, dm.node_idx, Y,
+                                                                dm.fine_dir, d);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_rhs_restrict(const DeviceMesh& dm, OpParams p, const T* xc, const T* d, T* b_fine,
+                                T* b_coarse, T* partial, T* partial_c, cudaStream_t s, int* launches) {
+    patch_operator_kernel<T, MODE_RHS><<<blocks_for(dm.nc, kPatchesPerBlock), 64, 0, s>>>(
+        dm.nc, dm.cells, dm.patch_map, xyz_of<T>(dm), xc, d, T(p.m), T(p.theta), T(p.nu), partial,
+        partial_c);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    *launches += 1;
+    if (b_fine) {
+        node_reduce_kernel<T, MODE_RHS><<<blocks_for(dm.n_fine, 256), 256, 0, s>>>(
+            dm.n_fine, dm.node_ptr, dm.node_idx, partial, dm.fine_dir, nullptr, b_fine);
+        *launches += 1;
+    }
+    if (b_coarse) {
+        vertex_reduce_kernel<T><<<blocks_for(dm.nv, 256), 256, 0, s>>>(dm.nv, dm.vert_ptr, dm.vert_idx,
+                                                                      partial_c, dm.coarse_dir, b_coarse);
+        *launches += 1;
+    }
+    return cudaGetLastError();
+}
+
+template <typename TA, typename TW, typename TC, typename TS>
+cudaError_t launch_layer_simt(const TA* A, int64_t lda, const TW* W, int64_t ldw, const TS* scale,
+                              const TS* shift, TC* C, int64_t ldc, const TA* R, int64_t ldr, int64_t M,
+                              int N, int K, bool relu, cudaStream_t s) {
+    if (K % 16) return cudaErrorInvalidValue;
+    if (M == 0) return cudaSuccess;
+    using TACC = typename AccOf<TS>::type;
+    dim3 grid(unsigned((M + 63) / 64), unsigned((N + 63) / 64));
+    layer_simt_kernel<TA, TW, TC, TS, TACC><<<grid, 256, 0, s>>>(A, lda, W, ldw, scale, shift, C, ldc, R, ldr,
+                                                                  M, N, K, relu ? 1 : 0);
+    return cudaGetLastError();
+}
+
+#define DNNMG_INST(T)                                                                                  \
+    template cudaError_t launch_prolongate<T>(const DeviceMesh&, const T*, T*, cudaStream_t);         \
+    template cudaError_t launch_residual<T>(const DeviceMesh&, OpParams, const T*, const T*, T*, T*,  \
+                                            cudaStream_t, int*);                                      \
+    template cudaError_t launch_extend<T>(const DeviceMesh&, const T*, T*, cudaStream_t);             \
+    template cudaError_t launch_rhs_restrict<T>(const DeviceMesh&, OpParams, const T*, const T*, T*,  \
+                                                T*, T*, T*, cudaStream_t, int*);
+DNNMG_INST(double)
+DNNMG_INST(float)
+template cudaError_t launch_local_restrict<double, double>(const DeviceMesh&, const double*, const double*,
+                                                           double*, cudaStream_t);
+template cudaError_t launch_local_restrict<float, float>(const DeviceMesh&, const float*, const float*, float*,
+                                                         cudaStream_t);
+template cudaError_t launch_local_restrict<float, __nv_bfloat16>(const DeviceMesh&, const float*, const float*,
+                                                                 __nv_bfloat16*, cudaStream_t);
+template cudaError_t launch_layer_simt<double, double, double, double>(const double*, int64_t, const double*,
+                                                                       int64_t, const double*, const double*,
+                                                                       double*, int64_t, const double*, int64_t,
+                                                                       int64_t, int, int, bool, cudaStream_t);
+template cudaError_t launch_layer_simt<float, float, float, float>(const float*, int64_t, const float*, int64_t,
+                                                                   const float*, const float*, float*, int64_t,
+                                                                   const float*, int64_t, int64_t, int, int, bool,
+                                                                   cudaStream_t);
+template cudaError_t launch_layer_simt<__nv_bfloat16, __nv_bfloat16, __nv_bfloat16, float>(
+    const __nv_bfloat16*, int64_t, const __nv_bfloat16*, int64_t, const float*, const float*, __nv_bfloat16*,
+    int64_t, const __nv_bfloat16*, int64_t, int64_t, int, int, bool, cudaStream_t);
+template cudaError_t launch_layer_simt<__nv_bfloat16, __nv_bfloat16, float, float>(
+    const __nv_bfloat16*, int64_t, const __nv_bfloat16*, int64_t, const float*, const float*, float*, int64_t,
+    const __nv_bfloat16*, int64_t, int64_t, int, int, bool, cudaStream_t);
+
+}  // namespace dnnmg

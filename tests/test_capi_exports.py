@@ -1,0 +1,50 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point
+include/dnnmg.h declares (no GPU needed: no compute calls)."""
+import os
+import re
+
+import pytest
+
+from paper_2307_14837_gb300 import build, capi
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "dnnmg.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(dnnmg_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return capi.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_binding_names_match_header():
+    assert sorted(capi.exported_symbols()) == _declared()
+
+
+def test_status_strings(lib):
+    assert capi.load().dnnmg_strerror(0) == b"ok"
+    assert capi.load().dnnmg_strerror(-1) == b"invalid argument"
+    assert capi.load().dnnmg_strerror(-99) == b"unknown status"
+
+
+def test_create_rejects_bad_arguments_without_a_gpu(lib):
+    # argument validation happens before any CUDA call
+    mesh = dict(xyz=[[0.0, 0, 0]], cells=[[0, 0, 0, 0, 0, 0, 0, 0]], vertex_bc=[0])
+    with pytest.raises(capi.DnnmgError) as e:
+        capi.dnnmg_create(mesh, 0.01, 0.01, 1.0, capi.FP64)
+    assert e.value.status == -1
+    with pytest.raises(capi.DnnmgError):
+        capi.dnnmg_create(mesh, 0.01, -1.0, 1.0, capi.FP64)     # dt <= 0
+
