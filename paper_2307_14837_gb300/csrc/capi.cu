@@ -245,10 +245,14 @@ dnnmg_status dnnmg_set_network(dnnmg_ctx* ctx, const dnnmg_net_desc* net, const 
     ctx->npad.resize(L);
     int maxw = 16;
     for (int i = 0; i < L; ++i) {
-        ctx->kpad[i] = i == 0 ? kNInPad : ctx->widths[i];
-        ctx->npad[i] = ctx->widths[i + 1];
+        const bool bf16 = ctx->precision == DNNMG_BF16;
+        // tensor-core layers read K in blocks of 64 and the last layer's W
+        // as a 96-row tile; padding is zero
+        ctx->kpad[i] = i == 0 ? kNInPad : (bf16 ? (ctx->widths[i] + 63) / 64 * 64 : ctx->widths[i]);
+        ctx->npad[i] = (bf16 && i == L - 1) ? 96 : ctx->widths[i + 1];
         if (i < L - 1) maxw = std::max(maxw, ctx->widths[i + 1]);
     }
+    if (ctx->precision == DNNMG_BF16) maxw = (maxw + 63) / 64 * 64;
     dnnmg_status st;
     for (int i = 0; i < L; ++i) {
         const int N = ctx->npad[i], K = ctx->kpad[i], n_true = ctx->widths[i + 1], k_true = ctx->widths[i];
@@ -295,8 +299,11 @@ dnnmg_status dnnmg_set_network(dnnmg_ctx* ctx, const dnnmg_net_desc* net, const 
     ctx->act_rows = std::max<int64_t>(ctx->host.nc, 1);
     ctx->act_ld = maxw;
     const size_t ae = ctx->precision == DNNMG_FP64 ? 8 : (ctx->precision == DNNMG_FP32 ? 4 : 2);
-    for (int b = 0; b < 2; ++b)
+    for (int b = 0; b < 2; ++b) {
         if ((st = alloc(ctx, size_t(ctx->act_rows) * maxw * ae, &ctx->act[b])) != DNNMG_OK) return st;
+        // columns beyond a layer's width are never written and must read as 0
+        CK(ctx, cudaMemset(ctx->act[b], 0, size_t(ctx->act_rows) * maxw * ae));
+    }
     ctx->has_net = true;
     return DNNMG_OK;
 }
@@ -361,14 +368,10 @@ dnnmg_status dnnmg_network(dnnmg_ctx* ctx, const void* X_dev, void* Y_dev, int64
             e = launch_layer_simt((const float*)A, lda, (const float*)ctx->W[i], K, (const float*)ctx->scale[i],
                                   (const float*)ctx->shift[i], (float*)C, ldc, (const float*)R, lda, n_rows, N, K,
                                   !last, ctx->stream);
-        } else if (!last) {
-            e = launch_layer_simt((const __nv_bfloat16*)A, lda, (const __nv_bfloat16*)ctx->W[i], K,
-                                  (const float*)ctx->scale[i], (const float*)ctx->shift[i], (__nv_bfloat16*)C, ldc,
-                                  (const __nv_bfloat16*)R, lda, n_rows, N, K, true, ctx->stream);
         } else {
-            e = launch_layer_simt((const __nv_bfloat16*)A, lda, (const __nv_bfloat16*)ctx->W[i], K,
-                                  (const float*)ctx->scale[i], (const float*)ctx->shift[i], (float*)C, ldc,
-                                  (const __nv_bfloat16*)nullptr, lda, n_rows, N, K, false, ctx->stream);
+            e = launch_layer_tc((const __nv_bfloat16*)A, lda, (const __nv_bfloat16*)ctx->W[i], K, N,
+                                (const float*)ctx->scale[i], (const float*)ctx->shift[i], C, ldc, !last,
+                                (const __nv_bfloat16*)R, lda, n_rows, ctx->widths[i + 1], K, !last, ctx->stream);
         }
         ctx->launches += 1;
         if (e != cudaSuccess) return cuda_fail(ctx, e, "network layer");
@@ -448,7 +451,13 @@ dnnmg_status dnnmg_sync(dnnmg_ctx* ctx, int64_t timeout_us) {
     const auto t0 = std::chrono::steady_clock::now();
     for (;;) {
         cudaError_t e = cudaStreamQuery(ctx->stream);
-        if (e == cudaSuccess) return DNNMG_OK;
+        if (e == cudaSuccess) {
+            int code = 0;
+            CK(ctx, read_tc_error(&code));
+            if (code) return fail(ctx, DNNMG_ETIMEOUT, "tensor-core kernel: a bounded wait expired (code " +
+                                                          std::to_string(code) + ")");
+            return DNNMG_OK;
+        }
         if (e != cudaErrorNotReady) return cuda_fail(ctx, e, "cudaStreamQuery");
         if (timeout_us >= 0) {
             const auto us = std::chrono::duration_cast<std::chrono::microseconds>(

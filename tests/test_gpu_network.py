@@ -1,0 +1,61 @@
+"""The patch network on many rows (several output tiles per SM, pipeline
+stages wrapping around, both TMEM accumulators reused) against the FP64
+oracle, per row; and the tensor-core kernel's error flag stays clear."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from parity_util import patch_output_err  # noqa: E402
+from paper_2307_14837_gb300 import build, capi, inputs as I  # noqa: E402
+from paper_2307_14837_gb300.path import PatchPath  # noqa: E402
+from oracle import mlp as omlp  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+
+
+@pytest.fixture(scope="module")
+def mesh():
+    # any mesh works for network-only calls; rows come from the caller
+    return I.cavity_mesh(2)
+
+
+def _rows(M, seed):
+    X = np.zeros((M, 256))
+    X[:, :228] = I.splitmix_normal(900 + seed, M * 228).reshape(M, 228)
+    return X
+
+
+@pytest.mark.parametrize("precision,widths,M,bn", [
+    ("bf16", (228, 512, 512, 512, 81), 40000 + 77, True),   # 4-5 tiles per SM, ragged last tile
+    ("bf16", (228, 1024, 1024, 81), 9000 + 5, False),
+    ("bf16", (228, 192, 192, 81), 1000, True),              # N not a multiple of the tile
+    ("fp32", (228, 512, 512, 81), 5000 + 3, True),
+])
+def test_network_rows_against_oracle(mesh, precision, widths, M, bn):
+    p = PatchPath(mesh, 0.01, 0.01, 1.0, precision)
+    Ws, ss, ts = I.network_weights(widths, seed=7, scale_shift=bn)
+    # capacity of the context's activation buffers is its patch count, so
+    # use a context whose mesh has at least M patches
+    if p.n_patches < M:
+        p.close()
+        n = int(np.ceil(M ** (1 / 3)))
+        p = PatchPath(I.cavity_mesh(n + (n % 2)), 0.01, 0.01, 1.0, precision)
+    p.set_network(widths, Ws, ss, ts, skip=True)
+    X = _rows(M, 1)
+    Xd = torch.as_tensor(X, device="cuda").to(p.x_dtype)
+    Y = p.network(Xd, M)
+    torch.cuda.synchronize()
+    capi.dnnmg_sync(p.ctx, 10_000_000)                # raises if a bounded wait expired
+    Xo = Xd.double().cpu().numpy()[:, :228]           # the oracle sees the same (rounded) inputs
+    ref = omlp.forward(Xo, Ws, ss, ts, skip=True)
+    emax, ep99 = patch_output_err(Y.double().cpu().numpy(), ref)
+    tol = 2e-2 if precision == "bf16" else 1e-5
+    assert emax <= tol, (emax, ep99)
+    p.close()
