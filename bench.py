@@ -101,9 +101,9 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def build_workload(seed=0):
+def build_workload(seed=0, nz=NZ):
     from paper_2307_14837_gb300 import inputs as I
-    m = I.channel_mesh(NZ, seed=seed)
+    m = I.channel_mesh(nz, seed=seed)
     nu = m["meta"]["D"] / 200.0          # Re = mean inflow * D / nu = 200
     return m, nu
 
@@ -117,7 +117,7 @@ def run_ours(args, rank, world, local_rank):
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    m, nu = build_workload(seed=rank)
+    m, nu = build_workload(seed=rank, nz=args.nz)
     stream = torch.cuda.Stream(dev)
     p = PatchPath(m, nu, DT, THETA, "bf16", device=dev, stream=stream)
     Ws, ss, ts = I.network_weights(WIDTHS, seed=0)
@@ -262,6 +262,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--nz", type=int, default=NZ,
+                    help="channel resolution (cells across the height); the measured workload is nz=37")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -317,7 +319,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
         "data": "synthetic",
-        "config": {"workload": f"channel 2.5x0.41x0.41 with seeded cylinder, nz={NZ}: {nc} patches "
+        "config": {"workload": f"channel 2.5x0.41x0.41 with seeded cylinder, nz={args.nz}: {nc} patches "
                                f"(coarse hex), {nf} fine nodes; BF16 network {'-'.join(map(str, WIDTHS))}, "
                                f"FP32 fields, CN dt={DT}, Re=200",
                    "patches_per_step": nc, "l2": "working set > L2 (activations 644 MB per layer)",

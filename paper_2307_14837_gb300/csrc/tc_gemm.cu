@@ -36,6 +36,7 @@ constexpr int BM = 128;
 constexpr int BK = 64;                 // 64 bf16 = 128 bytes = one swizzle row
 constexpr int kThreads = 192;
 constexpr uint64_t kWaitNs = 1000000000ull;
+constexpr int kStageLd = 36;           // floats per staged row (32 + 4: conflict-free float4 access)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -69,6 +70,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
         : "r"(bar), "r"(parity)
         : "memory");
     return ok != 0;
+}
+
+// AND of `ok` over the 128 epilogue threads (named barrier 1); also a barrier.
+__device__ __forceinline__ bool epilogue_all(bool ok) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 q, %1, 0;\n\t"
+        "bar.red.and.pred p, 1, 128, q;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(r)
+        : "r"(uint32_t(ok))
+        : "memory");
+    return r != 0;
 }
 
 // Bounded wait for the phase with the given parity; false on expiry (the
@@ -149,11 +164,12 @@ struct Cfg {
     static constexpr int A_BYTES = BM * BK * 2;
     static constexpr int B_BYTES = BN * BK * 2;
     static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-    static constexpr int STAGES = (200 * 1024) / STAGE_BYTES > 8 ? 8 : (200 * 1024) / STAGE_BYTES;
+    static constexpr int STAGES = (192 * 1024) / STAGE_BYTES > 8 ? 8 : (192 * 1024) / STAGE_BYTES;
     static constexpr int ACC_COLS = BN <= 128 ? 128 : 256;      // TMEM columns per accumulator
     static constexpr int TMEM_COLS = 2 * ACC_COLS;              // power of two >= 32
-    static constexpr int BAR_BYTES = (2 * STAGES + 5) * 8 + 16;
-    static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + BAR_BYTES;
+    static constexpr int BAR_BYTES = ((2 * STAGES + 5) * 8 + 16 + 127) / 128 * 128;   // keeps what follows aligned
+    static constexpr int EP_BYTES = 4 * 32 * kStageLd * 4 + 2 * BN * 4;   // epilogue staging + scale/shift
+    static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + BAR_BYTES + EP_BYTES;
 };
 
 template <int BN, bool OUT_BF16>
@@ -174,6 +190,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_layer_kernel(
     const uint32_t done_bar = bars + 8u * (2 * C::STAGES + 4);
     volatile uint32_t* tmem_slot =
         reinterpret_cast<volatile uint32_t*>(gbase + C::STAGES * C::STAGE_BYTES + (2 * C::STAGES + 5) * 8);
+    float* ep_stage = reinterpret_cast<float*>(gbase + C::STAGES * C::STAGE_BYTES + C::BAR_BYTES);
+    float* ep_scale = ep_stage + 4 * 32 * kStageLd;
+    float* ep_shift = ep_scale + BN;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -272,70 +291,84 @@ __global__ void __launch_bounds__(kThreads, 1) tc_layer_kernel(
         mbar_wait(done_bar, 0, kErrDrain);
     } else if (warp >= 2) {
         // ---------------- epilogue: warp w reads TMEM lanes 32 (w % 4) ..
+        // Each 32 x 32 block goes TMEM -> registers (scale, shift, ReLU) ->
+        // padded shared memory -> coalesced global stores (8 rows x 64 bytes
+        // per warp instruction), with the skip input read the same way.
         const int quarter = warp & 3;
-        const int row_in_tile = quarter * 32 + lane;
+        const int et = threadIdx.x - 64;                 // 0..127 among epilogue threads
+        float* stage = ep_stage + (warp - 2) * (32 * kStageLd);
         int it = 0;
         for (int t = blockIdx.x; t < total; t += gridDim.x, ++it) {
             const int buf = it & 1;
             const uint32_t use = uint32_t(it >> 1);
-            if (!mbar_wait(tfull_bar(buf), use & 1u, kErrTmemFull)) break;
-            fence_after();
             const int m0 = (t / tiles_n) * BM, n0 = (t % tiles_n) * BN;
-            const int64_t row = int64_t(m0) + row_in_tile;
-            const bool row_ok = row < M;
+            // this tile's scale / shift columns into shared memory
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+            for (int c = et; c < BN; c += 128) {
+                const int n = n0 + c;
+                ep_scale[c] = n < N ? __ldg(scale + n) : 0.f;
+                ep_shift[c] = n < N ? __ldg(shift + n) : 0.f;
+            }
+            // the wait result is voted on so that all epilogue warps leave
+            // the loop together (the named barrier above must never be
+            // left waiting for a warp that has gone)
+            const bool ok = mbar_wait(tfull_bar(buf), use & 1u, kErrTmemFull);
+            if (!epilogue_all(ok)) break;
+            fence_after();
+            const int64_t row0 = int64_t(m0) + quarter * 32;
 #pragma unroll 1
             for (int c0 = 0; c0 < BN; c0 += 32) {
                 float v[32];
                 const uint32_t taddr = tmem_base + (uint32_t(quarter * 32) << 16) + uint32_t(buf * C::ACC_COLS + c0);
                 tmem_ld32(taddr, v);
                 const int n_base = n0 + c0;
-                if (!row_ok || n_base >= N) continue;
+                if (n_base >= N) continue;                 // warp-uniform
 #pragma unroll
                 for (int i = 0; i < 32; ++i) {
-                    const int n = n_base + i;
-                    const float s = n < N ? __ldg(scale + n) : 0.f;
-                    const float b = n < N ? __ldg(shift + n) : 0.f;
-                    float z = fmaf(s, v[i], b);
+                    float z = fmaf(ep_scale[c0 + i], v[i], ep_shift[c0 + i]);
                     if (relu) z = fmaxf(z, 0.f);
                     v[i] = z;
                 }
+                float4* srow = reinterpret_cast<float4*>(stage + lane * kStageLd);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) srow[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+                __syncwarp();
                 if constexpr (OUT_BF16) {
-                    __nv_bfloat16* out = static_cast<__nv_bfloat16*>(Cout) + row * ldc + n_base;
-                    if (n_base + 32 <= N) {
+                    // piece p = 8 columns of one row; lane handles p = lane + 32 i
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int p = lane + 32 * i;
+                        const int r = p >> 2, c8 = (p & 3) * 8;
+                        const int64_t row = row0 + r;
+                        if (row >= M || n_base + c8 >= N) continue;
+                        const float4 a = *reinterpret_cast<const float4*>(stage + r * kStageLd + c8);
+                        const float4 b = *reinterpret_cast<const float4*>(stage + r * kStageLd + c8 + 4);
+                        float z[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
                         if (R) {
-                            const uint4* rp = reinterpret_cast<const uint4*>(R + row * ldr + n_base);
+                            uint4 u = __ldg(reinterpret_cast<const uint4*>(R + row * ldr + n_base + c8));
+                            const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
 #pragma unroll
-                            for (int q = 0; q < 4; ++q) {
-                                uint4 u = __ldg(rp + q);
-                                const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
-#pragma unroll
-                                for (int e = 0; e < 4; ++e) {
-                                    const float2 f = __bfloat1622float2(h[e]);
-                                    v[8 * q + 2 * e] += f.x;
-                                    v[8 * q + 2 * e + 1] += f.y;
-                                }
+                            for (int e = 0; e < 4; ++e) {
+                                const float2 f = __bfloat1622float2(h[e]);
+                                z[2 * e] += f.x;
+                                z[2 * e + 1] += f.y;
                             }
                         }
-                        uint4* op = reinterpret_cast<uint4*>(out);
+                        uint4 o;
+                        __nv_bfloat162* ho = reinterpret_cast<__nv_bfloat162*>(&o);
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            uint4 u;
-                            __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&u);
-#pragma unroll
-                            for (int e = 0; e < 4; ++e) h[e] = __floats2bfloat162_rn(v[8 * q + 2 * e], v[8 * q + 2 * e + 1]);
-                            op[q] = u;
-                        }
-                    } else {
-                        for (int i = 0; i < 32 && n_base + i < N; ++i) {
-                            float z = v[i];
-                            if (R) z += __bfloat162float(R[row * ldr + n_base + i]);
-                            out[i] = __float2bfloat16_rn(z);
-                        }
+                        for (int e = 0; e < 4; ++e) ho[e] = __floats2bfloat162_rn(z[2 * e], z[2 * e + 1]);
+                        *reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(Cout) + row * ldc + n_base + c8) = o;
                     }
                 } else {
-                    float* out = static_cast<float*>(Cout) + row * ldc + n_base;
-                    for (int i = 0; i < 32 && n_base + i < N; ++i) out[i] = v[i];
+                    // fp32 rows of arbitrary stride: a warp writes 32 consecutive columns of one row
+                    const int n = n_base + lane;
+                    for (int r = 0; r < 32; ++r) {
+                        const int64_t row = row0 + r;
+                        if (row < M && n < N) static_cast<float*>(Cout)[row * ldc + n] = stage[r * kStageLd + lane];
+                    }
                 }
+                __syncwarp();
             }
             fence_before();
             mbar_arrive(tempty_bar(buf));
