@@ -401,7 +401,39 @@ __device__ __forceinline__ TX to_x(T v) {
         return cvt<TX>(v);
 }
 
+// Four values of the input row as one vector store (16 bytes for float /
+// bf16 pairs packed into 8 bytes; double stays scalar-pair).
+template <typename TX>
+struct Pack4 {};
+template <>
+struct alignas(8) Pack4<__nv_bfloat16> {
+    __nv_bfloat162 a, b;
+};
+template <>
+struct alignas(16) Pack4<float> {
+    float a, b, c, d;
+};
+template <>
+struct alignas(16) Pack4<double> {   // two 16-byte halves
+    double a, b, c, d;
+};
+template <typename TX, typename T>
+__device__ __forceinline__ void store4(TX* dst, T a, T b, T c, T d) {
+    if constexpr (sizeof(TX) == 2) {
+        Pack4<__nv_bfloat16> v{__floats2bfloat162_rn(float(a), float(b)), __floats2bfloat162_rn(float(c), float(d))};
+        *reinterpret_cast<Pack4<__nv_bfloat16>*>(dst) = v;
+    } else if constexpr (sizeof(TX) == 4) {
+        *reinterpret_cast<Pack4<float>*>(dst) = Pack4<float>{float(a), float(b), float(c), float(d)};
+    } else {
+        reinterpret_cast<double2*>(dst)[0] = make_double2(double(a), double(b));
+        reinterpret_cast<double2*>(dst)[1] = make_double2(double(c), double(d));
+    }
+}
+
 // One warp per patch: X[P] = [x~ at 27 nodes | r at 27 nodes | h^c | 0].
+// Lane iota < 27 writes node iota's 4 values of x~ and of r as one vector
+// each; lanes 0..9 write the 12 edge lengths and the zero padding (4 values
+// per lane).  Row stride 256, so every 4-value group is aligned.
 template <typename T, typename TX>
 __global__ void __launch_bounds__(256) local_restrict_kernel(
     int64_t nc, const int32_t* __restrict__ cells, const int32_t* __restrict__ patch_map,
@@ -410,9 +442,15 @@ __global__ void __launch_bounds__(256) local_restrict_kernel(
     const int lane = threadIdx.x & 31;
     const int64_t P = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     if (P >= nc) return;
+    // issue the independent loads first: corner ids, node ids, edge lengths
+    const int32_t v = lane < 8 ? __ldg(cells + 8 * P + lane) : 0;
+    const int32_t j = lane < 27 ? __ldg(patch_map + 27 * P + lane) : 0;
+    const T el = lane < 12 ? edge_len[12 * P + lane] : T(0);
+    V4<T> rv{T(0), T(0), T(0), T(0)};
+    if (lane < 27) rv = ld4(r + 4 * int64_t(j));
     T cu[4] = {T(0), T(0), T(0), T(0)};
     if (lane < 8) {
-        const V4<T> u = ld4(xc + 4 * int64_t(cells[8 * P + lane]));
+        const V4<T> u = ld4(xc + 4 * int64_t(v));
         cu[0] = u.x;
         cu[1] = u.y;
         cu[2] = u.z;
@@ -423,20 +461,22 @@ __global__ void __launch_bounds__(256) local_restrict_kernel(
     for (int k = 0; k < 8; ++k)
 #pragma unroll
         for (int d = 0; d < 4; ++d) corner[k][d] = __shfl_sync(0xffffffffu, cu[d], k);
+    // edge lengths 0..11 gathered for lanes 0..2 (4 each)
+    const T e0 = __shfl_sync(0xffffffffu, el, (4 * lane) & 31);
+    const T e1 = __shfl_sync(0xffffffffu, el, (4 * lane + 1) & 31);
+    const T e2 = __shfl_sync(0xffffffffu, el, (4 * lane + 2) & 31);
+    const T e3 = __shfl_sync(0xffffffffu, el, (4 * lane + 3) & 31);
     TX* row = X + P * kNInPad;
     if (lane < 27) {
         const int a = lane % 3, b = (lane / 3) % 3, c = lane / 9;
-#pragma unroll
-        for (int d = 0; d < 4; ++d) row[4 * lane + d] = to_x<T, TX>(interp27<T, 4>(&corner[0][0], d, a, b, c));
-        const int64_t j = patch_map[27 * P + lane];
-        const V4<T> rv = ld4(r + 4 * j);
-        row[108 + 4 * lane + 0] = to_x<T, TX>(rv.x);
-        row[108 + 4 * lane + 1] = to_x<T, TX>(rv.y);
-        row[108 + 4 * lane + 2] = to_x<T, TX>(rv.z);
-        row[108 + 4 * lane + 3] = to_x<T, TX>(rv.w);
+        store4<TX>(row + 4 * lane, interp27<T, 4>(&corner[0][0], 0, a, b, c), interp27<T, 4>(&corner[0][0], 1, a, b, c),
+                   interp27<T, 4>(&corner[0][0], 2, a, b, c), interp27<T, 4>(&corner[0][0], 3, a, b, c));
+        store4<TX>(row + 108 + 4 * lane, rv.x, rv.y, rv.z, rv.w);
     }
-    if (lane < 12) row[216 + lane] = to_x<T, TX>(edge_len[12 * P + lane]);
-    if (lane < kNInPad - kNIn) row[kNIn + lane] = to_x<T, TX>(T(0));
+    if (lane < 3)
+        store4<TX>(row + 216 + 4 * lane, e0, e1, e2, e3);
+    else if (lane < 10)   // columns 228..255
+        store4<TX>(row + 216 + 4 * lane, T(0), T(0), T(0), T(0));
 }
 
 // d_j = mu_j * sum_{(P,iota) in j} Y[P][3 iota + c], mu_j = 1 / valence.

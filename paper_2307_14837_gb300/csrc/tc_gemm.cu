@@ -309,13 +309,28 @@ __global__ void __launch_bounds__(kThreads, 1) tc_layer_kernel(
                 ep_scale[c] = n < N ? __ldg(scale + n) : 0.f;
                 ep_shift[c] = n < N ? __ldg(shift + n) : 0.f;
             }
+            const int64_t row0 = int64_t(m0) + quarter * 32;
+            // skip input of one 32-column chunk in the coalesced layout:
+            // piece i of this lane = 8 columns (c8) of row r
+            auto load_skip = [&](int c0, uint4 (&rr)[4]) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int p = lane + 32 * i;
+                    const int r = p >> 2, c8 = (p & 3) * 8;
+                    const int64_t row = row0 + r;
+                    const int n = n0 + c0 + c8;
+                    rr[i] = (R && row < M && n < N) ? __ldg(reinterpret_cast<const uint4*>(R + row * ldr + n))
+                                                   : make_uint4(0, 0, 0, 0);
+                }
+            };
+            uint4 rr[4];
+            if constexpr (OUT_BF16) load_skip(0, rr);    // in flight while waiting for the tile
             // the wait result is voted on so that all epilogue warps leave
             // the loop together (the named barrier above must never be
             // left waiting for a warp that has gone)
             const bool ok = mbar_wait(tfull_bar(buf), use & 1u, kErrTmemFull);
             if (!epilogue_all(ok)) break;
             fence_after();
-            const int64_t row0 = int64_t(m0) + quarter * 32;
 #pragma unroll 1
             for (int c0 = 0; c0 < BN; c0 += 32) {
                 float v[32];
@@ -323,6 +338,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_layer_kernel(
                 tmem_ld32(taddr, v);
                 const int n_base = n0 + c0;
                 if (n_base >= N) continue;                 // warp-uniform
+                uint4 rn[4];
+                if constexpr (OUT_BF16) {
+                    if (c0 + 32 < BN) load_skip(c0 + 32, rn);   // next chunk's skip input
+                }
 #pragma unroll
                 for (int i = 0; i < 32; ++i) {
                     float z = fmaf(ep_scale[c0 + i], v[i], ep_shift[c0 + i]);
@@ -334,7 +353,6 @@ __global__ void __launch_bounds__(kThreads, 1) tc_layer_kernel(
                 for (int j = 0; j < 8; ++j) srow[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
                 __syncwarp();
                 if constexpr (OUT_BF16) {
-                    // piece p = 8 columns of one row; lane handles p = lane + 32 i
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
                         const int p = lane + 32 * i;
@@ -345,8 +363,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_layer_kernel(
                         const float4 b = *reinterpret_cast<const float4*>(stage + r * kStageLd + c8 + 4);
                         float z[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
                         if (R) {
-                            uint4 u = __ldg(reinterpret_cast<const uint4*>(R + row * ldr + n_base + c8));
-                            const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
+                            const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&rr[i]);
 #pragma unroll
                             for (int e = 0; e < 4; ++e) {
                                 const float2 f = __bfloat1622float2(h[e]);
@@ -360,6 +377,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_layer_kernel(
                         for (int e = 0; e < 4; ++e) ho[e] = __floats2bfloat162_rn(z[2 * e], z[2 * e + 1]);
                         *reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(Cout) + row * ldc + n_base + c8) = o;
                     }
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) rr[i] = rn[i];
                 } else {
                     // fp32 rows of arbitrary stride: a warp writes 32 consecutive columns of one row
                     const int n = n_base + lane;
