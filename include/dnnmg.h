@@ -238,6 +238,45 @@ dnnmg_status dnnmg_sync(dnnmg_ctx* ctx, int64_t timeout_us);
 /* Number of kernel launches this context has issued (for accounting). */
 int64_t dnnmg_launch_count(const dnnmg_ctx* ctx);
 
+/* Largest mesh dnnmg_residual_noalloc accepts (coarse cells = patches). */
+#define DNNMG_NOALLOC_MAX_PATCHES 16384
+
+/* dnnmg_residual without any allocation, for callers that may not allocate
+ * device memory: a host application that hands out all device memory from
+ * its own pool, or a program that must not call cudaMalloc after set-up.
+ * The paper has no counterpart; this is a packaging of the same FP32
+ * residual kernels (prolongation fused with the Q1 element integrals, then
+ * the per-node reduction in patch order), with every array supplied by the
+ * caller and the per-patch partial sums (n_patches x 27 x 4 floats) kept in
+ * one fixed array of DNNMG_NOALLOC_MAX_PATCHES x 27 x 4 floats (6.75 MiB)
+ * that the library's device image holds on every GPU that loads it, until
+ * the process exits.  No context is needed; nothing is allocated or freed.
+ *
+ * Arguments (device pointers, caller-owned, FP32 form only):
+ *   cells_dev          int32 [n_patches][8]   coarse cells (lexicographic vertices)
+ *   xyz_dev            float [n_coarse_vertices][3]
+ *   node_ptr_dev       int32 [n_fine_nodes + 1] and
+ *   node_idx_dev       int32 [27 n_patches]: for fine node j the entries
+ *                      P*27 + iota with patch_map[P][iota] == j, sorted by P
+ *   fine_dirichlet_dev uint8 [n_fine_nodes]: 1 where the velocity is prescribed
+ *   x_coarse_dev       float [n_coarse_vertices][4], F_dev float [n_fine_nodes][4]
+ *   r_dev              float [n_fine_nodes][4] (output)
+ *   nu, dt, theta      as in dnnmg_params; cuda_stream a cudaStream_t (NULL = default)
+ * The first call on a device looks up the fixed array's device address
+ * (cudaGetSymbolAddress, once per device, under a lock); make that first
+ * call before any stream capture.  Every call uses the same array, whose
+ * contents persist between calls; each call overwrites all partial sums it
+ * reads, so nothing has to be cleared, but calls that overlap on the GPU
+ * (two streams, two threads) race on it.
+ * Errors: DNNMG_EINVAL for a null pointer, non-positive size, bad
+ * nu/dt/theta, or n_patches > DNNMG_NOALLOC_MAX_PATCHES (nothing is
+ * launched); DNNMG_ECUDA if the address lookup or a launch fails. */
+dnnmg_status dnnmg_residual_noalloc(int64_t n_patches, int64_t n_fine_nodes, const int32_t* cells_dev,
+                                    const float* xyz_dev, const int32_t* node_ptr_dev,
+                                    const int32_t* node_idx_dev, const uint8_t* fine_dirichlet_dev,
+                                    double nu, double dt, double theta, const float* x_coarse_dev,
+                                    const float* F_dev, float* r_dev, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

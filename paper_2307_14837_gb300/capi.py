@@ -72,6 +72,8 @@ _SIGS = {
     "dnnmg_get_buffer": ([_VP, ctypes.c_int32, ctypes.POINTER(_VP)], ctypes.c_int),
     "dnnmg_sync": ([_VP, ctypes.c_int64], ctypes.c_int),
     "dnnmg_launch_count": ([_VP], ctypes.c_int64),
+    "dnnmg_residual_noalloc": ([ctypes.c_int64, ctypes.c_int64, _VP, _VP, _VP, _VP, _VP, ctypes.c_double,
+                                ctypes.c_double, ctypes.c_double, _VP, _VP, _VP, _VP], ctypes.c_int),
 }
 
 _lib = None
@@ -218,3 +220,15 @@ def dnnmg_sync(ctx, timeout_us=-1):
 
 def dnnmg_launch_count(ctx) -> int:
     return int(load().dnnmg_launch_count(ctx))
+
+
+NOALLOC_MAX_PATCHES = 16384
+
+
+def dnnmg_residual_noalloc(n_patches, n_fine_nodes, cells, xyz, node_ptr, node_idx, fine_dirichlet,
+                           nu, dt, theta, x_coarse, F, r, stream=None):
+    """The residual without allocation (FP32): every array from the caller."""
+    s = getattr(stream, "cuda_stream", stream)
+    _check(None, load().dnnmg_residual_noalloc(int(n_patches), int(n_fine_nodes), _ptr(cells), _ptr(xyz),
+                                               _ptr(node_ptr), _ptr(node_idx), _ptr(fine_dirichlet), float(nu),
+                                               float(dt), float(theta), _ptr(x_coarse), _ptr(F), _ptr(r), s))

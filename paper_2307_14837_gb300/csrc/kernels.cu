@@ -13,6 +13,7 @@
 // Every reduction is a gather over a CSR list sorted by patch index, so the
 // results are bitwise reproducible run to run (no floating-point atomics).
 #include <cstdio>
+#include <mutex>
 
 #include "internal.h"
 
@@ -713,3 +714,59 @@ template cudaError_t launch_layer_simt<__nv_bfloat16, __nv_bfloat16, float, floa
     const __nv_bfloat16*, int64_t, int64_t, int, int, bool, cudaStream_t);
 
 }  // namespace dnnmg
+
+// ---- residual without allocation -----------------------------------------------
+// Callers that may not allocate device memory (a host application that owns
+// every device allocation through its own pool, or code that must not call
+// cudaMalloc once set-up is over) still need the fine residual.  This entry
+// point takes every array from the caller and keeps the per-patch partial
+// sums in a fixed array in the library's device image instead of a context
+// buffer.
+static __device__ __align__(256) float g_noalloc_partial[DNNMG_NOALLOC_MAX_PATCHES * 27 * 4];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+float* g_noalloc_addr[kMaxDevices] = {};
+
+// Device address of g_noalloc_partial on the current device (looked up once
+// per device; the host-side name is not a device address).
+cudaError_t noalloc_scratch(float** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_partial);
+        if (e != cudaSuccess) return e;
+        g_noalloc_addr[dev] = static_cast<float*>(p);
+    }
+    *out = g_noalloc_addr[dev];
+    return cudaSuccess;
+}
+}  // namespace
+
+extern "C" dnnmg_status dnnmg_residual_noalloc(int64_t n_patches, int64_t n_fine_nodes, const int32_t* cells_dev,
+                                               const float* xyz_dev, const int32_t* node_ptr_dev,
+                                               const int32_t* node_idx_dev, const uint8_t* fine_dirichlet_dev,
+                                               double nu, double dt, double theta, const float* x_coarse_dev,
+                                               const float* F_dev, float* r_dev, void* cuda_stream) {
+    using namespace dnnmg;
+    if (!cells_dev || !xyz_dev || !node_ptr_dev || !node_idx_dev || !fine_dirichlet_dev || !x_coarse_dev ||
+        !F_dev || !r_dev || n_patches <= 0 || n_fine_nodes <= 0 || !(dt > 0.0) || !(nu >= 0.0) ||
+        !(theta >= 0.0 && theta <= 1.0))
+        return DNNMG_EINVAL;
+    if (n_patches > DNNMG_NOALLOC_MAX_PATCHES) return DNNMG_EINVAL;   // beyond the fixed scratch
+    float* partial = nullptr;
+    if (noalloc_scratch(&partial) != cudaSuccess) return DNNMG_ECUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    patch_operator_kernel<float, MODE_RESIDUAL><<<blocks_for(n_patches, kPatchesPerBlock), 64, 0, s>>>(
+        n_patches, cells_dev, nullptr, xyz_dev, x_coarse_dev, nullptr, float(1.0 / dt), float(theta), float(nu),
+        partial, nullptr);
+    if (cudaGetLastError() != cudaSuccess) return DNNMG_ECUDA;
+    node_reduce_kernel<float, MODE_RESIDUAL><<<blocks_for(n_fine_nodes, 256), 256, 0, s>>>(
+        n_fine_nodes, node_ptr_dev, node_idx_dev, partial, fine_dirichlet_dev, F_dev, r_dev);
+    return cudaGetLastError() == cudaSuccess ? DNNMG_OK : DNNMG_ECUDA;
+}
