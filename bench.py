@@ -44,6 +44,22 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
+def network_traffic(n_patches):
+    """DRAM bytes of one network stage from the committed ncu record
+    (profiles/network_traffic.json: dram read + write of the 5 layer launches
+    on a smaller channel case, per patch), scaled to n_patches; None when the
+    GEMM source has changed since the counters were taken."""
+    import hashlib
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "network_traffic.json")))
+        src = open(os.path.join(ROOT, rec["source_file"]), "rb").read()
+    except (OSError, KeyError, ValueError):
+        return None
+    if hashlib.sha256(src).hexdigest()[:16] != rec.get("source_sha256_16"):
+        return None
+    return rec["bytes_per_patch"] * n_patches
+
+
 def network_flops_per_patch(widths=WIDTHS):
     return sum(2 * widths[i] * widths[i + 1] for i in range(len(widths) - 1))
 
@@ -327,7 +343,8 @@ def main():
         "patches_per_s": value * nc,
         "roofline": {"bound": "tensor", "kernel": "network layers (BF16 GEMM chain)",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "peak_source": f"{peak_src} bf16 sustained", "traffic": None,
+                     "peak_source": f"{peak_src} bf16 sustained", "traffic": network_traffic(nc),
+                     "traffic_unit": "bytes per network stage (ncu dram read+write, scaled from nz=25)",
                      "network_ms_per_step": net_ms, "network_share": net_ms / ms},
         "e2e": {"value": world * K / res["e2e_s"] if res["e2e_s"] > 0 else None, "unit": UNIT,
                 "h2d_bytes_per_step": (nv + nf) * 16, "d2h_bytes_per_step": (nf + nv) * 16},
