@@ -44,6 +44,23 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
+def max_over_ranks(x, world, device):
+    """Largest value of x over the ranks of the default process group (the
+    slowest replica bounds the whole job)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(steps, elapsed_ms, world):
+    """Steps per second of the whole job: every replica runs `steps` steps in
+    at most elapsed_ms (weak scaling, one simulation per rank)."""
+    return world * steps / (elapsed_ms / 1000.0)
+
+
 def network_traffic(n_patches):
     """DRAM bytes of one network stage from the committed ncu record
     (profiles/network_traffic.json: dram read + write of the 5 layer launches
@@ -313,18 +330,13 @@ def main():
     if world > 1:
         torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     res = run_ours(args, rank, world, local_rank)
-    # max over ranks of the timed region
-    el = res["elapsed_ms"]
-    if world > 1:
-        t = torch.tensor([el], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        el = float(t.item())
+    el = max_over_ranks(res["elapsed_ms"], world, "cuda")
     if rank != 0:
         torch.distributed.destroy_process_group()
         return
     K = args.steps
     ms = el / K
-    value = world * K / (el / 1000.0)
+    value = whole_job_rate(K, el, world)
     nc, nf, nv = res["nc"], res["nf"], res["nv"]
     peaks, peak_src = _peaks()
     net_ms = statistics.mean(res["net_ms"])
