@@ -238,6 +238,84 @@ dnnmg_status dnnmg_sync(dnnmg_ctx* ctx, int64_t timeout_us);
 /* Number of kernel launches this context has issued (for accounting). */
 int64_t dnnmg_launch_count(const dnnmg_ctx* ctx);
 
+/* ---- Newton solve on a level and the DNN-MG time loop (Sec. 3.4, Alg. 1) ----
+ *
+ * Levels: DNNMG_LEVEL_COARSE is level L (the context's mesh), solved with the
+ * two-level local projection when its cells come in consecutive groups of 8
+ * children of a parent (else without it); DNNMG_LEVEL_FINE is level L+1 (the
+ * patches are its groups), used as the fine-mesh reference.  Level fields are
+ * double [n_nodes][4] (u, v, w, p) device arrays in every precision form.
+ *
+ * The solver (FP64): Newton with the exact Jacobian of A_h (stabilisation
+ * parameters frozen, Sec. 3.4), re-assembled when the residual rate exceeds
+ * rho_max; restarted GMRES, right-preconditioned by additive group-Vanka (the
+ * 108 x 108 local problems of the 27-node groups, LU-factorised).  The paper
+ * uses GMRES with geometric multigrid and a Vanka smoother and allows any
+ * coarse solver (Sec. 3). */
+enum { DNNMG_LEVEL_COARSE = 0, DNNMG_LEVEL_FINE = 1 };
+
+typedef struct {
+    double alpha0, delta0;   /* local projection parameters of Eq. (8): 0.02, 0.1 */
+    double newton_atol;      /* stop when |b - A(x)|_2 <= atol ... */
+    double newton_rtol;      /* ... or <= rtol |b - A(x0)|_2 */
+    int32_t newton_max;
+    int32_t gmres_restart;   /* Krylov dimension per cycle (fixed at first use of a level) */
+    int32_t gmres_max;       /* GMRES iterations per Newton step */
+    int32_t reserved;        /* must be 0 */
+    double gmres_rtol;
+    double rho_max;          /* Jacobian re-assembly threshold, 0.1 or 0.05 in the paper */
+} dnnmg_solver_params;
+
+typedef struct {
+    int32_t newton_iterations, gmres_iterations, jacobian_assemblies, converged;
+    double residual0, residual;   /* l2 norms of b - A(x) at the start and the end */
+} dnnmg_solve_stats;
+
+/* Defaults: alpha0 0.02, delta0 0.1, atol 1e-11, rtol 1e-12, 25 Newton steps,
+ * restart 40, 400 GMRES iterations, gmres_rtol 1e-10, rho_max 0.1. */
+void dnnmg_solver_defaults(dnnmg_solver_params* p);
+
+/* Number of nodes of a level and whether it uses the local projection. */
+dnnmg_status dnnmg_level_info(dnnmg_ctx* ctx, int32_t level, int64_t* n_nodes, int32_t* grouped);
+
+/* A_h(x) of Eqs. (6), (9) on a level (no row modified).  x_dev, Ax_dev
+ * double [n][4].  prm may be NULL (defaults). */
+dnnmg_status dnnmg_level_operator(dnnmg_ctx* ctx, int32_t level, const dnnmg_solver_params* prm,
+                                  const double* x_dev, double* Ax_dev);
+
+/* Right-hand side of Eq. (6) on a level from the previous state x_old (no
+ * force); Dirichlet velocity rows and pressure rows are 0. */
+dnnmg_status dnnmg_level_rhs(dnnmg_ctx* ctx, int32_t level, const double* x_old_dev, double* b_dev);
+
+/* The assembled Newton matrix at x as a dense row-major host array
+ * [4n][4n] (rows of Dirichlet unknowns and of a pinned pressure are identity
+ * rows).  For small levels: EINVAL if 4n > 8192 or bytes too small. */
+dnnmg_status dnnmg_level_jacobian(dnnmg_ctx* ctx, int32_t level, const dnnmg_solver_params* prm,
+                                  const double* x_dev, double* dense_host, size_t bytes);
+
+/* Solve A_h(x) = b on a level by Newton's method.  x_dev holds the initial
+ * guess and the Dirichlet values on entry, the solution on return.  Where no
+ * boundary is do-nothing the pressure is normalised to zero mean.
+ * Synchronises.  Returns ENOCONV (stats filled, x the last iterate) when the
+ * Newton tolerance is not reached, ENAN on a non-finite residual. */
+dnnmg_status dnnmg_solve(dnnmg_ctx* ctx, int32_t level, const dnnmg_solver_params* prm, const double* b_dev,
+                         double* x_dev, dnnmg_solve_stats* stats);
+
+/* n_steps DNN-MG time steps (Alg. 1): solve the coarse system with b_coarse,
+ * then the patch correction with F (the previous fine rhs), which leaves the
+ * next fine rhs in F and the next coarse rhs in b_coarse.
+ *   x_coarse_dev double [n_coarse][4] (Dirichlet values set by the caller),
+ *   b_coarse_dev double [n_coarse][4],
+ *   F_dev        [n_fine][4] in the context's field type.
+ * Requires dnnmg_set_network.  stats (may be NULL) are the last coarse solve's. */
+dnnmg_status dnnmg_time_step(dnnmg_ctx* ctx, int32_t n_steps, const dnnmg_solver_params* prm,
+                             double* x_coarse_dev, double* b_coarse_dev, void* F_dev, dnnmg_solve_stats* stats);
+
+/* n_steps of the plain scheme on one level (no network): b = Rhs(x_old),
+ * solve A(x) = b.  x_dev double [n][4]. */
+dnnmg_status dnnmg_plain_step(dnnmg_ctx* ctx, int32_t level, int32_t n_steps, const dnnmg_solver_params* prm,
+                              double* x_dev, dnnmg_solve_stats* stats);
+
 /* Largest mesh dnnmg_residual_noalloc accepts (coarse cells = patches). */
 #define DNNMG_NOALLOC_MAX_PATCHES 16384
 

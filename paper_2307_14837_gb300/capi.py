@@ -232,3 +232,99 @@ def dnnmg_residual_noalloc(n_patches, n_fine_nodes, cells, xyz, node_ptr, node_i
     _check(None, load().dnnmg_residual_noalloc(int(n_patches), int(n_fine_nodes), _ptr(cells), _ptr(xyz),
                                                _ptr(node_ptr), _ptr(node_idx), _ptr(fine_dirichlet), float(nu),
                                                float(dt), float(theta), _ptr(x_coarse), _ptr(F), _ptr(r), s))
+
+
+# -- Newton solver and time loop -------------------------------------------------
+
+LEVEL_COARSE, LEVEL_FINE = 0, 1
+
+
+class SolverParams(ctypes.Structure):
+    _fields_ = [("alpha0", ctypes.c_double), ("delta0", ctypes.c_double), ("newton_atol", ctypes.c_double),
+                ("newton_rtol", ctypes.c_double), ("newton_max", ctypes.c_int32), ("gmres_restart", ctypes.c_int32),
+                ("gmres_max", ctypes.c_int32), ("reserved", ctypes.c_int32), ("gmres_rtol", ctypes.c_double),
+                ("rho_max", ctypes.c_double)]
+
+
+class SolveStats(ctypes.Structure):
+    _fields_ = [("newton_iterations", ctypes.c_int32), ("gmres_iterations", ctypes.c_int32),
+                ("jacobian_assemblies", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("residual0", ctypes.c_double), ("residual", ctypes.c_double)]
+
+
+_SIGS.update({
+    "dnnmg_solver_defaults": ([ctypes.POINTER(SolverParams)], None),
+    "dnnmg_level_info": ([_VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)],
+                         ctypes.c_int),
+    "dnnmg_level_operator": ([_VP, ctypes.c_int32, ctypes.POINTER(SolverParams), _VP, _VP], ctypes.c_int),
+    "dnnmg_level_rhs": ([_VP, ctypes.c_int32, _VP, _VP], ctypes.c_int),
+    "dnnmg_level_jacobian": ([_VP, ctypes.c_int32, ctypes.POINTER(SolverParams), _VP, _VP, ctypes.c_size_t],
+                             ctypes.c_int),
+    "dnnmg_solve": ([_VP, ctypes.c_int32, ctypes.POINTER(SolverParams), _VP, _VP, ctypes.POINTER(SolveStats)],
+                    ctypes.c_int),
+    "dnnmg_time_step": ([_VP, ctypes.c_int32, ctypes.POINTER(SolverParams), _VP, _VP, _VP,
+                         ctypes.POINTER(SolveStats)], ctypes.c_int),
+    "dnnmg_plain_step": ([_VP, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(SolverParams), _VP,
+                          ctypes.POINTER(SolveStats)], ctypes.c_int),
+})
+ENOCONV = -4
+
+
+def dnnmg_solver_defaults(**overrides) -> SolverParams:
+    p = SolverParams()
+    load().dnnmg_solver_defaults(ctypes.byref(p))
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+def _stats(s):
+    return {k: getattr(s, k) for k, _ in SolveStats._fields_}
+
+
+def dnnmg_level_info(ctx, level):
+    n, g = ctypes.c_int64(), ctypes.c_int32()
+    _check(ctx, load().dnnmg_level_info(ctx, int(level), ctypes.byref(n), ctypes.byref(g)))
+    return n.value, bool(g.value)
+
+
+def dnnmg_level_operator(ctx, level, x, Ax, prm=None):
+    _check(ctx, load().dnnmg_level_operator(ctx, int(level), ctypes.byref(prm) if prm else None, _ptr(x), _ptr(Ax)))
+
+
+def dnnmg_level_rhs(ctx, level, x_old, b):
+    _check(ctx, load().dnnmg_level_rhs(ctx, int(level), _ptr(x_old), _ptr(b)))
+
+
+def dnnmg_level_jacobian(ctx, level, x, prm=None):
+    n, _ = dnnmg_level_info(ctx, level)
+    out = np.empty((4 * n, 4 * n))
+    _check(ctx, load().dnnmg_level_jacobian(ctx, int(level), ctypes.byref(prm) if prm else None, _ptr(x),
+                                            out.ctypes.data, out.nbytes))
+    return out
+
+
+def _solve_status(ctx, status):
+    if status != ENOCONV:
+        _check(ctx, status)
+
+
+def dnnmg_solve(ctx, level, b, x, prm=None):
+    st = SolveStats()
+    _solve_status(ctx, load().dnnmg_solve(ctx, int(level), ctypes.byref(prm) if prm else None, _ptr(b), _ptr(x),
+                                          ctypes.byref(st)))
+    return _stats(st)
+
+
+def dnnmg_time_step(ctx, n_steps, x_coarse, b_coarse, F, prm=None):
+    st = SolveStats()
+    _check(ctx, load().dnnmg_time_step(ctx, int(n_steps), ctypes.byref(prm) if prm else None, _ptr(x_coarse),
+                                       _ptr(b_coarse), _ptr(F), ctypes.byref(st)))
+    return _stats(st)
+
+
+def dnnmg_plain_step(ctx, level, n_steps, x, prm=None):
+    st = SolveStats()
+    _check(ctx, load().dnnmg_plain_step(ctx, int(level), int(n_steps), ctypes.byref(prm) if prm else None, _ptr(x),
+                                        ctypes.byref(st)))
+    return _stats(st)

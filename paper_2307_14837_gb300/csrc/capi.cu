@@ -1,5 +1,6 @@
 // extern "C" entry points of libdnnmg (declared in include/dnnmg.h).
 #include <chrono>
+#include <cmath>
 #include <cstring>
 #include <new>
 #include <thread>
@@ -77,6 +78,10 @@ void dnnmg_destroy(dnnmg_ctx* ctx) {
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
     for (void* p : ctx->allocations) cudaFree(p);
+    for (auto*& L : ctx->level) {
+        destroy_level(L);
+        L = nullptr;
+    }
     cudaSetDevice(cur);
     delete ctx;
 }
@@ -466,6 +471,166 @@ dnnmg_status dnnmg_sync(dnnmg_ctx* ctx, int64_t timeout_us) {
         }
         std::this_thread::sleep_for(std::chrono::microseconds(20));
     }
+}
+
+
+// ---- Newton solver and time loop -------------------------------------------------
+
+void dnnmg_solver_defaults(dnnmg_solver_params* p) {
+    if (!p) return;
+    p->alpha0 = 0.02;
+    p->delta0 = 0.1;
+    p->newton_atol = 1e-11;
+    p->newton_rtol = 1e-12;
+    p->newton_max = 25;
+    p->gmres_restart = 40;
+    p->gmres_max = 400;
+    p->reserved = 0;
+    p->gmres_rtol = 1e-10;
+    p->rho_max = 0.1;
+}
+
+}  // extern "C"
+
+namespace {
+
+dnnmg_status get_level(dnnmg_ctx* ctx, int32_t level, const dnnmg_solver_params* prm, DeviceLevel** out) {
+    if (level != DNNMG_LEVEL_COARSE && level != DNNMG_LEVEL_FINE) return DNNMG_EINVAL;
+    if (!ctx->level[level]) {
+        const int krylov = prm && prm->gmres_restart > 0 ? prm->gmres_restart : 40;
+        if (krylov > 200) return fail(ctx, DNNMG_EINVAL, "gmres_restart > 200");
+        cudaError_t e = create_level(ctx->host, level == DNNMG_LEVEL_FINE, krylov, &ctx->level[level]);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "create_level");
+    }
+    *out = ctx->level[level];
+    return DNNMG_OK;
+}
+
+__global__ void to_float_kernel(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = float(a[i]);
+}
+__global__ void to_double_kernel(int64_t n, const float* __restrict__ a, double* __restrict__ b) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = double(a[i]);
+}
+
+}  // namespace
+
+extern "C" {
+
+dnnmg_status dnnmg_level_info(dnnmg_ctx* ctx, int32_t level, int64_t* n_nodes, int32_t* grouped) {
+    if (!ctx) return DNNMG_EINVAL;
+    DeviceLevel* L;
+    dnnmg_status st = get_level(ctx, level, nullptr, &L);
+    if (st != DNNMG_OK) return st;
+    if (n_nodes) *n_nodes = level_nodes(L);
+    if (grouped) *grouped = level_lps(L) ? 1 : 0;
+    return DNNMG_OK;
+}
+
+dnnmg_status dnnmg_level_operator(dnnmg_ctx* ctx, int32_t level, const dnnmg_solver_params* prm, const double* x_dev,
+                                  double* Ax_dev) {
+    if (!ctx || !x_dev || !Ax_dev) return DNNMG_EINVAL;
+    dnnmg_solver_params d;
+    dnnmg_solver_defaults(&d);
+    DeviceLevel* L;
+    dnnmg_status st = get_level(ctx, level, prm, &L);
+    if (st != DNNMG_OK) return st;
+    CK(ctx, level_operator(L, ctx->op, prm ? prm : &d, x_dev, Ax_dev, ctx->stream));
+    ctx->launches += 2;
+    return DNNMG_OK;
+}
+
+dnnmg_status dnnmg_level_rhs(dnnmg_ctx* ctx, int32_t level, const double* x_old_dev, double* b_dev) {
+    if (!ctx || !x_old_dev || !b_dev) return DNNMG_EINVAL;
+    DeviceLevel* L;
+    dnnmg_status st = get_level(ctx, level, nullptr, &L);
+    if (st != DNNMG_OK) return st;
+    CK(ctx, level_rhs(L, ctx->op, x_old_dev, b_dev, ctx->stream));
+    ctx->launches += 3;
+    return DNNMG_OK;
+}
+
+dnnmg_status dnnmg_level_jacobian(dnnmg_ctx* ctx, int32_t level, const dnnmg_solver_params* prm, const double* x_dev,
+                                  double* dense_host, size_t bytes) {
+    if (!ctx || !x_dev || !dense_host) return DNNMG_EINVAL;
+    dnnmg_solver_params d;
+    dnnmg_solver_defaults(&d);
+    DeviceLevel* L;
+    dnnmg_status st = get_level(ctx, level, prm, &L);
+    if (st != DNNMG_OK) return st;
+    const int64_t N = 4 * level_nodes(L);
+    if (N > 8192 || bytes < size_t(N) * size_t(N) * 8) return fail(ctx, DNNMG_EINVAL, "level too large for a dense Jacobian");
+    CK(ctx, level_jacobian(L, ctx->op, prm ? prm : &d, x_dev, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    CK(ctx, level_dense_jacobian(L, dense_host));
+    return DNNMG_OK;
+}
+
+dnnmg_status dnnmg_solve(dnnmg_ctx* ctx, int32_t level, const dnnmg_solver_params* prm, const double* b_dev,
+                         double* x_dev, dnnmg_solve_stats* stats) {
+    if (!ctx || !b_dev || !x_dev) return DNNMG_EINVAL;
+    dnnmg_solver_params d;
+    dnnmg_solver_defaults(&d);
+    if (!prm) prm = &d;
+    if (prm->reserved != 0 || prm->newton_max < 0 || prm->gmres_max < 1) return DNNMG_EINVAL;
+    DeviceLevel* L;
+    dnnmg_status st = get_level(ctx, level, prm, &L);
+    if (st != DNNMG_OK) return st;
+    dnnmg_solve_stats s{};
+    cudaError_t e = level_solve(L, ctx->op, prm, b_dev, x_dev, ctx->stream, &s);
+    if (stats) *stats = s;
+    if (e == cudaErrorUnknown && !std::isfinite(s.residual)) return fail(ctx, DNNMG_ENAN, "non-finite residual");
+    CK(ctx, e);
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return s.converged ? DNNMG_OK : fail(ctx, DNNMG_ENOCONV, "Newton tolerance not reached");
+}
+
+dnnmg_status dnnmg_time_step(dnnmg_ctx* ctx, int32_t n_steps, const dnnmg_solver_params* prm, double* x_coarse_dev,
+                             double* b_coarse_dev, void* F_dev, dnnmg_solve_stats* stats) {
+    if (!ctx || !x_coarse_dev || !b_coarse_dev || !F_dev || n_steps < 0) return DNNMG_EINVAL;
+    if (!ctx->has_net) return fail(ctx, DNNMG_ESTATE, "dnnmg_time_step before dnnmg_set_network");
+    const int64_t nv = ctx->host.nv;
+    dnnmg_status st;
+    if (!is_fp64(ctx) && !ctx->xc_field) {
+        if ((st = alloc(ctx, size_t(nv) * 4 * 4, &ctx->xc_field)) != DNNMG_OK) return st;
+        if ((st = alloc(ctx, size_t(nv) * 4 * 4, &ctx->bc_field)) != DNNMG_OK) return st;
+    }
+    for (int32_t k = 0; k < n_steps; ++k) {
+        st = dnnmg_solve(ctx, DNNMG_LEVEL_COARSE, prm, b_coarse_dev, x_coarse_dev, stats);
+        if (st != DNNMG_OK && st != DNNMG_ENOCONV) return st;
+        if (is_fp64(ctx)) {
+            if ((st = dnnmg_patch_step(ctx, x_coarse_dev, F_dev, F_dev, b_coarse_dev)) != DNNMG_OK) return st;
+        } else {
+            const unsigned blocks = unsigned((4 * nv + 255) / 256);
+            to_float_kernel<<<blocks, 256, 0, ctx->stream>>>(4 * nv, x_coarse_dev, (float*)ctx->xc_field);
+            CK(ctx, cudaGetLastError());
+            if ((st = dnnmg_patch_step(ctx, ctx->xc_field, F_dev, F_dev, ctx->bc_field)) != DNNMG_OK) return st;
+            to_double_kernel<<<blocks, 256, 0, ctx->stream>>>(4 * nv, (const float*)ctx->bc_field, b_coarse_dev);
+            CK(ctx, cudaGetLastError());
+            ctx->launches += 2;
+        }
+    }
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return DNNMG_OK;
+}
+
+dnnmg_status dnnmg_plain_step(dnnmg_ctx* ctx, int32_t level, int32_t n_steps, const dnnmg_solver_params* prm,
+                              double* x_dev, dnnmg_solve_stats* stats) {
+    if (!ctx || !x_dev || n_steps < 0) return DNNMG_EINVAL;
+    DeviceLevel* L;
+    dnnmg_status st = get_level(ctx, level, prm, &L);
+    if (st != DNNMG_OK) return st;
+    void* b = nullptr;
+    if ((st = alloc(ctx, size_t(level_nodes(L)) * 4 * 8, &b)) != DNNMG_OK) return st;
+    for (int32_t k = 0; k < n_steps; ++k) {
+        if ((st = dnnmg_level_rhs(ctx, level, x_dev, (double*)b)) != DNNMG_OK) return st;
+        st = dnnmg_solve(ctx, level, prm, (const double*)b, x_dev, stats);
+        if (st != DNNMG_OK && st != DNNMG_ENOCONV) return st;
+    }
+    // the scratch rhs is released with the context
+    return DNNMG_OK;
 }
 
 }  // extern "C"

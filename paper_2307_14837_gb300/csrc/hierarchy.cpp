@@ -291,3 +291,119 @@ dnnmg_status build_hierarchy(const dnnmg_mesh_desc* mesh, HostHierarchy* h, std:
 }
 
 }  // namespace dnnmg
+
+namespace dnnmg {
+
+void build_level(const HostHierarchy& h, bool fine, HostLevel* lv) {
+    if (fine) {
+        lv->n = h.n_fine;
+        lv->ng = h.nc;
+        lv->npg = 27;
+        lv->lps = true;
+        lv->groups = h.patch_map;
+        lv->xyz = h.xyz_f;
+        lv->dir.resize(size_t(h.n_fine));
+        bool outflow = false;
+        for (int64_t j = 0; j < h.n_fine; ++j) {
+            lv->dir[j] = (h.kind_f[j] == 1 || h.kind_f[j] == 2) ? 1 : 0;
+            outflow |= h.kind_f[j] == 3;
+        }
+        lv->mean_zero_pressure = !outflow;
+    } else {
+        lv->n = h.nv;
+        lv->xyz = h.xyz_c;
+        lv->dir.resize(size_t(h.nv));
+        bool outflow = false;
+        for (int64_t v = 0; v < h.nv; ++v) {
+            lv->dir[v] = (h.bc_c[v] == 1 || h.bc_c[v] == 2) ? 1 : 0;
+            outflow |= h.bc_c[v] == 3;
+        }
+        lv->mean_zero_pressure = !outflow;
+        // cells in consecutive groups of 8 children (i + 2j + 4k) of a parent?
+        bool grouped = h.nc % 8 == 0;
+        std::vector<int32_t> g27;
+        if (grouped) {
+            const int64_t ng = h.nc / 8;
+            g27.assign(size_t(27 * ng), -1);
+            for (int64_t g = 0; g < ng && grouped; ++g)
+                for (int t = 0; t < 8 && grouped; ++t)
+                    for (int k = 0; k < 8; ++k) {
+                        const int a = (t & 1) + (k & 1), b = ((t >> 1) & 1) + ((k >> 1) & 1),
+                                  c = ((t >> 2) & 1) + ((k >> 2) & 1);
+                        int32_t& slot = g27[size_t(27 * g + a + 3 * b + 9 * c)];
+                        const int32_t v = h.cells[size_t(8 * (8 * g + t) + k)];
+                        if (slot < 0)
+                            slot = v;
+                        else if (slot != v) {
+                            grouped = false;
+                            break;
+                        }
+                    }
+        }
+        if (grouped) {
+            lv->ng = h.nc / 8;
+            lv->npg = 27;
+            lv->lps = true;
+            lv->groups = g27;
+        } else {
+            lv->ng = h.nc;
+            lv->npg = 8;
+            lv->lps = false;
+            lv->groups = h.cells;
+        }
+    }
+    const int npg = lv->npg;
+    const int64_t n = lv->n, ng = lv->ng;
+    lv->pin = -1;
+    if (lv->mean_zero_pressure)
+        for (int64_t j = 0; j < n; ++j)
+            if (!lv->dir[j]) {
+                lv->pin = int32_t(j);
+                break;
+            }
+    // node -> (group, local) in group order
+    lv->node_ptr.assign(size_t(n + 1), 0);
+    for (int64_t e = 0; e < ng * npg; ++e) lv->node_ptr[lv->groups[e] + 1]++;
+    for (int64_t j = 0; j < n; ++j) lv->node_ptr[j + 1] += lv->node_ptr[j];
+    lv->node_idx.assign(size_t(ng * npg), 0);
+    {
+        std::vector<int32_t> fill(lv->node_ptr.begin(), lv->node_ptr.end() - 1);
+        for (int64_t e = 0; e < ng * npg; ++e) lv->node_idx[fill[lv->groups[e]]++] = int32_t(e);
+    }
+    // block sparsity: nodes i, j coupled when they share a group
+    std::vector<std::vector<int32_t>> cols(static_cast<size_t>(n));
+    for (int64_t g = 0; g < ng; ++g)
+        for (int i = 0; i < npg; ++i)
+            for (int j = 0; j < npg; ++j) cols[lv->groups[g * npg + i]].push_back(lv->groups[g * npg + j]);
+    lv->row_ptr.assign(size_t(n + 1), 0);
+    lv->col_idx.clear();
+    for (int64_t i = 0; i < n; ++i) {
+        auto& c = cols[i];
+        std::sort(c.begin(), c.end());
+        c.erase(std::unique(c.begin(), c.end()), c.end());
+        lv->col_idx.insert(lv->col_idx.end(), c.begin(), c.end());
+        lv->row_ptr[i + 1] = int32_t(lv->col_idx.size());
+        std::vector<int32_t>().swap(c);
+    }
+    const int64_t nnzb = int64_t(lv->col_idx.size());
+    auto block_of = [&](int32_t i, int32_t j) {
+        const int32_t* b = lv->col_idx.data() + lv->row_ptr[i];
+        const int32_t* e = lv->col_idx.data() + lv->row_ptr[i + 1];
+        return int32_t(std::lower_bound(b, e, j) - lv->col_idx.data());
+    };
+    lv->grp_blk.assign(size_t(ng * npg * npg), 0);
+    std::vector<int32_t> cnt(size_t(nnzb + 1), 0);
+    for (int64_t g = 0; g < ng; ++g)
+        for (int i = 0; i < npg; ++i)
+            for (int j = 0; j < npg; ++j) {
+                const int32_t b = block_of(lv->groups[g * npg + i], lv->groups[g * npg + j]);
+                lv->grp_blk[size_t((g * npg + i) * npg + j)] = b;
+                cnt[b + 1]++;
+            }
+    for (int64_t b = 0; b < nnzb; ++b) cnt[b + 1] += cnt[b];
+    lv->blk_ptr = cnt;
+    lv->blk_src.assign(size_t(ng * npg * npg), 0);
+    for (int64_t e = 0; e < ng * npg * npg; ++e) lv->blk_src[cnt[lv->grp_blk[e]]++] = int32_t(e);
+}
+
+}  // namespace dnnmg

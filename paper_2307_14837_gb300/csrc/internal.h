@@ -34,6 +34,48 @@ struct HostHierarchy {
 
 dnnmg_status build_hierarchy(const dnnmg_mesh_desc* mesh, HostHierarchy* h, std::string* err);
 
+// One mesh level for the Newton solve: cells in groups of 8 children of a
+// parent (27 nodes per group), which is the structure the two-level local
+// projection needs.  Level L+1 is always grouped (the patches); level L is
+// grouped when its cells come in such groups (else it is solved as 1-cell
+// "groups" without the projection terms).
+struct HostLevel {
+    int64_t n = 0;                   // nodes
+    int64_t ng = 0;                  // groups
+    int npg = 27;                    // nodes per group (27, or 8 without grouping)
+    bool lps = true;
+    bool mean_zero_pressure = false; // no do-nothing boundary: pressure up to a constant
+    int32_t pin = -1;                // node whose pressure row is pinned (mean-zero case)
+    std::vector<int32_t> groups;     // [ng][npg]
+    std::vector<double> xyz;         // [n][3]
+    std::vector<uint8_t> dir;        // [n] Dirichlet velocity
+    std::vector<int32_t> node_ptr, node_idx;   // node -> g*npg + local, group order
+    std::vector<int32_t> row_ptr, col_idx;     // node-node block sparsity (BSR, 4x4 blocks)
+    std::vector<int32_t> blk_ptr, blk_src;     // block -> local entries g*npg*npg + i*npg + j
+    std::vector<int32_t> grp_blk;              // [ng][npg][npg] block index
+};
+
+// Level L from the coarse mesh (grouped if its cells come in consistent
+// groups of 8) or level L+1 from the hierarchy.
+void build_level(const HostHierarchy& h, bool fine, HostLevel* lv);
+
+struct OpParams;
+struct DeviceLevel;   // solver.cu
+cudaError_t create_level(const HostHierarchy& hh, bool fine, int krylov, DeviceLevel** out);
+void destroy_level(DeviceLevel* L);
+int64_t level_nodes(const DeviceLevel* L);
+bool level_lps(const DeviceLevel* L);
+cudaError_t level_operator(DeviceLevel* L, const OpParams& op, const dnnmg_solver_params* sp, const double* x,
+                           double* Ax, cudaStream_t s);
+cudaError_t level_residual(DeviceLevel* L, const OpParams& op, const dnnmg_solver_params* sp, const double* x,
+                           const double* b, double* r, cudaStream_t s);
+cudaError_t level_rhs(DeviceLevel* L, const OpParams& op, const double* x_old, double* b, cudaStream_t s);
+cudaError_t level_jacobian(DeviceLevel* L, const OpParams& op, const dnnmg_solver_params* sp, const double* x,
+                           cudaStream_t s);
+cudaError_t level_dense_jacobian(DeviceLevel* L, double* dense_host);
+cudaError_t level_solve(DeviceLevel* L, const OpParams& op, const dnnmg_solver_params* sp, const double* b, double* x,
+                        cudaStream_t s, dnnmg_solve_stats* st);
+
 // Device copy of the mesh data the kernels read.
 struct DeviceMesh {
     int64_t nv = 0, nc = 0, n_fine = 0;
@@ -119,6 +161,11 @@ struct dnnmg_ctx {
     void* act[2] = {nullptr, nullptr};  // [nc][max width] activations
     int64_t act_rows = 0;
     int act_ld = 0;
+
+    // Newton solver levels (0: L, 1: L+1), created on first use
+    dnnmg::DeviceLevel* level[2] = {nullptr, nullptr};
+    void* xc_field = nullptr;   // [nv][4] x^L in the field type (time stepping)
+    void* bc_field = nullptr;   // [nv][4] b^L in the field type
 };
 
 namespace dnnmg {
