@@ -96,7 +96,7 @@ class Clocks:
     def __enter__(self):
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "20"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except OSError:
             self.p = None
@@ -247,6 +247,53 @@ def run_ours(args, rank, world, local_rank):
     return res
 
 
+def equal_error(steps=5):
+    """Velocity error of the DNN-MG time loop in the BF16 form and in the plain
+    FP64 form against a fine-level reference (the plain scheme on level L+1),
+    on the cavity workload (8^3 -> 16^3, Re 100, backward Euler dt 0.01,
+    network 228-256-256-81 from seed 0 with the last layer scaled by 0.05 as a
+    stand-in for a trained network's small corrections).  Errors are l2 norms
+    over the fine nodes after `steps` steps (E_v of Sec. 6.5 at one time)."""
+    import numpy as np
+    import torch
+
+    from paper_2307_14837_gb300 import capi, inputs as I
+    from paper_2307_14837_gb300.path import PatchPath
+
+    m = I.cavity_mesh(8)
+    widths = (228, 256, 256, 81)
+    Ws, ss, ts = I.network_weights(widths, seed=0)
+    Ws[-1] = 0.05 * Ws[-1]
+    bcv = I.dirichlet_values(m, m["xyz"], m["vertex_bc"])
+    dirc = (m["vertex_bc"] == 1) | (m["vertex_bc"] == 2)
+    x0 = np.zeros((m.n_vertices, 4))
+    x0[dirc, 0:3] = bcv[dirc]
+    res, t0 = {}, time.perf_counter()
+    ref = None
+    for prec in ("fp64", "bf16"):
+        p = PatchPath(m, 0.01, 0.01, 1.0, prec)
+        p.set_network(widths, Ws, ss, ts)
+        x = torch.as_tensor(x0, device="cuda")
+        bf, bcf = p.rhs_restrict(x.to(p.dtype), torch.zeros((p.n_fine, 3), dtype=p.dtype, device="cuda"))
+        bc = bcf.double().contiguous()
+        capi.dnnmg_time_step(p.ctx, steps, x, bc, bf)
+        res[prec] = p.prolongate(x.to(p.dtype)).double().cpu().numpy()
+        if ref is None:
+            kind = p.mesh_data(capi.FINE_KIND)
+            dirf = (kind == 1) | (kind == 2)
+            xr = p.prolongate(torch.as_tensor(x0, device="cuda")).cpu().numpy()
+            xr[dirf, 0:3] = I.dirichlet_values(m, p.mesh_data(capi.FINE_XYZ), kind)[dirf]
+            xr = torch.as_tensor(xr, device="cuda")
+            capi.dnnmg_plain_step(p.ctx, capi.LEVEL_FINE, steps, xr)
+            ref = xr.cpu().numpy()
+        p.close()
+    e = {k: float(np.linalg.norm(v[:, 0:3] - ref[:, 0:3])) for k, v in res.items()}
+    return {"workload": "cavity 8^3->16^3, Re 100, BE dt 0.01, 228-256-256-81 (last layer x0.05), "
+                        f"{steps} DNN-MG steps vs plain scheme on level L+1",
+            "e_v_fp64": e["fp64"], "e_v_bf16": e["bf16"],
+            "relative_difference": abs(e["bf16"] - e["fp64"]) / e["fp64"], "seconds": time.perf_counter() - t0}
+
+
 class OracleSample:
     """The FP64 oracle's patch step on a sample of the channel workload: the
     same channel family, time step and network at a smaller nz (nz = 10 has
@@ -364,6 +411,8 @@ def main():
         "clocks": res["clocks"],
         "fp64_plain": res["fp64"],
     }
+    if not args.no_fp64:
+        line["equal_error"] = equal_error()
     if not args.no_cpu_baseline:
         o = OracleSample(nz=10)
         secs, n = 0.0, 0
