@@ -208,6 +208,13 @@ dnnmg_status dnnmg_extend(dnnmg_ctx* ctx, const void* Y_dev, void* d_dev);
 dnnmg_status dnnmg_rhs_restrict(dnnmg_ctx* ctx, const void* x_coarse_dev, const void* d_dev,
                                 void* b_fine_dev, void* b_coarse_dev);
 
+/* Restriction R = P^T of a fine vector to level L (Alg. 1, restriction of
+ * the rhs): b_coarse = P^T b_fine with coarse Dirichlet velocity rows and
+ * the pressure row zero (velocity components of b_fine are used).
+ * b_fine_dev [n_fine_nodes][4], b_coarse_dev [n_coarse_vertices][4], field
+ * type.  Deterministic (gathers in patch order). */
+dnnmg_status dnnmg_restrict(dnnmg_ctx* ctx, const void* b_fine_dev, void* b_coarse_dev);
+
 /* The whole patch correction of one time step: prolongate, residual with
  * F_dev, local restriction, network, extension, rhs and restriction.  r, X,
  * Y and d live in context buffers (readable with dnnmg_get_buffer).
@@ -315,6 +322,48 @@ dnnmg_status dnnmg_time_step(dnnmg_ctx* ctx, int32_t n_steps, const dnnmg_solver
  * solve A(x) = b.  x_dev double [n][4]. */
 dnnmg_status dnnmg_plain_step(dnnmg_ctx* ctx, int32_t level, int32_t n_steps, const dnnmg_solver_params* prm,
                               double* x_dev, dnnmg_solve_stats* stats);
+
+/* ---- Training of the patch network (Sec. 4; loss and optimiser, Sec. 6.4) ----
+ *
+ * Training form of the network: hidden layer i computes relu(W_i h + b_i)
+ * (+ h where the skip applies), the last layer W_L h; the per-feature bias
+ * b_i stands for the normalisation of Sec. 4 (at inference it is the shift
+ * of dnnmg_set_network).  Weights and biases are caller-owned fp32 device
+ * arrays, W_i row-major [widths[i+1]][widths[i]], b_i [widths[i+1]].
+ * A trainer owns the saved activations of the last forward pass and the
+ * backward workspace for up to max_batch rows (a multiple of 64).
+ * Precision DNNMG_BF16: bf16 operands, fp32 accumulation (tensor cores);
+ * DNNMG_FP32: float throughout.  Input rows X as dnnmg_local_restrict writes
+ * them for a context of that precision: [batch][256], bf16 or float. */
+typedef struct dnnmg_trainer dnnmg_trainer;
+
+dnnmg_status dnnmg_trainer_create(const dnnmg_net_desc* net, int32_t precision, int64_t max_batch, void* cuda_stream,
+                                  dnnmg_trainer** out);
+void dnnmg_trainer_destroy(dnnmg_trainer* trainer);
+
+/* Y_dev [batch][81] fp32 = N(X) with the given weights; saves what the
+ * backward pass needs.  batch a multiple of 64, <= max_batch.  X_dev is
+ * read again by dnnmg_trainer_backward (first-layer weight gradient): it
+ * must stay valid and unchanged until then. */
+dnnmg_status dnnmg_trainer_forward(dnnmg_trainer* trainer, const void* X_dev, const float* const* W_dev,
+                                   const float* const* b_dev, float* Y_dev, int64_t batch);
+
+/* Gradients of sum(dY . Y) with respect to every W_i and b_i for the last
+ * forward pass (reverse-mode through the layers): dW_dev[i] and db_dev[i]
+ * are overwritten.  ESTATE without a forward pass. */
+dnnmg_status dnnmg_trainer_backward(dnnmg_trainer* trainer, const float* dY_dev, float* const* dW_dev,
+                                    float* const* db_dev);
+
+/* The l2 loss of Sec. 6.4 for one batch: loss = (1/batch) sum_P ||Y_P - T_P||^2
+ * (into loss_dev[0]) and dY = 2 (Y - T) / batch (dY_dev may be NULL);
+ * Y, T [batch][81] fp32. */
+dnnmg_status dnnmg_mse_loss(int64_t batch, const float* Y_dev, const float* T_dev, float* loss_dev, float* dY_dev,
+                            void* cuda_stream);
+
+/* One AdamW step (decoupled weight decay, bias-corrected moments, step >= 1)
+ * on n parameters w with gradient g and moments m, v (all fp32 device). */
+dnnmg_status dnnmg_adamw(int64_t n, float* w_dev, const float* g_dev, float* m_dev, float* v_dev, float lr,
+                         float beta1, float beta2, float eps, float weight_decay, int32_t step, void* cuda_stream);
 
 /* Largest mesh dnnmg_residual_noalloc accepts (coarse cells = patches). */
 #define DNNMG_NOALLOC_MAX_PATCHES 16384

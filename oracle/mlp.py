@@ -38,6 +38,45 @@ def forward(X, Ws, scales, shifts, skip=True, return_hidden=False):
     return (h, hidden) if return_hidden else h
 
 
+def loss_and_grads(X, Ws, bs, T, skip=True):
+    """Training loss of Sec. 6.4 for one batch and its gradients (float64).
+
+    The network is trained with the normalisation replaced by a per-feature
+    bias b_i on hidden layers (scale 1): f_i(h) = relu(W_i h + b_i) (+ h).
+    loss = (1 / B) sum_P ||Y_P - T_P||^2 (l2 over a patch's outputs, averaged
+    over the B patches of the batch).  Returns (loss, dWs, dbs) by reverse-mode
+    differentiation of that composition."""
+    h = np.asarray(X, dtype=np.float64)
+    B = h.shape[0]
+    L = len(Ws)
+    hs, zs, sk = [h], [], []
+    for i in range(L - 1):
+        z = h @ Ws[i].T + bs[i][None, :]
+        a = relu(z)
+        s = skip and i > 0 and a.shape[1] == h.shape[1]
+        h = a + h if s else a
+        zs.append(z)
+        sk.append(s)
+        hs.append(h)
+    Y = h @ Ws[L - 1].T
+    diff = Y - T
+    loss = float(np.sum(diff * diff) / B)
+    dWs = [None] * L
+    dbs = [None] * (L - 1)
+    dz = 2.0 * diff / B
+    dWs[L - 1] = dz.T @ hs[L - 1]
+    dh = dz @ Ws[L - 1]
+    for i in range(L - 2, -1, -1):
+        dzi = dh * (zs[i] > 0)
+        dWs[i] = dzi.T @ hs[i]
+        dbs[i] = dzi.sum(axis=0)
+        dprev = dzi @ Ws[i]
+        if sk[i]:
+            dprev = dprev + dh
+        dh = dprev
+    return loss, dWs, dbs
+
+
 def fold_batchnorm(gamma, beta, mu, s):
     """(scale, shift) equivalent to (z - mu) / s * gamma + beta."""
     scale = gamma / s

@@ -328,3 +328,56 @@ def dnnmg_plain_step(ctx, level, n_steps, x, prm=None):
     _check(ctx, load().dnnmg_plain_step(ctx, int(level), int(n_steps), ctypes.byref(prm) if prm else None, _ptr(x),
                                         ctypes.byref(st)))
     return _stats(st)
+
+
+_SIGS.update({
+    "dnnmg_restrict": ([_VP, _VP, _VP], ctypes.c_int),
+    "dnnmg_trainer_create": ([ctypes.POINTER(NetDesc), ctypes.c_int32, ctypes.c_int64, _VP, ctypes.POINTER(_VP)],
+                             ctypes.c_int),
+    "dnnmg_trainer_destroy": ([_VP], None),
+    "dnnmg_trainer_forward": ([_VP, _VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _VP, ctypes.c_int64], ctypes.c_int),
+    "dnnmg_trainer_backward": ([_VP, _VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP)], ctypes.c_int),
+    "dnnmg_mse_loss": ([ctypes.c_int64, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
+    "dnnmg_adamw": ([ctypes.c_int64, _VP, _VP, _VP, _VP, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                     ctypes.c_float, ctypes.c_float, ctypes.c_int32, _VP], ctypes.c_int),
+})
+
+
+def dnnmg_restrict(ctx, b_fine, b_coarse):
+    _check(ctx, load().dnnmg_restrict(ctx, _ptr(b_fine), _ptr(b_coarse)))
+
+
+def _ptr_array(ts):
+    return (_VP * len(ts))(*[_ptr(t) for t in ts]) if ts else None
+
+
+def dnnmg_trainer_create(widths, precision, max_batch, stream=None, skip=True):
+    w = np.ascontiguousarray(widths, dtype=np.int32)
+    desc = NetDesc(len(widths) - 1, w.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), 1 if skip else 0)
+    h = _VP()
+    s = getattr(stream, "cuda_stream", stream)
+    _check(None, load().dnnmg_trainer_create(ctypes.byref(desc), int(precision), int(max_batch), s, ctypes.byref(h)))
+    return h.value
+
+
+def dnnmg_trainer_destroy(tr):
+    load().dnnmg_trainer_destroy(tr)
+
+
+def dnnmg_trainer_forward(tr, X, Ws, bs, Y, batch):
+    _check(None, load().dnnmg_trainer_forward(tr, _ptr(X), _ptr_array(Ws), _ptr_array(bs), _ptr(Y), int(batch)))
+
+
+def dnnmg_trainer_backward(tr, dY, dWs, dbs):
+    _check(None, load().dnnmg_trainer_backward(tr, _ptr(dY), _ptr_array(dWs), _ptr_array(dbs)))
+
+
+def dnnmg_mse_loss(batch, Y, T, loss, dY=None, stream=None):
+    _check(None, load().dnnmg_mse_loss(int(batch), _ptr(Y), _ptr(T), _ptr(loss), _ptr(dY),
+                                       getattr(stream, "cuda_stream", stream)))
+
+
+def dnnmg_adamw(w, g, m, v, lr, beta1, beta2, eps, weight_decay, step, stream=None):
+    _check(None, load().dnnmg_adamw(int(w.numel()), _ptr(w), _ptr(g), _ptr(m), _ptr(v), float(lr), float(beta1),
+                                    float(beta2), float(eps), float(weight_decay), int(step),
+                                    getattr(stream, "cuda_stream", stream)))

@@ -410,6 +410,17 @@ dnnmg_status dnnmg_rhs_restrict(dnnmg_ctx* ctx, const void* x_coarse_dev, const 
     return DNNMG_OK;
 }
 
+dnnmg_status dnnmg_restrict(dnnmg_ctx* ctx, const void* b_fine_dev, void* b_coarse_dev) {
+    if (!ctx || !b_fine_dev || !b_coarse_dev) return DNNMG_EINVAL;
+    cudaError_t e = is_fp64(ctx) ? launch_restrict(ctx->dm, (const double*)b_fine_dev, (double*)b_coarse_dev,
+                                                   (double*)ctx->partial_c, ctx->stream)
+                                 : launch_restrict(ctx->dm, (const float*)b_fine_dev, (float*)b_coarse_dev,
+                                                   (float*)ctx->partial_c, ctx->stream);
+    ctx->launches += 2;
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "restrict");
+    return DNNMG_OK;
+}
+
 dnnmg_status dnnmg_patch_step(dnnmg_ctx* ctx, const void* x_coarse_dev, const void* F_dev, void* b_fine_dev,
                               void* b_coarse_dev) {
     if (!ctx || !x_coarse_dev || !F_dev) return DNNMG_EINVAL;

@@ -111,6 +111,8 @@ cudaError_t launch_local_restrict(const DeviceMesh& dm, const T* xc, const T* r,
 template <typename T>
 cudaError_t launch_extend(const DeviceMesh& dm, const T* Y, T* d, cudaStream_t s);
 template <typename T>
+cudaError_t launch_restrict(const DeviceMesh& dm, const T* b_fine, T* b_coarse, T* partial_c, cudaStream_t s);
+template <typename T>
 cudaError_t launch_rhs_restrict(const DeviceMesh& dm, OpParams p, const T* xc, const T* d,
                                 T* b_fine, T* b_coarse, T* partial, T* partial_c,
                                 cudaStream_t s, int* launches);

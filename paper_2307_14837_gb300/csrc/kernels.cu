@@ -355,6 +355,35 @@ __global__ void __launch_bounds__(256) vertex_reduce_kernel(
     st4(out + 4 * v, V4<T>{acc[0], acc[1], acc[2], T(0)});
 }
 
+// Restriction of a fine vector, patch part: corner k of patch P collects
+// sum_iota w(iota, k) b[dof(P, iota)] / valence(dof(P, iota)); summed over the
+// patches containing a coarse vertex (vertex_reduce) this is (P^T b)_v,
+// because every patch containing a fine node contains all its parents.
+template <typename T>
+__global__ void __launch_bounds__(256) restrict_patch_kernel(
+    int64_t nc, const int32_t* __restrict__ patch_map, const int32_t* __restrict__ node_ptr,
+    const T* __restrict__ b, T* __restrict__ partial_c) {
+    const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;   // P * 8 + k
+    if (e >= 8 * nc) return;
+    const int64_t P = e >> 3;
+    const int k = int(e & 7);
+    const int kx = k & 1, ky = (k >> 1) & 1, kz = (k >> 2) & 1;
+    T acc[3] = {T(0), T(0), T(0)};
+    for (int iota = 0; iota < 27; ++iota) {
+        const int a = iota % 3, bb = (iota / 3) % 3, c = iota / 9;
+        const T wx = a == 1 ? T(0.5) : ((a == 2) == (kx == 1) ? T(1) : T(0));
+        const T wy = bb == 1 ? T(0.5) : ((bb == 2) == (ky == 1) ? T(1) : T(0));
+        const T wz = c == 1 ? T(0.5) : ((c == 2) == (kz == 1) ? T(1) : T(0));
+        const T w = wx * wy * wz;
+        if (w == T(0)) continue;
+        const int64_t j = patch_map[27 * P + iota];
+        const T s = w / T(node_ptr[j + 1] - node_ptr[j]);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) acc[d] += s * b[4 * j + d];
+    }
+    st4(partial_c + 4 * e, V4<T>{acc[0], acc[1], acc[2], T(0)});
+}
+
 // x_fine[j] from the first patch containing j (deterministic).
 template <typename T>
 __global__ void __launch_bounds__(256) prolongate_kernel(
@@ -640,6 +669,19 @@ cudaError_t launch_local_restrict(const DeviceMesh& dm, const T* xc, const T* r,
         dm.nc, dm.cells, dm.patch_map, xc, r, edge_of<T>(dm), X);
     return cudaGetLastError();
 }
+
+template <typename T>
+cudaError_t launch_restrict(const DeviceMesh& dm, const T* b_fine, T* b_coarse, T* partial_c, cudaStream_t s) {
+    restrict_patch_kernel<T><<<blocks_for(8 * dm.nc, 256), 256, 0, s>>>(dm.nc, dm.patch_map, dm.node_ptr, b_fine,
+                                                                         partial_c);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    vertex_reduce_kernel<T><<<blocks_for(dm.nv, 256), 256, 0, s>>>(dm.nv, dm.vert_ptr, dm.vert_idx, partial_c,
+                                                                   dm.coarse_dir, b_coarse);
+    return cudaGetLastError();
+}
+template cudaError_t launch_restrict<double>(const DeviceMesh&, const double*, double*, double*, cudaStream_t);
+template cudaError_t launch_restrict<float>(const DeviceMesh&, const float*, float*, float*, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_extend(const DeviceMesh& dm, const T* Y, T* d, cudaStream_t s) {

@@ -3,6 +3,7 @@ loops, folded normalisation and the skip rule."""
 import os
 
 import numpy as np
+import pytest
 
 from paper_2307_14837_gb300 import inputs as I
 from oracle import mlp
@@ -60,3 +61,33 @@ def test_skip_only_where_widths_match():
     assert np.allclose(hid[0], X)            # first layer: no skip
     assert np.allclose(hid[1], 2 * X)        # second layer: relu(x) + x
     assert np.allclose(Y, 2 * X.sum(axis=1, keepdims=True) * np.ones((1, 2)))
+
+
+def test_training_gradients_match_finite_differences():
+    # the oracle's backpropagation against central differences of its loss
+    widths = (9, 6, 6, 6, 4)
+    Ws, _, _ = I.network_weights(widths, seed=2)
+    rng = np.random.default_rng(0)
+    bs = [0.1 * rng.standard_normal(w) for w in widths[1:-1]]
+    X = rng.standard_normal((7, 9))
+    T = rng.standard_normal((7, 4))
+    loss, dWs, dbs = mlp.loss_and_grads(X, Ws, bs, T, skip=True)
+    eps = 1e-6
+    for li in range(len(Ws)):
+        for (r, c) in [(0, 0), (1, 2), (Ws[li].shape[0] - 1, Ws[li].shape[1] - 1)]:
+            Wp = [w.copy() for w in Ws]
+            Wm = [w.copy() for w in Ws]
+            Wp[li][r, c] += eps
+            Wm[li][r, c] -= eps
+            fd = (mlp.loss_and_grads(X, Wp, bs, T)[0] - mlp.loss_and_grads(X, Wm, bs, T)[0]) / (2 * eps)
+            assert abs(fd - dWs[li][r, c]) <= 1e-7 * max(1.0, abs(fd))
+    for li in range(len(bs)):
+        bp = [b.copy() for b in bs]
+        bm = [b.copy() for b in bs]
+        bp[li][1] += eps
+        bm[li][1] -= eps
+        fd = (mlp.loss_and_grads(X, Ws, bp, T)[0] - mlp.loss_and_grads(X, Ws, bm, T)[0]) / (2 * eps)
+        assert abs(fd - dbs[li][1]) <= 1e-7 * max(1.0, abs(fd))
+    # the loss is the forward pass's output error
+    Y = mlp.forward(X, Ws, [np.ones(w) for w in widths[1:]], bs + [np.zeros(4)], skip=True)
+    assert loss == pytest.approx(np.sum((Y - T) ** 2) / 7, rel=1e-12)
