@@ -12,6 +12,7 @@
 // so the tensor-core kernel serves every product (its operands are K-major).
 // Reductions (bias gradients, loss) are two-pass and deterministic.
 #include <algorithm>
+#include <cmath>
 #include <vector>
 
 #include "internal.h"
@@ -138,13 +139,13 @@ __global__ void __launch_bounds__(1024) mse_kernel(int64_t n, float inv_b, const
 
 // AdamW (decoupled weight decay), bias-corrected moments
 __global__ void adamw_kernel(int64_t n, float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
-                             float* __restrict__ v, float lr, float b1, float b2, float eps, float wd, float c1,
-                             float c2) {
+                             float* __restrict__ v, float lr, float b1, float omb1, float b2, float omb2, float eps,
+                             float wd, float c1, float c2) {
     const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float gi = g[i];
-    const float mi = b1 * m[i] + (1.f - b1) * gi;
-    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    const float mi = b1 * m[i] + omb1 * gi;
+    const float vi = b2 * v[i] + omb2 * gi * gi;
     m[i] = mi;
     v[i] = vi;
     const float mh = mi / c1, vh = vi / c2;
@@ -380,12 +381,15 @@ dnnmg_status dnnmg_mse_loss(int64_t batch, const float* Y_dev, const float* T_de
     return cudaGetLastError() == cudaSuccess ? DNNMG_OK : DNNMG_ECUDA;
 }
 
-dnnmg_status dnnmg_adamw(int64_t n, float* w_dev, const float* g_dev, float* m_dev, float* v_dev, float lr, float beta1,
-                         float beta2, float eps, float weight_decay, int32_t step, void* cuda_stream) {
+dnnmg_status dnnmg_adamw(int64_t n, float* w_dev, const float* g_dev, float* m_dev, float* v_dev, double lr,
+                         double beta1, double beta2, double eps, double weight_decay, int32_t step, void* cuda_stream) {
     if (n <= 0 || !w_dev || !g_dev || !m_dev || !v_dev || step < 1) return DNNMG_EINVAL;
-    const float c1 = 1.f - powf(beta1, float(step)), c2 = 1.f - powf(beta2, float(step));
-    adamw_kernel<<<nb(n, 256), 256, 0, static_cast<cudaStream_t>(cuda_stream)>>>(n, w_dev, g_dev, m_dev, v_dev, lr, beta1,
-                                                                                  beta2, eps, weight_decay, c1, c2);
+    // 1 - beta and the bias corrections in double: rounding beta to float first
+    // would cost 1 - 0.999 about 1e-5 of its value
+    const double c1 = 1.0 - std::pow(beta1, double(step)), c2 = 1.0 - std::pow(beta2, double(step));
+    adamw_kernel<<<nb(n, 256), 256, 0, static_cast<cudaStream_t>(cuda_stream)>>>(
+        n, w_dev, g_dev, m_dev, v_dev, float(lr), float(beta1), float(1.0 - beta1), float(beta2), float(1.0 - beta2),
+        float(eps), float(weight_decay), float(c1), float(c2));
     return cudaGetLastError() == cudaSuccess ? DNNMG_OK : DNNMG_ECUDA;
 }
 
