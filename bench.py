@@ -247,6 +247,79 @@ def run_ours(args, rank, world, local_rank):
     return res
 
 
+SERVING_SIMS = 64
+
+
+def serving_requests(n=SERVING_SIMS, seed=5, rate=12.0, steps=(50, 500), cells=(4000, 300000)):
+    """The serving stream: n simulations arriving as a Poisson process (rate
+    per second), each a channel or a cavity (even odds) whose coarse mesh
+    size is log-uniform in `cells` and whose step count is uniform in
+    `steps`; each starts from a seeded smooth coarse state.  Draws are
+    SplitMix64."""
+    import numpy as np
+    from paper_2307_14837_gb300 import inputs as I
+    from paper_2307_14837_gb300.serve import Request, poisson_requests
+    u = I.splitmix_uniform(seed * 104729 + 3, 3 * n).reshape(n, 3)
+    chan_cells = {}
+
+    def channel_for(target):
+        # channel cell counts grow ~ nz^3; take the nz with the nearest count
+        best = None
+        for nz in range(6, 40):
+            if nz not in chan_cells:
+                chan_cells[nz] = len(I.channel_mesh(nz, seed=0)["cells"])
+            if best is None or abs(math.log(chan_cells[nz] / target)) < abs(math.log(chan_cells[best] / target)):
+                best = nz
+        return best
+
+    def make(i, _):
+        target = cells[0] * (cells[1] / cells[0]) ** u[i, 0]
+        n_steps = int(steps[0] + (steps[1] - steps[0]) * u[i, 1])
+        if u[i, 2] < 0.5:
+            m = I.channel_mesh(channel_for(target), seed=i)
+            nu = m["meta"]["D"] / 200.0
+            dt, theta = DT, THETA
+        else:
+            k = max(16, 2 * int(round(target ** (1.0 / 3.0) / 2)))
+            m = I.cavity_mesh(k, jitter=0.1, seed=i)
+            nu, dt, theta = 0.01, 0.01, 1.0
+        return Request(f"sim{i}", m, nu, dt, theta, n_steps, solve=False, x0=I.coarse_state(m, seed=i))
+
+    return poisson_requests(n, rate, seed, make)
+
+
+def run_serving(args):
+    """Serve the stream with one BF16 network launch per server step over all
+    live patches; each simulation's coarse state is held fixed (the patch
+    correction alone, as in the step benchmark)."""
+    import torch
+    from paper_2307_14837_gb300 import inputs as I
+    from paper_2307_14837_gb300.serve import Server
+    torch.cuda.set_device(0)
+    reqs = serving_requests(n=args.serving_sims)
+    Ws, ss, ts = I.network_weights(WIDTHS, seed=0)
+    budget = int(args.serving_budget_gb * (1 << 30))
+    srv = Server(WIDTHS, Ws, ss, ts, memory_budget=budget, max_rows=args.serving_rows, precision="bf16")
+    with Clocks(0) as clk:
+        stats = srv.run(reqs, timeout=1800.0)
+    srv.close()
+    cells = [len(r.mesh["cells"]) for r in reqs]
+    line = {"metric": "serving: aggregate patches/s over a Poisson stream of simulations, one BF16 network "
+                      "launch per server step", "value": stats["patches_per_s"], "unit": "patches/s",
+            "n_gpus": 1, "higher_is_better": True, "dtype": "bf16", "data": "synthetic",
+            "p50_step_latency_ms": stats["p50_step_latency_ms"], "p99_step_latency_ms": stats["p99_step_latency_ms"],
+            "server_steps": stats["server_steps"], "network_launches": stats["network_launches"],
+            "wall_s": stats["wall_s"], "simulations": stats["simulations"],
+            "config": {"workload": f"{len(reqs)} simulations, channel/cavity mix, coarse meshes "
+                                   f"{min(cells)}-{max(cells)} hex (log-uniform 4k-300k), 50-500 steps each, "
+                                   f"Poisson arrivals 12/s; network {'-'.join(map(str, WIDTHS))}; "
+                                   "patch correction only (coarse state held)",
+                       "memory_budget_gb": args.serving_budget_gb, "max_rows": args.serving_rows,
+                       "total_patch_steps": int(sum(c * r.n_steps for c, r in zip(cells, reqs)))},
+            "clocks": clk.summary()}
+    print(json.dumps(line))
+
+
 def equal_error(steps=5):
     """Velocity error of the DNN-MG time loop in the BF16 form and in the plain
     FP64 form against a fine-level reference (the plain scheme on level L+1),
@@ -342,6 +415,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serving", action="store_true",
+                    help="serve a Poisson stream of simulations instead of the step benchmark")
+    ap.add_argument("--serving-sims", type=int, default=SERVING_SIMS)
+    ap.add_argument("--serving-budget-gb", type=float, default=96.0)
+    ap.add_argument("--serving-rows", type=int, default=6_000_000)
     ap.add_argument("--nz", type=int, default=NZ,
                     help="channel resolution (cells across the height); the measured workload is nz=37")
     args = ap.parse_args()
@@ -371,6 +449,11 @@ def main():
                 "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
                 "patches_per_s": pps, "wall_s": time.perf_counter() - t0}
         print(json.dumps(line))
+        return
+
+    if args.serving:
+        if rank == 0:
+            run_serving(args)
         return
 
     import torch

@@ -318,6 +318,30 @@ dnnmg_status dnnmg_solve(dnnmg_ctx* ctx, int32_t level, const dnnmg_solver_param
 dnnmg_status dnnmg_time_step(dnnmg_ctx* ctx, int32_t n_steps, const dnnmg_solver_params* prm,
                              double* x_coarse_dev, double* b_coarse_dev, void* F_dev, dnnmg_solve_stats* stats);
 
+/* One DNN-MG step in two halves, so that several contexts can share one
+ * network launch (dnnmg_net_create) between them:
+ *   dnnmg_step_begin: (solve != 0) the coarse solve with b_coarse, then the
+ *     fine residual with F and the network input rows of this mesh into
+ *     X_dev ([n_patches][n_in_padded], the context's X element type; may
+ *     point into a larger shared buffer).  Returns ENOCONV if the coarse
+ *     solve missed its tolerance (the step still proceeds).
+ *   dnnmg_step_end: extension of Y_dev ([n_patches][81], the context's Y
+ *     type; may point into a shared buffer), then the next fine rhs into
+ *     F_dev and its restriction into b_coarse_dev (double).
+ * dnnmg_time_step = begin, dnnmg_network on the context's buffers, end. */
+dnnmg_status dnnmg_step_begin(dnnmg_ctx* ctx, const dnnmg_solver_params* prm, int32_t solve, double* x_coarse_dev,
+                              const double* b_coarse_dev, const void* F_dev, void* X_dev, dnnmg_solve_stats* stats);
+dnnmg_status dnnmg_step_end(dnnmg_ctx* ctx, const void* Y_dev, void* F_dev, double* b_coarse_dev);
+
+/* A network-only context for serving: no mesh; supports dnnmg_network (up
+ * to max_rows rows), dnnmg_set_network, dnnmg_set_stream, dnnmg_sync,
+ * dnnmg_launch_count, dnnmg_destroy; every call that needs a mesh returns
+ * DNNMG_EINVAL on it.  Weights as in dnnmg_set_network.  The context
+ * allocates its activations for max_rows rows once; the caller owns X and Y. */
+dnnmg_status dnnmg_net_create(const dnnmg_net_desc* net, const double* const* W, const double* const* scale,
+                              const double* const* shift, int32_t precision, int64_t max_rows, void* cuda_stream,
+                              dnnmg_ctx** out);
+
 /* n_steps of the plain scheme on one level (no network): b = Rhs(x_old),
  * solve A(x) = b.  x_dev double [n][4]. */
 dnnmg_status dnnmg_plain_step(dnnmg_ctx* ctx, int32_t level, int32_t n_steps, const dnnmg_solver_params* prm,
@@ -361,9 +385,11 @@ dnnmg_status dnnmg_mse_loss(int64_t batch, const float* Y_dev, const float* T_de
                             void* cuda_stream);
 
 /* One AdamW step (decoupled weight decay, bias-corrected moments, step >= 1)
- * on n parameters w with gradient g and moments m, v (all fp32 device). */
-dnnmg_status dnnmg_adamw(int64_t n, float* w_dev, const float* g_dev, float* m_dev, float* v_dev, float lr,
-                         float beta1, float beta2, float eps, float weight_decay, int32_t step, void* cuda_stream);
+ * on n parameters w with gradient g and moments m, v (all fp32 device).
+ * Hyperparameters in double: 1 - beta and the bias corrections 1 - beta^step
+ * are formed in double and rounded once to fp32 for the update. */
+dnnmg_status dnnmg_adamw(int64_t n, float* w_dev, const float* g_dev, float* m_dev, float* v_dev, double lr,
+                         double beta1, double beta2, double eps, double weight_decay, int32_t step, void* cuda_stream);
 
 /* Largest mesh dnnmg_residual_noalloc accepts (coarse cells = patches). */
 #define DNNMG_NOALLOC_MAX_PATCHES 16384

@@ -338,9 +338,43 @@ _SIGS.update({
     "dnnmg_trainer_forward": ([_VP, _VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _VP, ctypes.c_int64], ctypes.c_int),
     "dnnmg_trainer_backward": ([_VP, _VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP)], ctypes.c_int),
     "dnnmg_mse_loss": ([ctypes.c_int64, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
-    "dnnmg_adamw": ([ctypes.c_int64, _VP, _VP, _VP, _VP, ctypes.c_float, ctypes.c_float, ctypes.c_float,
-                     ctypes.c_float, ctypes.c_float, ctypes.c_int32, _VP], ctypes.c_int),
+    "dnnmg_adamw": ([ctypes.c_int64, _VP, _VP, _VP, _VP, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                     ctypes.c_double, ctypes.c_double, ctypes.c_int32, _VP], ctypes.c_int),
 })
+
+
+_SIGS.update({
+    "dnnmg_step_begin": ([_VP, ctypes.POINTER(SolverParams), ctypes.c_int32, _VP, _VP, _VP, _VP,
+                          ctypes.POINTER(SolveStats)], ctypes.c_int),
+    "dnnmg_step_end": ([_VP, _VP, _VP, _VP], ctypes.c_int),
+    "dnnmg_net_create": ([ctypes.POINTER(NetDesc), ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_VP),
+                          ctypes.c_int32, ctypes.c_int64, _VP, ctypes.POINTER(_VP)], ctypes.c_int),
+})
+
+
+def dnnmg_step_begin(ctx, x_coarse, b_coarse, F, X, solve=True, prm=None):
+    st = SolveStats()
+    _solve_status(ctx, load().dnnmg_step_begin(ctx, ctypes.byref(prm) if prm else None, 1 if solve else 0,
+                                               _ptr(x_coarse), _ptr(b_coarse), _ptr(F), _ptr(X), ctypes.byref(st)))
+    return _stats(st)
+
+
+def dnnmg_step_end(ctx, Y, F, b_coarse):
+    _check(ctx, load().dnnmg_step_end(ctx, _ptr(Y), _ptr(F), _ptr(b_coarse)))
+
+
+def dnnmg_net_create(widths, Ws, scales, shifts, precision, max_rows, stream=None, skip=True):
+    L = len(Ws)
+    w = np.ascontiguousarray(widths, dtype=np.int32)
+    keep = [np.ascontiguousarray(W, dtype=np.float64) for W in Ws]
+    ks = [np.ascontiguousarray(s, dtype=np.float64) for s in scales] if scales is not None else None
+    kt = [np.ascontiguousarray(t, dtype=np.float64) for t in shifts] if shifts is not None else None
+    arr = lambda lst: (_VP * L)(*[a.ctypes.data for a in lst]) if lst is not None else None
+    desc = NetDesc(L, w.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), 1 if skip else 0)
+    h = _VP()
+    _check(None, load().dnnmg_net_create(ctypes.byref(desc), arr(keep), arr(ks), arr(kt), int(precision),
+                                         int(max_rows), getattr(stream, "cuda_stream", stream), ctypes.byref(h)))
+    return h.value
 
 
 def dnnmg_restrict(ctx, b_fine, b_coarse):

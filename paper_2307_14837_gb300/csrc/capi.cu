@@ -188,7 +188,7 @@ dnnmg_status dnnmg_get_sizes(const dnnmg_ctx* ctx, dnnmg_sizes* out) {
 }
 
 dnnmg_status dnnmg_get_mesh_data(const dnnmg_ctx* ctx, int32_t item, void* host_buf, size_t bytes) {
-    if (!ctx || !host_buf) return DNNMG_EINVAL;
+    if (!ctx || ctx->net_only || !host_buf) return DNNMG_EINVAL;
     const HostHierarchy& h = ctx->host;
     const void* src = nullptr;
     size_t n = 0;
@@ -301,7 +301,7 @@ dnnmg_status dnnmg_set_network(dnnmg_ctx* ctx, const dnnmg_net_desc* net, const 
         ctx->scale.push_back(ds);
         ctx->shift.push_back(dt);
     }
-    ctx->act_rows = std::max<int64_t>(ctx->host.nc, 1);
+    ctx->act_rows = ctx->net_capacity > 0 ? ctx->net_capacity : std::max<int64_t>(ctx->host.nc, 1);
     ctx->act_ld = maxw;
     const size_t ae = ctx->precision == DNNMG_FP64 ? 8 : (ctx->precision == DNNMG_FP32 ? 4 : 2);
     for (int b = 0; b < 2; ++b) {
@@ -314,7 +314,7 @@ dnnmg_status dnnmg_set_network(dnnmg_ctx* ctx, const dnnmg_net_desc* net, const 
 }
 
 dnnmg_status dnnmg_prolongate(dnnmg_ctx* ctx, const void* x_coarse_dev, void* x_fine_dev) {
-    if (!ctx || !x_coarse_dev || !x_fine_dev) return DNNMG_EINVAL;
+    if (!ctx || ctx->net_only || !x_coarse_dev || !x_fine_dev) return DNNMG_EINVAL;
     cudaError_t e = is_fp64(ctx) ? launch_prolongate(ctx->dm, (const double*)x_coarse_dev, (double*)x_fine_dev, ctx->stream)
                                  : launch_prolongate(ctx->dm, (const float*)x_coarse_dev, (float*)x_fine_dev, ctx->stream);
     ctx->launches += 1;
@@ -323,7 +323,7 @@ dnnmg_status dnnmg_prolongate(dnnmg_ctx* ctx, const void* x_coarse_dev, void* x_
 }
 
 dnnmg_status dnnmg_residual(dnnmg_ctx* ctx, const void* x_coarse_dev, const void* F_dev, void* r_dev) {
-    if (!ctx || !x_coarse_dev || !F_dev || !r_dev) return DNNMG_EINVAL;
+    if (!ctx || ctx->net_only || !x_coarse_dev || !F_dev || !r_dev) return DNNMG_EINVAL;
     int launches = 0;
     cudaError_t e = is_fp64(ctx)
                         ? launch_residual(ctx->dm, ctx->op, (const double*)x_coarse_dev, (const double*)F_dev,
@@ -336,7 +336,7 @@ dnnmg_status dnnmg_residual(dnnmg_ctx* ctx, const void* x_coarse_dev, const void
 }
 
 dnnmg_status dnnmg_local_restrict(dnnmg_ctx* ctx, const void* x_coarse_dev, const void* r_dev, void* X_dev) {
-    if (!ctx || !x_coarse_dev || !r_dev || !X_dev) return DNNMG_EINVAL;
+    if (!ctx || ctx->net_only || !x_coarse_dev || !r_dev || !X_dev) return DNNMG_EINVAL;
     cudaError_t e;
     if (ctx->precision == DNNMG_FP64)
         e = launch_local_restrict(ctx->dm, (const double*)x_coarse_dev, (const double*)r_dev, (double*)X_dev, ctx->stream);
@@ -385,7 +385,7 @@ dnnmg_status dnnmg_network(dnnmg_ctx* ctx, const void* X_dev, void* Y_dev, int64
 }
 
 dnnmg_status dnnmg_extend(dnnmg_ctx* ctx, const void* Y_dev, void* d_dev) {
-    if (!ctx || !Y_dev || !d_dev) return DNNMG_EINVAL;
+    if (!ctx || ctx->net_only || !Y_dev || !d_dev) return DNNMG_EINVAL;
     cudaError_t e = is_fp64(ctx) ? launch_extend(ctx->dm, (const double*)Y_dev, (double*)d_dev, ctx->stream)
                                  : launch_extend(ctx->dm, (const float*)Y_dev, (float*)d_dev, ctx->stream);
     ctx->launches += 1;
@@ -395,7 +395,7 @@ dnnmg_status dnnmg_extend(dnnmg_ctx* ctx, const void* Y_dev, void* d_dev) {
 
 dnnmg_status dnnmg_rhs_restrict(dnnmg_ctx* ctx, const void* x_coarse_dev, const void* d_dev, void* b_fine_dev,
                                 void* b_coarse_dev) {
-    if (!ctx || !x_coarse_dev || !d_dev) return DNNMG_EINVAL;
+    if (!ctx || ctx->net_only || !x_coarse_dev || !d_dev) return DNNMG_EINVAL;
     int launches = 0;
     cudaError_t e =
         is_fp64(ctx)
@@ -411,7 +411,7 @@ dnnmg_status dnnmg_rhs_restrict(dnnmg_ctx* ctx, const void* x_coarse_dev, const 
 }
 
 dnnmg_status dnnmg_restrict(dnnmg_ctx* ctx, const void* b_fine_dev, void* b_coarse_dev) {
-    if (!ctx || !b_fine_dev || !b_coarse_dev) return DNNMG_EINVAL;
+    if (!ctx || ctx->net_only || !b_fine_dev || !b_coarse_dev) return DNNMG_EINVAL;
     cudaError_t e = is_fp64(ctx) ? launch_restrict(ctx->dm, (const double*)b_fine_dev, (double*)b_coarse_dev,
                                                    (double*)ctx->partial_c, ctx->stream)
                                  : launch_restrict(ctx->dm, (const float*)b_fine_dev, (float*)b_coarse_dev,
@@ -423,7 +423,7 @@ dnnmg_status dnnmg_restrict(dnnmg_ctx* ctx, const void* b_fine_dev, void* b_coar
 
 dnnmg_status dnnmg_patch_step(dnnmg_ctx* ctx, const void* x_coarse_dev, const void* F_dev, void* b_fine_dev,
                               void* b_coarse_dev) {
-    if (!ctx || !x_coarse_dev || !F_dev) return DNNMG_EINVAL;
+    if (!ctx || ctx->net_only || !x_coarse_dev || !F_dev) return DNNMG_EINVAL;
     if (!ctx->has_net) return fail(ctx, DNNMG_ESTATE, "dnnmg_patch_step before dnnmg_set_network");
     dnnmg_status st;
     if ((st = dnnmg_residual(ctx, x_coarse_dev, F_dev, ctx->buf_r)) != DNNMG_OK) return st;
@@ -435,7 +435,7 @@ dnnmg_status dnnmg_patch_step(dnnmg_ctx* ctx, const void* x_coarse_dev, const vo
 
 dnnmg_status dnnmg_patch_step_host(dnnmg_ctx* ctx, const void* x_coarse_host, const void* F_host,
                                    void* b_fine_host, void* b_coarse_host) {
-    if (!ctx || !x_coarse_host || !F_host) return DNNMG_EINVAL;
+    if (!ctx || ctx->net_only || !x_coarse_host || !F_host) return DNNMG_EINVAL;
     const size_t fe = field_elem(ctx->precision);
     const size_t nv = size_t(ctx->host.nv), nf = size_t(ctx->host.n_fine);
     CK(ctx, cudaMemcpyAsync(ctx->buf_xc, x_coarse_host, nv * 4 * fe, cudaMemcpyHostToDevice, ctx->stream));
@@ -542,7 +542,7 @@ dnnmg_status dnnmg_level_info(dnnmg_ctx* ctx, int32_t level, int64_t* n_nodes, i
 
 dnnmg_status dnnmg_level_operator(dnnmg_ctx* ctx, int32_t level, const dnnmg_solver_params* prm, const double* x_dev,
                                   double* Ax_dev) {
-    if (!ctx || !x_dev || !Ax_dev) return DNNMG_EINVAL;
+    if (!ctx || ctx->net_only || !x_dev || !Ax_dev) return DNNMG_EINVAL;
     dnnmg_solver_params d;
     dnnmg_solver_defaults(&d);
     DeviceLevel* L;
@@ -554,7 +554,7 @@ dnnmg_status dnnmg_level_operator(dnnmg_ctx* ctx, int32_t level, const dnnmg_sol
 }
 
 dnnmg_status dnnmg_level_rhs(dnnmg_ctx* ctx, int32_t level, const double* x_old_dev, double* b_dev) {
-    if (!ctx || !x_old_dev || !b_dev) return DNNMG_EINVAL;
+    if (!ctx || ctx->net_only || !x_old_dev || !b_dev) return DNNMG_EINVAL;
     DeviceLevel* L;
     dnnmg_status st = get_level(ctx, level, nullptr, &L);
     if (st != DNNMG_OK) return st;
@@ -565,7 +565,7 @@ dnnmg_status dnnmg_level_rhs(dnnmg_ctx* ctx, int32_t level, const double* x_old_
 
 dnnmg_status dnnmg_level_jacobian(dnnmg_ctx* ctx, int32_t level, const dnnmg_solver_params* prm, const double* x_dev,
                                   double* dense_host, size_t bytes) {
-    if (!ctx || !x_dev || !dense_host) return DNNMG_EINVAL;
+    if (!ctx || ctx->net_only || !x_dev || !dense_host) return DNNMG_EINVAL;
     dnnmg_solver_params d;
     dnnmg_solver_defaults(&d);
     DeviceLevel* L;
@@ -581,7 +581,7 @@ dnnmg_status dnnmg_level_jacobian(dnnmg_ctx* ctx, int32_t level, const dnnmg_sol
 
 dnnmg_status dnnmg_solve(dnnmg_ctx* ctx, int32_t level, const dnnmg_solver_params* prm, const double* b_dev,
                          double* x_dev, dnnmg_solve_stats* stats) {
-    if (!ctx || !b_dev || !x_dev) return DNNMG_EINVAL;
+    if (!ctx || ctx->net_only || !b_dev || !x_dev) return DNNMG_EINVAL;
     dnnmg_solver_params d;
     dnnmg_solver_defaults(&d);
     if (!prm) prm = &d;
@@ -600,7 +600,7 @@ dnnmg_status dnnmg_solve(dnnmg_ctx* ctx, int32_t level, const dnnmg_solver_param
 
 dnnmg_status dnnmg_time_step(dnnmg_ctx* ctx, int32_t n_steps, const dnnmg_solver_params* prm, double* x_coarse_dev,
                              double* b_coarse_dev, void* F_dev, dnnmg_solve_stats* stats) {
-    if (!ctx || !x_coarse_dev || !b_coarse_dev || !F_dev || n_steps < 0) return DNNMG_EINVAL;
+    if (!ctx || ctx->net_only || !x_coarse_dev || !b_coarse_dev || !F_dev || n_steps < 0) return DNNMG_EINVAL;
     if (!ctx->has_net) return fail(ctx, DNNMG_ESTATE, "dnnmg_time_step before dnnmg_set_network");
     const int64_t nv = ctx->host.nv;
     dnnmg_status st;
@@ -609,27 +609,86 @@ dnnmg_status dnnmg_time_step(dnnmg_ctx* ctx, int32_t n_steps, const dnnmg_solver
         if ((st = alloc(ctx, size_t(nv) * 4 * 4, &ctx->bc_field)) != DNNMG_OK) return st;
     }
     for (int32_t k = 0; k < n_steps; ++k) {
-        st = dnnmg_solve(ctx, DNNMG_LEVEL_COARSE, prm, b_coarse_dev, x_coarse_dev, stats);
+        st = dnnmg_step_begin(ctx, prm, 1, x_coarse_dev, b_coarse_dev, F_dev, ctx->buf_X, stats);
         if (st != DNNMG_OK && st != DNNMG_ENOCONV) return st;
-        if (is_fp64(ctx)) {
-            if ((st = dnnmg_patch_step(ctx, x_coarse_dev, F_dev, F_dev, b_coarse_dev)) != DNNMG_OK) return st;
-        } else {
-            const unsigned blocks = unsigned((4 * nv + 255) / 256);
-            to_float_kernel<<<blocks, 256, 0, ctx->stream>>>(4 * nv, x_coarse_dev, (float*)ctx->xc_field);
-            CK(ctx, cudaGetLastError());
-            if ((st = dnnmg_patch_step(ctx, ctx->xc_field, F_dev, F_dev, ctx->bc_field)) != DNNMG_OK) return st;
-            to_double_kernel<<<blocks, 256, 0, ctx->stream>>>(4 * nv, (const float*)ctx->bc_field, b_coarse_dev);
-            CK(ctx, cudaGetLastError());
-            ctx->launches += 2;
-        }
+        if ((st = dnnmg_network(ctx, ctx->buf_X, ctx->buf_Y, ctx->host.nc)) != DNNMG_OK) return st;
+        if ((st = dnnmg_step_end(ctx, ctx->buf_Y, F_dev, b_coarse_dev)) != DNNMG_OK) return st;
     }
     CK(ctx, cudaStreamSynchronize(ctx->stream));
     return DNNMG_OK;
 }
 
+dnnmg_status dnnmg_step_begin(dnnmg_ctx* ctx, const dnnmg_solver_params* prm, int32_t solve, double* x_coarse_dev,
+                              const double* b_coarse_dev, const void* F_dev, void* X_dev, dnnmg_solve_stats* stats) {
+    if (!ctx || ctx->net_only || !x_coarse_dev || !F_dev || !X_dev || (solve && !b_coarse_dev)) return DNNMG_EINVAL;
+    const int64_t nv = ctx->host.nv;
+    dnnmg_status st = DNNMG_OK, solve_st = DNNMG_OK;
+    if (!is_fp64(ctx) && !ctx->xc_field) {
+        if ((st = alloc(ctx, size_t(nv) * 4 * 4, &ctx->xc_field)) != DNNMG_OK) return st;
+        if ((st = alloc(ctx, size_t(nv) * 4 * 4, &ctx->bc_field)) != DNNMG_OK) return st;
+    }
+    if (solve) {
+        solve_st = dnnmg_solve(ctx, DNNMG_LEVEL_COARSE, prm, b_coarse_dev, x_coarse_dev, stats);
+        if (solve_st != DNNMG_OK && solve_st != DNNMG_ENOCONV) return solve_st;
+    }
+    const void* xf = x_coarse_dev;
+    if (!is_fp64(ctx)) {
+        to_float_kernel<<<unsigned((4 * nv + 255) / 256), 256, 0, ctx->stream>>>(4 * nv, x_coarse_dev,
+                                                                                (float*)ctx->xc_field);
+        CK(ctx, cudaGetLastError());
+        ctx->launches += 1;
+        xf = ctx->xc_field;
+    }
+    if ((st = dnnmg_residual(ctx, xf, F_dev, ctx->buf_r)) != DNNMG_OK) return st;
+    if ((st = dnnmg_local_restrict(ctx, xf, ctx->buf_r, X_dev)) != DNNMG_OK) return st;
+    ctx->last_xc = xf;
+    return solve_st;
+}
+
+dnnmg_status dnnmg_step_end(dnnmg_ctx* ctx, const void* Y_dev, void* F_dev, double* b_coarse_dev) {
+    if (!ctx || ctx->net_only || !Y_dev || !F_dev || !b_coarse_dev) return DNNMG_EINVAL;
+    if (!ctx->last_xc) return fail(ctx, DNNMG_ESTATE, "dnnmg_step_end before dnnmg_step_begin");
+    const int64_t nv = ctx->host.nv;
+    dnnmg_status st;
+    if ((st = dnnmg_extend(ctx, Y_dev, ctx->buf_d)) != DNNMG_OK) return st;
+    // the coarse state of the last dnnmg_step_begin (caller's array in FP64, else its float copy)
+    if (is_fp64(ctx)) return dnnmg_rhs_restrict(ctx, ctx->last_xc, ctx->buf_d, F_dev, b_coarse_dev);
+    if ((st = dnnmg_rhs_restrict(ctx, ctx->last_xc, ctx->buf_d, F_dev, ctx->bc_field)) != DNNMG_OK) return st;
+    to_double_kernel<<<unsigned((4 * nv + 255) / 256), 256, 0, ctx->stream>>>(4 * nv, (const float*)ctx->bc_field,
+                                                                             b_coarse_dev);
+    CK(ctx, cudaGetLastError());
+    ctx->launches += 1;
+    return DNNMG_OK;
+}
+
+dnnmg_status dnnmg_net_create(const dnnmg_net_desc* net, const double* const* W, const double* const* scale,
+                              const double* const* shift, int32_t precision, int64_t max_rows, void* cuda_stream,
+                              dnnmg_ctx** out) {
+    if (!out) return DNNMG_EINVAL;
+    *out = nullptr;
+    if (precision < DNNMG_FP64 || precision > DNNMG_BF16 || max_rows <= 0) return DNNMG_EINVAL;
+    dnnmg_ctx* ctx = new (std::nothrow) dnnmg_ctx();
+    if (!ctx) return DNNMG_ENOMEM;
+    ctx->net_only = true;
+    ctx->net_capacity = max_rows;
+    ctx->precision = precision;
+    ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+    if (cudaGetDevice(&ctx->device) != cudaSuccess) {
+        delete ctx;
+        return DNNMG_ECUDA;
+    }
+    dnnmg_status st = dnnmg_set_network(ctx, net, W, scale, shift);
+    if (st != DNNMG_OK) {
+        dnnmg_destroy(ctx);
+        return st;
+    }
+    *out = ctx;
+    return DNNMG_OK;
+}
+
 dnnmg_status dnnmg_plain_step(dnnmg_ctx* ctx, int32_t level, int32_t n_steps, const dnnmg_solver_params* prm,
                               double* x_dev, dnnmg_solve_stats* stats) {
-    if (!ctx || !x_dev || n_steps < 0) return DNNMG_EINVAL;
+    if (!ctx || ctx->net_only || !x_dev || n_steps < 0) return DNNMG_EINVAL;
     DeviceLevel* L;
     dnnmg_status st = get_level(ctx, level, prm, &L);
     if (st != DNNMG_OK) return st;

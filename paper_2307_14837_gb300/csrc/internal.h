@@ -163,6 +163,9 @@ struct dnnmg_ctx {
     void* act[2] = {nullptr, nullptr};  // [nc][max width] activations
     int64_t act_rows = 0;
     int act_ld = 0;
+    int64_t net_capacity = 0;    // rows of a network-only context (no mesh)
+    bool net_only = false;
+    const void* last_xc = nullptr;   // coarse state (field type) of the last dnnmg_step_begin
 
     // Newton solver levels (0: L, 1: L+1), created on first use
     dnnmg::DeviceLevel* level[2] = {nullptr, nullptr};
