@@ -11,8 +11,11 @@
 //               swizzle, into a ring of STAGES shared-memory stages
 //   warp 1      allocates TMEM and issues tcgen05.mma (M=128, N=BN, K=16)
 //               from one thread; tcgen05.commit frees stages / publishes tiles
-//   warps 2..5  epilogue: tcgen05.ld 32 lanes x 32 columns per warp,
-//               scale/shift/ReLU/skip, vector stores
+//   warps 2..9  epilogue: warp w reads TMEM lanes 32 (w % 4) ..; the two
+//               warps of a lane quarter take alternate 32-column chunks
+//               (tcgen05.ld 32 lanes x 32 columns), scale/shift/ReLU/skip,
+//               vector stores; two warps per scheduler hide each other's
+//               TMEM and memory latency
 // Two TMEM accumulators let the epilogue of one tile overlap the MMAs of
 // the next.  Every mbarrier wait is bounded (~1 s of %globaltimer); on
 // expiry the thread records an error code in tc_error, stops issuing work,
@@ -34,9 +37,10 @@ enum TcErr { kErrFull = 1, kErrEmpty = 2, kErrTmemFull = 3, kErrTmemEmpty = 4, k
 
 constexpr int BM = 128;
 constexpr int BK = 64;                 // 64 bf16 = 128 bytes = one swizzle row
-constexpr int kThreads = 192;
+constexpr int kEpiWarps = 8;
+constexpr int kEpiThreads = 32 * kEpiWarps;
+constexpr int kThreads = 64 + kEpiThreads;
 constexpr uint64_t kWaitNs = 1000000000ull;
-constexpr int kStageLd = 36;           // floats per staged row (32 + 4: conflict-free float4 access)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -72,13 +76,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
-// AND of `ok` over the 128 epilogue threads (named barrier 1); also a barrier.
+// AND of `ok` over the epilogue threads (named barrier 1); also a barrier.
 __device__ __forceinline__ bool epilogue_all(bool ok) {
     uint32_t r;
     asm volatile(
         "{\n\t.reg .pred p, q;\n\t"
         "setp.ne.u32 q, %1, 0;\n\t"
-        "bar.red.and.pred p, 1, 128, q;\n\t"
+        "bar.red.and.pred p, 1, 256, q;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(r)
         : "r"(uint32_t(ok))
@@ -168,8 +172,9 @@ struct Cfg {
     static constexpr int ACC_COLS = BN <= 128 ? 128 : 256;      // TMEM columns per accumulator
     static constexpr int TMEM_COLS = 2 * ACC_COLS;              // power of two >= 32
     static constexpr int BAR_BYTES = ((2 * STAGES + 5) * 8 + 16 + 127) / 128 * 128;   // keeps what follows aligned
-    static constexpr int EP_BYTES = 4 * 32 * kStageLd * 4 + 2 * BN * 4;   // epilogue staging + scale/shift
+    static constexpr int EP_BYTES = kEpiWarps * 32 * 32 * 4;             // one 32 x 32 fp32 block per epilogue warp
     static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + BAR_BYTES + EP_BYTES;
+    static_assert(SMEM <= 227 * 1024, "shared memory per CTA");
 };
 
 template <int BN, bool OUT_BF16>
@@ -191,8 +196,6 @@ __global__ void __launch_bounds__(kThreads, 1) tc_layer_kernel(
     volatile uint32_t* tmem_slot =
         reinterpret_cast<volatile uint32_t*>(gbase + C::STAGES * C::STAGE_BYTES + (2 * C::STAGES + 5) * 8);
     float* ep_stage = reinterpret_cast<float*>(gbase + C::STAGES * C::STAGE_BYTES + C::BAR_BYTES);
-    float* ep_scale = ep_stage + 4 * 32 * kStageLd;
-    float* ep_shift = ep_scale + BN;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -202,7 +205,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_layer_kernel(
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(tfull_bar(b), 1);
-            mbar_init(tempty_bar(b), 128);
+            mbar_init(tempty_bar(b), kEpiThreads);
         }
         mbar_init(done_bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -291,24 +294,20 @@ __global__ void __launch_bounds__(kThreads, 1) tc_layer_kernel(
         mbar_wait(done_bar, 0, kErrDrain);
     } else if (warp >= 2) {
         // ---------------- epilogue: warp w reads TMEM lanes 32 (w % 4) ..
-        // Each 32 x 32 block goes TMEM -> registers (scale, shift, ReLU) ->
-        // padded shared memory -> coalesced global stores (8 rows x 64 bytes
-        // per warp instruction), with the skip input read the same way.
+        // and the 32-column chunks c0 = 32 half, 32 half + 64, ...  Each
+        // 32 x 32 block goes TMEM -> registers (scale, shift, ReLU) -> shared
+        // memory -> coalesced global stores (8 rows x 64 bytes per warp
+        // instruction), with the skip input read the same way.  The staged
+        // block holds row r's float4 number q at q ^ (r & 7): conflict-free
+        // both when a lane writes its row and when 8 lanes read 2 rows.
         const int quarter = warp & 3;
-        const int et = threadIdx.x - 64;                 // 0..127 among epilogue threads
-        float* stage = ep_stage + (warp - 2) * (32 * kStageLd);
+        const int half = (warp - 2) >> 2;
+        float* stage = ep_stage + (warp - 2) * (32 * 32);
         int it = 0;
         for (int t = blockIdx.x; t < total; t += gridDim.x, ++it) {
             const int buf = it & 1;
             const uint32_t use = uint32_t(it >> 1);
             const int m0 = (t / tiles_n) * BM, n0 = (t % tiles_n) * BN;
-            // this tile's scale / shift columns into shared memory
-            asm volatile("bar.sync 1, 128;" ::: "memory");
-            for (int c = et; c < BN; c += 128) {
-                const int n = n0 + c;
-                ep_scale[c] = n < N ? __ldg(scale + n) : 0.f;
-                ep_shift[c] = n < N ? __ldg(shift + n) : 0.f;
-            }
             const int64_t row0 = int64_t(m0) + quarter * 32;
             // skip input of one 32-column chunk in the coalesced layout:
             // piece i of this lane = 8 columns (c8) of row r
@@ -324,33 +323,51 @@ __global__ void __launch_bounds__(kThreads, 1) tc_layer_kernel(
                 }
             };
             uint4 rr[4];
-            if constexpr (OUT_BF16) load_skip(0, rr);    // in flight while waiting for the tile
+            if constexpr (OUT_BF16) load_skip(half * 32, rr);   // in flight while waiting for the tile
             // the wait result is voted on so that all epilogue warps leave
-            // the loop together (the named barrier above must never be
-            // left waiting for a warp that has gone)
+            // the loop together (the named barrier must never be left
+            // waiting for a warp that has gone)
             const bool ok = mbar_wait(tfull_bar(buf), use & 1u, kErrTmemFull);
             if (!epilogue_all(ok)) break;
             fence_after();
 #pragma unroll 1
-            for (int c0 = 0; c0 < BN; c0 += 32) {
+            for (int c0 = half * 32; c0 < BN; c0 += 64) {
                 float v[32];
                 const uint32_t taddr = tmem_base + (uint32_t(quarter * 32) << 16) + uint32_t(buf * C::ACC_COLS + c0);
                 tmem_ld32(taddr, v);
                 const int n_base = n0 + c0;
-                if (n_base >= N) continue;                 // warp-uniform
+                if (n_base >= N) continue;                 // warp-uniform; later chunks are past N too
                 uint4 rn[4];
                 if constexpr (OUT_BF16) {
-                    if (c0 + 32 < BN) load_skip(c0 + 32, rn);   // next chunk's skip input
+                    if (c0 + 64 < BN) load_skip(c0 + 64, rn);   // next chunk's skip input
                 }
+                // per-column scale / shift (the same address in every lane: L1 broadcast)
+                if (n_base + 32 <= N) {
+                    const float4* sc4 = reinterpret_cast<const float4*>(scale + n_base);
+                    const float4* sh4 = reinterpret_cast<const float4*>(shift + n_base);
 #pragma unroll
-                for (int i = 0; i < 32; ++i) {
-                    float z = fmaf(ep_scale[c0 + i], v[i], ep_shift[c0 + i]);
-                    if (relu) z = fmaxf(z, 0.f);
-                    v[i] = z;
+                    for (int j = 0; j < 8; ++j) {
+                        const float4 a = __ldg(sc4 + j), b = __ldg(sh4 + j);
+                        v[4 * j] = fmaf(a.x, v[4 * j], b.x);
+                        v[4 * j + 1] = fmaf(a.y, v[4 * j + 1], b.y);
+                        v[4 * j + 2] = fmaf(a.z, v[4 * j + 2], b.z);
+                        v[4 * j + 3] = fmaf(a.w, v[4 * j + 3], b.w);
+                    }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) {
+                        const int n = n_base + i;
+                        v[i] = n < N ? fmaf(__ldg(scale + n), v[i], __ldg(shift + n)) : 0.f;
+                    }
                 }
-                float4* srow = reinterpret_cast<float4*>(stage + lane * kStageLd);
+                if (relu) {
 #pragma unroll
-                for (int j = 0; j < 8; ++j) srow[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+                    for (int i = 0; i < 32; ++i) v[i] = fmaxf(v[i], 0.f);
+                }
+                float4* srow = reinterpret_cast<float4*>(stage + lane * 32);
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    srow[j ^ (lane & 7)] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
                 __syncwarp();
                 if constexpr (OUT_BF16) {
 #pragma unroll
@@ -359,8 +376,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_layer_kernel(
                         const int r = p >> 2, c8 = (p & 3) * 8;
                         const int64_t row = row0 + r;
                         if (row >= M || n_base + c8 >= N) continue;
-                        const float4 a = *reinterpret_cast<const float4*>(stage + r * kStageLd + c8);
-                        const float4 b = *reinterpret_cast<const float4*>(stage + r * kStageLd + c8 + 4);
+                        const float4* sr = reinterpret_cast<const float4*>(stage + r * 32);
+                        const int q = c8 >> 2;
+                        const float4 a = sr[q ^ (r & 7)];
+                        const float4 b = sr[(q + 1) ^ (r & 7)];
                         float z[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
                         if (R) {
                             const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&rr[i]);
@@ -382,9 +401,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_layer_kernel(
                 } else {
                     // fp32 rows of arbitrary stride: a warp writes 32 consecutive columns of one row
                     const int n = n_base + lane;
+                    const int q = lane >> 2, e = lane & 3;
                     for (int r = 0; r < 32; ++r) {
                         const int64_t row = row0 + r;
-                        if (row < M && n < N) static_cast<float*>(Cout)[row * ldc + n] = stage[r * kStageLd + lane];
+                        if (row < M && n < N)
+                            static_cast<float*>(Cout)[row * ldc + n] = stage[r * 32 + ((q ^ (r & 7)) << 2) + e];
                     }
                 }
                 __syncwarp();
