@@ -61,70 +61,95 @@ __device__ __forceinline__ T interp27(const T* c, int comp, int a, int b, int cz
     return lerp_axis(cz, f0, f1);
 }
 
-// Q1 basis on [0,1]^3 at 2x2x2 Gauss point q = qa + 2 qb + 4 qc.
-template <typename T>
-__device__ __forceinline__ T gpt(int i) {
-    return i ? T(0.5 + kGaussOff) : T(0.5 - kGaussOff);
-}
-template <typename T>
-__device__ __forceinline__ T basis(int k, int q) {
-    T r = T(1);
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        const T xi = gpt<T>((q >> d) & 1);
-        r *= ((k >> d) & 1) ? xi : T(1) - xi;
-    }
-    return r;
-}
-template <typename T>
-__device__ __forceinline__ T dbasis(int k, int q, int e) {
-    T r = T(1);
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        const T xi = gpt<T>((q >> d) & 1);
-        if (d == e)
-            r *= ((k >> d) & 1) ? T(1) : T(-1);
-        else
-            r *= ((k >> d) & 1) ? xi : T(1) - xi;
-    }
-    return r;
-}
-
 enum { MODE_RESIDUAL = 0, MODE_RHS = 1 };
+
+// A trilinear function on [0,1]^3 with nodal values f_k (k = k0 + 2 k1 +
+// 4 k2) is sum_S c_S phi_S with the monomials phi_S = prod_{d in S} xi_d (S a
+// bit mask over the axes).  to_monomials maps f to c in place (one
+// difference per axis pair); from_moments maps moments M_S = integrals
+// against phi_S back to integrals against the nodal basis,
+// R_k = sum_{S >= k} (-1)^{|S|-|k|} M_S, which is the transpose map.
+template <typename T>
+__device__ __forceinline__ void to_monomials(T (&c)[8]) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int S = 0; S < 8; ++S)
+            if (!(S & (1 << d))) c[S | (1 << d)] -= c[S];
+}
+template <typename T>
+__device__ __forceinline__ void from_moments(T (&c)[8]) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int S = 0; S < 8; ++S)
+            if (!(S & (1 << d))) c[S] -= c[S | (1 << d)];
+}
 
 // Element integrals of one fine cell with vertex coordinates x[k] and nodal
 // values u[k] (smem pointers with per-vertex strides 3 and 4), accumulated
-// into R[8][4].
+// into R[8][4], with the 2x2x2 Gauss rule:
 //   MODE_RESIDUAL: Galerkin part of A_h (Eq. (6) left-hand side):
 //     R_kc += w [ (m v_c + th conv_c) N_k + th nu Dv_c . g_k - p (g_k)_c ]
 //     R_k3 += w div(v) N_k
 //   MODE_RHS: right-hand side of Eq. (6) without force:
 //     R_kc += w [ (m v_c - (1-th) conv_c) N_k - (1-th) nu Dv_c . g_k ]
-// with g_k = J^{-T} grad_ref N_k and w = det J / 8.  The gradient terms are
-// applied in reference coordinates: Dv_c . g_k - p (g_k)_c =
-// sum_e dN_k/dxi_e * Fhat_ce with Fhat_ce = sum_d Jinv_ed (coef Dv_cd - p delta_cd).
+// with g_k = J^{-T} grad_ref N_k and w = det J / 8.  Geometry and fields are
+// evaluated from their monomial coefficients (J and the reference gradient
+// in 4 terms each); the gradient terms are applied in reference coordinates,
+// Dv_c . g_k - p (g_k)_c = sum_e dN_k/dxi_e Fhat_ce / w with
+// Fhat_ce = w sum_d Jinv_ed (coef Dv_cd - p delta_cd), and the test
+// functions enter through the moments of the monomials.
 template <typename T, int MODE>
 __device__ __forceinline__ void element(const T* const (&xs)[8], const T* const (&us)[8], T (&R)[8][4],
                                         T m, T th, T nu) {
+    T X[3][8], U[4][8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) X[d][k] = xs[k][d];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) U[c][k] = (MODE == MODE_RESIDUAL || c < 3) ? us[k][c] : T(0);
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) to_monomials(X[d]);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) to_monomials(U[c]);
+    T M[4][8];
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int S = 0; S < 8; ++S) M[c][S] = T(0);
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-        T J[3][3];
+        const T x0 = (q & 1) ? T(0.5 + kGaussOff) : T(0.5 - kGaussOff);
+        const T x1 = (q & 2) ? T(0.5 + kGaussOff) : T(0.5 - kGaussOff);
+        const T x2 = (q & 4) ? T(0.5 + kGaussOff) : T(0.5 - kGaussOff);
+        auto val = [&](const T (&c)[8]) {
+            return c[0] + c[1] * x0 + c[2] * x1 + c[3] * (x0 * x1) + c[4] * x2 + c[5] * (x0 * x2) + c[6] * (x1 * x2) +
+                   c[7] * (x0 * x1 * x2);
+        };
+        auto d0 = [&](const T (&c)[8]) { return c[1] + c[3] * x1 + c[5] * x2 + c[7] * (x1 * x2); };
+        auto d1 = [&](const T (&c)[8]) { return c[2] + c[3] * x0 + c[6] * x2 + c[7] * (x0 * x2); };
+        auto d2 = [&](const T (&c)[8]) { return c[4] + c[5] * x0 + c[6] * x1 + c[7] * (x0 * x1); };
+        T J[3][3], Dr[3][3], v[3];   // J[d][e] = dx_d/dxi_e, Dr[c][e] = dv_c/dxi_e
 #pragma unroll
-        for (int d = 0; d < 3; ++d)
-#pragma unroll
-            for (int e = 0; e < 3; ++e) {
-                T s = T(0);
-#pragma unroll
-                for (int k = 0; k < 8; ++k) s += xs[k][d] * dbasis<T>(k, q, e);
-                J[d][e] = s;
-            }
+        for (int d = 0; d < 3; ++d) {
+            J[d][0] = d0(X[d]);
+            J[d][1] = d1(X[d]);
+            J[d][2] = d2(X[d]);
+            Dr[d][0] = d0(U[d]);
+            Dr[d][1] = d1(U[d]);
+            Dr[d][2] = d2(U[d]);
+            v[d] = val(U[d]);
+        }
+        const T p = MODE == MODE_RESIDUAL ? val(U[3]) : T(0);
         const T c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
         const T c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
         const T c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
         const T det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
         const T idet = T(1) / det;
-        // Jinv[e][d] = d xi_e / d x_d
-        T Ji[3][3];
+        T Ji[3][3];   // Jinv[e][d] = d xi_e / d x_d
         Ji[0][0] = c00 * idet;
         Ji[1][0] = c01 * idet;
         Ji[2][0] = c02 * idet;
@@ -135,59 +160,63 @@ __device__ __forceinline__ void element(const T* const (&xs)[8], const T* const 
         Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) * idet;
         Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) * idet;
         const T w = det * T(0.125);
-
-        T v[3] = {T(0), T(0), T(0)}, p = T(0);
-        T Dr[3][3];   // d v_c / d xi_e
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-#pragma unroll
-            for (int e = 0; e < 3; ++e) Dr[c][e] = T(0);
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const T Nk = basis<T>(k, q);
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const T uk = us[k][c];
-                v[c] += Nk * uk;
-#pragma unroll
-                for (int e = 0; e < 3; ++e) Dr[c][e] += uk * dbasis<T>(k, q, e);
-            }
-            if (MODE == MODE_RESIDUAL) p += Nk * us[k][3];
-        }
         T Dv[3][3];   // d v_c / d x_d
 #pragma unroll
         for (int c = 0; c < 3; ++c)
 #pragma unroll
             for (int d = 0; d < 3; ++d) Dv[c][d] = Dr[c][0] * Ji[0][d] + Dr[c][1] * Ji[1][d] + Dr[c][2] * Ji[2][d];
-        T a[3], F[3][3];
-        const T visc = (MODE == MODE_RESIDUAL ? th : th - T(1)) * nu * w;
+        const T tc = MODE == MODE_RESIDUAL ? th : th - T(1);
+        const T visc = tc * nu * w;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const T conv = v[0] * Dv[c][0] + v[1] * Dv[c][1] + v[2] * Dv[c][2];
-            a[c] = w * (m * v[c] + (MODE == MODE_RESIDUAL ? th : th - T(1)) * conv);
+            const T a = w * (m * v[c] + tc * conv);
             T G[3];
 #pragma unroll
             for (int d = 0; d < 3; ++d) G[d] = visc * Dv[c][d] - (MODE == MODE_RESIDUAL && d == c ? w * p : T(0));
-#pragma unroll
-            for (int e = 0; e < 3; ++e) F[c][e] = Ji[e][0] * G[0] + Ji[e][1] * G[1] + Ji[e][2] * G[2];
+            const T F0 = Ji[0][0] * G[0] + Ji[0][1] * G[1] + Ji[0][2] * G[2];
+            const T F1 = Ji[1][0] * G[0] + Ji[1][1] * G[1] + Ji[1][2] * G[2];
+            const T F2 = Ji[2][0] * G[0] + Ji[2][1] * G[1] + Ji[2][2] * G[2];
+            // a phi_S + Fhat . grad_ref phi_S for the 8 monomials
+            M[c][0] += a;
+            M[c][1] += a * x0 + F0;
+            M[c][2] += a * x1 + F1;
+            M[c][3] += a * (x0 * x1) + F0 * x1 + F1 * x0;
+            M[c][4] += a * x2 + F2;
+            M[c][5] += a * (x0 * x2) + F0 * x2 + F2 * x0;
+            M[c][6] += a * (x1 * x2) + F1 * x2 + F2 * x1;
+            M[c][7] += a * (x0 * x1 * x2) + F0 * (x1 * x2) + F1 * (x0 * x2) + F2 * (x0 * x1);
         }
-        const T wdiv = w * (Dv[0][0] + Dv[1][1] + Dv[2][2]);
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const T Nk = basis<T>(k, q);
-            const T d0 = dbasis<T>(k, q, 0), d1 = dbasis<T>(k, q, 1), d2 = dbasis<T>(k, q, 2);
-#pragma unroll
-            for (int c = 0; c < 3; ++c) R[k][c] += a[c] * Nk + F[c][0] * d0 + F[c][1] * d1 + F[c][2] * d2;
-            if (MODE == MODE_RESIDUAL) R[k][3] += wdiv * Nk;
+        if (MODE == MODE_RESIDUAL) {
+            const T s = w * (Dv[0][0] + Dv[1][1] + Dv[2][2]);
+            M[3][0] += s;
+            M[3][1] += s * x0;
+            M[3][2] += s * x1;
+            M[3][3] += s * (x0 * x1);
+            M[3][4] += s * x2;
+            M[3][5] += s * (x0 * x2);
+            M[3][6] += s * (x1 * x2);
+            M[3][7] += s * (x0 * x1 * x2);
         }
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        from_moments(M[c]);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) R[k][c] += M[c][k];
     }
 }
 
 constexpr int kPatchesPerBlock = 8;   // 8 fine cells each -> 64 threads
 
 // One thread per fine cell; 8 consecutive threads form a patch.
+// 128 registers (8 blocks of 64 threads per SM) for float: the element's
+// arithmetic is latency-bound at fewer warps
+template <typename T>
+constexpr int patch_min_blocks() { return sizeof(T) == 4 ? 8 : 4; }
+
 template <typename T, int MODE>
-__global__ void __launch_bounds__(64) patch_operator_kernel(
+__global__ void __launch_bounds__(64, patch_min_blocks<T>()) patch_operator_kernel(
     int64_t nc, const int32_t* __restrict__ cells, const int32_t* __restrict__ patch_map,
     const T* __restrict__ xyz, const T* __restrict__ xc, const T* __restrict__ dfine, T m, T th, T nu,
     T* __restrict__ partial, T* __restrict__ partial_c) {
@@ -216,8 +245,15 @@ __global__ void __launch_bounds__(64) patch_operator_kernel(
     if (active) {
         for (int iota = t; iota < 27; iota += 8) {
             const int a = iota % 3, b = (iota / 3) % 3, c = iota / 9;
+            // coordinates relative to corner 0 (the element needs only
+            // differences; this keeps them exact in float)
 #pragma unroll
-            for (int d = 0; d < 3; ++d) s_nx[lp][iota][d] = interp27<T, 3>(&s_cx[lp][0][0], d, a, b, c);
+            for (int d = 0; d < 3; ++d) {
+                T cr[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) cr[k] = s_cx[lp][k][d] - s_cx[lp][0][d];
+                s_nx[lp][iota][d] = interp27<T, 1>(cr, 0, a, b, c);
+            }
 #pragma unroll
             for (int d = 0; d < 4; ++d) s_nu[lp][iota][d] = interp27<T, 4>(&s_cu[lp][0][0], d, a, b, c);
             if (MODE == MODE_RHS) {   // corrected velocity x~ + d
