@@ -13,9 +13,10 @@
 //               from one thread; tcgen05.commit frees stages / publishes tiles
 //   warps 2..9  epilogue: warp w reads TMEM lanes 32 (w % 4) ..; the two
 //               warps of a lane quarter take alternate 32-column chunks
-//               (tcgen05.ld 32 lanes x 32 columns), scale/shift/ReLU/skip,
-//               vector stores; two warps per scheduler hide each other's
-//               TMEM and memory latency
+//               (tcgen05.ld 32 lanes x 32 columns), scale/shift/ReLU; bf16
+//               outputs go through a swizzled 32 x 32 shared-memory box to a
+//               TMA store, and the skip input comes in the same way by a TMA
+//               load, so no lane issues global loads or stores per element
 // Two TMEM accumulators let the epilogue of one tile overlap the MMAs of
 // the next.  Every mbarrier wait is bounded (~1 s of %globaltimer); on
 // expiry the thread records an error code in tc_error, stops issuing work,
@@ -33,7 +34,7 @@ __device__ int tc_error = 0;   // 0 ok; otherwise which wait expired (see TcErr)
 
 namespace {
 
-enum TcErr { kErrFull = 1, kErrEmpty = 2, kErrTmemFull = 3, kErrTmemEmpty = 4, kErrDrain = 5 };
+enum TcErr { kErrFull = 1, kErrEmpty = 2, kErrTmemFull = 3, kErrTmemEmpty = 4, kErrDrain = 5, kErrSkip = 6 };
 
 constexpr int BM = 128;
 constexpr int BK = 64;                 // 64 bf16 = 128 bytes = one swizzle row
@@ -111,6 +112,21 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
         : "memory");
 }
 
+// Shared -> global tiled copy (bulk-group completion); coordinates past the
+// tensor's extent are not written.
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, uint32_t src, int c0, int c1) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];"
+                 ::"l"(reinterpret_cast<uint64_t>(map)), "r"(src), "r"(c0), "r"(c1)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// the source shared memory of every committed store has been read
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// every committed store is complete
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// generic-proxy writes to shared memory become visible to the async proxy (TMA)
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
 // Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
 // 128 bytes, 8-row core-matrix groups 1024 bytes apart.
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
@@ -168,18 +184,24 @@ struct Cfg {
     static constexpr int A_BYTES = BM * BK * 2;
     static constexpr int B_BYTES = BN * BK * 2;
     static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-    static constexpr int STAGES = (192 * 1024) / STAGE_BYTES > 8 ? 8 : (192 * 1024) / STAGE_BYTES;
     static constexpr int ACC_COLS = BN <= 128 ? 128 : 256;      // TMEM columns per accumulator
     static constexpr int TMEM_COLS = 2 * ACC_COLS;              // power of two >= 32
-    static constexpr int BAR_BYTES = ((2 * STAGES + 5) * 8 + 16 + 127) / 128 * 128;   // keeps what follows aligned
-    static constexpr int EP_BYTES = kEpiWarps * 32 * 32 * 4;             // one 32 x 32 fp32 block per epilogue warp
-    static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + BAR_BYTES + EP_BYTES;
-    static_assert(SMEM <= 227 * 1024, "shared memory per CTA");
+    // per epilogue warp 4 KB: bf16 output box + skip box (2 KB each), or
+    // one 32 x 32 fp32 staging block
+    static constexpr int EP_WARP_BYTES = 4096;
+    static constexpr int EP_BYTES = kEpiWarps * EP_WARP_BYTES;
+    static constexpr int BAR_BYTES = 256;   // (2 STAGES + 5) barriers, TMEM slot (16), kEpiWarps skip barriers
+    static constexpr int STAGES_FIT = (227 * 1024 - 1024 - BAR_BYTES - EP_BYTES) / STAGE_BYTES;
+    static constexpr int STAGES = STAGES_FIT > 8 ? 8 : STAGES_FIT;
+    static constexpr int SMEM = STAGES * STAGE_BYTES + EP_BYTES + BAR_BYTES + 1024;
+    static_assert(STAGES >= 2 && SMEM <= 227 * 1024, "shared memory per CTA");
+    static_assert((2 * STAGES + 5) * 8 + 16 + kEpiWarps * 8 <= BAR_BYTES, "barrier area");
 };
 
 template <int BN, bool OUT_BF16>
 __global__ void __launch_bounds__(kThreads, 1) tc_layer_kernel(
     const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmW,
+    const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmR,
     const float* __restrict__ scale, const float* __restrict__ shift, void* __restrict__ Cout, int64_t ldc,
     const __nv_bfloat16* __restrict__ R, int64_t ldr, int M, int N, int K, int relu) {
     using C = Cfg<BN>;
@@ -187,15 +209,17 @@ __global__ void __launch_bounds__(kThreads, 1) tc_layer_kernel(
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;            // 1024-aligned stage buffers
     uint8_t* gbase = smem_raw + (base - raw);
-    const uint32_t bars = base + C::STAGES * C::STAGE_BYTES;
+    const uint32_t ep_base = base + C::STAGES * C::STAGE_BYTES;        // 1024-aligned, 4 KB per epilogue warp
+    float* ep_stage = reinterpret_cast<float*>(gbase + C::STAGES * C::STAGE_BYTES);
+    const uint32_t bars = ep_base + C::EP_BYTES;
     auto full_bar = [&](int s) { return bars + 8u * s; };
     auto empty_bar = [&](int s) { return bars + 8u * (C::STAGES + s); };
     auto tfull_bar = [&](int b) { return bars + 8u * (2 * C::STAGES + b); };
     auto tempty_bar = [&](int b) { return bars + 8u * (2 * C::STAGES + 2 + b); };
     const uint32_t done_bar = bars + 8u * (2 * C::STAGES + 4);
-    volatile uint32_t* tmem_slot =
-        reinterpret_cast<volatile uint32_t*>(gbase + C::STAGES * C::STAGE_BYTES + (2 * C::STAGES + 5) * 8);
-    float* ep_stage = reinterpret_cast<float*>(gbase + C::STAGES * C::STAGE_BYTES + C::BAR_BYTES);
+    volatile uint32_t* tmem_slot = reinterpret_cast<volatile uint32_t*>(
+        gbase + C::STAGES * C::STAGE_BYTES + C::EP_BYTES + (2 * C::STAGES + 5) * 8);
+    auto skip_bar = [&](int w) { return bars + 8u * (2 * C::STAGES + 5) + 16u + 8u * w; };
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -208,6 +232,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_layer_kernel(
             mbar_init(tempty_bar(b), kEpiThreads);
         }
         mbar_init(done_bar, 1);
+        for (int w = 0; w < kEpiWarps; ++w) mbar_init(skip_bar(w), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmW)) : "memory");
@@ -294,36 +319,33 @@ __global__ void __launch_bounds__(kThreads, 1) tc_layer_kernel(
         mbar_wait(done_bar, 0, kErrDrain);
     } else if (warp >= 2) {
         // ---------------- epilogue: warp w reads TMEM lanes 32 (w % 4) ..
-        // and the 32-column chunks c0 = 32 half, 32 half + 64, ...  Each
-        // 32 x 32 block goes TMEM -> registers (scale, shift, ReLU) -> shared
-        // memory -> coalesced global stores (8 rows x 64 bytes per warp
-        // instruction), with the skip input read the same way.  The staged
-        // block holds row r's float4 number q at q ^ (r & 7): conflict-free
-        // both when a lane writes its row and when 8 lanes read 2 rows.
+        // (its 32 rows) and the 32-column chunks c0 = 32 half, 32 half + 64, ...
         const int quarter = warp & 3;
         const int half = (warp - 2) >> 2;
-        float* stage = ep_stage + (warp - 2) * (32 * 32);
+        const int ew = warp - 2;
+        float* stage = ep_stage + ew * (C::EP_WARP_BYTES / 4);          // fp32 output
+        const uint32_t obox = ep_base + uint32_t(ew * C::EP_WARP_BYTES);   // bf16 output box
+        const uint32_t rbox = obox + 2048u;                               // skip input box
+        const uint32_t rbar = skip_bar(ew);
+        const bool has_r = OUT_BF16 && R != nullptr;
+        uint32_t rphase = 0;
+        bool r_pending = false;
+        // TMA load of the skip box of chunk c0 of the tile at (m0, n0)
+        auto issue_skip = [&](int m0, int n0, int c0) {
+            if (lane == 0) {
+                mbar_arrive_expect_tx(rbar, 2048u);
+                tma_load_2d(rbox, &tmR, rbar, n0 + c0, m0 + quarter * 32);
+            }
+            r_pending = true;
+        };
         int it = 0;
         for (int t = blockIdx.x; t < total; t += gridDim.x, ++it) {
             const int buf = it & 1;
             const uint32_t use = uint32_t(it >> 1);
             const int m0 = (t / tiles_n) * BM, n0 = (t % tiles_n) * BN;
             const int64_t row0 = int64_t(m0) + quarter * 32;
-            // skip input of one 32-column chunk in the coalesced layout:
-            // piece i of this lane = 8 columns (c8) of row r
-            auto load_skip = [&](int c0, uint4 (&rr)[4]) {
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int p = lane + 32 * i;
-                    const int r = p >> 2, c8 = (p & 3) * 8;
-                    const int64_t row = row0 + r;
-                    const int n = n0 + c0 + c8;
-                    rr[i] = (R && row < M && n < N) ? __ldg(reinterpret_cast<const uint4*>(R + row * ldr + n))
-                                                   : make_uint4(0, 0, 0, 0);
-                }
-            };
-            uint4 rr[4];
-            if constexpr (OUT_BF16) load_skip(half * 32, rr);   // in flight while waiting for the tile
+            const bool rows_live = row0 < M;                 // warp-uniform
+            if (has_r && rows_live && n0 + half * 32 < N) issue_skip(m0, n0, half * 32);   // in flight during the wait
             // the wait result is voted on so that all epilogue warps leave
             // the loop together (the named barrier must never be left
             // waiting for a warp that has gone)
@@ -336,11 +358,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_layer_kernel(
                 const uint32_t taddr = tmem_base + (uint32_t(quarter * 32) << 16) + uint32_t(buf * C::ACC_COLS + c0);
                 tmem_ld32(taddr, v);
                 const int n_base = n0 + c0;
-                if (n_base >= N) continue;                 // warp-uniform; later chunks are past N too
-                uint4 rn[4];
-                if constexpr (OUT_BF16) {
-                    if (c0 + 64 < BN) load_skip(c0 + 64, rn);   // next chunk's skip input
-                }
+                // warp-uniform: later chunks are past N too; rows past M have nothing to store
+                if (n_base >= N || !rows_live) continue;
                 // per-column scale / shift (the same address in every lane: L1 broadcast)
                 if (n_base + 32 <= N) {
                     const float4* sc4 = reinterpret_cast<const float4*>(scale + n_base);
@@ -364,55 +383,86 @@ __global__ void __launch_bounds__(kThreads, 1) tc_layer_kernel(
 #pragma unroll
                     for (int i = 0; i < 32; ++i) v[i] = fmaxf(v[i], 0.f);
                 }
-                float4* srow = reinterpret_cast<float4*>(stage + lane * 32);
-#pragma unroll
-                for (int j = 0; j < 8; ++j)
-                    srow[j ^ (lane & 7)] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
-                __syncwarp();
                 if constexpr (OUT_BF16) {
+                    // A 32 x 32 bf16 box in shared memory, as the 64-byte TMA
+                    // swizzle lays it out: row r (this lane) at r * 64, its
+                    // 16-byte piece j at piece j ^ ((r >> 1) & 3); both the
+                    // row writes and the row reads are bank-conflict-free.
+                    const uint32_t row_off = uint32_t(lane) * 64u;
+                    const uint32_t sw = uint32_t((lane >> 1) & 3);
+                    if (has_r) {
+                        if (!mbar_wait(rbar, rphase, kErrSkip)) { /* recorded; values are garbage */ }
+                        rphase ^= 1u;
+                        r_pending = false;
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const int p = lane + 32 * i;
-                        const int r = p >> 2, c8 = (p & 3) * 8;
-                        const int64_t row = row0 + r;
-                        if (row >= M || n_base + c8 >= N) continue;
-                        const float4* sr = reinterpret_cast<const float4*>(stage + r * 32);
-                        const int q = c8 >> 2;
-                        const float4 a = sr[q ^ (r & 7)];
-                        const float4 b = sr[(q + 1) ^ (r & 7)];
-                        float z[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-                        if (R) {
-                            const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&rr[i]);
+                        for (int j = 0; j < 4; ++j) {
+                            uint4 r;
+                            asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
+                                         : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+                                         : "r"(rbox + row_off + ((uint32_t(j) ^ sw) << 4)));
+                            const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&r);
 #pragma unroll
                             for (int e = 0; e < 4; ++e) {
                                 const float2 f = __bfloat1622float2(h[e]);
-                                z[2 * e] += f.x;
-                                z[2 * e + 1] += f.y;
+                                v[8 * j + 2 * e] += f.x;
+                                v[8 * j + 2 * e + 1] += f.y;
                             }
                         }
-                        uint4 o;
-                        __nv_bfloat162* ho = reinterpret_cast<__nv_bfloat162*>(&o);
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) ho[e] = __floats2bfloat162_rn(z[2 * e], z[2 * e + 1]);
-                        *reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(Cout) + row * ldc + n_base + c8) = o;
+                        __syncwarp();                      // every lane has read the skip box
+                        if (c0 + 64 < BN && n_base + 64 < N) issue_skip(m0, n0, c0 + 64);
                     }
+                    // the previous store must have read the output box
+                    if (lane == 0) bulk_wait_read();
+                    __syncwarp();
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) rr[i] = rn[i];
+                    for (int j = 0; j < 4; ++j) {
+                        uint32_t o[4];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const __nv_bfloat162 hb = __floats2bfloat162_rn(v[8 * j + 2 * e], v[8 * j + 2 * e + 1]);
+                            o[e] = *reinterpret_cast<const uint32_t*>(&hb);
+                        }
+                        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};"
+                                     ::"r"(obox + row_off + ((uint32_t(j) ^ sw) << 4)), "r"(o[0]), "r"(o[1]),
+                                       "r"(o[2]), "r"(o[3])
+                                     : "memory");
+                    }
+                    fence_proxy_async();
+                    __syncwarp();
+                    if (lane == 0) {
+                        tma_store_2d(&tmC, obox, n_base, int(row0));
+                        bulk_commit();
+                    }
                 } else {
-                    // fp32 rows of arbitrary stride: a warp writes 32 consecutive columns of one row
+                    // fp32 rows of arbitrary stride: through a 32 x 32 block in
+                    // shared memory (row r's float4 number q at q ^ (r & 7),
+                    // conflict-free both ways), then a warp writes 32
+                    // consecutive columns of one row
+                    float4* srow = reinterpret_cast<float4*>(stage + lane * 32);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j)
+                        srow[j ^ (lane & 7)] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+                    __syncwarp();
                     const int n = n_base + lane;
                     const int q = lane >> 2, e = lane & 3;
                     for (int r = 0; r < 32; ++r) {
-                        const int64_t row = row0 + r;
-                        if (row < M && n < N)
-                            static_cast<float*>(Cout)[row * ldc + n] = stage[r * 32 + ((q ^ (r & 7)) << 2) + e];
+                        const int64_t rw = row0 + r;
+                        if (rw < M && n < N)
+                            static_cast<float*>(Cout)[rw * ldc + n] = stage[r * 32 + ((q ^ (r & 7)) << 2) + e];
                     }
+                    __syncwarp();
                 }
-                __syncwarp();
             }
             fence_before();
             mbar_arrive(tempty_bar(buf));
         }
+        // drain: a skip load still in flight (only after an early exit) and
+        // every output store must complete before the CTA exits
+        if (r_pending) mbar_wait(rbar, rphase, kErrDrain);
+        if constexpr (OUT_BF16) {
+            if (lane == 0) bulk_wait_all();
+        }
+        __syncwarp();
     }
     fence_before();
     __syncthreads();
@@ -443,16 +493,19 @@ EncodeTiledFn encode_fn() {
     return fn;
 }
 
-// 2D bf16 tensor [rows][cols] with row stride ld (elements), box [box_rows][64].
-bool make_map(CUtensorMap* map, const void* ptr, int64_t rows, int64_t cols, int64_t ld, int box_rows) {
+// 2D bf16 tensor [rows][cols] with row stride ld (elements), box
+// [box_rows][box_cols]: operand boxes are 64 columns (128 bytes, 128-byte
+// swizzle), epilogue boxes 32 x 32 (64 bytes, 64-byte swizzle).
+bool make_map(CUtensorMap* map, const void* ptr, int64_t rows, int64_t cols, int64_t ld, int box_rows,
+              int box_cols = BK, CUtensorMapSwizzle swz = CU_TENSOR_MAP_SWIZZLE_128B) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return false;
     cuuint64_t dims[2] = {cuuint64_t(cols), cuuint64_t(rows)};
     cuuint64_t strides[1] = {cuuint64_t(ld * 2)};
-    cuuint32_t box[2] = {cuuint32_t(BK), cuuint32_t(box_rows)};
+    cuuint32_t box[2] = {cuuint32_t(box_cols), cuuint32_t(box_rows)};
     cuuint32_t estr[2] = {1, 1};
     return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, estr,
-              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -479,12 +532,16 @@ cudaError_t launch_tc(const __nv_bfloat16* A, int64_t lda, const __nv_bfloat16* 
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    CUtensorMap ta, tw;
+    CUtensorMap ta, tw, tc = {}, tr = {};
     if (!make_map(&ta, A, M, K, lda, BM) || !make_map(&tw, W, n_rows_w, K, ldw, BN)) return cudaErrorInvalidValue;
+    // bf16 output and skip input as [M][N] tensors in 32 x 32 boxes (the
+    // store clips at M and N)
+    if (OUT_BF16 && !make_map(&tc, C, M, N, ldc, 32, 32, CU_TENSOR_MAP_SWIZZLE_64B)) return cudaErrorInvalidValue;
+    if (OUT_BF16 && R && !make_map(&tr, R, M, N, ldr, 32, 32, CU_TENSOR_MAP_SWIZZLE_64B)) return cudaErrorInvalidValue;
     const int64_t tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
     const int grid = int(std::min<int64_t>(tiles, sm_count()));
-    tc_layer_kernel<BN, OUT_BF16><<<grid, kThreads, Cf::SMEM, s>>>(ta, tw, scale, shift, C, ldc, R, ldr, int(M), N, K,
-                                                                    relu ? 1 : 0);
+    tc_layer_kernel<BN, OUT_BF16><<<grid, kThreads, Cf::SMEM, s>>>(ta, tw, tc, tr, scale, shift, C, ldc, R, ldr, int(M),
+                                                                    N, K, relu ? 1 : 0);
     return cudaGetLastError();
 }
 
