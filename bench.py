@@ -34,6 +34,26 @@ UNIT = "steps/s"
 WIDTHS = (228, 1024, 1024, 1024, 1024, 81)
 NZ = 37
 DT, THETA = 0.005, 0.5
+STAGES = ("residual", "local_restrict", "network", "extend", "rhs_restrict")
+FP32_LANES_PER_SM = 128          # FP32 FMA lanes per SM (sm_100 family)
+# Work per patch of each stage (FP32 fields, BF16 network input), counted
+# from the kernels' arithmetic and the unique data they must move:
+#   residual: element integrals 64 Gauss points x ~274 FMA-pipe operations
+#     (monomial form) = 17.5k ops = 35.1 kflop, plus the gather of the
+#     per-patch partials (27 x 16 B written and read, CSR 27 x 4 B, F and r
+#     at ~8 unique fine nodes x 16 B each)
+#   local_restrict: x^L (~1 unique coarse node x 16 B), r (~8 x 16 B), edge
+#     lengths 48 B read; X row 256 x 2 B written
+#   extend: Y 81 x 4 B and the CSR 27 x 4 B read, d (~8 x 12 B) written
+#   rhs_restrict: element integrals 64 x ~253 ops = 32.4 kflop, gathers of
+#     the partials (27 x 16 B) and corner partials (8 x 16 B), b (~8 x 16 B)
+#     and b^L (~1 x 16 B) written
+STAGE_WORK = {
+    "residual": {"bound": "alu", "flop": 64 * 274 * 2, "bytes": 16 + 27 * 16 * 2 + 27 * 4 + 8 * 16 * 2},
+    "local_restrict": {"bound": "hbm", "bytes": 16 + 8 * 16 + 48 + 256 * 2},
+    "extend": {"bound": "hbm", "bytes": 81 * 4 + 27 * 4 + 8 * 12},
+    "rhs_restrict": {"bound": "alu", "flop": 64 * 253 * 2, "bytes": 16 + 8 * 12 + 27 * 16 * 2 + 8 * 16 * 2 + 8 * 16 + 16},
+}
 
 
 def _peaks():
@@ -75,6 +95,36 @@ def network_traffic(n_patches):
     if hashlib.sha256(src).hexdigest()[:16] != rec.get("source_sha256_16"):
         return None
     return rec["bytes_per_patch"] * n_patches
+
+
+def stage_rooflines(stage_ms, n_patches, peaks, peak_src, clocks):
+    """Per-stage time and the fraction of the roof that binds it: FP32 ALU
+    (152 SMs x 128 lanes x 2 flop x the median SM clock under load) for the
+    element-integral stages, HBM (measured copy bandwidth) for the gathers,
+    BF16 tensor (measured sustained) for the network."""
+    sm_ghz = (clocks.get("sm_mhz") or 2070.0) / 1000.0
+    alu_tflops = 152 * FP32_LANES_PER_SM * 2 * sm_ghz / 1000.0
+    out = {}
+    for name in STAGES:
+        ms = stage_ms[name]
+        e = {"ms": round(ms, 4)}
+        if name == "network":
+            tf = network_flops_per_patch() * n_patches / (ms / 1000.0) / 1e12
+            pk = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+            e.update(bound="tensor", achieved=round(tf, 1), peak=pk, unit="TFLOP/s", frac=round(tf / pk, 3))
+        else:
+            w = STAGE_WORK[name]
+            gbs = w["bytes"] * n_patches / (ms / 1000.0) / 1e9
+            if w["bound"] == "alu":
+                tf = w["flop"] * n_patches / (ms / 1000.0) / 1e12
+                e.update(bound="alu", achieved=round(tf, 2), peak=round(alu_tflops, 1), unit="TFLOP/s",
+                         frac=round(tf / alu_tflops, 3), hbm_gbs=round(gbs, 1))
+            else:
+                e.update(bound="hbm", achieved=round(gbs, 1), peak=peaks["hbm_gbs"], unit="GB/s",
+                         frac=round(gbs / peaks["hbm_gbs"], 3))
+        out[name] = e
+    out["peak_source"] = f"{peak_src} (HBM copy, BF16 sustained); FP32 ALU from unit counts x median SM clock"
+    return out
 
 
 def network_flops_per_patch(widths=WIDTHS):
@@ -169,17 +219,23 @@ def run_ours(args, rank, world, local_rank):
     ctx = p.ctx
 
     def step(F_in, F_out, ev=None):
-        # the stages of dnnmg_patch_step, called one by one so that the
-        # network stage can be timed on its own (same kernels, same order)
+        # the stages of dnnmg_patch_step, called one by one so that each
+        # stage can be timed on its own (same kernels, same order); ev[i]
+        # is recorded before stage i and ev[5] after the last
+        def mark(i):
+            if ev:
+                ev[i].record(stream)
+        mark(0)
         capi.dnnmg_residual(ctx, xc, F_in, r)
+        mark(1)
         capi.dnnmg_local_restrict(ctx, xc, r, X)
-        if ev:
-            ev[0].record(stream)
+        mark(2)
         capi.dnnmg_network(ctx, X, Y, nc)
-        if ev:
-            ev[1].record(stream)
+        mark(3)
         capi.dnnmg_extend(ctx, Y, d)
+        mark(4)
         capi.dnnmg_rhs_restrict(ctx, xc, d, F_out, bc)
+        mark(5)
 
     with torch.cuda.stream(stream):
         for i in range(args.warmup):
@@ -190,8 +246,7 @@ def run_ours(args, rank, world, local_rank):
             torch.distributed.barrier()
         torch.cuda.synchronize(dev)
         n0 = capi.dnnmg_launch_count(ctx)
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in range(args.steps)]
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
         with Clocks(local_rank) as clk:
@@ -205,7 +260,8 @@ def run_ours(args, rank, world, local_rank):
         if world > 1:
             torch.distributed.barrier()
         elapsed_ms = t0.elapsed_time(t1)
-        net_ms = [a.elapsed_time(b) for a, b in evs]
+        stage_ms = {name: statistics.mean(e[i].elapsed_time(e[i + 1]) for e in evs) for i, name in enumerate(STAGES)}
+        net_ms = [e[2].elapsed_time(e[3]) for e in evs]
 
     # end to end through the C ABI with host buffers (pinned)
     xc_p = torch.from_numpy(xc_h).pin_memory()
@@ -241,8 +297,29 @@ def run_ours(args, rank, world, local_rank):
                 "patches_per_s": round(nc * 1000.0 / ms, 1), "timed_steps": 1}
         q.close()
 
-    res = dict(elapsed_ms=elapsed_ms, net_ms=net_ms, launches=launches, clocks=clk.summary(),
-               e2e_s=e2e_s, nc=nc, nf=nf, nv=nv, fp64=fp64)
+    # the FP32 form (FP32 fields, FP32 SIMT network) of the same step
+    fp32 = None
+    if not args.no_fp64 and rank == 0:
+        q = PatchPath(m, nu, DT, THETA, "fp32", device=dev, stream=stream)
+        q.set_network(WIDTHS, Ws, ss, ts, skip=True)
+        xq, Fq = q.to_device(xc_h), q.to_device(F_h)
+        bfq, bcq = q.field(nf, 4), q.field(nv, 4)
+        with torch.cuda.stream(stream):
+            q.step(xq, Fq, bfq, bcq)
+            torch.cuda.synchronize(dev)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(3):
+                q.step(xq, Fq, bfq, bcq)
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+        ms = a.elapsed_time(b) / 3
+        fp32 = {"ms_per_step": round(ms, 3), "steps_per_s": round(1000.0 / ms, 3),
+                "patches_per_s": round(nc * 1000.0 / ms, 1), "timed_steps": 3}
+        q.close()
+
+    res = dict(elapsed_ms=elapsed_ms, net_ms=net_ms, stage_ms=stage_ms, launches=launches, clocks=clk.summary(),
+               e2e_s=e2e_s, nc=nc, nf=nf, nv=nv, fp64=fp64, fp32=fp32)
     p.close()
     return res
 
@@ -490,6 +567,8 @@ def main():
                      "network_ms_per_step": net_ms, "network_share": net_ms / ms},
         "e2e": {"value": world * K / res["e2e_s"] if res["e2e_s"] > 0 else None, "unit": UNIT,
                 "h2d_bytes_per_step": (nv + nf) * 16, "d2h_bytes_per_step": (nf + nv) * 16},
+        "stages": stage_rooflines(res["stage_ms"], nc, peaks, peak_src, res["clocks"]),
+        "fp32_form": res["fp32"],
         "gpu_launches": res["launches"],
         "clocks": res["clocks"],
         "fp64_plain": res["fp64"],

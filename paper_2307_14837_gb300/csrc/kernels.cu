@@ -223,8 +223,11 @@ __global__ void __launch_bounds__(64, patch_min_blocks<T>()) patch_operator_kern
     __shared__ T s_cx[kPatchesPerBlock][8][3];    // corner coordinates
     __shared__ T s_cu[kPatchesPerBlock][8][4];    // corner values
     __shared__ T s_nx[kPatchesPerBlock][27][3];   // patch node coordinates
-    __shared__ T s_nu[kPatchesPerBlock][27][4];   // patch node values
-    __shared__ T s_R[kPatchesPerBlock][8][8][4];  // per-cell contributions
+    __shared__ T s_nu[kPatchesPerBlock][27][5];   // patch node values (u, v, w, p; stride 5 spreads
+                                                  // the 8 nodes a cell reads over distinct banks)
+    // per-cell contributions, one padded row of 8 x 4 per cell: the 8 cells'
+    // threads store with a stride of 33 words (no bank conflicts)
+    __shared__ T s_R[kPatchesPerBlock][8][33];
 
     const int lp = threadIdx.x >> 3;   // patch within block
     const int t = threadIdx.x & 7;     // child cell / corner
@@ -283,7 +286,7 @@ __global__ void __launch_bounds__(64, patch_min_blocks<T>()) patch_operator_kern
 #pragma unroll
         for (int k = 0; k < 8; ++k)
 #pragma unroll
-            for (int c = 0; c < 4; ++c) s_R[lp][t][k][c] = R[k][c];
+            for (int c = 0; c < 4; ++c) s_R[lp][t][4 * k + c] = R[k][c];
     }
     __syncthreads();
     // sum the children's contributions at each patch node, children in order
@@ -302,7 +305,7 @@ __global__ void __launch_bounds__(64, patch_min_blocks<T>()) patch_operator_kern
                     const int child = ci + 2 * cj + 4 * ck;
                     const int vert = i2 + 2 * j2 + 4 * k2;
 #pragma unroll
-                    for (int d = 0; d < 4; ++d) acc[d] += s_R[lp][child][vert][d];
+                    for (int d = 0; d < 4; ++d) acc[d] += s_R[lp][child][4 * vert + d];
                 }
             }
         }
