@@ -37,8 +37,9 @@
  *       d         [n_fine_nodes][3]       velocity correction
  *       b_coarse  [n_coarse_vertices][4]
  *       X         [n_patches][n_in_padded]: columns 0..107 x~ at the 27 patch
- *                 nodes (u,v,w,p), 108..215 r likewise, 216..227 edge
- *                 lengths, 228.. zero
+ *                 nodes (u,v,w,p), 108..215 r likewise, 216.. the
+ *                 geometry features (12 edge lengths, or 24 features, see
+ *                 dnnmg_params.features), zero after them
  *       Y         [n_patches][81]: 27 x (u, v, w)
  *     Patch node iota = a + 3b + 9c, (a,b,c) in {0,1,2}^3 along the coarse
  *     cell's reference axes.
@@ -97,7 +98,12 @@ typedef struct {
     double dt;          /* time step k */
     double theta;
     int32_t precision;  /* dnnmg_precision */
-    int32_t reserved;   /* must be 0 */
+    int32_t features;   /* geometry features per patch in the network input
+                         * (Sec. 5.2): 0 or 12 = the 12 edge lengths (228
+                         * inputs); 24 = edge lengths, the 4 space diagonals
+                         * (vertex k to 7 - k) and per vertex the mean of the
+                         * 3 angles between the faces meeting there, in
+                         * radians (240 inputs, as in Table 2) */
 } dnnmg_params;
 
 /* Patch network of Sec. 4 in inference form: layer i computes
@@ -105,7 +111,7 @@ typedef struct {
  * skip != 0 and i >= 1 (0-based) and widths match, add their input. */
 typedef struct {
     int32_t n_layers;        /* number of weight matrices, >= 1 */
-    const int32_t* widths;   /* n_layers + 1 entries; widths[0] == 228, widths[n_layers] == 81 */
+    const int32_t* widths;   /* n_layers + 1 entries; widths[0] == n_in (228 or 240), widths[n_layers] == 81 */
     int32_t skip;
 } dnnmg_net_desc;
 
@@ -115,7 +121,7 @@ typedef struct {
     int64_t n_fine_nodes;
     int64_t n_coarse_edges;
     int64_t n_coarse_faces;
-    int32_t n_in;              /* 228 */
+    int32_t n_in;              /* 228, or 240 with 24 geometry features */
     int32_t n_in_padded;       /* row stride of X */
     int32_t n_out;             /* 81 */
     int32_t precision;
@@ -127,7 +133,8 @@ typedef enum {
     DNNMG_VALENCE = 1,      /* int32 [n_fine_nodes]: patches containing each node (1/mu) */
     DNNMG_FINE_KIND = 2,    /* int32 [n_fine_nodes]: boundary kind 0..3 */
     DNNMG_FINE_XYZ = 3,     /* double [n_fine_nodes][3] */
-    DNNMG_EDGE_LENGTHS = 4  /* double [n_patches][12] */
+    DNNMG_EDGE_LENGTHS = 4, /* double [n_patches][12] */
+    DNNMG_GEOMETRY = 5      /* double [n_patches][12 or 24]: the geometry features of the input row */
 } dnnmg_mesh_item;
 
 /* Build the level-(L+1) hierarchy of a coarse mesh on the host, upload it to
@@ -163,9 +170,10 @@ dnnmg_status dnnmg_set_stream(dnnmg_ctx* ctx, void* cuda_stream);
 /* Load the patch network (Sec. 4).  W[i] points to widths[i+1] x widths[i]
  * doubles (row-major), scale[i] / shift[i] to widths[i+1] doubles (NULL =
  * 1 / 0).  Host memory; copied and converted to the context's precision.
- * Synchronises the stream.  Errors: EINVAL (widths[0] != 228,
- * widths[n_layers] != 81, width > 4096 or not a multiple of 16 for hidden
- * layers in the BF16 form), ENOMEM, ECUDA. */
+ * Synchronises the stream.  Hidden widths need not be multiples of
+ * anything: K is zero-padded to 64 (BF16) or 16 (FP32/FP64) internally.
+ * Errors: EINVAL (widths[0] != n_in, widths[n_layers] != 81, a hidden
+ * width outside [1, 4096]), ENOMEM, ECUDA. */
 dnnmg_status dnnmg_set_network(dnnmg_ctx* ctx, const dnnmg_net_desc* net,
                                const double* const* W, const double* const* scale,
                                const double* const* shift);
@@ -333,7 +341,8 @@ dnnmg_status dnnmg_step_begin(dnnmg_ctx* ctx, const dnnmg_solver_params* prm, in
                               const double* b_coarse_dev, const void* F_dev, void* X_dev, dnnmg_solve_stats* stats);
 dnnmg_status dnnmg_step_end(dnnmg_ctx* ctx, const void* Y_dev, void* F_dev, double* b_coarse_dev);
 
-/* A network-only context for serving: no mesh; supports dnnmg_network (up
+/* A network-only context for serving: no mesh (the input width, 228 or 240,
+ * is widths[0]); supports dnnmg_network (up
  * to max_rows rows), dnnmg_set_network, dnnmg_set_stream, dnnmg_sync,
  * dnnmg_launch_count, dnnmg_destroy; every call that needs a mesh returns
  * DNNMG_EINVAL on it.  Weights as in dnnmg_set_network.  The context

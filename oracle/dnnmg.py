@@ -11,8 +11,9 @@ to a plain Newton-multigrid time step:
 
 Input row layout of X (the paper gives only the order x~, r, geometry):
 columns 0..107 are x~ at the 27 patch nodes, node-major (u, v, w, p);
-columns 108..215 the residual in the same order; 216..227 the 12 edge lengths
-of the coarse cell.  Output row Y[P]: 27 x (u, v, w) in the same node order;
+columns 108..215 the residual in the same order; 216.. the geometry features
+of the coarse cell: its 12 edge lengths (228 inputs), or with 24 features also
+its 4 diagonals and 8 mean face angles (240 inputs, Table 2).  Output row Y[P]: 27 x (u, v, w) in the same node order;
 the pressure outputs are absent (Table 2: N_out = 81).
 Dirichlet velocity nodes receive no correction.
 
@@ -46,10 +47,10 @@ def local_restriction(h, field: np.ndarray) -> np.ndarray:
     return out
 
 
-def gather(h, x_fine, r_fine) -> np.ndarray:
-    """Network input rows [N_c, 228]."""
+def gather(h, x_fine, r_fine, features: int = 12) -> np.ndarray:
+    """Network input rows [N_c, 216 + features]."""
     return np.concatenate([local_restriction(h, x_fine), local_restriction(h, r_fine),
-                           h.edge_lengths()], axis=1)
+                           h.geometry(features)], axis=1)
 
 
 def extend(h, Y) -> np.ndarray:
@@ -65,13 +66,14 @@ def extend(h, Y) -> np.ndarray:
     return d
 
 
-def hot_path_step(h, net, x_coarse, F, prm, level=None):
+def hot_path_step(h, net, x_coarse, F, prm, level=None, features: int = 12):
     """The patch-correction steps of Alg. 1 for one time step.  ``net`` = (Ws, scales,
-    shifts, skip).  Returns every intermediate as a dict."""
+    shifts, skip); ``features`` = geometry features per patch (12 or 24).
+    Returns every intermediate as a dict."""
     lev = level if level is not None else fine_level(h)
     x_f = transfer.prolongate(h, x_coarse)
     r = lev.residual(x_f, F, prm)
-    X = gather(h, x_f, r)
+    X = gather(h, x_f, r, features)
     Ws, ss, ts, skip = net
     Y = mlp.forward(X, Ws, ss, ts, skip=skip)
     d = extend(h, Y)

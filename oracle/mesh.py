@@ -226,6 +226,50 @@ class Hierarchy:
                 out[c, e] = np.sqrt(np.sum(d * d))
         return out
 
+    def diagonals(self) -> np.ndarray:
+        """The 4 diagonals of each coarse cell that join vertices sharing no
+        face (Sec. 5.2, network inputs): vertex k to vertex 7 - k, k = 0..3.
+        [N_c, 4]"""
+        out = np.empty((self.n_patches, 4))
+        for c in range(self.n_patches):
+            X = self.xyz_c[self.cells_c[c]]
+            for k in range(4):
+                out[c, k] = np.linalg.norm(X[7 - k] - X[k])
+        return out
+
+    def face_angles(self) -> np.ndarray:
+        """For each vertex of each coarse cell the mean of the 3 angles
+        between the cell's faces that meet at the vertex (Sec. 5.2, network
+        inputs), in radians.  Two faces through vertex v share one of the
+        three edges e at v; their angle is the angle between their normals at
+        v, e x u and e x w, where u and w are the other two edges at v (the
+        interior angle: u and w point into the cell's side of each face).
+        [N_c, 8], vertex order k = 0..7."""
+        out = np.empty((self.n_patches, 8))
+        for c in range(self.n_patches):
+            X = self.xyz_c[self.cells_c[c]]
+            for v in range(8):
+                edges = [X[v ^ (1 << a)] - X[v] for a in range(3)]
+                angles = []
+                for a in range(3):
+                    e, u, w = edges[a], edges[(a + 1) % 3], edges[(a + 2) % 3]
+                    n1, n2 = np.cross(e, u), np.cross(e, w)
+                    cs = np.dot(n1, n2) / (np.linalg.norm(n1) * np.linalg.norm(n2))
+                    angles.append(np.arccos(np.clip(cs, -1.0, 1.0)))
+                out[c, v] = np.mean(angles)
+        return out
+
+    def geometry(self, n_features: int = 12) -> np.ndarray:
+        """Geometry part of the network input row: the 12 edge lengths, or
+        with n_features = 24 the edge lengths, the 4 diagonals and the 8 mean
+        face angles (the three kinds of Sec. 5.2; Table 2's N_in = 240 =
+        2 x 108 + 24).  [N_c, n_features]"""
+        if n_features == 12:
+            return self.edge_lengths()
+        if n_features == 24:
+            return np.concatenate([self.edge_lengths(), self.diagonals(), self.face_angles()], axis=1)
+        raise ValueError("n_features must be 12 or 24")
+
     def fine_mesh(self) -> dict:
         """Level L+1 as a mesh in the same format as the input (cells come in
         patch groups of 8 children)."""

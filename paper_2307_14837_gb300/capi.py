@@ -16,7 +16,7 @@ import numpy as np
 from . import build as _build
 
 FP64, FP32, BF16 = 0, 1, 2
-PATCH_MAP, VALENCE, FINE_KIND, FINE_XYZ, EDGE_LENGTHS = 0, 1, 2, 3, 4
+PATCH_MAP, VALENCE, FINE_KIND, FINE_XYZ, EDGE_LENGTHS, GEOMETRY = 0, 1, 2, 3, 4, 5
 BUF_R, BUF_X, BUF_Y, BUF_D = 0, 1, 2, 3
 N_IN, N_OUT = 228, 81
 
@@ -35,7 +35,7 @@ class MeshDesc(ctypes.Structure):
 
 class Params(ctypes.Structure):
     _fields_ = [("nu", ctypes.c_double), ("dt", ctypes.c_double), ("theta", ctypes.c_double),
-                ("precision", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("precision", ctypes.c_int32), ("features", ctypes.c_int32)]
 
 
 class NetDesc(ctypes.Structure):
@@ -124,9 +124,10 @@ def _check(ctx, status):
 
 # -- thin wrappers with the C names ------------------------------------------
 
-def dnnmg_create(mesh, nu, dt, theta, precision, stream=None):
+def dnnmg_create(mesh, nu, dt, theta, precision, stream=None, features=12):
     """mesh: dict with xyz [nv,3] float64, cells [nc,8] int32, vertex_bc [nv] int32.
-    stream: a torch.cuda.Stream, an int handle, or None (default stream)."""
+    stream: a torch.cuda.Stream, an int handle, or None (default stream).
+    features: geometry features per patch, 12 (edge lengths) or 24."""
     lib = load()
     xyz = np.ascontiguousarray(mesh["xyz"], dtype=np.float64)
     cells = np.ascontiguousarray(mesh["cells"], dtype=np.int32)
@@ -134,7 +135,7 @@ def dnnmg_create(mesh, nu, dt, theta, precision, stream=None):
     desc = MeshDesc(int(xyz.shape[0]), xyz.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                     int(cells.shape[0]), cells.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                     bc.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
-    prm = Params(float(nu), float(dt), float(theta), int(precision), 0)
+    prm = Params(float(nu), float(dt), float(theta), int(precision), int(features))
     handle = _VP()
     s = getattr(stream, "cuda_stream", stream)
     _check(None, lib.dnnmg_create(ctypes.byref(desc), ctypes.byref(prm), s, ctypes.byref(handle)))
@@ -155,7 +156,8 @@ def dnnmg_get_mesh_data(ctx, item):
     sz = dnnmg_get_sizes(ctx)
     shape, dt = {PATCH_MAP: ((sz["n_patches"], 27), np.int32), VALENCE: ((sz["n_fine_nodes"],), np.int32),
                  FINE_KIND: ((sz["n_fine_nodes"],), np.int32), FINE_XYZ: ((sz["n_fine_nodes"], 3), np.float64),
-                 EDGE_LENGTHS: ((sz["n_patches"], 12), np.float64)}[item]
+                 EDGE_LENGTHS: ((sz["n_patches"], 12), np.float64),
+                 GEOMETRY: ((sz["n_patches"], sz["n_in"] - 216), np.float64)}[item]
     out = np.empty(shape, dtype=dt)
     _check(ctx, load().dnnmg_get_mesh_data(ctx, item, out.ctypes.data, out.nbytes))
     return out

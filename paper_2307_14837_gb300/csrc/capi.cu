@@ -57,6 +57,9 @@ size_t field_elem(int precision) { return precision == DNNMG_FP64 ? sizeof(doubl
 
 bool is_fp64(const dnnmg_ctx* c) { return c->precision == DNNMG_FP64; }
 
+// network inputs per patch: 2 x 27 x 4 node values + the geometry features
+int n_in(const dnnmg_ctx* c) { return c->host.n_geo == 24 ? kNInGeo24 : kNIn; }
+
 }  // namespace
 
 extern "C" {
@@ -91,13 +94,14 @@ dnnmg_status dnnmg_create(const dnnmg_mesh_desc* mesh, const dnnmg_params* param
     if (!out) return DNNMG_EINVAL;
     *out = nullptr;
     if (!mesh || !params) return DNNMG_EINVAL;
-    if (params->precision < DNNMG_FP64 || params->precision > DNNMG_BF16 || params->reserved != 0 ||
+    if (params->features != 0 && params->features != 12 && params->features != 24) return DNNMG_EINVAL;
+    if (params->precision < DNNMG_FP64 || params->precision > DNNMG_BF16 ||
         !(params->dt > 0.0) || !(params->nu >= 0.0) || !(params->theta >= 0.0 && params->theta <= 1.0))
         return DNNMG_EINVAL;
     dnnmg_ctx* ctx = new (std::nothrow) dnnmg_ctx();
     if (!ctx) return DNNMG_ENOMEM;
     std::string err;
-    dnnmg_status st = build_hierarchy(mesh, &ctx->host, &err);
+    dnnmg_status st = build_hierarchy(mesh, params->features == 24 ? 24 : 12, &ctx->host, &err);
     if (st != DNNMG_OK) {
         delete ctx;
         return st;
@@ -114,6 +118,7 @@ dnnmg_status dnnmg_create(const dnnmg_mesh_desc* mesh, const dnnmg_params* param
     dm.nv = h.nv;
     dm.nc = h.nc;
     dm.n_fine = h.n_fine;
+    dm.n_geo = h.n_geo;
     auto done = [&](dnnmg_status s) {
         if (s != DNNMG_OK) {
             dnnmg_destroy(ctx);
@@ -148,15 +153,15 @@ dnnmg_status dnnmg_create(const dnnmg_mesh_desc* mesh, const dnnmg_params* param
         double* pd;
         if ((st = upload(ctx, h.xyz_c.data(), h.xyz_c.size(), &pd)) != DNNMG_OK) return done(st);
         dm.xyz_d = pd;
-        if ((st = upload(ctx, h.edge_len.data(), h.edge_len.size(), &pd)) != DNNMG_OK) return done(st);
-        dm.edge_d = pd;
+        if ((st = upload(ctx, h.geo.data(), h.geo.size(), &pd)) != DNNMG_OK) return done(st);
+        dm.geo_d = pd;
     } else {
-        std::vector<float> xf(h.xyz_c.begin(), h.xyz_c.end()), ef(h.edge_len.begin(), h.edge_len.end());
+        std::vector<float> xf(h.xyz_c.begin(), h.xyz_c.end()), ef(h.geo.begin(), h.geo.end());
         float* pf;
         if ((st = upload(ctx, xf.data(), xf.size(), &pf)) != DNNMG_OK) return done(st);
         dm.xyz_f = pf;
         if ((st = upload(ctx, ef.data(), ef.size(), &pf)) != DNNMG_OK) return done(st);
-        dm.edge_f = pf;
+        dm.geo_f = pf;
     }
     const size_t fe = field_elem(ctx->precision);
     const size_t xe = ctx->precision == DNNMG_BF16 ? 2 : fe;
@@ -180,7 +185,7 @@ dnnmg_status dnnmg_get_sizes(const dnnmg_ctx* ctx, dnnmg_sizes* out) {
     out->n_fine_nodes = ctx->host.n_fine;
     out->n_coarse_edges = ctx->host.ne;
     out->n_coarse_faces = ctx->host.nf;
-    out->n_in = kNIn;
+    out->n_in = n_in(ctx);
     out->n_in_padded = kNInPad;
     out->n_out = kNOut;
     out->precision = ctx->precision;
@@ -197,7 +202,15 @@ dnnmg_status dnnmg_get_mesh_data(const dnnmg_ctx* ctx, int32_t item, void* host_
         case DNNMG_VALENCE: src = h.valence.data(); n = h.valence.size() * 4; break;
         case DNNMG_FINE_KIND: src = h.kind_f.data(); n = h.kind_f.size() * 4; break;
         case DNNMG_FINE_XYZ: src = h.xyz_f.data(); n = h.xyz_f.size() * 8; break;
-        case DNNMG_EDGE_LENGTHS: src = h.edge_len.data(); n = h.edge_len.size() * 8; break;
+        case DNNMG_EDGE_LENGTHS: {   // the first 12 of each patch's geometry features
+            n = size_t(h.nc) * 12 * 8;
+            if (bytes < n) return DNNMG_EINVAL;
+            double* dst = static_cast<double*>(host_buf);
+            for (int64_t c = 0; c < h.nc; ++c)
+                std::memcpy(dst + 12 * c, h.geo.data() + size_t(h.n_geo) * size_t(c), 12 * 8);
+            return DNNMG_OK;
+        }
+        case DNNMG_GEOMETRY: src = h.geo.data(); n = h.geo.size() * 8; break;
         default: return DNNMG_EINVAL;
     }
     if (bytes < n) return DNNMG_EINVAL;
@@ -215,12 +228,11 @@ dnnmg_status dnnmg_set_network(dnnmg_ctx* ctx, const dnnmg_net_desc* net, const 
                                const double* const* scale, const double* const* shift) {
     if (!ctx || !net || !W || !net->widths || net->n_layers < 1 || net->n_layers > 64) return DNNMG_EINVAL;
     const int L = net->n_layers;
-    if (net->widths[0] != kNIn || net->widths[L] != kNOut)
-        return fail(ctx, DNNMG_EINVAL, "network widths must start at 228 and end at 81");
+    if (net->widths[0] != n_in(ctx) || net->widths[L] != kNOut)
+        return fail(ctx, DNNMG_EINVAL, "network widths must start at the input width (228 or 240) and end at 81");
     for (int i = 1; i < L; ++i) {
         const int w = net->widths[i];
-        if (w < 16 || w > 4096 || w % 16)
-            return fail(ctx, DNNMG_EINVAL, "hidden widths must be multiples of 16 in [16, 4096]");
+        if (w < 1 || w > 4096) return fail(ctx, DNNMG_EINVAL, "hidden widths must be in [1, 4096]");
     }
     for (int i = 0; i < L; ++i)
         if (!W[i]) return DNNMG_EINVAL;
@@ -252,12 +264,12 @@ dnnmg_status dnnmg_set_network(dnnmg_ctx* ctx, const dnnmg_net_desc* net, const 
     for (int i = 0; i < L; ++i) {
         const bool bf16 = ctx->precision == DNNMG_BF16;
         // tensor-core layers read K in blocks of 64 and the last layer's W
-        // as a 96-row tile; padding is zero
-        ctx->kpad[i] = i == 0 ? kNInPad : (bf16 ? (ctx->widths[i] + 63) / 64 * 64 : ctx->widths[i]);
+        // as a 96-row tile, SIMT layers K in steps of 16; padding is zero
+        ctx->kpad[i] = i == 0 ? kNInPad : (bf16 ? (ctx->widths[i] + 63) / 64 * 64 : (ctx->widths[i] + 15) / 16 * 16);
         ctx->npad[i] = (bf16 && i == L - 1) ? 96 : ctx->widths[i + 1];
         if (i < L - 1) maxw = std::max(maxw, ctx->widths[i + 1]);
     }
-    if (ctx->precision == DNNMG_BF16) maxw = (maxw + 63) / 64 * 64;
+    maxw = ctx->precision == DNNMG_BF16 ? (maxw + 63) / 64 * 64 : (maxw + 15) / 16 * 16;
     dnnmg_status st;
     for (int i = 0; i < L; ++i) {
         const int N = ctx->npad[i], K = ctx->kpad[i], n_true = ctx->widths[i + 1], k_true = ctx->widths[i];
@@ -671,6 +683,7 @@ dnnmg_status dnnmg_net_create(const dnnmg_net_desc* net, const double* const* W,
     if (!ctx) return DNNMG_ENOMEM;
     ctx->net_only = true;
     ctx->net_capacity = max_rows;
+    ctx->host.n_geo = net && net->widths && net->widths[0] == kNInGeo24 ? 24 : 12;   // input width 228 or 240
     ctx->precision = precision;
     ctx->stream = static_cast<cudaStream_t>(cuda_stream);
     if (cudaGetDevice(&ctx->device) != cudaSuccess) {

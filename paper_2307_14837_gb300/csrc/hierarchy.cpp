@@ -84,7 +84,7 @@ LocalEntity local_entity(int iota) {
 
 }  // namespace
 
-dnnmg_status build_hierarchy(const dnnmg_mesh_desc* mesh, HostHierarchy* h, std::string* err) {
+dnnmg_status build_hierarchy(const dnnmg_mesh_desc* mesh, int n_geo, HostHierarchy* h, std::string* err) {
     if (!mesh || !mesh->xyz || !mesh->cell_vertices || !mesh->vertex_bc || mesh->n_vertices <= 0 ||
         mesh->n_cells <= 0) {
         *err = "mesh: null array or non-positive size";
@@ -274,17 +274,50 @@ dnnmg_status build_hierarchy(const dnnmg_mesh_desc* mesh, HostHierarchy* h, std:
         for (int64_t e = 0; e < 8 * nc; ++e) h->vert_idx[fill[h->cells[e]]++] = int32_t(e);
     }
 
-    // ---- geometry features: the 12 edge lengths of each coarse cell
-    h->edge_len.resize(size_t(12 * nc));
+    // ---- geometry features of each coarse cell (Sec. 5.2, network inputs):
+    // the 12 edge lengths; with n_geo = 24 also the 4 lengths of the space
+    // diagonals (vertex k to vertex 7 - k, k = 0..3) and, for each vertex k,
+    // the mean of the 3 interior angles between the faces that meet there
+    // (radians; the angle between two faces along their common edge e is
+    // the angle between the other two edges at k projected orthogonally to e)
+    h->n_geo = n_geo;
+    h->geo.assign(size_t(n_geo) * size_t(nc), 0.0);
+    auto vec = [&](int32_t a, int32_t b, double* t) {
+        for (int d = 0; d < 3; ++d) t[d] = h->xyz_c[3 * size_t(b) + d] - h->xyz_c[3 * size_t(a) + d];
+    };
+    auto dot = [](const double* a, const double* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; };
     for (int64_t c = 0; c < nc; ++c) {
         const int32_t* cv = &h->cells[8 * c];
+        double* g = &h->geo[size_t(n_geo) * size_t(c)];
+        double t[3];
         for (int e = 0; e < 12; ++e) {
-            double s = 0.0;
-            for (int d = 0; d < 3; ++d) {
-                const double t = h->xyz_c[3 * cv[kEdges[e][1]] + d] - h->xyz_c[3 * cv[kEdges[e][0]] + d];
-                s += t * t;
+            vec(cv[kEdges[e][0]], cv[kEdges[e][1]], t);
+            g[e] = std::sqrt(dot(t, t));
+        }
+        if (n_geo < 24) continue;
+        for (int k = 0; k < 4; ++k) {
+            vec(cv[k], cv[7 - k], t);
+            g[12 + k] = std::sqrt(dot(t, t));
+        }
+        for (int k = 0; k < 8; ++k) {
+            double ed[3][3];   // edges from vertex k along the three axes
+            for (int a = 0; a < 3; ++a) vec(cv[k], cv[k ^ (1 << a)], ed[a]);
+            double sum = 0.0;
+            for (int a = 0; a < 3; ++a) {
+                const double* e = ed[a];
+                const double* u = ed[(a + 1) % 3];
+                const double* w = ed[(a + 2) % 3];
+                const double ee = dot(e, e), ue = dot(u, e) / ee, we = dot(w, e) / ee;
+                double up[3], wp[3];
+                for (int d = 0; d < 3; ++d) {
+                    up[d] = u[d] - ue * e[d];
+                    wp[d] = w[d] - we * e[d];
+                }
+                double cs = dot(up, wp) / std::sqrt(dot(up, up) * dot(wp, wp));
+                cs = cs > 1.0 ? 1.0 : (cs < -1.0 ? -1.0 : cs);
+                sum += std::acos(cs);
             }
-            h->edge_len[size_t(12 * c + e)] = std::sqrt(s);
+            g[16 + k] = sum / 3.0;
         }
     }
     return DNNMG_OK;

@@ -499,14 +499,15 @@ __device__ __forceinline__ void store4(TX* dst, T a, T b, T c, T d) {
     }
 }
 
-// One warp per patch: X[P] = [x~ at 27 nodes | r at 27 nodes | h^c | 0].
+// One warp per patch: X[P] = [x~ at 27 nodes | r at 27 nodes | geometry | 0].
 // Lane iota < 27 writes node iota's 4 values of x~ and of r as one vector
-// each; lanes 0..9 write the 12 edge lengths and the zero padding (4 values
-// per lane).  Row stride 256, so every 4-value group is aligned.
+// each; lanes 0..9 write the n_geo (12 or 24) geometry features and the zero
+// padding (4 values per lane).  Row stride 256, so every 4-value group is
+// aligned.
 template <typename T, typename TX>
 __global__ void __launch_bounds__(256) local_restrict_kernel(
     int64_t nc, const int32_t* __restrict__ cells, const int32_t* __restrict__ patch_map,
-    const T* __restrict__ xc, const T* __restrict__ r, const T* __restrict__ edge_len,
+    const T* __restrict__ xc, const T* __restrict__ r, const T* __restrict__ geo, int n_geo,
     TX* __restrict__ X) {
     const int lane = threadIdx.x & 31;
     const int64_t P = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
@@ -514,7 +515,7 @@ __global__ void __launch_bounds__(256) local_restrict_kernel(
     // issue the independent loads first: corner ids, node ids, edge lengths
     const int32_t v = lane < 8 ? __ldg(cells + 8 * P + lane) : 0;
     const int32_t j = lane < 27 ? __ldg(patch_map + 27 * P + lane) : 0;
-    const T el = lane < 12 ? edge_len[12 * P + lane] : T(0);
+    const T el = lane < n_geo ? geo[int64_t(n_geo) * P + lane] : T(0);
     V4<T> rv{T(0), T(0), T(0), T(0)};
     if (lane < 27) rv = ld4(r + 4 * int64_t(j));
     T cu[4] = {T(0), T(0), T(0), T(0)};
@@ -530,11 +531,13 @@ __global__ void __launch_bounds__(256) local_restrict_kernel(
     for (int k = 0; k < 8; ++k)
 #pragma unroll
         for (int d = 0; d < 4; ++d) corner[k][d] = __shfl_sync(0xffffffffu, cu[d], k);
-    // edge lengths 0..11 gathered for lanes 0..2 (4 each)
-    const T e0 = __shfl_sync(0xffffffffu, el, (4 * lane) & 31);
-    const T e1 = __shfl_sync(0xffffffffu, el, (4 * lane + 1) & 31);
-    const T e2 = __shfl_sync(0xffffffffu, el, (4 * lane + 2) & 31);
-    const T e3 = __shfl_sync(0xffffffffu, el, (4 * lane + 3) & 31);
+    // geometry features 4 lane .. 4 lane + 3 (zero past n_geo)
+    T e[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const T g = __shfl_sync(0xffffffffu, el, (4 * lane + i) & 31);
+        e[i] = 4 * lane + i < n_geo ? g : T(0);
+    }
     TX* row = X + P * kNInPad;
     if (lane < 27) {
         const int a = lane % 3, b = (lane / 3) % 3, c = lane / 9;
@@ -542,10 +545,8 @@ __global__ void __launch_bounds__(256) local_restrict_kernel(
                    interp27<T, 4>(&corner[0][0], 2, a, b, c), interp27<T, 4>(&corner[0][0], 3, a, b, c));
         store4<TX>(row + 108 + 4 * lane, rv.x, rv.y, rv.z, rv.w);
     }
-    if (lane < 3)
-        store4<TX>(row + 216 + 4 * lane, e0, e1, e2, e3);
-    else if (lane < 10)   // columns 228..255
-        store4<TX>(row + 216 + 4 * lane, T(0), T(0), T(0), T(0));
+    if (lane < 10)   // columns 216..255
+        store4<TX>(row + 216 + 4 * lane, e[0], e[1], e[2], e[3]);
 }
 
 // d_j = mu_j * sum_{(P,iota) in j} Y[P][3 iota + c], mu_j = 1 / valence.
@@ -677,9 +678,9 @@ const float* xyz_of<float>(const DeviceMesh& dm) { return dm.xyz_f; }
 template <typename T>
 static const T* edge_of(const DeviceMesh& dm);
 template <>
-const double* edge_of<double>(const DeviceMesh& dm) { return dm.edge_d; }
+const double* edge_of<double>(const DeviceMesh& dm) { return dm.geo_d; }
 template <>
-const float* edge_of<float>(const DeviceMesh& dm) { return dm.edge_f; }
+const float* edge_of<float>(const DeviceMesh& dm) { return dm.geo_f; }
 
 template <typename T>
 cudaError_t launch_prolongate(const DeviceMesh& dm, const T* xc, T* xf, cudaStream_t s) {
@@ -705,7 +706,7 @@ cudaError_t launch_residual(const DeviceMesh& dm, OpParams p, const T* xc, const
 template <typename T, typename TX>
 cudaError_t launch_local_restrict(const DeviceMesh& dm, const T* xc, const T* r, TX* X, cudaStream_t s) {
     local_restrict_kernel<T, TX><<<blocks_for(dm.nc * 32, 256), 256, 0, s>>>(
-        dm.nc, dm.cells, dm.patch_map, xc, r, edge_of<T>(dm), X);
+        dm.nc, dm.cells, dm.patch_map, xc, r, edge_of<T>(dm), dm.n_geo, X);
     return cudaGetLastError();
 }
 

@@ -292,7 +292,7 @@ dnnmg_status dnnmg_trainer_create(const dnnmg_net_desc* net, int32_t precision, 
         (precision != DNNMG_BF16 && precision != DNNMG_FP32))
         return DNNMG_EINVAL;
     const int L = net->n_layers;
-    if (net->widths[0] != kNIn || net->widths[L] != kNOut) return DNNMG_EINVAL;
+    if ((net->widths[0] != kNIn && net->widths[0] != kNInGeo24) || net->widths[L] != kNOut) return DNNMG_EINVAL;
     for (int i = 1; i < L; ++i)
         if (net->widths[i] < 16 || net->widths[i] > 4096 || net->widths[i] % 16) return DNNMG_EINVAL;
     dnnmg_trainer* t = new dnnmg_trainer();

@@ -17,7 +17,7 @@ PRECISIONS = {"fp64": capi.FP64, "fp32": capi.FP32, "bf16": capi.BF16}
 
 
 class PatchPath:
-    def __init__(self, mesh, nu, dt, theta, precision, device="cuda", stream=None):
+    def __init__(self, mesh, nu, dt, theta, precision, device="cuda", stream=None, features=12):
         if isinstance(precision, str):
             precision = PRECISIONS[precision]
         self.device = torch.device(device)
@@ -26,7 +26,7 @@ class PatchPath:
         torch.cuda.set_device(self.device)
         self.precision = precision
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
-        self.ctx = capi.dnnmg_create(mesh, nu, dt, theta, precision, self.stream)
+        self.ctx = capi.dnnmg_create(mesh, nu, dt, theta, precision, self.stream, features=features)
         self.sizes = capi.dnnmg_get_sizes(self.ctx)
         self.dtype = _FIELD_DTYPE[precision]
         self.x_dtype = _X_DTYPE[precision]

@@ -86,8 +86,9 @@ class PatchNet:
         Ws = [w.detach().double().cpu().numpy() for w in self.W]
         bs = [b.detach().double().cpu().numpy() for b in self.b]
         if norm is not None:
-            mu = torch.as_tensor(norm[0]).double().cpu().numpy()[:228]
-            sig = torch.as_tensor(norm[1]).double().cpu().numpy()[:228]
+            n_in = self.widths[0]
+            mu = torch.as_tensor(norm[0]).double().cpu().numpy()[:n_in]
+            sig = torch.as_tensor(norm[1]).double().cpu().numpy()[:n_in]
             ts = float(norm[2])
             W1 = Ws[0] / sig[None, :]
             bs[0] = bs[0] - W1 @ mu
@@ -143,14 +144,14 @@ class _MSE(torch.autograd.Function):
         return dY * g, None
 
 
-def make_samples(mesh, nu, dt, theta, n_steps, x_dtype=torch.bfloat16, solver=None):
+def make_samples(mesh, nu, dt, theta, n_steps, x_dtype=torch.bfloat16, solver=None, features=12):
     """(X, T) training pairs from a fine-level simulation started at rest
-    with the mesh's Dirichlet data.  X [n_steps * N_c][256] in x_dtype, T
-    [n_steps * N_c][81] fp32.  Also returns the per-step arrays for
-    evaluation."""
+    with the mesh's Dirichlet data.  X [n_steps * N_c][256] in x_dtype (216 +
+    features used columns), T [n_steps * N_c][81] fp32.  Also returns the
+    per-step arrays for evaluation."""
     prec = "bf16" if x_dtype == torch.bfloat16 else "fp32"
     f64 = PatchPath(mesh, nu, dt, theta, "fp64")          # fine solves, restriction
-    low = PatchPath(mesh, nu, dt, theta, prec)            # network inputs as at inference
+    low = PatchPath(mesh, nu, dt, theta, prec, features=features)   # network inputs as at inference
     dev = f64.device
     nv, nf, nc = f64.n_coarse, f64.n_fine, f64.n_patches
     kind = f64.mesh_data(capi.FINE_KIND)
@@ -215,10 +216,11 @@ def trajectory_errors(mesh, nu, dt, theta, steps, network=None, solver=None):
     return errs
 
 
-def fit_normalization(X, T):
+def fit_normalization(X, T, n_in=228):
     """Per-column mean and standard deviation of the input rows (padding
     columns and constant columns get mean 0 / sigma 1) and one scale for the
-    targets (their root mean square)."""
+    targets (their root mean square).  n_in = 228 (edge lengths) or 240
+    (edge lengths, diagonals, angles)."""
     Xf = X.float()
     mu = Xf.mean(dim=0)
     sig = Xf.std(dim=0)
@@ -227,13 +229,15 @@ def fit_normalization(X, T):
     # amplified without bound: floor sigma at 5% of the kind's median
     groups = [list(range(c, 108, 4)) for c in range(4)] + [list(range(108 + c, 216, 4)) for c in range(4)]
     groups.append(list(range(216, 228)))
+    if n_in > 228:
+        groups += [list(range(228, 232)), list(range(232, n_in))]   # diagonals, angles
     for g in groups:
         floor = 0.05 * float(sig[g].median())
         if floor <= 0.0:
             floor = 1.0
         sig[g] = torch.clamp(sig[g], min=floor)
-    mu[228:] = 0.0
-    sig[228:] = 1.0
+    mu[n_in:] = 0.0
+    sig[n_in:] = 1.0
     ts = float(torch.sqrt((T.float() ** 2).mean()))
     return mu, sig, (ts if ts > 0 else 1.0)
 

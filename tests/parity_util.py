@@ -30,6 +30,11 @@ CASES = {
     # a single patch: every node has valence 1
     "single_cell": dict(mesh=("cavity_plain", 1, 0.0), nu=0.01, dt=0.01, theta=1.0,
                         widths=(228, 16, 81), bn=False),
+    # the paper's 24 geometry features (240 inputs, Table 2) on non-affine cells
+    "cavity6_jitter_geo24": dict(mesh=("cavity", 6, 0.2), nu=0.01, dt=0.01, theta=0.5,
+                                 widths=(240, 64, 64, 64, 81), bn=True, features=24),
+    "channel4_geo24": dict(mesh=("channel", 4, 0.0), nu=5e-4, dt=0.005, theta=0.5,
+                           widths=(240, 128, 128, 81), bn=True, features=24),
 }
 
 TOL = {"fp64": 1e-12, "fp32": 1e-5, "bf16": 2e-2}
@@ -57,7 +62,7 @@ def case_data(name, seed=0):
     Ws, ss, ts = I.network_weights(c["widths"], seed=0, scale_shift=c["bn"])
     prm = dict(m=1.0 / c["dt"], theta=c["theta"], nu=c["nu"], alpha0=0.02, delta0=0.1)
     lev = odnnmg.fine_level(h)
-    out = odnnmg.hot_path_step(h, (Ws, ss, ts, True), xc, F, prm, level=lev)
+    out = odnnmg.hot_path_step(h, (Ws, ss, ts, True), xc, F, prm, level=lev, features=c.get("features", 12))
     from oracle import transfer
     A = lev.operator(transfer.prolongate(h, xc), prm)
     return dict(case=c, mesh=m, h=h, xc=xc, F=F, net=(Ws, ss, ts), prm=prm, out=out, A=A)

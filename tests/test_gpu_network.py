@@ -26,9 +26,9 @@ def mesh():
     return I.cavity_mesh(2)
 
 
-def _rows(M, seed):
+def _rows(M, seed, n_in=228):
     X = np.zeros((M, 256))
-    X[:, :228] = I.splitmix_normal(900 + seed, M * 228).reshape(M, 228)
+    X[:, :n_in] = I.splitmix_normal(900 + seed, M * n_in).reshape(M, n_in)
     return X
 
 
@@ -37,23 +37,30 @@ def _rows(M, seed):
     ("bf16", (228, 1024, 1024, 81), 9000 + 5, False),
     ("bf16", (228, 192, 192, 81), 1000, True),              # N not a multiple of the tile
     ("fp32", (228, 512, 512, 81), 5000 + 3, True),
+    # the paper's networks (Table 2): 240 inputs, 8 hidden layers of width
+    # 750 or 512 with batch normalisation and skips; 750 is not a multiple
+    # of the 256-column tile or of the 64-column K block
+    ("bf16", (240,) + (750,) * 8 + (81,), 20000 + 19, True),
+    ("bf16", (240,) + (512,) * 8 + (81,), 3000 + 1, True),
+    ("fp32", (240,) + (750,) * 8 + (81,), 2000 + 3, True),
 ])
 def test_network_rows_against_oracle(mesh, precision, widths, M, bn):
-    p = PatchPath(mesh, 0.01, 0.01, 1.0, precision)
+    feats = widths[0] - 216
+    p = PatchPath(mesh, 0.01, 0.01, 1.0, precision, features=feats)
     Ws, ss, ts = I.network_weights(widths, seed=7, scale_shift=bn)
     # capacity of the context's activation buffers is its patch count, so
     # use a context whose mesh has at least M patches
     if p.n_patches < M:
         p.close()
         n = int(np.ceil(M ** (1 / 3)))
-        p = PatchPath(I.cavity_mesh(n + (n % 2)), 0.01, 0.01, 1.0, precision)
+        p = PatchPath(I.cavity_mesh(n + (n % 2)), 0.01, 0.01, 1.0, precision, features=feats)
     p.set_network(widths, Ws, ss, ts, skip=True)
-    X = _rows(M, 1)
+    X = _rows(M, 1, widths[0])
     Xd = torch.as_tensor(X, device="cuda").to(p.x_dtype)
     Y = p.network(Xd, M)
     torch.cuda.synchronize()
     capi.dnnmg_sync(p.ctx, 10_000_000)                # raises if a bounded wait expired
-    Xo = Xd.double().cpu().numpy()[:, :228]           # the oracle sees the same (rounded) inputs
+    Xo = Xd.double().cpu().numpy()[:, :widths[0]]     # the oracle sees the same (rounded) inputs
     ref = omlp.forward(Xo, Ws, ss, ts, skip=True)
     emax, ep99 = patch_output_err(Y.double().cpu().numpy(), ref)
     tol = 2e-2 if precision == "bf16" else 1e-5

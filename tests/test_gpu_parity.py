@@ -22,7 +22,7 @@ def _lib():
 
 def _path(d, precision):
     c = d["case"]
-    p = PatchPath(d["mesh"], c["nu"], c["dt"], c["theta"], precision)
+    p = PatchPath(d["mesh"], c["nu"], c["dt"], c["theta"], precision, features=c.get("features", 12))
     Ws, ss, ts = d["net"]
     p.set_network(c["widths"], Ws, ss, ts, skip=True)
     return p
@@ -36,13 +36,17 @@ def _np(t):
 def test_mesh_data_bit_exact(name):
     d = case_data(name)
     h = d["h"]
-    p = PatchPath(d["mesh"], 0.01, 0.01, 1.0, "fp64")
+    nf = d["case"].get("features", 12)
+    p = PatchPath(d["mesh"], 0.01, 0.01, 1.0, "fp64", features=nf)
     assert p.n_fine == h.n_fine and p.n_patches == h.n_patches
+    assert p.sizes["n_in"] == 216 + nf
     assert np.array_equal(p.mesh_data(capi.PATCH_MAP), h.patch_map)
     assert np.array_equal(p.mesh_data(capi.VALENCE), h.mult)
     assert np.array_equal(p.mesh_data(capi.FINE_KIND), h.bc_f)
     assert np.allclose(p.mesh_data(capi.FINE_XYZ), h.xyz_f, rtol=0, atol=1e-15)
     assert np.allclose(p.mesh_data(capi.EDGE_LENGTHS), h.edge_lengths(), rtol=1e-15, atol=0)
+    # the geometry features in double: lengths to rounding, angles through acos
+    assert np.allclose(p.mesh_data(capi.GEOMETRY), h.geometry(nf), rtol=1e-13, atol=1e-13)
     p.close()
 
 
@@ -65,12 +69,13 @@ def test_stagewise_parity(name, precision):
     ftol = 1e-12 if precision == "fp64" else 1e-5
     assert rel_max(_np(xf), o["x_fine"]) <= ftol
     assert residual_err(_np(r), d) <= ftol
-    Xn = _np(X)[:, :228]
+    n_in = p.sizes["n_in"]
+    Xn = _np(X)[:, :n_in]
     if precision == "bf16":
         assert np.all(np.abs(Xn - o["X"]) <= 2.0 ** -8 * np.abs(o["X"]) + 1e-5 * np.abs(o["X"]).max())
     else:
         assert rel_max(Xn, o["X"]) <= ftol
-    assert np.all(_np(X)[:, 228:] == 0)
+    assert np.all(_np(X)[:, n_in:] == 0)
     emax, ep99 = patch_output_err(_np(Y), o["Y"])
     assert emax <= tol, (emax, ep99)
     assert rel_max(_np(dd), o["d"]) <= tol
@@ -131,6 +136,8 @@ def test_errors_and_empty_batch():
         capi.dnnmg_network(p.ctx, X, Y, p.n_patches + 1)
     assert e.value.status == -1
     with pytest.raises(capi.DnnmgError):
-        p.set_network((228, 20, 81), [np.zeros((20, 228)), np.zeros((81, 20))])   # width not /16
+        p.set_network((228, 5000, 81), [np.zeros((5000, 228)), np.zeros((81, 5000))])   # width > 4096
+    with pytest.raises(capi.DnnmgError):
+        p.set_network((240, 20, 81), [np.zeros((20, 240)), np.zeros((81, 20))])   # input width of the other form
     capi.dnnmg_sync(p.ctx, 10_000_000)
     p.close()

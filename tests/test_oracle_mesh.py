@@ -107,6 +107,60 @@ def test_edge_lengths_cube():
     assert np.allclose(e[:, 0:4], 0.25) and np.allclose(e[:, 4:8], 0.5) and np.allclose(e[:, 8:12], 0.75)
 
 
+def _one_cell(X):
+    """A single hexahedron with corners X[k], k = k0 + 2 k1 + 4 k2."""
+    return mesh.Hierarchy(np.asarray(X, dtype=np.float64), np.arange(8, dtype=np.int32)[None, :],
+                          np.ones(8, dtype=np.int32))
+
+
+def _parallelepiped(a, b, c, origin=(0.0, 0.0, 0.0)):
+    o = np.asarray(origin, dtype=np.float64)
+    return [o + (k & 1) * np.asarray(a) + ((k >> 1) & 1) * np.asarray(b) + ((k >> 2) & 1) * np.asarray(c)
+            for k in range(8)]
+
+
+def test_geometry_features_cube_and_box():
+    h = _one_cell(_parallelepiped((0.3, 0, 0), (0, 0.5, 0), (0, 0, 0.7)))
+    g = h.geometry(24)
+    assert g.shape == (1, 24)
+    assert np.allclose(g[0, 12:16], np.sqrt(0.3 ** 2 + 0.5 ** 2 + 0.7 ** 2), rtol=0, atol=1e-15)
+    assert np.allclose(g[0, 16:24], np.pi / 2, rtol=0, atol=1e-14)
+    assert np.array_equal(h.geometry(12), g[:, :12])
+
+
+def test_face_angles_sheared_cell_closed_form():
+    # a parallelepiped sheared in the xy-plane by the angle phi: the faces
+    # through the z-edge at vertex 0 meet at phi, the other pairs at pi/2;
+    # at vertex 1 the z-edge pair meets at pi - phi
+    phi = 1.1
+    a, b, c = np.array([1.0, 0, 0]), np.array([np.cos(phi), np.sin(phi), 0]), np.array([0, 0, 1.0])
+    h = _one_cell(_parallelepiped(a, b, c))
+    ang = h.face_angles()[0]
+    assert abs(ang[0] - (np.pi + phi) / 3) < 1e-14
+    assert abs(ang[1] - (2 * np.pi - phi) / 3) < 1e-14
+    assert abs(ang[2] - (2 * np.pi - phi) / 3) < 1e-14     # vertex b: edges -b, a, c
+    assert abs(ang[3] - (np.pi + phi) / 3) < 1e-14         # vertex a + b: edges -a, -b, c
+    d = h.diagonals()[0]
+    for k, ref in enumerate([a + b + c, b + c - a, a + c - b, c - a - b]):
+        assert abs(d[k] - np.linalg.norm(ref)) < 1e-14
+
+
+def test_geometry_features_invariance():
+    # a general (non-planar-faced) hexahedron: lengths scale with the cell,
+    # angles do not; both are unchanged by a rotation and a translation
+    rng = np.random.default_rng(4)
+    X = np.array(_parallelepiped((1, 0, 0), (0, 1, 0), (0, 0, 1))) + 0.15 * rng.standard_normal((8, 3))
+    g = _one_cell(X).geometry(24)[0]
+    q, _ = np.linalg.qr(rng.standard_normal((3, 3)))
+    g_rot = _one_cell(X @ q.T + np.array([3.0, -1.0, 2.0])).geometry(24)[0]
+    assert np.allclose(g_rot, g, rtol=1e-12, atol=1e-13)
+    g_scaled = _one_cell(2.5 * X).geometry(24)[0]
+    assert np.allclose(g_scaled[:16], 2.5 * g[:16], rtol=1e-13)
+    assert np.allclose(g_scaled[16:], g[16:], rtol=1e-12)
+    # a skewed cell is not a box: some mean angle differs from pi / 2
+    assert np.abs(g[16:] - np.pi / 2).max() > 1e-3
+
+
 def test_golden_patch_sizes():
     path = os.path.join(os.path.dirname(__file__), "golden", "patch_sizes.txt")
     rows = [list(map(int, l.split())) for l in open(path) if l.strip() and not l.startswith("#")]
