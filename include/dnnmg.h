@@ -37,12 +37,13 @@
  *       d         [n_fine_nodes][3]       velocity correction
  *       b_coarse  [n_coarse_vertices][4]
  *       X         [n_patches][n_in_padded]: columns 0..107 x~ at the 27 patch
- *                 nodes (u,v,w,p), 108..215 r likewise, 216.. the
+ *                 nodes (u,v,w,p), 108..215 r likewise (J = 2: 0..499 and
+ *                 500..999 for the 125 nodes), then the
  *                 geometry features (12 edge lengths, or 24 features, see
  *                 dnnmg_params.features), zero after them
- *       Y         [n_patches][81]: 27 x (u, v, w)
+ *       Y         [n_patches][n_out]: 27 x (u, v, w) (J = 2: 125 x 3 = 375)
  *     Patch node iota = a + 3b + 9c, (a,b,c) in {0,1,2}^3 along the coarse
- *     cell's reference axes.
+ *     cell's reference axes (J = 2: a + 5b + 25c, (a,b,c) in {0..4}^3).
  *   - Dirichlet velocity rows (fine node kinds 1 and 2) of r, d and b_fine,
  *     and coarse Dirichlet velocity rows of b_coarse are zero; pressure rows
  *     of b_fine and b_coarse are zero.
@@ -61,7 +62,7 @@
 extern "C" {
 #endif
 
-#define DNNMG_ABI_VERSION 1
+#define DNNMG_ABI_VERSION 2
 
 typedef struct dnnmg_ctx dnnmg_ctx;
 
@@ -104,6 +105,13 @@ typedef struct {
                          * (vertex k to 7 - k) and per vertex the mean of the
                          * 3 angles between the faces meeting there, in
                          * radians (240 inputs, as in Table 2) */
+    int32_t patch_levels; /* J of Sec. 5.2: 0 or 1 = patches of one coarse
+                           * cell refined once (27 nodes, level L+1); 2 =
+                           * refined twice (125 nodes, level L+2, which is
+                           * level L+1 refined again by the same rules).
+                           * J = 2: n_in = 1000 + features, X row stride
+                           * 1024, n_out = 375 (Table 2) */
+    int32_t reserved;     /* must be 0 */
 } dnnmg_params;
 
 /* Patch network of Sec. 4 in inference form: layer i computes
@@ -121,15 +129,15 @@ typedef struct {
     int64_t n_fine_nodes;
     int64_t n_coarse_edges;
     int64_t n_coarse_faces;
-    int32_t n_in;              /* 228, or 240 with 24 geometry features */
-    int32_t n_in_padded;       /* row stride of X */
-    int32_t n_out;             /* 81 */
+    int32_t n_in;              /* 8 x nodes per patch + geometry features: 228 / 240 (J = 1), 1012 / 1024 (J = 2) */
+    int32_t n_in_padded;       /* row stride of X: 256 (J = 1), 1024 (J = 2) */
+    int32_t n_out;             /* 3 x nodes per patch: 81 (J = 1), 375 (J = 2) */
     int32_t precision;
 } dnnmg_sizes;
 
 /* Mesh data a caller can read back (dnnmg_get_mesh_data). */
 typedef enum {
-    DNNMG_PATCH_MAP = 0,    /* int32 [n_patches][27]: dof(P, iota) of Sec. 5.2 */
+    DNNMG_PATCH_MAP = 0,    /* int32 [n_patches][27 or 125]: dof(P, iota) of Sec. 5.2 */
     DNNMG_VALENCE = 1,      /* int32 [n_fine_nodes]: patches containing each node (1/mu) */
     DNNMG_FINE_KIND = 2,    /* int32 [n_fine_nodes]: boundary kind 0..3 */
     DNNMG_FINE_XYZ = 3,     /* double [n_fine_nodes][3] */

@@ -37,12 +37,13 @@ def fine_level(h) -> Level:
 
 
 def local_restriction(h, field: np.ndarray) -> np.ndarray:
-    """Q of Eqs. (13)-(14): row P holds field[dof(P, iota)] for iota = 0..26,
-    flattened node-major.  field [n_fine, c] -> [N_c, 27 c]."""
-    nc = h.n_patches
-    out = np.empty((nc, 27 * field.shape[1]))
+    """Q of Eqs. (13)-(14): row P holds field[dof(P, iota)] for the patch's
+    nodes iota (27, or 125 for J = 2), flattened node-major.
+    field [n_fine, c] -> [N_c, nodes c]."""
+    nc, npn = h.patch_map.shape
+    out = np.empty((nc, npn * field.shape[1]))
     for P in range(nc):
-        for iota in range(27):
+        for iota in range(npn):
             out[P, iota * field.shape[1]:(iota + 1) * field.shape[1]] = field[h.patch_map[P, iota]]
     return out
 
@@ -55,10 +56,11 @@ def gather(h, x_fine, r_fine, features: int = 12) -> np.ndarray:
 
 def extend(h, Y) -> np.ndarray:
     """L of Eq. (15): d = mu . sum_P L(Y[P], P), mu = 1 / valence; summed in
-    patch order; zero at Dirichlet velocity nodes.  Y [N_c, 81] -> [n_fine, 3]."""
+    patch order; zero at Dirichlet velocity nodes.  Y [N_c, 3 nodes] -> [n_fine, 3]."""
     acc = np.zeros((h.n_fine, 3))
+    npn = h.patch_map.shape[1]
     for P in range(h.n_patches):
-        for iota in range(27):
+        for iota in range(npn):
             j = h.patch_map[P, iota]
             acc[j] = acc[j] + Y[P, 3 * iota:3 * iota + 3]
     d = acc * (1.0 / h.mult)[:, None]
@@ -83,7 +85,7 @@ def hot_path_step(h, net, x_coarse, F, prm, level=None, features: int = 12):
     return dict(x_fine=x_f, r=r, X=X, Y=Y, d=d, b_fine=b_f, b_coarse=b_c)
 
 
-def run(h, coarse, net, x0, n_steps, prm, bc_values, newton_tol=1e-13):
+def run(h, coarse, net, x0, n_steps, prm, bc_values, newton_tol=1e-13, features=12):
     """DNN-MG time stepping (Alg. 1) on the coarse level ``coarse`` (a
     fem.Level on the cells of h) with the patch correction on level L+1.
 
@@ -103,7 +105,7 @@ def run(h, coarse, net, x0, n_steps, prm, bc_values, newton_tol=1e-13):
         xi[coarse.dirichlet, 0:3] = bc_values(t)[coarse.dirichlet]
         x, _ = newton(coarse, xi, b, prm, tol=newton_tol)
         states.append(x.copy())
-        last = hot_path_step(h, net, x, F, prm, level=lev)
+        last = hot_path_step(h, net, x, F, prm, level=lev, features=features)
         F, b = last["b_fine"], last["b_coarse"]
     return states, last
 

@@ -275,3 +275,59 @@ class Hierarchy:
         patch groups of 8 children)."""
         return dict(xyz=self.xyz_f, cells=self.cells_f, vertex_bc=self.bc_f,
                     patch_groups=True)
+
+
+class Hierarchy2:
+    """Patches of J = 2 (Sec. 5.2): each coarse cell of level L with the
+    64 cells and 125 nodes of its twofold refinement.  Level L+2 is level
+    L+1 (``Hierarchy``, with its fine cells as the mesh: cell 8 P + t is
+    child t of coarse cell P) refined once more by the same rules, so its
+    node numbering, boundary kinds and cell grouping follow from those of
+    one refinement.  The patch node iota = a + 5 b + 25 c, (a, b, c) in
+    {0..4}^3 along the coarse cell's reference axes, is node (a - 2 i,
+    b - 2 j, c - 2 k) of child (i, j, k), i = min(a // 2, 1) etc. (nodes on
+    the children's common faces are the same node in either child).
+
+    Pinned by the same closed forms as ``Hierarchy`` (node counts, valences,
+    trilinear node positions) on twofold refinements; see
+    tests/test_oracle_mesh.py."""
+
+    J = 2
+
+    def __init__(self, xyz, cells, vertex_bc):
+        self.h1 = Hierarchy(xyz, cells, vertex_bc)
+        self.h2 = Hierarchy(self.h1.xyz_f, self.h1.cells_f, self.h1.bc_f)
+        self.levels = (self.h1, self.h2)
+        h1, h2 = self.h1, self.h2
+        self.n_patches = h1.n_patches
+        self.n_coarse_vertices = h1.n_coarse_vertices
+        self.xyz_c, self.cells_c = h1.xyz_c, h1.cells_c
+        self.n_fine = h2.n_fine
+        self.xyz_f, self.cells_f, self.bc_f = h2.xyz_f, h2.cells_f, h2.bc_f
+        nc = self.n_patches
+        pm = np.empty((nc, 125), dtype=np.int64)
+        for P in range(nc):
+            for iota in range(125):
+                a, b, c = iota % 5, (iota // 5) % 5, iota // 25
+                i, j, k = min(a // 2, 1), min(b // 2, 1), min(c // 2, 1)
+                child = i + 2 * j + 4 * k
+                local = (a - 2 * i) + 3 * (b - 2 * j) + 9 * (c - 2 * k)
+                pm[P, iota] = h2.patch_map[8 * P + child, local]
+        self.patch_map = pm
+        self.mult = np.bincount(pm.ravel(), minlength=self.n_fine)
+
+    def dirichlet_fine(self) -> np.ndarray:
+        return self.h2.dirichlet_fine()
+
+    def dirichlet_coarse(self) -> np.ndarray:
+        return self.h1.dirichlet_coarse()
+
+    def edge_lengths(self) -> np.ndarray:
+        return self.h1.edge_lengths()
+
+    def geometry(self, n_features: int = 12) -> np.ndarray:
+        return self.h1.geometry(n_features)
+
+    def fine_mesh(self) -> dict:
+        return self.h2.fine_mesh()
+

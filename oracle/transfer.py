@@ -27,7 +27,13 @@ def prolongation_matrix(h) -> sp.csr_matrix:
 
 
 def prolongate(h, x_coarse: np.ndarray) -> np.ndarray:
-    """x_fine[j] = mean over parents(j) of x_coarse (any trailing shape)."""
+    """x_fine[j] = mean over parents(j) of x_coarse (any trailing shape).
+    For patches of two levels (``h.levels``) the product of the two
+    one-level prolongations."""
+    if hasattr(h, "levels"):
+        for lv in h.levels:
+            x_coarse = prolongate(lv, x_coarse)
+        return x_coarse
     out = np.empty((h.n_fine,) + x_coarse.shape[1:])
     for j, par in enumerate(h.parents):
         s = np.zeros(x_coarse.shape[1:])
@@ -39,7 +45,14 @@ def prolongate(h, x_coarse: np.ndarray) -> np.ndarray:
 
 def restrict(h, b_fine: np.ndarray) -> np.ndarray:
     """(P^T b)[v] = sum over fine nodes j with parent v of b[j] / |parents(j)|;
-    velocity rows at coarse Dirichlet vertices are then set to zero."""
+    velocity rows at coarse Dirichlet vertices are then set to zero.  For
+    patches of two levels the two one-level restrictions in turn (the
+    intermediate zeroing changes nothing: a Dirichlet node of level L+1 has
+    only Dirichlet parents)."""
+    if hasattr(h, "levels"):
+        for lv in reversed(h.levels):
+            b_fine = restrict(lv, b_fine)
+        return b_fine
     out = np.zeros((h.n_coarse_vertices,) + b_fine.shape[1:])
     for j, par in enumerate(h.parents):
         for v in par:

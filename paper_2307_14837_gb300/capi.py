@@ -35,7 +35,8 @@ class MeshDesc(ctypes.Structure):
 
 class Params(ctypes.Structure):
     _fields_ = [("nu", ctypes.c_double), ("dt", ctypes.c_double), ("theta", ctypes.c_double),
-                ("precision", ctypes.c_int32), ("features", ctypes.c_int32)]
+                ("precision", ctypes.c_int32), ("features", ctypes.c_int32),
+                ("patch_levels", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class NetDesc(ctypes.Structure):
@@ -124,10 +125,11 @@ def _check(ctx, status):
 
 # -- thin wrappers with the C names ------------------------------------------
 
-def dnnmg_create(mesh, nu, dt, theta, precision, stream=None, features=12):
+def dnnmg_create(mesh, nu, dt, theta, precision, stream=None, features=12, patch_levels=1):
     """mesh: dict with xyz [nv,3] float64, cells [nc,8] int32, vertex_bc [nv] int32.
     stream: a torch.cuda.Stream, an int handle, or None (default stream).
-    features: geometry features per patch, 12 (edge lengths) or 24."""
+    features: geometry features per patch, 12 (edge lengths) or 24.
+    patch_levels: J of the patches, 1 (27 nodes) or 2 (125 nodes)."""
     lib = load()
     xyz = np.ascontiguousarray(mesh["xyz"], dtype=np.float64)
     cells = np.ascontiguousarray(mesh["cells"], dtype=np.int32)
@@ -135,7 +137,7 @@ def dnnmg_create(mesh, nu, dt, theta, precision, stream=None, features=12):
     desc = MeshDesc(int(xyz.shape[0]), xyz.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                     int(cells.shape[0]), cells.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                     bc.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
-    prm = Params(float(nu), float(dt), float(theta), int(precision), int(features))
+    prm = Params(float(nu), float(dt), float(theta), int(precision), int(features), int(patch_levels), 0)
     handle = _VP()
     s = getattr(stream, "cuda_stream", stream)
     _check(None, lib.dnnmg_create(ctypes.byref(desc), ctypes.byref(prm), s, ctypes.byref(handle)))
@@ -154,10 +156,10 @@ def dnnmg_get_sizes(ctx) -> dict:
 
 def dnnmg_get_mesh_data(ctx, item):
     sz = dnnmg_get_sizes(ctx)
-    shape, dt = {PATCH_MAP: ((sz["n_patches"], 27), np.int32), VALENCE: ((sz["n_fine_nodes"],), np.int32),
+    shape, dt = {PATCH_MAP: ((sz["n_patches"], sz["n_out"] // 3), np.int32), VALENCE: ((sz["n_fine_nodes"],), np.int32),
                  FINE_KIND: ((sz["n_fine_nodes"],), np.int32), FINE_XYZ: ((sz["n_fine_nodes"], 3), np.float64),
                  EDGE_LENGTHS: ((sz["n_patches"], 12), np.float64),
-                 GEOMETRY: ((sz["n_patches"], sz["n_in"] - 216), np.float64)}[item]
+                 GEOMETRY: ((sz["n_patches"], sz["n_in"] - 8 * (sz["n_out"] // 3)), np.float64)}[item]
     out = np.empty(shape, dtype=dt)
     _check(ctx, load().dnnmg_get_mesh_data(ctx, item, out.ctypes.data, out.nbytes))
     return out

@@ -57,8 +57,11 @@ size_t field_elem(int precision) { return precision == DNNMG_FP64 ? sizeof(doubl
 
 bool is_fp64(const dnnmg_ctx* c) { return c->precision == DNNMG_FP64; }
 
-// network inputs per patch: 2 x 27 x 4 node values + the geometry features
-int n_in(const dnnmg_ctx* c) { return c->host.n_geo == 24 ? kNInGeo24 : kNIn; }
+// network inputs per patch: 2 x nodes x 4 values + the geometry features;
+// the row stride of X; outputs per patch (3 per node)
+int n_in(const dnnmg_ctx* c) { return 8 * c->host.npn + c->host.n_geo; }
+int n_in_pad(const dnnmg_ctx* c) { return c->host.J == 2 ? kNInPadJ2 : kNInPad; }
+int n_out(const dnnmg_ctx* c) { return 3 * c->host.npn; }
 
 }  // namespace
 
@@ -95,13 +98,15 @@ dnnmg_status dnnmg_create(const dnnmg_mesh_desc* mesh, const dnnmg_params* param
     *out = nullptr;
     if (!mesh || !params) return DNNMG_EINVAL;
     if (params->features != 0 && params->features != 12 && params->features != 24) return DNNMG_EINVAL;
+    if (params->patch_levels < 0 || params->patch_levels > 2 || params->reserved != 0) return DNNMG_EINVAL;
+    const int J = params->patch_levels == 2 ? 2 : 1;
     if (params->precision < DNNMG_FP64 || params->precision > DNNMG_BF16 ||
         !(params->dt > 0.0) || !(params->nu >= 0.0) || !(params->theta >= 0.0 && params->theta <= 1.0))
         return DNNMG_EINVAL;
     dnnmg_ctx* ctx = new (std::nothrow) dnnmg_ctx();
     if (!ctx) return DNNMG_ENOMEM;
     std::string err;
-    dnnmg_status st = build_hierarchy(mesh, params->features == 24 ? 24 : 12, &ctx->host, &err);
+    dnnmg_status st = build_hierarchy(mesh, params->features == 24 ? 24 : 12, J, &ctx->host, &err);
     if (st != DNNMG_OK) {
         delete ctx;
         return st;
@@ -119,6 +124,7 @@ dnnmg_status dnnmg_create(const dnnmg_mesh_desc* mesh, const dnnmg_params* param
     dm.nc = h.nc;
     dm.n_fine = h.n_fine;
     dm.n_geo = h.n_geo;
+    dm.J = h.J;
     auto done = [&](dnnmg_status s) {
         if (s != DNNMG_OK) {
             dnnmg_destroy(ctx);
@@ -166,11 +172,12 @@ dnnmg_status dnnmg_create(const dnnmg_mesh_desc* mesh, const dnnmg_params* param
     const size_t fe = field_elem(ctx->precision);
     const size_t xe = ctx->precision == DNNMG_BF16 ? 2 : fe;
     const size_t nc = size_t(h.nc), nf = size_t(h.n_fine), nv = size_t(h.nv);
-    if ((st = alloc(ctx, nc * 27 * 4 * fe, &ctx->partial)) != DNNMG_OK) return done(st);
+    const size_t npn = size_t(h.npn);
+    if ((st = alloc(ctx, nc * npn * 4 * fe, &ctx->partial)) != DNNMG_OK) return done(st);
     if ((st = alloc(ctx, nc * 8 * 4 * fe, &ctx->partial_c)) != DNNMG_OK) return done(st);
     if ((st = alloc(ctx, nf * 4 * fe, &ctx->buf_r)) != DNNMG_OK) return done(st);
-    if ((st = alloc(ctx, nc * kNInPad * xe, &ctx->buf_X)) != DNNMG_OK) return done(st);
-    if ((st = alloc(ctx, nc * kNOut * fe, &ctx->buf_Y)) != DNNMG_OK) return done(st);
+    if ((st = alloc(ctx, nc * size_t(n_in_pad(ctx)) * xe, &ctx->buf_X)) != DNNMG_OK) return done(st);
+    if ((st = alloc(ctx, nc * size_t(n_out(ctx)) * fe, &ctx->buf_Y)) != DNNMG_OK) return done(st);
     if ((st = alloc(ctx, nf * 3 * fe, &ctx->buf_d)) != DNNMG_OK) return done(st);
     if ((st = alloc(ctx, nv * 4 * fe, &ctx->buf_xc)) != DNNMG_OK) return done(st);
     if ((st = alloc(ctx, nf * 4 * fe, &ctx->buf_F)) != DNNMG_OK) return done(st);
@@ -186,8 +193,8 @@ dnnmg_status dnnmg_get_sizes(const dnnmg_ctx* ctx, dnnmg_sizes* out) {
     out->n_coarse_edges = ctx->host.ne;
     out->n_coarse_faces = ctx->host.nf;
     out->n_in = n_in(ctx);
-    out->n_in_padded = kNInPad;
-    out->n_out = kNOut;
+    out->n_in_padded = n_in_pad(ctx);
+    out->n_out = n_out(ctx);
     out->precision = ctx->precision;
     return DNNMG_OK;
 }
@@ -228,8 +235,8 @@ dnnmg_status dnnmg_set_network(dnnmg_ctx* ctx, const dnnmg_net_desc* net, const 
                                const double* const* scale, const double* const* shift) {
     if (!ctx || !net || !W || !net->widths || net->n_layers < 1 || net->n_layers > 64) return DNNMG_EINVAL;
     const int L = net->n_layers;
-    if (net->widths[0] != n_in(ctx) || net->widths[L] != kNOut)
-        return fail(ctx, DNNMG_EINVAL, "network widths must start at the input width (228 or 240) and end at 81");
+    if (net->widths[0] != n_in(ctx) || net->widths[L] != n_out(ctx))
+        return fail(ctx, DNNMG_EINVAL, "network widths must start at n_in and end at n_out of the context");
     for (int i = 1; i < L; ++i) {
         const int w = net->widths[i];
         if (w < 1 || w > 4096) return fail(ctx, DNNMG_EINVAL, "hidden widths must be in [1, 4096]");
@@ -265,8 +272,8 @@ dnnmg_status dnnmg_set_network(dnnmg_ctx* ctx, const dnnmg_net_desc* net, const 
         const bool bf16 = ctx->precision == DNNMG_BF16;
         // tensor-core layers read K in blocks of 64 and the last layer's W
         // as a 96-row tile, SIMT layers K in steps of 16; padding is zero
-        ctx->kpad[i] = i == 0 ? kNInPad : (bf16 ? (ctx->widths[i] + 63) / 64 * 64 : (ctx->widths[i] + 15) / 16 * 16);
-        ctx->npad[i] = (bf16 && i == L - 1) ? 96 : ctx->widths[i + 1];
+        ctx->kpad[i] = i == 0 ? n_in_pad(ctx) : (bf16 ? (ctx->widths[i] + 63) / 64 * 64 : (ctx->widths[i] + 15) / 16 * 16);
+        ctx->npad[i] = (bf16 && i == L - 1) ? std::max(96, ctx->widths[i + 1]) : ctx->widths[i + 1];
         if (i < L - 1) maxw = std::max(maxw, ctx->widths[i + 1]);
     }
     maxw = ctx->precision == DNNMG_BF16 ? (maxw + 63) / 64 * 64 : (maxw + 15) / 16 * 16;
@@ -370,9 +377,9 @@ dnnmg_status dnnmg_network(dnnmg_ctx* ctx, const void* X_dev, void* Y_dev, int64
     for (int i = 0; i < L; ++i) {
         const bool last = i == L - 1;
         const void* A = i == 0 ? X_dev : ctx->act[(i - 1) & 1];
-        const int64_t lda = i == 0 ? kNInPad : ctx->act_ld;
+        const int64_t lda = i == 0 ? n_in_pad(ctx) : ctx->act_ld;
         void* C = last ? Y_dev : ctx->act[i & 1];
-        const int64_t ldc = last ? kNOut : ctx->act_ld;
+        const int64_t ldc = last ? n_out(ctx) : ctx->act_ld;
         const bool skip = ctx->skip && i >= 1 && !last && ctx->widths[i] == ctx->widths[i + 1];
         const void* R = skip ? A : nullptr;
         const int N = ctx->npad[i], K = ctx->kpad[i];
@@ -519,6 +526,8 @@ namespace {
 
 dnnmg_status get_level(dnnmg_ctx* ctx, int32_t level, const dnnmg_solver_params* prm, DeviceLevel** out) {
     if (level != DNNMG_LEVEL_COARSE && level != DNNMG_LEVEL_FINE) return DNNMG_EINVAL;
+    if (level == DNNMG_LEVEL_FINE && ctx->host.J != 1)
+        return fail(ctx, DNNMG_EUNSUPPORTED, "the fine-level solver is built for J = 1 patches only");
     if (!ctx->level[level]) {
         const int krylov = prm && prm->gmres_restart > 0 ? prm->gmres_restart : 40;
         if (krylov > 200) return fail(ctx, DNNMG_EINVAL, "gmres_restart > 200");
@@ -683,7 +692,14 @@ dnnmg_status dnnmg_net_create(const dnnmg_net_desc* net, const double* const* W,
     if (!ctx) return DNNMG_ENOMEM;
     ctx->net_only = true;
     ctx->net_capacity = max_rows;
-    ctx->host.n_geo = net && net->widths && net->widths[0] == kNInGeo24 ? 24 : 12;   // input width 228 or 240
+    // the input / output widths from the network: 216 or 1000 node values
+    // (J = 1, 2) + 12 or 24 geometry features, 81 or 375 outputs
+    if (net && net->widths && net->n_layers >= 1) {
+        const bool j2 = net->widths[net->n_layers] == kNOutJ2;
+        ctx->host.J = j2 ? 2 : 1;
+        ctx->host.npn = j2 ? 125 : 27;
+        ctx->host.n_geo = net->widths[0] - 8 * ctx->host.npn == 24 ? 24 : 12;
+    }
     ctx->precision = precision;
     ctx->stream = static_cast<cudaStream_t>(cuda_stream);
     if (cudaGetDevice(&ctx->device) != cudaSuccess) {

@@ -84,7 +84,10 @@ LocalEntity local_entity(int iota) {
 
 }  // namespace
 
-dnnmg_status build_hierarchy(const dnnmg_mesh_desc* mesh, int n_geo, HostHierarchy* h, std::string* err) {
+namespace {
+
+// Level L+1 of a mesh and its 27-node patches (J = 1).
+dnnmg_status build_one(const dnnmg_mesh_desc* mesh, int n_geo, HostHierarchy* h, std::string* err) {
     if (!mesh || !mesh->xyz || !mesh->cell_vertices || !mesh->vertex_bc || mesh->n_vertices <= 0 ||
         mesh->n_cells <= 0) {
         *err = "mesh: null array or non-positive size";
@@ -98,6 +101,8 @@ dnnmg_status build_hierarchy(const dnnmg_mesh_desc* mesh, int n_geo, HostHierarc
     }
     h->nv = nv;
     h->nc = nc;
+    h->J = 1;
+    h->npn = 27;
     h->xyz_c.assign(mesh->xyz, mesh->xyz + 3 * nv);
     h->cells.assign(mesh->cell_vertices, mesh->cell_vertices + 8 * nc);
     h->bc_c.assign(mesh->vertex_bc, mesh->vertex_bc + nv);
@@ -319,6 +324,69 @@ dnnmg_status build_hierarchy(const dnnmg_mesh_desc* mesh, int n_geo, HostHierarc
             }
             g[16 + k] = sum / 3.0;
         }
+    }
+    return DNNMG_OK;
+}
+
+}  // namespace
+
+dnnmg_status build_hierarchy(const dnnmg_mesh_desc* mesh, int n_geo, int J, HostHierarchy* h, std::string* err) {
+    if (J == 1) return build_one(mesh, n_geo, h, err);
+    if (J != 2) {
+        *err = "patch levels must be 1 or 2";
+        return DNNMG_EINVAL;
+    }
+    // J = 2: level L+2 is level L+1 refined by the same rules, with level
+    // L+1 as a mesh whose cell 8 P + (ci + 2 cj + 4 ck) is child (ci, cj, ck)
+    // of coarse cell P (vertices in lexicographic order)
+    HostHierarchy h1;
+    dnnmg_status st = build_one(mesh, n_geo, &h1, err);
+    if (st != DNNMG_OK) return st;
+    const int64_t nc = h1.nc;
+    std::vector<int32_t> cells1(size_t(64 * nc));
+    for (int64_t P = 0; P < nc; ++P)
+        for (int child = 0; child < 8; ++child) {
+            const int ci = child & 1, cj = (child >> 1) & 1, ck = (child >> 2) & 1;
+            for (int k = 0; k < 8; ++k) {
+                const int iota = (ci + (k & 1)) + 3 * (cj + ((k >> 1) & 1)) + 9 * (ck + ((k >> 2) & 1));
+                cells1[size_t(8 * (8 * P + child) + k)] = h1.patch_map[size_t(27 * P + iota)];
+            }
+        }
+    dnnmg_mesh_desc m1;
+    m1.n_vertices = int32_t(h1.n_fine);
+    m1.xyz = h1.xyz_f.data();
+    m1.n_cells = int32_t(8 * nc);
+    m1.cell_vertices = cells1.data();
+    m1.vertex_bc = h1.kind_f.data();
+    HostHierarchy h2;
+    if ((st = build_one(&m1, 12, &h2, err)) != DNNMG_OK) return st;
+    // the patch of coarse cell P: node (a, b, c) in {0..4}^3 is node
+    // (a - 2 ci, b - 2 cj, c - 2 ck) of child (ci, cj, ck), ci = min(a / 2, 1)
+    *h = std::move(h1);
+    h->J = 2;
+    h->npn = 125;
+    h->n_fine = h2.n_fine;
+    h->kind_f = std::move(h2.kind_f);
+    h->xyz_f = std::move(h2.xyz_f);
+    h->patch_map.assign(size_t(125 * nc), 0);
+    for (int64_t P = 0; P < nc; ++P)
+        for (int iota = 0; iota < 125; ++iota) {
+            const int a = iota % 5, b = (iota / 5) % 5, c = iota / 25;
+            const int ci = std::min(a / 2, 1), cj = std::min(b / 2, 1), ck = std::min(c / 2, 1);
+            const int child = ci + 2 * cj + 4 * ck;
+            const int l = (a - 2 * ci) + 3 * (b - 2 * cj) + 9 * (c - 2 * ck);
+            h->patch_map[size_t(125 * P + iota)] = h2.patch_map[size_t(27 * (8 * P + child) + l)];
+        }
+    // valences and the node -> (patch, iota) CSR in patch order
+    const int64_t n_fine = h->n_fine;
+    h->valence.assign(size_t(n_fine), 0);
+    for (int64_t e = 0; e < 125 * nc; ++e) h->valence[h->patch_map[e]]++;
+    h->node_ptr.assign(size_t(n_fine + 1), 0);
+    for (int64_t j = 0; j < n_fine; ++j) h->node_ptr[j + 1] = h->node_ptr[j] + h->valence[j];
+    h->node_idx.assign(size_t(125 * nc), 0);
+    {
+        std::vector<int32_t> fill(h->node_ptr.begin(), h->node_ptr.end() - 1);
+        for (int64_t e = 0; e < 125 * nc; ++e) h->node_idx[fill[h->patch_map[e]]++] = int32_t(e);
     }
     return DNNMG_OK;
 }

@@ -15,7 +15,9 @@ namespace dnnmg {
 constexpr int kNodes = 27;     // fine nodes per patch
 constexpr int kNIn = 228;      // network inputs per patch with the 12 edge lengths
 constexpr int kNInGeo24 = 240; // with the 24 geometry features (edges, diagonals, angles)
-constexpr int kNInPad = 256;   // row stride of X
+constexpr int kNInPad = 256;   // row stride of X (J = 1)
+constexpr int kNInPadJ2 = 1024;  // row stride of X for J = 2: 2 x 125 x 4 + 24 = 1024
+constexpr int kNOutJ2 = 375;   // network outputs per patch for J = 2 (125 x 3)
 constexpr int kNOut = 81;      // network outputs per patch
 
 // Level L+1 of a coarse mesh and the patch data, built on the host.
@@ -28,13 +30,17 @@ struct HostHierarchy {
     std::vector<int32_t> kind_f;     // [n_fine]
     std::vector<int32_t> valence;    // [n_fine]
     std::vector<double> xyz_f;       // [n_fine][3]
+    int J = 1;                       // refinement levels per patch (1 or 2)
+    int npn = 27;                    // nodes per patch (27, 125)
     int n_geo = 12;                  // geometry features per patch: 12 or 24
     std::vector<double> geo;         // [nc][n_geo]: 12 edge lengths (+ 4 diagonals, 8 mean dihedral angles)
     std::vector<int32_t> node_ptr, node_idx;   // fine node -> P*27+iota, patch order
     std::vector<int32_t> vert_ptr, vert_idx;   // coarse vertex -> P*8+k, patch order
 };
 
-dnnmg_status build_hierarchy(const dnnmg_mesh_desc* mesh, int n_geo, HostHierarchy* h, std::string* err);
+// Level L+J (J = 1 or 2) of a coarse mesh and its patches; level L+2 is
+// level L+1 refined once more by the same rules.
+dnnmg_status build_hierarchy(const dnnmg_mesh_desc* mesh, int n_geo, int J, HostHierarchy* h, std::string* err);
 
 // One mesh level for the Newton solve: cells in groups of 8 children of a
 // parent (27 nodes per group), which is the structure the two-level local
@@ -91,6 +97,7 @@ struct DeviceMesh {
     const uint8_t* coarse_dir = nullptr; // [nv]
     const double* xyz_d = nullptr;       // [nv][3] double
     const float* xyz_f = nullptr;        // [nv][3] float
+    int J = 1;                           // refinement levels per patch
     int n_geo = 12;                      // geometry features per patch
     const double* geo_d = nullptr;       // [nc][n_geo]
     const float* geo_f = nullptr;        // [nc][n_geo]

@@ -43,22 +43,42 @@ __device__ __forceinline__ void st4(T* p, V4<T> v) {
     *reinterpret_cast<V4<T>*>(p) = v;
 }
 
+// Patches of J levels (Sec. 5.2): a coarse cell refined J times, NC = 2^J
+// cells and NS = NC + 1 nodes per axis; node iota = a + NS b + NS^2 c.
+template <int J>
+struct PatchGeom {
+    static constexpr int NC = 1 << J;
+    static constexpr int NS = NC + 1;
+    static constexpr int NPN = NS * NS * NS;   // nodes per patch (27, 125)
+    static constexpr int NCELL = NC * NC * NC; // fine cells per patch (8, 64)
+};
+
 // Interpolate corner values c[8] (corner k at (k&1, (k>>1)&1, (k>>2)&1)) to
-// the patch node with grid coordinates (a, b, cz) in {0,1,2}^3: along each
-// axis coordinate 0 takes corner 0, 2 corner 1, 1 the mean of both.
-template <typename T>
+// the patch node with grid coordinates (a, b, cz) in {0..NS-1}^3: along each
+// axis the node sits at t = a / (NS - 1); t = 0 takes corner 0, t = 1
+// corner 1, in between (1 - t) c0 + t c1 (for t = 1/2 the mean).
+template <typename T, int NS>
 __device__ __forceinline__ T lerp_axis(int a, T c0, T c1) {
-    return a == 0 ? c0 : (a == 2 ? c1 : T(0.5) * (c0 + c1));
+    if (a == 0) return c0;
+    if (a == NS - 1) return c1;
+    const T t = T(a) / T(NS - 1);
+    return (T(1) - t) * c0 + t * c1;
 }
-template <typename T, int STRIDE>
+template <typename T, int STRIDE, int NS = 3>
 __device__ __forceinline__ T interp27(const T* c, int comp, int a, int b, int cz) {
-    T e00 = lerp_axis(a, c[0 * STRIDE + comp], c[1 * STRIDE + comp]);
-    T e10 = lerp_axis(a, c[2 * STRIDE + comp], c[3 * STRIDE + comp]);
-    T e01 = lerp_axis(a, c[4 * STRIDE + comp], c[5 * STRIDE + comp]);
-    T e11 = lerp_axis(a, c[6 * STRIDE + comp], c[7 * STRIDE + comp]);
-    T f0 = lerp_axis(b, e00, e10);
-    T f1 = lerp_axis(b, e01, e11);
-    return lerp_axis(cz, f0, f1);
+    T e00 = lerp_axis<T, NS>(a, c[0 * STRIDE + comp], c[1 * STRIDE + comp]);
+    T e10 = lerp_axis<T, NS>(a, c[2 * STRIDE + comp], c[3 * STRIDE + comp]);
+    T e01 = lerp_axis<T, NS>(a, c[4 * STRIDE + comp], c[5 * STRIDE + comp]);
+    T e11 = lerp_axis<T, NS>(a, c[6 * STRIDE + comp], c[7 * STRIDE + comp]);
+    T f0 = lerp_axis<T, NS>(b, e00, e10);
+    T f1 = lerp_axis<T, NS>(b, e01, e11);
+    return lerp_axis<T, NS>(cz, f0, f1);
+}
+// trilinear weight of corner bit kd at node coordinate a (of NS per axis)
+template <typename T, int NS>
+__device__ __forceinline__ T corner_weight(int a, int kd) {
+    const T t = T(a) / T(NS - 1);
+    return kd ? t : T(1) - t;
 }
 
 enum { MODE_RESIDUAL = 0, MODE_RHS = 1 };
@@ -207,34 +227,40 @@ __device__ __forceinline__ void element(const T* const (&xs)[8], const T* const 
     }
 }
 
-constexpr int kPatchesPerBlock = 8;   // 8 fine cells each -> 64 threads
+constexpr int kPatchThreads = 64;   // threads per block of the patch operator
+template <int J>
+constexpr int patches_per_block() { return kPatchThreads / PatchGeom<J>::NCELL; }   // 8 (J = 1), 1 (J = 2)
 
-// One thread per fine cell; 8 consecutive threads form a patch.
+// One thread per fine cell; the NCELL consecutive threads of a patch share
+// its nodes in shared memory.
 // 128 registers (8 blocks of 64 threads per SM) for float: the element's
 // arithmetic is latency-bound at fewer warps
 template <typename T>
 constexpr int patch_min_blocks() { return sizeof(T) == 4 ? 8 : 4; }
 
-template <typename T, int MODE>
-__global__ void __launch_bounds__(64, patch_min_blocks<T>()) patch_operator_kernel(
+template <typename T, int MODE, int J>
+__global__ void __launch_bounds__(kPatchThreads, patch_min_blocks<T>()) patch_operator_kernel(
     int64_t nc, const int32_t* __restrict__ cells, const int32_t* __restrict__ patch_map,
     const T* __restrict__ xyz, const T* __restrict__ xc, const T* __restrict__ dfine, T m, T th, T nu,
     T* __restrict__ partial, T* __restrict__ partial_c) {
-    __shared__ T s_cx[kPatchesPerBlock][8][3];    // corner coordinates
-    __shared__ T s_cu[kPatchesPerBlock][8][4];    // corner values
-    __shared__ T s_nx[kPatchesPerBlock][27][3];   // patch node coordinates
-    __shared__ T s_nu[kPatchesPerBlock][27][5];   // patch node values (u, v, w, p; stride 5 spreads
+    using G = PatchGeom<J>;
+    constexpr int PPB = patches_per_block<J>();
+    constexpr int TPP = G::NCELL;                 // threads per patch
+    __shared__ T s_cx[PPB][8][3];                 // corner coordinates
+    __shared__ T s_cu[PPB][8][4];                 // corner values
+    __shared__ T s_nx[PPB][G::NPN][3];            // patch node coordinates
+    __shared__ T s_nu[PPB][G::NPN][5];            // patch node values (u, v, w, p; stride 5 spreads
                                                   // the 8 nodes a cell reads over distinct banks)
-    // per-cell contributions, one padded row of 8 x 4 per cell: the 8 cells'
+    // per-cell contributions, one padded row of 8 x 4 per cell: the cells'
     // threads store with a stride of 33 words (no bank conflicts)
-    __shared__ T s_R[kPatchesPerBlock][8][33];
+    __shared__ T s_R[PPB][G::NCELL][33];
 
-    const int lp = threadIdx.x >> 3;   // patch within block
-    const int t = threadIdx.x & 7;     // child cell / corner
-    const int64_t P = int64_t(blockIdx.x) * kPatchesPerBlock + lp;
+    const int lp = threadIdx.x / TPP;   // patch within block
+    const int t = threadIdx.x % TPP;    // fine cell of the patch / node / corner
+    const int64_t P = int64_t(blockIdx.x) * PPB + lp;
     const bool active = P < nc;
 
-    if (active) {
+    if (active && t < 8) {
         const int32_t v = cells[8 * P + t];
 #pragma unroll
         for (int d = 0; d < 3; ++d) s_cx[lp][t][d] = xyz[3 * int64_t(v) + d];
@@ -246,8 +272,8 @@ __global__ void __launch_bounds__(64, patch_min_blocks<T>()) patch_operator_kern
     }
     __syncthreads();
     if (active) {
-        for (int iota = t; iota < 27; iota += 8) {
-            const int a = iota % 3, b = (iota / 3) % 3, c = iota / 9;
+        for (int iota = t; iota < G::NPN; iota += TPP) {
+            const int a = iota % G::NS, b = (iota / G::NS) % G::NS, c = iota / (G::NS * G::NS);
             // coordinates relative to corner 0 (the element needs only
             // differences; this keeps them exact in float)
 #pragma unroll
@@ -255,12 +281,12 @@ __global__ void __launch_bounds__(64, patch_min_blocks<T>()) patch_operator_kern
                 T cr[8];
 #pragma unroll
                 for (int k = 0; k < 8; ++k) cr[k] = s_cx[lp][k][d] - s_cx[lp][0][d];
-                s_nx[lp][iota][d] = interp27<T, 1>(cr, 0, a, b, c);
+                s_nx[lp][iota][d] = interp27<T, 1, G::NS>(cr, 0, a, b, c);
             }
 #pragma unroll
-            for (int d = 0; d < 4; ++d) s_nu[lp][iota][d] = interp27<T, 4>(&s_cu[lp][0][0], d, a, b, c);
+            for (int d = 0; d < 4; ++d) s_nu[lp][iota][d] = interp27<T, 4, G::NS>(&s_cu[lp][0][0], d, a, b, c);
             if (MODE == MODE_RHS) {   // corrected velocity x~ + d
-                const int64_t j = patch_map[27 * P + iota];
+                const int64_t j = patch_map[G::NPN * P + iota];
 #pragma unroll
                 for (int d = 0; d < 3; ++d) s_nu[lp][iota][d] += dfine[3 * j + d];
             }
@@ -268,12 +294,13 @@ __global__ void __launch_bounds__(64, patch_min_blocks<T>()) patch_operator_kern
     }
     __syncthreads();
     if (active) {
-        const int ci = t & 1, cj = (t >> 1) & 1, ck = (t >> 2) & 1;
+        const int ci = t % G::NC, cj = (t / G::NC) % G::NC, ck = t / (G::NC * G::NC);
         const T* xs[8];
         const T* us[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-            const int node = (ci + (k & 1)) + 3 * (cj + ((k >> 1) & 1)) + 9 * (ck + ((k >> 2) & 1));
+            const int node =
+                (ci + (k & 1)) + G::NS * (cj + ((k >> 1) & 1)) + G::NS * G::NS * (ck + ((k >> 2) & 1));
             xs[k] = &s_nx[lp][node][0];
             us[k] = &s_nu[lp][node][0];
         }
@@ -289,28 +316,28 @@ __global__ void __launch_bounds__(64, patch_min_blocks<T>()) patch_operator_kern
             for (int c = 0; c < 4; ++c) s_R[lp][t][4 * k + c] = R[k][c];
     }
     __syncthreads();
-    // sum the children's contributions at each patch node, children in order
-    for (int iota = t; active && iota < 27; iota += 8) {
-        const int a = iota % 3, b = (iota / 3) % 3, c = iota / 9;
+    // sum the contributions of the cells containing each patch node, in a fixed order
+    for (int iota = t; active && iota < G::NPN; iota += TPP) {
+        const int a = iota % G::NS, b = (iota / G::NS) % G::NS, c = iota / (G::NS * G::NS);
         T acc[4] = {T(0), T(0), T(0), T(0)};
         for (int k2 = 0; k2 < 2; ++k2) {
             const int ck = c - k2;
-            if (ck < 0 || ck > 1) continue;
+            if (ck < 0 || ck >= G::NC) continue;
             for (int j2 = 0; j2 < 2; ++j2) {
                 const int cj = b - j2;
-                if (cj < 0 || cj > 1) continue;
+                if (cj < 0 || cj >= G::NC) continue;
                 for (int i2 = 0; i2 < 2; ++i2) {
                     const int ci = a - i2;
-                    if (ci < 0 || ci > 1) continue;
-                    const int child = ci + 2 * cj + 4 * ck;
+                    if (ci < 0 || ci >= G::NC) continue;
+                    const int cell = ci + G::NC * cj + G::NC * G::NC * ck;
                     const int vert = i2 + 2 * j2 + 4 * k2;
 #pragma unroll
-                    for (int d = 0; d < 4; ++d) acc[d] += s_R[lp][child][4 * vert + d];
+                    for (int d = 0; d < 4; ++d) acc[d] += s_R[lp][cell][4 * vert + d];
                 }
             }
         }
         if (MODE == MODE_RHS) acc[3] = T(0);
-        st4(partial + (27 * P + iota) * 4, V4<T>{acc[0], acc[1], acc[2], acc[3]});
+        st4(partial + (G::NPN * P + iota) * 4, V4<T>{acc[0], acc[1], acc[2], acc[3]});
         if (MODE == MODE_RHS) {
             // keep the node sums for the restriction below
 #pragma unroll
@@ -319,18 +346,16 @@ __global__ void __launch_bounds__(64, patch_min_blocks<T>()) patch_operator_kern
     }
     if (MODE == MODE_RHS) {
         __syncthreads();
-        if (!active) return;
+        if (!active || t >= 8) return;
         // restriction P^T of the patch's partial rhs onto its 8 corners:
         // corner k collects node iota with the trilinear weight of k at iota
         const int k = t;
         const int kx = k & 1, ky = (k >> 1) & 1, kz = (k >> 2) & 1;
         T acc[3] = {T(0), T(0), T(0)};
-        for (int iota = 0; iota < 27; ++iota) {
-            const int a = iota % 3, b = (iota / 3) % 3, c = iota / 9;
-            const T wx = a == 1 ? T(0.5) : ((a == 2) == (kx == 1) ? T(1) : T(0));
-            const T wy = b == 1 ? T(0.5) : ((b == 2) == (ky == 1) ? T(1) : T(0));
-            const T wz = c == 1 ? T(0.5) : ((c == 2) == (kz == 1) ? T(1) : T(0));
-            const T wgt = wx * wy * wz;
+        for (int iota = 0; iota < G::NPN; ++iota) {
+            const int a = iota % G::NS, b = (iota / G::NS) % G::NS, c = iota / (G::NS * G::NS);
+            const T wgt = corner_weight<T, G::NS>(a, kx) * corner_weight<T, G::NS>(b, ky) *
+                          corner_weight<T, G::NS>(c, kz);
             if (wgt != T(0)) {
 #pragma unroll
                 for (int d = 0; d < 3; ++d) acc[d] += wgt * s_nu[lp][iota][d];
@@ -398,7 +423,7 @@ __global__ void __launch_bounds__(256) vertex_reduce_kernel(
 // sum_iota w(iota, k) b[dof(P, iota)] / valence(dof(P, iota)); summed over the
 // patches containing a coarse vertex (vertex_reduce) this is (P^T b)_v,
 // because every patch containing a fine node contains all its parents.
-template <typename T>
+template <typename T, int J>
 __global__ void __launch_bounds__(256) restrict_patch_kernel(
     int64_t nc, const int32_t* __restrict__ patch_map, const int32_t* __restrict__ node_ptr,
     const T* __restrict__ b, T* __restrict__ partial_c) {
@@ -407,15 +432,14 @@ __global__ void __launch_bounds__(256) restrict_patch_kernel(
     const int64_t P = e >> 3;
     const int k = int(e & 7);
     const int kx = k & 1, ky = (k >> 1) & 1, kz = (k >> 2) & 1;
+    using G = PatchGeom<J>;
     T acc[3] = {T(0), T(0), T(0)};
-    for (int iota = 0; iota < 27; ++iota) {
-        const int a = iota % 3, bb = (iota / 3) % 3, c = iota / 9;
-        const T wx = a == 1 ? T(0.5) : ((a == 2) == (kx == 1) ? T(1) : T(0));
-        const T wy = bb == 1 ? T(0.5) : ((bb == 2) == (ky == 1) ? T(1) : T(0));
-        const T wz = c == 1 ? T(0.5) : ((c == 2) == (kz == 1) ? T(1) : T(0));
-        const T w = wx * wy * wz;
+    for (int iota = 0; iota < G::NPN; ++iota) {
+        const int a = iota % G::NS, bb = (iota / G::NS) % G::NS, c = iota / (G::NS * G::NS);
+        const T w = corner_weight<T, G::NS>(a, kx) * corner_weight<T, G::NS>(bb, ky) *
+                    corner_weight<T, G::NS>(c, kz);
         if (w == T(0)) continue;
-        const int64_t j = patch_map[27 * P + iota];
+        const int64_t j = patch_map[G::NPN * P + iota];
         const T s = w / T(node_ptr[j + 1] - node_ptr[j]);
 #pragma unroll
         for (int d = 0; d < 3; ++d) acc[d] += s * b[4 * j + d];
@@ -424,16 +448,17 @@ __global__ void __launch_bounds__(256) restrict_patch_kernel(
 }
 
 // x_fine[j] from the first patch containing j (deterministic).
-template <typename T>
+template <typename T, int J>
 __global__ void __launch_bounds__(256) prolongate_kernel(
     int64_t n, const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
     const int32_t* __restrict__ cells, const T* __restrict__ xc, T* __restrict__ xf) {
     const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (j >= n) return;
+    using G = PatchGeom<J>;
     const int32_t e = idx[ptr[j]];
-    const int64_t P = e / 27;
-    const int iota = e % 27;
-    const int a = iota % 3, b = (iota / 3) % 3, c = iota / 9;
+    const int64_t P = e / G::NPN;
+    const int iota = e % G::NPN;
+    const int a = iota % G::NS, b = (iota / G::NS) % G::NS, c = iota / (G::NS * G::NS);
     T cu[8][4];
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
@@ -444,10 +469,10 @@ __global__ void __launch_bounds__(256) prolongate_kernel(
         cu[k][3] = u.w;
     }
     V4<T> o;
-    o.x = interp27<T, 4>(&cu[0][0], 0, a, b, c);
-    o.y = interp27<T, 4>(&cu[0][0], 1, a, b, c);
-    o.z = interp27<T, 4>(&cu[0][0], 2, a, b, c);
-    o.w = interp27<T, 4>(&cu[0][0], 3, a, b, c);
+    o.x = interp27<T, 4, G::NS>(&cu[0][0], 0, a, b, c);
+    o.y = interp27<T, 4, G::NS>(&cu[0][0], 1, a, b, c);
+    o.z = interp27<T, 4, G::NS>(&cu[0][0], 2, a, b, c);
+    o.w = interp27<T, 4, G::NS>(&cu[0][0], 3, a, b, c);
     st4(xf + 4 * j, o);
 }
 
@@ -499,25 +524,36 @@ __device__ __forceinline__ void store4(TX* dst, T a, T b, T c, T d) {
     }
 }
 
-// One warp per patch: X[P] = [x~ at 27 nodes | r at 27 nodes | geometry | 0].
-// Lane iota < 27 writes node iota's 4 values of x~ and of r as one vector
-// each; lanes 0..9 write the n_geo (12 or 24) geometry features and the zero
-// padding (4 values per lane).  Row stride 256, so every 4-value group is
-// aligned.
-template <typename T, typename TX>
+// One warp per patch: X[P] = [x~ at the NPN nodes | r at the NPN nodes |
+// geometry | 0] with row stride LD = 256 (J = 1) or 1024 (J = 2).  Lane l
+// writes nodes l, l + 32, ... (4 values of x~ and of r as one vector each);
+// the first (LD - 8 NPN) / 4 lanes write the n_geo (12 or 24) geometry
+// features and the zeros after them up to the row end.  Every 4-value group
+// is aligned.
+template <typename T, typename TX, int J>
 __global__ void __launch_bounds__(256) local_restrict_kernel(
     int64_t nc, const int32_t* __restrict__ cells, const int32_t* __restrict__ patch_map,
     const T* __restrict__ xc, const T* __restrict__ r, const T* __restrict__ geo, int n_geo,
     TX* __restrict__ X) {
+    using G = PatchGeom<J>;
+    constexpr int LD = J == 1 ? kNInPad : kNInPadJ2;
+    constexpr int NODES_PER_LANE = (G::NPN + 31) / 32;
     const int lane = threadIdx.x & 31;
     const int64_t P = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     if (P >= nc) return;
-    // issue the independent loads first: corner ids, node ids, edge lengths
+    // issue the independent loads first: corner ids, node ids, geometry
     const int32_t v = lane < 8 ? __ldg(cells + 8 * P + lane) : 0;
-    const int32_t j = lane < 27 ? __ldg(patch_map + 27 * P + lane) : 0;
+    int32_t jn[NODES_PER_LANE];
+#pragma unroll
+    for (int i = 0; i < NODES_PER_LANE; ++i) {
+        const int iota = lane + 32 * i;
+        jn[i] = iota < G::NPN ? __ldg(patch_map + int64_t(G::NPN) * P + iota) : 0;
+    }
     const T el = lane < n_geo ? geo[int64_t(n_geo) * P + lane] : T(0);
-    V4<T> rv{T(0), T(0), T(0), T(0)};
-    if (lane < 27) rv = ld4(r + 4 * int64_t(j));
+    V4<T> rv[NODES_PER_LANE];
+#pragma unroll
+    for (int i = 0; i < NODES_PER_LANE; ++i)
+        rv[i] = lane + 32 * i < G::NPN ? ld4(r + 4 * int64_t(jn[i])) : V4<T>{T(0), T(0), T(0), T(0)};
     T cu[4] = {T(0), T(0), T(0), T(0)};
     if (lane < 8) {
         const V4<T> u = ld4(xc + 4 * int64_t(v));
@@ -538,15 +574,22 @@ __global__ void __launch_bounds__(256) local_restrict_kernel(
         const T g = __shfl_sync(0xffffffffu, el, (4 * lane + i) & 31);
         e[i] = 4 * lane + i < n_geo ? g : T(0);
     }
-    TX* row = X + P * kNInPad;
-    if (lane < 27) {
-        const int a = lane % 3, b = (lane / 3) % 3, c = lane / 9;
-        store4<TX>(row + 4 * lane, interp27<T, 4>(&corner[0][0], 0, a, b, c), interp27<T, 4>(&corner[0][0], 1, a, b, c),
-                   interp27<T, 4>(&corner[0][0], 2, a, b, c), interp27<T, 4>(&corner[0][0], 3, a, b, c));
-        store4<TX>(row + 108 + 4 * lane, rv.x, rv.y, rv.z, rv.w);
+    TX* row = X + P * LD;
+#pragma unroll
+    for (int i = 0; i < NODES_PER_LANE; ++i) {
+        const int iota = lane + 32 * i;
+        if (iota >= G::NPN) continue;
+        const int a = iota % G::NS, b = (iota / G::NS) % G::NS, c = iota / (G::NS * G::NS);
+        store4<TX>(row + 4 * iota, interp27<T, 4, G::NS>(&corner[0][0], 0, a, b, c),
+                   interp27<T, 4, G::NS>(&corner[0][0], 1, a, b, c), interp27<T, 4, G::NS>(&corner[0][0], 2, a, b, c),
+                   interp27<T, 4, G::NS>(&corner[0][0], 3, a, b, c));
+        store4<TX>(row + 4 * G::NPN + 4 * iota, rv[i].x, rv[i].y, rv[i].z, rv[i].w);
     }
-    if (lane < 10)   // columns 216..255
-        store4<TX>(row + 216 + 4 * lane, e[0], e[1], e[2], e[3]);
+    constexpr int GEO0 = 8 * G::NPN;              // first geometry column (216, 1000)
+    constexpr int GEO_GROUPS = (LD - GEO0) / 4;   // 4-column groups up to the row end (10, 6)
+    static_assert(GEO_GROUPS <= 32 && 4 * GEO_GROUPS >= 24 && GEO0 + 4 * GEO_GROUPS == LD, "input row layout");
+    if (lane < GEO_GROUPS)   // columns GEO0 .. LD - 1: the features, then zeros
+        store4<TX>(row + GEO0 + 4 * lane, e[0], e[1], e[2], e[3]);
 }
 
 // d_j = mu_j * sum_{(P,iota) in j} Y[P][3 iota + c], mu_j = 1 / valence.
@@ -560,9 +603,7 @@ __global__ void __launch_bounds__(256) extend_kernel(
     const int32_t e0 = ptr[j], e1 = ptr[j + 1];
     for (int32_t e = e0; e < e1; ++e) {
         const int32_t pe = idx[e];
-        const int64_t P = pe / 27;
-        const int iota = pe - int32_t(P) * 27;
-        const T* y = Y + P * kNOut + 3 * iota;
+        const T* y = Y + 3 * int64_t(pe);   // Y[P][3 iota]: rows of 3 x nodes per patch
         acc[0] += y[0];
         acc[1] += y[1];
         acc[2] += y[2];
@@ -684,17 +725,33 @@ const float* edge_of<float>(const DeviceMesh& dm) { return dm.geo_f; }
 
 template <typename T>
 cudaError_t launch_prolongate(const DeviceMesh& dm, const T* xc, T* xf, cudaStream_t s) {
-    prolongate_kernel<T><<<blocks_for(dm.n_fine, 256), 256, 0, s>>>(dm.n_fine, dm.node_ptr, dm.node_idx,
-                                                                     dm.cells, xc, xf);
+    if (dm.J == 2)
+        prolongate_kernel<T, 2><<<blocks_for(dm.n_fine, 256), 256, 0, s>>>(dm.n_fine, dm.node_ptr, dm.node_idx,
+                                                                            dm.cells, xc, xf);
+    else
+        prolongate_kernel<T, 1><<<blocks_for(dm.n_fine, 256), 256, 0, s>>>(dm.n_fine, dm.node_ptr, dm.node_idx,
+                                                                            dm.cells, xc, xf);
     return cudaGetLastError();
+}
+
+// patch operator launch for J = 1 or 2 (64-thread blocks of 8 or 1 patches)
+template <typename T, int MODE>
+void launch_patch_operator(const DeviceMesh& dm, OpParams p, const T* xc, const T* dfine, T* partial, T* partial_c,
+                           cudaStream_t s) {
+    if (dm.J == 2)
+        patch_operator_kernel<T, MODE, 2><<<blocks_for(dm.nc, patches_per_block<2>()), kPatchThreads, 0, s>>>(
+            dm.nc, dm.cells, dm.patch_map, xyz_of<T>(dm), xc, dfine, T(p.m), T(p.theta), T(p.nu), partial,
+            partial_c);
+    else
+        patch_operator_kernel<T, MODE, 1><<<blocks_for(dm.nc, patches_per_block<1>()), kPatchThreads, 0, s>>>(
+            dm.nc, dm.cells, dm.patch_map, xyz_of<T>(dm), xc, dfine, T(p.m), T(p.theta), T(p.nu), partial,
+            partial_c);
 }
 
 template <typename T>
 cudaError_t launch_residual(const DeviceMesh& dm, OpParams p, const T* xc, const T* F, T* r, T* partial,
                             cudaStream_t s, int* launches) {
-    patch_operator_kernel<T, MODE_RESIDUAL><<<blocks_for(dm.nc, kPatchesPerBlock), 64, 0, s>>>(
-        dm.nc, dm.cells, dm.patch_map, xyz_of<T>(dm), xc, nullptr, T(p.m), T(p.theta), T(p.nu), partial,
-        nullptr);
+    launch_patch_operator<T, MODE_RESIDUAL>(dm, p, xc, nullptr, partial, nullptr, s);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     node_reduce_kernel<T, MODE_RESIDUAL><<<blocks_for(dm.n_fine, 256), 256, 0, s>>>(
@@ -705,15 +762,23 @@ cudaError_t launch_residual(const DeviceMesh& dm, OpParams p, const T* xc, const
 
 template <typename T, typename TX>
 cudaError_t launch_local_restrict(const DeviceMesh& dm, const T* xc, const T* r, TX* X, cudaStream_t s) {
-    local_restrict_kernel<T, TX><<<blocks_for(dm.nc * 32, 256), 256, 0, s>>>(
-        dm.nc, dm.cells, dm.patch_map, xc, r, edge_of<T>(dm), dm.n_geo, X);
+    if (dm.J == 2)
+        local_restrict_kernel<T, TX, 2><<<blocks_for(dm.nc * 32, 256), 256, 0, s>>>(
+            dm.nc, dm.cells, dm.patch_map, xc, r, edge_of<T>(dm), dm.n_geo, X);
+    else
+        local_restrict_kernel<T, TX, 1><<<blocks_for(dm.nc * 32, 256), 256, 0, s>>>(
+            dm.nc, dm.cells, dm.patch_map, xc, r, edge_of<T>(dm), dm.n_geo, X);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_restrict(const DeviceMesh& dm, const T* b_fine, T* b_coarse, T* partial_c, cudaStream_t s) {
-    restrict_patch_kernel<T><<<blocks_for(8 * dm.nc, 256), 256, 0, s>>>(dm.nc, dm.patch_map, dm.node_ptr, b_fine,
-                                                                         partial_c);
+    if (dm.J == 2)
+        restrict_patch_kernel<T, 2><<<blocks_for(8 * dm.nc, 256), 256, 0, s>>>(dm.nc, dm.patch_map, dm.node_ptr,
+                                                                                b_fine, partial_c);
+    else
+        restrict_patch_kernel<T, 1><<<blocks_for(8 * dm.nc, 256), 256, 0, s>>>(dm.nc, dm.patch_map, dm.node_ptr,
+                                                                                b_fine, partial_c);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     vertex_reduce_kernel<T><<<blocks_for(dm.nv, 256), 256, 0, s>>>(dm.nv, dm.vert_ptr, dm.vert_idx, partial_c,
@@ -733,9 +798,7 @@ cudaError_t launch_extend(const DeviceMesh& dm, const T* Y, T* d, cudaStream_t s
 template <typename T>
 cudaError_t launch_rhs_restrict(const DeviceMesh& dm, OpParams p, const T* xc, const T* d, T* b_fine,
                                 T* b_coarse, T* partial, T* partial_c, cudaStream_t s, int* launches) {
-    patch_operator_kernel<T, MODE_RHS><<<blocks_for(dm.nc, kPatchesPerBlock), 64, 0, s>>>(
-        dm.nc, dm.cells, dm.patch_map, xyz_of<T>(dm), xc, d, T(p.m), T(p.theta), T(p.nu), partial,
-        partial_c);
+    launch_patch_operator<T, MODE_RHS>(dm, p, xc, d, partial, partial_c, s);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     *launches += 1;
@@ -844,7 +907,7 @@ extern "C" dnnmg_status dnnmg_residual_noalloc(int64_t n_patches, int64_t n_fine
     float* partial = nullptr;
     if (noalloc_scratch(&partial) != cudaSuccess) return DNNMG_ECUDA;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-    patch_operator_kernel<float, MODE_RESIDUAL><<<blocks_for(n_patches, kPatchesPerBlock), 64, 0, s>>>(
+    patch_operator_kernel<float, MODE_RESIDUAL, 1><<<blocks_for(n_patches, patches_per_block<1>()), kPatchThreads, 0, s>>>(
         n_patches, cells_dev, nullptr, xyz_dev, x_coarse_dev, nullptr, float(1.0 / dt), float(theta), float(nu),
         partial, nullptr);
     if (cudaGetLastError() != cudaSuccess) return DNNMG_ECUDA;

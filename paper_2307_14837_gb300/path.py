@@ -17,7 +17,7 @@ PRECISIONS = {"fp64": capi.FP64, "fp32": capi.FP32, "bf16": capi.BF16}
 
 
 class PatchPath:
-    def __init__(self, mesh, nu, dt, theta, precision, device="cuda", stream=None, features=12):
+    def __init__(self, mesh, nu, dt, theta, precision, device="cuda", stream=None, features=12, patch_levels=1):
         if isinstance(precision, str):
             precision = PRECISIONS[precision]
         self.device = torch.device(device)
@@ -26,7 +26,8 @@ class PatchPath:
         torch.cuda.set_device(self.device)
         self.precision = precision
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
-        self.ctx = capi.dnnmg_create(mesh, nu, dt, theta, precision, self.stream, features=features)
+        self.ctx = capi.dnnmg_create(mesh, nu, dt, theta, precision, self.stream, features=features,
+                                     patch_levels=patch_levels)
         self.sizes = capi.dnnmg_get_sizes(self.ctx)
         self.dtype = _FIELD_DTYPE[precision]
         self.x_dtype = _X_DTYPE[precision]
@@ -76,7 +77,7 @@ class PatchPath:
 
     def network(self, X, n_rows=None):
         n = X.shape[0] if n_rows is None else n_rows
-        Y = self.field(n, capi.N_OUT)
+        Y = self.field(n, self.sizes["n_out"])
         capi.dnnmg_network(self.ctx, X, Y, n)
         return Y
 

@@ -35,6 +35,11 @@ CASES = {
                                  widths=(240, 64, 64, 64, 81), bn=True, features=24),
     "channel4_geo24": dict(mesh=("channel", 4, 0.0), nu=5e-4, dt=0.005, theta=0.5,
                            widths=(240, 128, 128, 81), bn=True, features=24),
+    # J = 2 patches (125 nodes, 1024 / 1012 inputs, 375 outputs, Table 2)
+    "cavity4_j2": dict(mesh=("cavity", 4, 0.0), nu=0.01, dt=0.01, theta=1.0,
+                       widths=(1024, 128, 128, 375), bn=False, features=24, patch_levels=2),
+    "cavity2_jitter_j2": dict(mesh=("cavity", 2, 0.2), nu=0.01, dt=0.01, theta=0.5,
+                              widths=(1012, 64, 64, 64, 375), bn=True, features=12, patch_levels=2),
 }
 
 TOL = {"fp64": 1e-12, "fp32": 1e-5, "bf16": 2e-2}
@@ -54,7 +59,8 @@ def case_data(name, seed=0):
     """Inputs and the oracle's intermediates of one hot-path step."""
     c = CASES[name]
     m = make_mesh(c["mesh"], seed)
-    h = omesh.Hierarchy(m["xyz"], m["cells"], m["vertex_bc"])
+    hier = omesh.Hierarchy2 if c.get("patch_levels", 1) == 2 else omesh.Hierarchy
+    h = hier(m["xyz"], m["cells"], m["vertex_bc"])
     xc = I.coarse_state(m, seed)
     # F stands in for the previous step's rhs: magnitude (1/dt) |v| |cell|
     ext = m["xyz"].max(axis=0) - m["xyz"].min(axis=0)

@@ -22,7 +22,8 @@ def _lib():
 
 def _path(d, precision):
     c = d["case"]
-    p = PatchPath(d["mesh"], c["nu"], c["dt"], c["theta"], precision, features=c.get("features", 12))
+    p = PatchPath(d["mesh"], c["nu"], c["dt"], c["theta"], precision, features=c.get("features", 12),
+                  patch_levels=c.get("patch_levels", 1))
     Ws, ss, ts = d["net"]
     p.set_network(c["widths"], Ws, ss, ts, skip=True)
     return p
@@ -37,9 +38,11 @@ def test_mesh_data_bit_exact(name):
     d = case_data(name)
     h = d["h"]
     nf = d["case"].get("features", 12)
-    p = PatchPath(d["mesh"], 0.01, 0.01, 1.0, "fp64", features=nf)
+    J = d["case"].get("patch_levels", 1)
+    p = PatchPath(d["mesh"], 0.01, 0.01, 1.0, "fp64", features=nf, patch_levels=J)
     assert p.n_fine == h.n_fine and p.n_patches == h.n_patches
-    assert p.sizes["n_in"] == 216 + nf
+    npn = h.patch_map.shape[1]
+    assert p.sizes["n_in"] == 8 * npn + nf and p.sizes["n_out"] == 3 * npn
     assert np.array_equal(p.mesh_data(capi.PATCH_MAP), h.patch_map)
     assert np.array_equal(p.mesh_data(capi.VALENCE), h.mult)
     assert np.array_equal(p.mesh_data(capi.FINE_KIND), h.bc_f)

@@ -83,3 +83,41 @@ def test_zero_network_reproduces_plain_coarse_scheme():
     Ws2, _, _ = I.network_weights(widths, seed=0)
     dn2, _ = dnnmg.run(h, coarse, (Ws2, ss, ts, True), x0, 2, prm, bcv)
     assert np.abs(dn2[-1] - pl[1]).max() > 1e-6
+
+
+def test_j2_zero_network_reproduces_plain_coarse_scheme():
+    # J = 2: with W_L = 0 and backward Euler (rhs = mass term, which nested
+    # Q1 spaces restrict exactly) the two-level patch step gives the plain
+    # coarse right-hand side, so the trajectories agree
+    m = I.cavity_mesh(2)
+    h = mesh.Hierarchy2(m["xyz"], m["cells"], m["vertex_bc"])
+    coarse = fem.Level(m["xyz"], m["cells"], m["vertex_bc"], True)
+    prm = dict(m=100.0, theta=1.0, nu=0.01, alpha0=0.02, delta0=0.1)
+    widths = (1012, 16, 375)
+    Ws, ss, ts = I.network_weights(widths, seed=0)
+    Ws[-1] = np.zeros_like(Ws[-1])
+    x0 = np.zeros((m["xyz"].shape[0], 4))
+    bcv = lambda t: I.dirichlet_values(m, m["xyz"], m["vertex_bc"], t)
+    dn, last = dnnmg.run(h, coarse, (Ws, ss, ts, True), x0, 2, prm, bcv)
+    pl = dnnmg.run_plain(coarse, x0, 2, prm, bcv)
+    assert last["X"].shape == (8, 1012) and last["Y"].shape == (8, 375)
+    for a, b in zip(dn, pl):
+        assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max()
+
+
+def test_j2_gather_by_position():
+    m = I.cavity_mesh(2, jitter=0.15, seed=2)
+    h = mesh.Hierarchy2(m["xyz"], m["cells"], m["vertex_bc"])
+    xf = transfer.prolongate(h, I.coarse_state(m, 0))
+    r = I.fine_rhs(h.n_fine, 1)
+    X = dnnmg.gather(h, xf, r, features=24)
+    assert X.shape == (8, 1024)
+    for P in (0, 5):
+        for iota in (0, 31, 62, 124):
+            t = np.array([iota % 5, (iota // 5) % 5, iota // 25]) / 4.0
+            w = np.array([np.prod([t[d] if (k >> d) & 1 else 1 - t[d] for d in range(3)]) for k in range(8)])
+            pos = w @ m["xyz"][m["cells"][P]]
+            j = int(np.argmin(np.sum((h.xyz_f - pos) ** 2, axis=1)))
+            assert np.array_equal(X[P, 4 * iota:4 * iota + 4], xf[j])
+            assert np.array_equal(X[P, 500 + 4 * iota:504 + 4 * iota], r[j])
+    assert np.allclose(X[:, 1000:], h.geometry(24), rtol=0, atol=0)

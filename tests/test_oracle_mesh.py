@@ -166,7 +166,45 @@ def test_golden_patch_sizes():
     rows = [list(map(int, l.split())) for l in open(path) if l.strip() and not l.startswith("#")]
     J1 = rows[0]
     assert J1[1] == 27 and J1[2] == 4 * 27 and J1[4] == 2 * J1[2] + J1[3] and J1[5] == 3 * 27
-    # the build's patch: 27 nodes per coarse cell
+    # the build's patches: 27 and 125 nodes per coarse cell, input rows of
+    # 2 N_dof^P + n_Geo with the 24 geometry features
     m = I.cavity_mesh(2)
     h = _hier(m)
     assert h.patch_map.shape[1] == J1[1]
+    J2 = rows[1]
+    assert J2[0] == 2 and J2[5] == 3 * J2[1] and J2[4] == 2 * J2[2] + J2[3]
+    h2 = mesh.Hierarchy2(m["xyz"], m["cells"], m["vertex_bc"])
+    assert h2.patch_map.shape[1] == J2[1]
+    from oracle import dnnmg
+    X = dnnmg.gather(h2, np.zeros((h2.n_fine, 4)), np.zeros((h2.n_fine, 4)), features=J2[3])
+    assert X.shape[1] == J2[4]
+    assert dnnmg.gather(h, np.zeros((h.n_fine, 4)), np.zeros((h.n_fine, 4)), features=J1[3]).shape[1] == J1[4]
+
+
+@pytest.mark.parametrize("n", [1, 2])
+def test_j2_counts_valences_closed_form(n):
+    # twofold refinement of the n^3 cavity: the (4n+1)^3 grid; a node lies in
+    # 2 patches per axis where its grid index is an interior multiple of 4
+    m = I.cavity_mesh(n, grouped=False)
+    h = mesh.Hierarchy2(m["xyz"], m["cells"], m["vertex_bc"])
+    assert h.n_fine == (4 * n + 1) ** 3 and h.patch_map.shape == (n ** 3, 125)
+    ijk = np.rint(h.xyz_f * 4 * n).astype(int)
+
+    def m1(i):
+        return np.where(i % 4 != 0, 1, np.where((i == 0) | (i == 4 * n), 1, 2))
+    assert np.array_equal(h.mult, m1(ijk[:, 0]) * m1(ijk[:, 1]) * m1(ijk[:, 2]))
+    assert all(len(set(r)) == 125 for r in h.patch_map.tolist())
+
+
+def test_j2_patch_map_points_at_trilinear_positions():
+    m = I.cavity_mesh(2, jitter=0.2, seed=5)
+    h = mesh.Hierarchy2(m["xyz"], m["cells"], m["vertex_bc"])
+    X = m["xyz"][m["cells"]]
+    for iota in range(125):
+        t = np.array([iota % 5, (iota // 5) % 5, iota // 25]) / 4.0
+        w = np.array([np.prod([t[d] if (k >> d) & 1 else 1 - t[d] for d in range(3)]) for k in range(8)])
+        assert np.allclose(h.xyz_f[h.patch_map[:, iota]], np.einsum("k,nkd->nd", w, X), rtol=0, atol=1e-15)
+    # every fine node of level L+2 belongs to some patch, Dirichlet kinds on the lid
+    assert np.array_equal(np.unique(h.patch_map), np.arange(h.n_fine))
+    top = np.isclose(h.xyz_f[:, 2], 1.0)
+    assert np.all(h.bc_f[top] > 0)
