@@ -318,8 +318,41 @@ def run_ours(args, rank, world, local_rank):
                 "patches_per_s": round(nc * 1000.0 / ms, 1), "timed_steps": 3}
         q.close()
 
+    # the paper's forms (Sec. 5.2, Table 2): 24 geometry features and 8 hidden
+    # layers of width 750 with skips, for J = 1 on this workload and for
+    # J = 2 (125-node patches on level L+2) on a coarser channel with about
+    # as many fine cells
+    paper = None
+    if not args.no_fp64 and rank == 0:
+        paper = {}
+        for name, J, nz_p in (("j1_240_750x8_81", 1, args.nz), ("j2_1024_750x8_375", 2, max(4, args.nz // 2))):
+            mp, nup = build_workload(seed=rank, nz=nz_p)
+            q = PatchPath(mp, nup, DT, THETA, "bf16", device=dev, stream=stream, features=24, patch_levels=J)
+            wd = (q.sizes["n_in"],) + (750,) * 8 + (q.sizes["n_out"],)
+            Wp, sp, tp = I.network_weights(wd, seed=0, scale_shift=True)
+            q.set_network(wd, Wp, sp, tp, skip=True)
+            xq = q.to_device(I.coarse_state(mp, seed=rank).astype(np.float32))
+            Fq = q.to_device(I.fine_rhs(q.n_fine, seed=rank, scale=(1 / DT) * 0.42 / (8 * q.n_patches)).astype(np.float32))
+            bfq, bcq = q.field(q.n_fine, 4), q.field(q.n_coarse, 4)
+            with torch.cuda.stream(stream):
+                for _ in range(2):
+                    q.step(xq, Fq, bfq, bcq)
+                torch.cuda.synchronize(dev)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                for _ in range(5):
+                    q.step(xq, Fq, bfq, bcq)
+                b.record(stream)
+                torch.cuda.synchronize(dev)
+            ms = a.elapsed_time(b) / 5
+            paper[name] = {"workload": f"channel nz={nz_p}: {q.n_patches} patches, {q.n_fine} fine nodes (level L+{J}), "
+                                       f"BF16 network {wd[0]}-750x8-{wd[-1]}",
+                           "ms_per_step": round(ms, 3), "steps_per_s": round(1000.0 / ms, 2),
+                           "patches_per_s": round(q.n_patches * 1000.0 / ms, 1), "timed_steps": 5}
+            q.close()
+
     res = dict(elapsed_ms=elapsed_ms, net_ms=net_ms, stage_ms=stage_ms, launches=launches, clocks=clk.summary(),
-               e2e_s=e2e_s, nc=nc, nf=nf, nv=nv, fp64=fp64, fp32=fp32)
+               e2e_s=e2e_s, nc=nc, nf=nf, nv=nv, fp64=fp64, fp32=fp32, paper=paper)
     p.close()
     return res
 
@@ -569,6 +602,7 @@ def main():
                 "h2d_bytes_per_step": (nv + nf) * 16, "d2h_bytes_per_step": (nf + nv) * 16},
         "stages": stage_rooflines(res["stage_ms"], nc, peaks, peak_src, res["clocks"]),
         "fp32_form": res["fp32"],
+        "paper_forms": res["paper"],
         "gpu_launches": res["launches"],
         "clocks": res["clocks"],
         "fp64_plain": res["fp64"],
