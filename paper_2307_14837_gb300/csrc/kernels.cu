@@ -524,12 +524,15 @@ __device__ __forceinline__ void store4(TX* dst, T a, T b, T c, T d) {
     }
 }
 
-// One warp per patch: X[P] = [x~ at the NPN nodes | r at the NPN nodes |
+// One warp per 2 patches (J = 1) or 1 (J = 2): X[P] = [x~ at the NPN nodes | r at the NPN nodes |
 // geometry | 0] with row stride LD = 256 (J = 1) or 1024 (J = 2).  Lane l
 // writes nodes l, l + 32, ... (4 values of x~ and of r as one vector each);
 // the first (LD - 8 NPN) / 4 lanes write the n_geo (12 or 24) geometry
 // features and the zeros after them up to the row end.  Every 4-value group
 // is aligned.
+template <int J>
+constexpr int restrict_patches_per_warp() { return J == 1 ? 2 : 1; }   // independent gathers in flight
+
 template <typename T, typename TX, int J>
 __global__ void __launch_bounds__(256) local_restrict_kernel(
     int64_t nc, const int32_t* __restrict__ cells, const int32_t* __restrict__ patch_map,
@@ -537,59 +540,76 @@ __global__ void __launch_bounds__(256) local_restrict_kernel(
     TX* __restrict__ X) {
     using G = PatchGeom<J>;
     constexpr int LD = J == 1 ? kNInPad : kNInPadJ2;
-    constexpr int NODES_PER_LANE = (G::NPN + 31) / 32;
+    constexpr int NPL = (G::NPN + 31) / 32;            // nodes per lane
+    constexpr int PPW = restrict_patches_per_warp<J>();
     const int lane = threadIdx.x & 31;
-    const int64_t P = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-    if (P >= nc) return;
-    // issue the independent loads first: corner ids, node ids, geometry
-    const int32_t v = lane < 8 ? __ldg(cells + 8 * P + lane) : 0;
-    int32_t jn[NODES_PER_LANE];
+    const int64_t P0 = ((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5) * PPW;
+    if (P0 >= nc) return;   // warp-uniform
+    // issue every independent load of the warp's patches first: corner ids,
+    // node ids and geometry, then the node residuals and corner values
+    int32_t v[PPW], jn[PPW][NPL];
+    T el[PPW];
 #pragma unroll
-    for (int i = 0; i < NODES_PER_LANE; ++i) {
-        const int iota = lane + 32 * i;
-        jn[i] = iota < G::NPN ? __ldg(patch_map + int64_t(G::NPN) * P + iota) : 0;
+    for (int p = 0; p < PPW; ++p) {
+        const int64_t P = P0 + p;
+        const bool ok = P < nc;
+        v[p] = ok && lane < 8 ? __ldg(cells + 8 * P + lane) : 0;
+#pragma unroll
+        for (int i = 0; i < NPL; ++i) {
+            const int iota = lane + 32 * i;
+            jn[p][i] = ok && iota < G::NPN ? __ldg(patch_map + int64_t(G::NPN) * P + iota) : 0;
+        }
+        el[p] = ok && lane < n_geo ? geo[int64_t(n_geo) * P + lane] : T(0);
     }
-    const T el = lane < n_geo ? geo[int64_t(n_geo) * P + lane] : T(0);
-    V4<T> rv[NODES_PER_LANE];
+    V4<T> rv[PPW][NPL];
+    T cu[PPW][4];
 #pragma unroll
-    for (int i = 0; i < NODES_PER_LANE; ++i)
-        rv[i] = lane + 32 * i < G::NPN ? ld4(r + 4 * int64_t(jn[i])) : V4<T>{T(0), T(0), T(0), T(0)};
-    T cu[4] = {T(0), T(0), T(0), T(0)};
-    if (lane < 8) {
-        const V4<T> u = ld4(xc + 4 * int64_t(v));
-        cu[0] = u.x;
-        cu[1] = u.y;
-        cu[2] = u.z;
-        cu[3] = u.w;
+    for (int p = 0; p < PPW; ++p) {
+        const bool ok = P0 + p < nc;
+#pragma unroll
+        for (int i = 0; i < NPL; ++i)
+            rv[p][i] = ok && lane + 32 * i < G::NPN ? ld4(r + 4 * int64_t(jn[p][i])) : V4<T>{T(0), T(0), T(0), T(0)};
+        V4<T> u{T(0), T(0), T(0), T(0)};
+        if (ok && lane < 8) u = ld4(xc + 4 * int64_t(v[p]));
+        cu[p][0] = u.x;
+        cu[p][1] = u.y;
+        cu[p][2] = u.z;
+        cu[p][3] = u.w;
     }
-    T corner[8][4];
 #pragma unroll
-    for (int k = 0; k < 8; ++k)
+    for (int p = 0; p < PPW; ++p) {
+        const int64_t P = P0 + p;
+        if (P >= nc) break;   // warp-uniform
+        T corner[8][4];
 #pragma unroll
-        for (int d = 0; d < 4; ++d) corner[k][d] = __shfl_sync(0xffffffffu, cu[d], k);
-    // geometry features 4 lane .. 4 lane + 3 (zero past n_geo)
-    T e[4];
+        for (int k = 0; k < 8; ++k)
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const T g = __shfl_sync(0xffffffffu, el, (4 * lane + i) & 31);
-        e[i] = 4 * lane + i < n_geo ? g : T(0);
+            for (int d = 0; d < 4; ++d) corner[k][d] = __shfl_sync(0xffffffffu, cu[p][d], k);
+        // geometry features 4 lane .. 4 lane + 3 (zero past n_geo)
+        T e[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const T g = __shfl_sync(0xffffffffu, el[p], (4 * lane + i) & 31);
+            e[i] = 4 * lane + i < n_geo ? g : T(0);
+        }
+        TX* row = X + P * LD;
+#pragma unroll
+        for (int i = 0; i < NPL; ++i) {
+            const int iota = lane + 32 * i;
+            if (iota >= G::NPN) continue;
+            const int a = iota % G::NS, b = (iota / G::NS) % G::NS, c = iota / (G::NS * G::NS);
+            store4<TX>(row + 4 * iota, interp27<T, 4, G::NS>(&corner[0][0], 0, a, b, c),
+                       interp27<T, 4, G::NS>(&corner[0][0], 1, a, b, c),
+                       interp27<T, 4, G::NS>(&corner[0][0], 2, a, b, c),
+                       interp27<T, 4, G::NS>(&corner[0][0], 3, a, b, c));
+            store4<TX>(row + 4 * G::NPN + 4 * iota, rv[p][i].x, rv[p][i].y, rv[p][i].z, rv[p][i].w);
+        }
+        constexpr int GEO0 = 8 * G::NPN;              // first geometry column (216, 1000)
+        constexpr int GEO_GROUPS = (LD - GEO0) / 4;   // 4-column groups up to the row end (10, 6)
+        static_assert(GEO_GROUPS <= 32 && 4 * GEO_GROUPS >= 24 && GEO0 + 4 * GEO_GROUPS == LD, "input row layout");
+        if (lane < GEO_GROUPS)   // columns GEO0 .. LD - 1: the features, then zeros
+            store4<TX>(row + GEO0 + 4 * lane, e[0], e[1], e[2], e[3]);
     }
-    TX* row = X + P * LD;
-#pragma unroll
-    for (int i = 0; i < NODES_PER_LANE; ++i) {
-        const int iota = lane + 32 * i;
-        if (iota >= G::NPN) continue;
-        const int a = iota % G::NS, b = (iota / G::NS) % G::NS, c = iota / (G::NS * G::NS);
-        store4<TX>(row + 4 * iota, interp27<T, 4, G::NS>(&corner[0][0], 0, a, b, c),
-                   interp27<T, 4, G::NS>(&corner[0][0], 1, a, b, c), interp27<T, 4, G::NS>(&corner[0][0], 2, a, b, c),
-                   interp27<T, 4, G::NS>(&corner[0][0], 3, a, b, c));
-        store4<TX>(row + 4 * G::NPN + 4 * iota, rv[i].x, rv[i].y, rv[i].z, rv[i].w);
-    }
-    constexpr int GEO0 = 8 * G::NPN;              // first geometry column (216, 1000)
-    constexpr int GEO_GROUPS = (LD - GEO0) / 4;   // 4-column groups up to the row end (10, 6)
-    static_assert(GEO_GROUPS <= 32 && 4 * GEO_GROUPS >= 24 && GEO0 + 4 * GEO_GROUPS == LD, "input row layout");
-    if (lane < GEO_GROUPS)   // columns GEO0 .. LD - 1: the features, then zeros
-        store4<TX>(row + GEO0 + 4 * lane, e[0], e[1], e[2], e[3]);
 }
 
 // d_j = mu_j * sum_{(P,iota) in j} Y[P][3 iota + c], mu_j = 1 / valence.
@@ -762,11 +782,12 @@ cudaError_t launch_residual(const DeviceMesh& dm, OpParams p, const T* xc, const
 
 template <typename T, typename TX>
 cudaError_t launch_local_restrict(const DeviceMesh& dm, const T* xc, const T* r, TX* X, cudaStream_t s) {
+    // one warp per restrict_patches_per_warp<J>() patches
     if (dm.J == 2)
         local_restrict_kernel<T, TX, 2><<<blocks_for(dm.nc * 32, 256), 256, 0, s>>>(
             dm.nc, dm.cells, dm.patch_map, xc, r, edge_of<T>(dm), dm.n_geo, X);
     else
-        local_restrict_kernel<T, TX, 1><<<blocks_for(dm.nc * 32, 256), 256, 0, s>>>(
+        local_restrict_kernel<T, TX, 1><<<blocks_for((dm.nc + 1) / 2 * 32, 256), 256, 0, s>>>(
             dm.nc, dm.cells, dm.patch_map, xc, r, edge_of<T>(dm), dm.n_geo, X);
     return cudaGetLastError();
 }
