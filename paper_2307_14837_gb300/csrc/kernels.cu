@@ -272,19 +272,22 @@ __global__ void __launch_bounds__(kPatchThreads, patch_min_blocks<T>()) patch_op
     }
     __syncthreads();
     if (active) {
+        // the 8 corners in registers once (coordinates relative to corner 0:
+        // the element needs only differences, which stay exact in float)
+        T cr[3][8], cv[8][4];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+#pragma unroll
+            for (int d = 0; d < 3; ++d) cr[d][k] = s_cx[lp][k][d] - s_cx[lp][0][d];
+#pragma unroll
+            for (int d = 0; d < 4; ++d) cv[k][d] = s_cu[lp][k][d];
+        }
         for (int iota = t; iota < G::NPN; iota += TPP) {
             const int a = iota % G::NS, b = (iota / G::NS) % G::NS, c = iota / (G::NS * G::NS);
-            // coordinates relative to corner 0 (the element needs only
-            // differences; this keeps them exact in float)
 #pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                T cr[8];
+            for (int d = 0; d < 3; ++d) s_nx[lp][iota][d] = interp27<T, 1, G::NS>(cr[d], 0, a, b, c);
 #pragma unroll
-                for (int k = 0; k < 8; ++k) cr[k] = s_cx[lp][k][d] - s_cx[lp][0][d];
-                s_nx[lp][iota][d] = interp27<T, 1, G::NS>(cr, 0, a, b, c);
-            }
-#pragma unroll
-            for (int d = 0; d < 4; ++d) s_nu[lp][iota][d] = interp27<T, 4, G::NS>(&s_cu[lp][0][0], d, a, b, c);
+            for (int d = 0; d < 4; ++d) s_nu[lp][iota][d] = interp27<T, 4, G::NS>(&cv[0][0], d, a, b, c);
             if (MODE == MODE_RHS) {   // corrected velocity x~ + d
                 const int64_t j = patch_map[G::NPN * P + iota];
 #pragma unroll
