@@ -20,13 +20,18 @@ stream.  One server step advances every live simulation by one DNN-MG step:
 Finished simulations release their memory at the end of the step, and
 waiting requests are admitted at the start of the next one, so requests that
 arrive while others run join as slots and memory free up (continuous
-batching).  Every stage is deterministic and network rows are independent,
+batching).  Building a context (the host hierarchy, uploads, the first
+right-hand side) takes up to a second for the largest meshes, so by default
+worker threads prepare queued requests while the server steps: memory and
+rows are reserved when preparation starts, and requests are still admitted
+in FIFO order as soon as the head of the queue is ready.  Every stage is deterministic and network rows are independent,
 so a simulation's result does not depend on which others share its steps.
 """
 from __future__ import annotations
 
 import collections
 import time
+from concurrent.futures import ThreadPoolExecutor
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -88,7 +93,7 @@ def memory_estimate(mesh, precision="bf16", solve=True):
 
 class Server:
     def __init__(self, widths, Ws, scales, shifts, memory_budget, max_rows, precision="bf16", device="cuda",
-                 solver=None):
+                 solver=None, prepare_workers=2):
         self.device = torch.device(device)
         if self.device.index is None:
             self.device = torch.device("cuda", torch.cuda.current_device())
@@ -113,6 +118,12 @@ class Server:
         self.ev_net = torch.cuda.Event()
         self.step_latencies = []
         self.patches = 0
+        # background preparation of queued requests (0 workers: inside the step)
+        self.pool = ThreadPoolExecutor(max_workers=prepare_workers) if prepare_workers > 0 else None
+        self.preparing = {}          # id(request) -> (future, memory, rows)
+        self.reserved = 0
+        self.rows_reserved = 0
+        self.admission_s = 0.0       # host time the step loop spent admitting
 
     # -- admission -----------------------------------------------------------
     def submit(self, req: Request):
@@ -121,21 +132,54 @@ class Server:
     def _rows(self):
         return sum(s.path.n_patches for s in self.live)
 
+    def _needs(self, req):
+        return memory_estimate(req.mesh, self.precision, req.solve), int(np.asarray(req.mesh["cells"]).shape[0])
+
+    def _prepare(self, now):
+        """Start preparing queued requests, in FIFO order, while their memory
+        and rows fit beside the live and already reserved ones."""
+        for req in self.queue:
+            if id(req) in self.preparing:
+                continue
+            mem, nc = self._needs(req)
+            if mem > self.budget or nc > self.max_rows:
+                continue                                        # rejected when it reaches the head
+            if (self.used + self.reserved + mem > self.budget or
+                    self._rows() + self.rows_reserved + nc > self.max_rows):
+                break
+            self.preparing[id(req)] = (self.pool.submit(self._start, req, mem, now), mem, nc)
+            self.reserved += mem
+            self.rows_reserved += nc
+
     def _admit(self, now):
+        t0 = time.perf_counter()
+        if self.pool is not None:
+            self._prepare(now)
         while self.queue:
             req = self.queue[0]
-            mem = memory_estimate(req.mesh, self.precision, req.solve)
-            nc = int(np.asarray(req.mesh["cells"]).shape[0])
+            mem, nc = self._needs(req)
             if mem > self.budget or nc > self.max_rows:
                 self.queue.popleft()
                 self.log.append(("rejected", req.name, now))
                 continue
-            if self.used + mem > self.budget or self._rows() + nc > self.max_rows:
-                break                                           # FIFO: wait for memory / rows
-            self.queue.popleft()
-            self.live.append(self._start(req, mem, now))
+            if self.pool is not None:
+                entry = self.preparing.get(id(req))
+                if entry is None or not entry[0].done():
+                    break                                       # FIFO: the head is not ready yet
+                self.queue.popleft()
+                del self.preparing[id(req)]
+                sim = entry[0].result()
+                self.reserved -= mem
+                self.rows_reserved -= nc
+            else:
+                if self.used + mem > self.budget or self._rows() + nc > self.max_rows:
+                    break                                       # FIFO: wait for memory / rows
+                self.queue.popleft()
+                sim = self._start(req, mem, now)
+            self.live.append(sim)
             self.used += mem
             self.log.append(("admitted", req.name, now))
+        self.admission_s += time.perf_counter() - t0
 
     def _start(self, req, mem, now):
         stream = torch.cuda.Stream(self.device)
@@ -161,6 +205,8 @@ class Server:
     def step(self, now=0.0):
         self._admit(now)
         if not self.live:
+            if self.preparing:
+                time.sleep(0.0005)                      # leave the preparing threads the interpreter
             return 0
         t0 = time.perf_counter()
         xb = self.X.element_size() * N_IN_PAD
@@ -227,9 +273,14 @@ class Server:
                     patches_per_s=self.patches / wall if wall > 0 else 0.0,
                     p50_step_latency_ms=float(np.percentile(lat, 50) * 1e3) if lat.size else None,
                     p99_step_latency_ms=float(np.percentile(lat, 99) * 1e3) if lat.size else None,
-                    network_launches=len(self.step_latencies))
+                    network_launches=len(self.step_latencies), admission_s=self.admission_s)
 
     def close(self):
+        if self.pool is not None:
+            self.pool.shutdown(wait=True)
+            for fut, _, _ in self.preparing.values():
+                fut.result().path.close()
+            self.preparing = {}
         for s in self.live:
             s.path.close()
         self.live = []

@@ -63,19 +63,22 @@ def _alone(req, precision, Ws, ss, ts):
     return out
 
 
-@pytest.mark.parametrize("precision", ["fp64", "bf16"])
-def test_mixed_equals_alone(precision):
+@pytest.mark.parametrize("precision,workers", [("fp64", 0), ("bf16", 0), ("bf16", 2)])
+def test_mixed_equals_alone(precision, workers):
     Ws, ss, ts = _net()
     reqs = _requests()
-    srv = Server(WIDTHS, Ws, ss, ts, memory_budget=1 << 33, max_rows=4096, precision=precision)
+    srv = Server(WIDTHS, Ws, ss, ts, memory_budget=1 << 33, max_rows=4096, precision=precision,
+                 prepare_workers=workers)
     for r in reqs[:3]:
         srv.submit(r)
-    srv.step()                                  # a, b, c live
-    srv.submit(reqs[3])                         # d joins at the next step
+    while len(srv.live) + len(srv.results) < 3:
+        srv.step()                              # a, b, c admitted (prepared in the background with workers)
+    srv.submit(reqs[3])                         # d joins at a later step
     while srv.live or srv.queue:
         srv.step()
     srv.close()
-    assert len(srv.step_latencies) == 4         # c has 4 steps; d joined at step 2 and ran 2
+    if workers == 0:
+        assert len(srv.step_latencies) == 4     # c has 4 steps; d joined at step 2 and ran 2
     for r in reqs:
         xa, Fa = _alone(r, precision, Ws, ss, ts)
         got = srv.results[r.name]
