@@ -83,6 +83,12 @@ void dnnmg_destroy(dnnmg_ctx* ctx) {
     cudaGetDevice(&cur);
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
+    if (ctx->copy_stream) {
+        cudaStreamSynchronize(ctx->copy_stream);
+        cudaStreamDestroy(ctx->copy_stream);
+        cudaEventDestroy(ctx->ev_ready);
+        cudaEventDestroy(ctx->ev_input);
+    }
     for (void* p : ctx->allocations) cudaFree(p);
     for (auto*& L : ctx->level) {
         destroy_level(L);
@@ -341,18 +347,25 @@ dnnmg_status dnnmg_prolongate(dnnmg_ctx* ctx, const void* x_coarse_dev, void* x_
     return DNNMG_OK;
 }
 
-dnnmg_status dnnmg_residual(dnnmg_ctx* ctx, const void* x_coarse_dev, const void* F_dev, void* r_dev) {
-    if (!ctx || ctx->net_only || !x_coarse_dev || !F_dev || !r_dev) return DNNMG_EINVAL;
+// the residual; the gather reading F waits for F_ready when given
+static dnnmg_status residual_impl(dnnmg_ctx* ctx, const void* x_coarse_dev, const void* F_dev, void* r_dev,
+                           cudaEvent_t F_ready) {
     int launches = 0;
     cudaError_t e = is_fp64(ctx)
                         ? launch_residual(ctx->dm, ctx->op, (const double*)x_coarse_dev, (const double*)F_dev,
-                                          (double*)r_dev, (double*)ctx->partial, ctx->stream, &launches)
+                                          (double*)r_dev, (double*)ctx->partial, ctx->stream, &launches, F_ready)
                         : launch_residual(ctx->dm, ctx->op, (const float*)x_coarse_dev, (const float*)F_dev,
-                                          (float*)r_dev, (float*)ctx->partial, ctx->stream, &launches);
+                                          (float*)r_dev, (float*)ctx->partial, ctx->stream, &launches, F_ready);
     ctx->launches += launches;
     if (e != cudaSuccess) return cuda_fail(ctx, e, "residual");
     return DNNMG_OK;
 }
+
+dnnmg_status dnnmg_residual(dnnmg_ctx* ctx, const void* x_coarse_dev, const void* F_dev, void* r_dev) {
+    if (!ctx || ctx->net_only || !x_coarse_dev || !F_dev || !r_dev) return DNNMG_EINVAL;
+    return residual_impl(ctx, x_coarse_dev, F_dev, r_dev, nullptr);
+}
+
 
 dnnmg_status dnnmg_local_restrict(dnnmg_ctx* ctx, const void* x_coarse_dev, const void* r_dev, void* X_dev) {
     if (!ctx || ctx->net_only || !x_coarse_dev || !r_dev || !X_dev) return DNNMG_EINVAL;
@@ -455,12 +468,28 @@ dnnmg_status dnnmg_patch_step(dnnmg_ctx* ctx, const void* x_coarse_dev, const vo
 dnnmg_status dnnmg_patch_step_host(dnnmg_ctx* ctx, const void* x_coarse_host, const void* F_host,
                                    void* b_fine_host, void* b_coarse_host) {
     if (!ctx || ctx->net_only || !x_coarse_host || !F_host) return DNNMG_EINVAL;
+    if (!ctx->has_net) return fail(ctx, DNNMG_ESTATE, "dnnmg_patch_step_host before dnnmg_set_network");
     const size_t fe = field_elem(ctx->precision);
     const size_t nv = size_t(ctx->host.nv), nf = size_t(ctx->host.n_fine);
+    if (!ctx->copy_stream) {
+        CK(ctx, cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+        CK(ctx, cudaEventCreateWithFlags(&ctx->ev_ready, cudaEventDisableTiming));
+        CK(ctx, cudaEventCreateWithFlags(&ctx->ev_input, cudaEventDisableTiming));
+    }
+    // x^L on the context's stream; F (the large input) on the copy stream,
+    // after everything already queued on the context's stream, while the
+    // element kernel of the residual (which needs only x^L) runs
+    CK(ctx, cudaEventRecord(ctx->ev_ready, ctx->stream));
+    CK(ctx, cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_ready, 0));
     CK(ctx, cudaMemcpyAsync(ctx->buf_xc, x_coarse_host, nv * 4 * fe, cudaMemcpyHostToDevice, ctx->stream));
-    CK(ctx, cudaMemcpyAsync(ctx->buf_F, F_host, nf * 4 * fe, cudaMemcpyHostToDevice, ctx->stream));
-    dnnmg_status st = dnnmg_patch_step(ctx, ctx->buf_xc, ctx->buf_F, ctx->buf_F, ctx->buf_bc);
-    if (st != DNNMG_OK) return st;
+    CK(ctx, cudaMemcpyAsync(ctx->buf_F, F_host, nf * 4 * fe, cudaMemcpyHostToDevice, ctx->copy_stream));
+    CK(ctx, cudaEventRecord(ctx->ev_input, ctx->copy_stream));
+    dnnmg_status st;
+    if ((st = residual_impl(ctx, ctx->buf_xc, ctx->buf_F, ctx->buf_r, ctx->ev_input)) != DNNMG_OK) return st;
+    if ((st = dnnmg_local_restrict(ctx, ctx->buf_xc, ctx->buf_r, ctx->buf_X)) != DNNMG_OK) return st;
+    if ((st = dnnmg_network(ctx, ctx->buf_X, ctx->buf_Y, ctx->host.nc)) != DNNMG_OK) return st;
+    if ((st = dnnmg_extend(ctx, ctx->buf_Y, ctx->buf_d)) != DNNMG_OK) return st;
+    if ((st = dnnmg_rhs_restrict(ctx, ctx->buf_xc, ctx->buf_d, ctx->buf_F, ctx->buf_bc)) != DNNMG_OK) return st;
     if (b_fine_host)
         CK(ctx, cudaMemcpyAsync(b_fine_host, ctx->buf_F, nf * 4 * fe, cudaMemcpyDeviceToHost, ctx->stream));
     if (b_coarse_host)

@@ -112,9 +112,11 @@ struct OpParams {
 // ---- patch kernels (kernels.cu); T = double or float -------------------
 template <typename T>
 cudaError_t launch_prolongate(const DeviceMesh& dm, const T* xc, T* xf, cudaStream_t s);
+// F_ready (may be null): an event the gather waits for before reading F,
+// so that F can still be arriving while the element kernel runs
 template <typename T>
 cudaError_t launch_residual(const DeviceMesh& dm, OpParams p, const T* xc, const T* F, T* r,
-                            T* partial, cudaStream_t s, int* launches);
+                            T* partial, cudaStream_t s, int* launches, cudaEvent_t F_ready = nullptr);
 template <typename T, typename TX>
 cudaError_t launch_local_restrict(const DeviceMesh& dm, const T* xc, const T* r, TX* X,
                                   cudaStream_t s);
@@ -160,6 +162,8 @@ struct dnnmg_ctx {
     void* buf_xc = nullptr;      // [nv][4]  (host-buffer step)
     void* buf_F = nullptr;       // [n_fine][4]
     void* buf_bc = nullptr;      // [nv][4]
+    cudaStream_t copy_stream = nullptr;   // host-buffer step: F upload beside the element kernel
+    cudaEvent_t ev_ready = nullptr, ev_input = nullptr;
 
     // network
     bool has_net = false;

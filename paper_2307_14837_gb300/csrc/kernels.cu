@@ -773,10 +773,11 @@ void launch_patch_operator(const DeviceMesh& dm, OpParams p, const T* xc, const 
 
 template <typename T>
 cudaError_t launch_residual(const DeviceMesh& dm, OpParams p, const T* xc, const T* F, T* r, T* partial,
-                            cudaStream_t s, int* launches) {
+                            cudaStream_t s, int* launches, cudaEvent_t F_ready) {
     launch_patch_operator<T, MODE_RESIDUAL>(dm, p, xc, nullptr, partial, nullptr, s);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    if (F_ready && (e = cudaStreamWaitEvent(s, F_ready, 0)) != cudaSuccess) return e;
     node_reduce_kernel<T, MODE_RESIDUAL><<<blocks_for(dm.n_fine, 256), 256, 0, s>>>(
         dm.n_fine, dm.node_ptr, dm.node_idx, partial, dm.fine_dir, F, r);
     *launches += 2;
@@ -855,7 +856,7 @@ cudaError_t launch_layer_simt(const TA* A, int64_t lda, const TW* W, int64_t ldw
 #define DNNMG_INST(T)                                                                                  \
     template cudaError_t launch_prolongate<T>(const DeviceMesh&, const T*, T*, cudaStream_t);         \
     template cudaError_t launch_residual<T>(const DeviceMesh&, OpParams, const T*, const T*, T*, T*,  \
-                                            cudaStream_t, int*);                                      \
+                                            cudaStream_t, int*, cudaEvent_t);                         \
     template cudaError_t launch_extend<T>(const DeviceMesh&, const T*, T*, cudaStream_t);             \
     template cudaError_t launch_rhs_restrict<T>(const DeviceMesh&, OpParams, const T*, const T*, T*,  \
                                                 T*, T*, T*, cudaStream_t, int*);
