@@ -497,29 +497,35 @@ __global__ void vanka_average_kernel(int64_t n, const int32_t* __restrict__ ptr,
 // ---- vector kernels (FP64, deterministic reductions) -------------------------
 constexpr int kRedBlocks = 256;
 
-__global__ void dot_partial_kernel(int64_t n, const double* __restrict__ a, const double* __restrict__ b,
-                                   double* __restrict__ part) {
-    __shared__ double s[256];
+// sum over a warp by shuffles (a fixed tree: deterministic)
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+// sum over a block of 256 threads: warp shuffles, then the 8 warp sums by warp 0
+__device__ __forceinline__ double block_sum256(double v) {
+    __shared__ double ws[8];
+    v = warp_sum(v);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = threadIdx.x < 8 ? ws[threadIdx.x] : 0.0;
+    if (threadIdx.x < 32) t = warp_sum(t);
+    return t;   // valid in thread 0
+}
+
+__global__ void __launch_bounds__(256) dot_partial_kernel(int64_t n, const double* __restrict__ a,
+                                                          const double* __restrict__ b, double* __restrict__ part) {
     double acc = 0.0;
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
         acc += a[i] * b[i];
-    s[threadIdx.x] = acc;
-    __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-        if (threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) part[blockIdx.x] = s[0];
+    acc = block_sum256(acc);
+    if (threadIdx.x == 0) part[blockIdx.x] = acc;
 }
-__global__ void dot_final_kernel(const double* __restrict__ part, int np, double* __restrict__ out) {
-    __shared__ double s[256];
-    s[threadIdx.x] = threadIdx.x < np ? part[threadIdx.x] : 0.0;
-    __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-        if (threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) *out = s[0];
+__global__ void __launch_bounds__(256) dot_final_kernel(const double* __restrict__ part, int np,
+                                                        double* __restrict__ out) {
+    const double t = block_sum256(threadIdx.x < np ? part[threadIdx.x] : 0.0);
+    if (threadIdx.x == 0) *out = t;
 }
 // y += sgn * coef[0] * x
 __global__ void axpy_dev_kernel(int64_t n, const double* __restrict__ coef, double sgn, const double* __restrict__ x,

@@ -166,3 +166,74 @@ def test_manufactured_solution_convergence():
     assert rates[0] > 1.8, rates      # velocity L2 ~ h^2
     assert rates[1] > 0.95, rates     # velocity H1 ~ h
     assert rates[2] > 1.5, rates      # pressure L2 (LPS: at least h)
+
+
+def _brute_force_jacobian(xyz, cells, v0, m, th, nu):
+    """The linearised Q1/Q1 operator (without stabilisation) at velocity v0,
+    assembled cell by cell from explicit basis functions and a 3-point Gauss
+    rule per axis: unknown 4 j + c, rows
+      momentum (k, c):  m (v_c, N_k) + th [nu (grad v_c, grad N_k)
+                        + ((dv . grad) v0_c + (v0 . grad) dv_c, N_k)] - (p, d_c N_k)
+      continuity (k):   (div v, N_k)."""
+    g, w = np.polynomial.legendre.leggauss(3)
+    g, w = 0.5 * (g + 1.0), 0.5 * w
+    n = xyz.shape[0]
+    J = np.zeros((4 * n, 4 * n))
+    for cell in cells:
+        X = xyz[cell]                                       # [8, 3]
+        for a in range(3):
+            for b in range(3):
+                for c in range(3):
+                    xi = (g[a], g[b], g[c])
+                    wq = w[a] * w[b] * w[c]
+                    N = np.empty(8)
+                    dN = np.empty((8, 3))                   # reference derivatives
+                    for k in range(8):
+                        f = [xi[d] if (k >> d) & 1 else 1.0 - xi[d] for d in range(3)]
+                        s = [1.0 if (k >> d) & 1 else -1.0 for d in range(3)]
+                        N[k] = f[0] * f[1] * f[2]
+                        dN[k] = [s[0] * f[1] * f[2], f[0] * s[1] * f[2], f[0] * f[1] * s[2]]
+                    Jm = X.T @ dN                           # dx_d / dxi_e
+                    det = np.linalg.det(Jm)
+                    G = dN @ np.linalg.inv(Jm)              # physical gradients [8, 3]
+                    dv = wq * det
+                    V0 = v0[cell]                           # [8, 3]
+                    vq = N @ V0                             # v0 at the point
+                    Dv0 = V0.T @ G                          # d v0_c / d x_e
+                    for k in range(8):
+                        rk = 4 * cell[k]
+                        for l in range(8):
+                            cl = 4 * cell[l]
+                            adv = vq @ G[l]                 # (v0 . grad) N_l
+                            for cc in range(3):
+                                J[rk + cc, cl + cc] += dv * (m * N[l] * N[k] + th * nu * (G[l] @ G[k])
+                                                             + th * adv * N[k])
+                                for e in range(3):
+                                    J[rk + cc, cl + e] += dv * th * N[l] * Dv0[cc, e] * N[k]
+                                J[rk + cc, cl + 3] += -dv * N[l] * G[k, cc]
+                                J[rk + 3, cl + cc] += dv * G[l, cc] * N[k]
+    return J
+
+
+def test_brute_force_assembled_matrix_matches_matrix_free_operator():
+    # the 2^3 cavity under a shear: parallelepiped cells, on which both Gauss
+    # rules integrate every term exactly; the oracle's matrix-free operator,
+    # linearised at a non-zero velocity (exact complex-step derivative),
+    # against the matrix assembled by brute force
+    m_ = I.cavity_mesh(2)
+    S = np.array([[1.0, 0.3, -0.2], [0.1, 0.9, 0.25], [0.0, -0.15, 1.1]])
+    xyz = m_["xyz"] @ S.T
+    lev = fem.Level(xyz, m_["cells"], m_["vertex_bc"], True)
+    rng = np.random.default_rng(3)
+    x0 = np.zeros((lev.n, 4))
+    x0[:, 0:3] = rng.standard_normal((lev.n, 3))
+    x0[:, 3] = rng.standard_normal(lev.n)
+    prm = dict(m=37.0, theta=0.5, nu=0.3, alpha0=0.02, delta0=0.1, lps=False)
+    Jo = lev.jacobian(x0, prm).toarray()
+    Jb = _brute_force_jacobian(xyz, np.asarray(m_["cells"]), x0[:, 0:3], 37.0, 0.5, 0.3)
+    assert np.abs(Jo - Jb).max() <= 1e-12 * np.abs(Jb).max()
+    # and the operator itself at a state with zero velocity (where it is linear in p)
+    xp = np.zeros((lev.n, 4))
+    xp[:, 3] = rng.standard_normal(lev.n)
+    Ao = lev.operator(xp, prm).ravel()
+    assert np.abs(Ao - Jb @ xp.ravel()).max() <= 1e-12 * np.abs(Ao).max()
