@@ -325,6 +325,31 @@ def run_ours(args, rank, world, local_rank):
     paper = None
     if not args.no_fp64 and rank == 0:
         paper = {}
+        # the channel at ~40k coarse hex with the FP32 network 228-512x3-81
+        mc, nuc = build_workload(seed=rank, nz=19)
+        q = PatchPath(mc, nuc, DT, THETA, "fp32", device=dev, stream=stream)
+        wd = (228, 512, 512, 512, 81)
+        Wp, sp, tp = I.network_weights(wd, seed=0)
+        q.set_network(wd, Wp, sp, tp, skip=True)
+        xq = q.to_device(I.coarse_state(mc, seed=rank).astype(np.float32))
+        Fq = q.to_device(I.fine_rhs(q.n_fine, seed=rank, scale=(1 / DT) * 0.42 / (8 * q.n_patches)).astype(np.float32))
+        bfq, bcq = q.field(q.n_fine, 4), q.field(q.n_coarse, 4)
+        with torch.cuda.stream(stream):
+            for _ in range(2):
+                q.step(xq, Fq, bfq, bcq)
+            torch.cuda.synchronize(dev)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(10):
+                q.step(xq, Fq, bfq, bcq)
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+        ms = a.elapsed_time(b) / 10
+        paper["channel_40k_fp32_228_512x3_81"] = {
+            "workload": f"channel nz=19: {q.n_patches} patches, {q.n_fine} fine nodes, FP32 fields and network",
+            "ms_per_step": round(ms, 3), "steps_per_s": round(1000.0 / ms, 2),
+            "patches_per_s": round(q.n_patches * 1000.0 / ms, 1), "timed_steps": 10}
+        q.close()
         for name, J, nz_p in (("j1_240_750x8_81", 1, args.nz), ("j2_1024_750x8_375", 2, max(4, args.nz // 2))):
             mp, nup = build_workload(seed=rank, nz=nz_p)
             q = PatchPath(mp, nup, DT, THETA, "bf16", device=dev, stream=stream, features=24, patch_levels=J)
@@ -430,13 +455,16 @@ def run_serving(args):
     print(json.dumps(line))
 
 
-def equal_error(steps=5):
+def equal_error(steps=20):
     """Velocity error of the DNN-MG time loop in the BF16 form and in the plain
     FP64 form against a fine-level reference (the plain scheme on level L+1),
     on the cavity workload (8^3 -> 16^3, Re 100, backward Euler dt 0.01,
-    network 228-256-256-81 from seed 0 with the last layer scaled by 0.05 as a
-    stand-in for a trained network's small corrections).  Errors are l2 norms
-    over the fine nodes after `steps` steps (E_v of Sec. 6.5 at one time)."""
+    20 steps, network 228-256-256-81 from seed 0 with the last layer scaled by
+    0.05 as a stand-in for a trained network's small corrections).  Errors are
+    l2 norms over the fine nodes after `steps` steps (E_v of Sec. 6.5 at one
+    time).  Also the rate of whole DNN-MG time steps (GPU Newton-GMRES coarse
+    solve + patch correction) of each form, steps 2..steps timed with CUDA
+    events, beside the plain coarse scheme and the fine-level scheme."""
     import numpy as np
     import torch
 
@@ -451,15 +479,27 @@ def equal_error(steps=5):
     dirc = (m["vertex_bc"] == 1) | (m["vertex_bc"] == 2)
     x0 = np.zeros((m.n_vertices, 4))
     x0[dirc, 0:3] = bcv[dirc]
-    res, t0 = {}, time.perf_counter()
+    res, rate, t0 = {}, {}, time.perf_counter()
     ref = None
+
+    def timed(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b)
+
     for prec in ("fp64", "bf16"):
         p = PatchPath(m, 0.01, 0.01, 1.0, prec)
         p.set_network(widths, Ws, ss, ts)
         x = torch.as_tensor(x0, device="cuda")
         bf, bcf = p.rhs_restrict(x.to(p.dtype), torch.zeros((p.n_fine, 3), dtype=p.dtype, device="cuda"))
         bc = bcf.double().contiguous()
-        capi.dnnmg_time_step(p.ctx, steps, x, bc, bf)
+        capi.dnnmg_time_step(p.ctx, 1, x, bc, bf)          # first step: builds the coarse solver level
+        ms = timed(lambda: capi.dnnmg_time_step(p.ctx, steps - 1, x, bc, bf))
+        rate[f"dnnmg_{prec}"] = round(1000.0 * (steps - 1) / ms, 2)
         res[prec] = p.prolongate(x.to(p.dtype)).double().cpu().numpy()
         if ref is None:
             kind = p.mesh_data(capi.FINE_KIND)
@@ -467,14 +507,21 @@ def equal_error(steps=5):
             xr = p.prolongate(torch.as_tensor(x0, device="cuda")).cpu().numpy()
             xr[dirf, 0:3] = I.dirichlet_values(m, p.mesh_data(capi.FINE_XYZ), kind)[dirf]
             xr = torch.as_tensor(xr, device="cuda")
-            capi.dnnmg_plain_step(p.ctx, capi.LEVEL_FINE, steps, xr)
+            capi.dnnmg_plain_step(p.ctx, capi.LEVEL_FINE, 1, xr)
+            ms = timed(lambda: capi.dnnmg_plain_step(p.ctx, capi.LEVEL_FINE, steps - 1, xr))
+            rate["plain_fine_fp64"] = round(1000.0 * (steps - 1) / ms, 2)
             ref = xr.cpu().numpy()
+            xp = torch.as_tensor(x0, device="cuda")
+            capi.dnnmg_plain_step(p.ctx, capi.LEVEL_COARSE, 1, xp)
+            ms = timed(lambda: capi.dnnmg_plain_step(p.ctx, capi.LEVEL_COARSE, steps - 1, xp))
+            rate["plain_coarse_fp64"] = round(1000.0 * (steps - 1) / ms, 2)
         p.close()
     e = {k: float(np.linalg.norm(v[:, 0:3] - ref[:, 0:3])) for k, v in res.items()}
     return {"workload": "cavity 8^3->16^3, Re 100, BE dt 0.01, 228-256-256-81 (last layer x0.05), "
                         f"{steps} DNN-MG steps vs plain scheme on level L+1",
             "e_v_fp64": e["fp64"], "e_v_bf16": e["bf16"],
-            "relative_difference": abs(e["bf16"] - e["fp64"]) / e["fp64"], "seconds": time.perf_counter() - t0}
+            "relative_difference": abs(e["bf16"] - e["fp64"]) / e["fp64"],
+            "time_steps_per_s": rate, "seconds": time.perf_counter() - t0}
 
 
 class OracleSample:

@@ -13,10 +13,12 @@
 //     part (frozen, Eq. (8)); local 108 x 108 matrices are summed into a
 //     4 x 4-block CSR matrix by a gather in group order (deterministic);
 //   * the preconditioner is additive group-Vanka: the global matrix
-//     restricted to each group's 108 unknowns, LU-factorised, applied to the
-//     group's residual and averaged over the groups sharing a node;
-//   * right-preconditioned restarted GMRES with modified Gram-Schmidt; all
-//     vectors, dot products (two-pass, fixed order) and norms in FP64;
+//     restricted to each group's 108 unknowns, LU-factorised and inverted
+//     once per assembly, the inverse applied to the group's residual as a
+//     dense product and averaged over the groups sharing a node;
+//   * right-preconditioned restarted GMRES with classical Gram-Schmidt
+//     applied twice; all vectors, dot products (warp shuffles, then a second
+//     pass over the blocks: fixed order) and norms in FP64;
 //   * Newton re-assembles the Jacobian when the residual rate
 //     rho = |r_{j+1}| / |r_j| exceeds rho_max (Sec. 3.4).
 // Dirichlet velocity unknowns keep the values given in x; where no boundary
@@ -397,14 +399,20 @@ __global__ void bsr_spmv_kernel(int64_t n, const int32_t* __restrict__ rp, const
     y[tid] = acc;
 }
 
-// Group block of the global matrix, LU with partial pivoting in shared memory.
+// Group block of the global matrix: LU with partial pivoting in shared
+// memory, then its inverse (one column per thread: the pivots, a forward and
+// a back substitution of a unit vector), stored column-major in Ainv so that
+// applying it is a coalesced dense product.  A zero pivot gives a zero
+// component, as a triangular solve with that convention would.
 template <int NPG>
 __global__ void vanka_factor_kernel(int64_t ng, const int32_t* __restrict__ grp_blk, const double* __restrict__ A,
-                                    double* __restrict__ LU, int32_t* __restrict__ piv) {
+                                    double* __restrict__ Ainv, int32_t* __restrict__ piv) {
     constexpr int NL = 4 * NPG;
     extern __shared__ double sm[];
     double* M = sm;                          // NL x NL
+    double* X = sm + NL * NL;                // NL x NL: X[i * NL + c] = (A^{-1})_{ic}
     __shared__ int s_p;
+    __shared__ int s_piv[NL];
     const int64_t g = blockIdx.x;
     for (int e = threadIdx.x; e < NL * NL; e += blockDim.x) {
         const int i = e / NL, j = e % NL;
@@ -422,6 +430,7 @@ __global__ void vanka_factor_kernel(int64_t ng, const int32_t* __restrict__ grp_
                     best = i;
                 }
             s_p = best;
+            s_piv[k] = best;
             piv[g * NL + k] = best;
         }
         __syncthreads();
@@ -444,41 +453,54 @@ __global__ void vanka_factor_kernel(int64_t ng, const int32_t* __restrict__ grp_
         }
         __syncthreads();
     }
-    for (int e = threadIdx.x; e < NL * NL; e += blockDim.x) LU[g * NL * NL + e] = M[e];
-}
-
-// z_g = A_g^{-1} r restricted to group g; one thread per group
-template <int NPG>
-__global__ void vanka_solve_kernel(int64_t ng, const int32_t* __restrict__ groups, const double* __restrict__ LU,
-                                   const int32_t* __restrict__ piv, const double* __restrict__ r,
-                                   double* __restrict__ zloc) {
-    constexpr int NL = 4 * NPG;
-    const int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (g >= ng) return;
-    double y[NL];
-    for (int i = 0; i < NPG; ++i)
-        for (int c = 0; c < 4; ++c) y[4 * i + c] = r[4 * int64_t(groups[g * NPG + i]) + c];
-    const double* M = LU + g * NL * NL;
-    for (int k = 0; k < NL; ++k) {
-        const int p = piv[g * NL + k];
-        if (p != k) {
-            const double t = y[k];
-            y[k] = y[p];
-            y[p] = t;
+    const int c = threadIdx.x;
+    if (c < NL) {
+        for (int i = 0; i < NL; ++i) X[i * NL + c] = i == c ? 1.0 : 0.0;
+        for (int k = 0; k < NL; ++k) {
+            const int pr = s_piv[k];
+            if (pr != k) {
+                const double t = X[k * NL + c];
+                X[k * NL + c] = X[pr * NL + c];
+                X[pr * NL + c] = t;
+            }
+        }
+        for (int i = 1; i < NL; ++i) {
+            double acc = X[i * NL + c];
+            for (int j = 0; j < i; ++j) acc -= M[i * NL + j] * X[j * NL + c];
+            X[i * NL + c] = acc;
+        }
+        for (int i = NL - 1; i >= 0; --i) {
+            double acc = X[i * NL + c];
+            for (int j = i + 1; j < NL; ++j) acc -= M[i * NL + j] * X[j * NL + c];
+            const double d = M[i * NL + i];
+            X[i * NL + c] = d != 0.0 ? acc / d : 0.0;
         }
     }
-    for (int i = 0; i < NL; ++i) {
-        double s = y[i];
-        for (int j = 0; j < i; ++j) s -= M[i * NL + j] * y[j];
-        y[i] = s;
+    __syncthreads();
+    // column-major: Ainv[g][j * NL + i] = (A^{-1})_{ij}
+    for (int e = threadIdx.x; e < NL * NL; e += blockDim.x) {
+        const int j = e / NL, i = e % NL;
+        Ainv[g * NL * NL + e] = X[i * NL + j];
     }
-    for (int i = NL - 1; i >= 0; --i) {
-        double s = y[i];
-        for (int j = i + 1; j < NL; ++j) s -= M[i * NL + j] * y[j];
-        const double d = M[i * NL + i];
-        y[i] = d != 0.0 ? s / d : 0.0;
+}
+
+// z_g = A_g^{-1} r restricted to group g: one block per group, thread i
+// computes row i of the dense product (column-major inverse: coalesced).
+template <int NPG>
+__global__ void __launch_bounds__(128) vanka_apply_kernel(int64_t ng, const int32_t* __restrict__ groups,
+                                                          const double* __restrict__ Ainv,
+                                                          const double* __restrict__ r, double* __restrict__ zloc) {
+    constexpr int NL = 4 * NPG;
+    __shared__ double s_r[NL];
+    const int64_t g = blockIdx.x;
+    for (int e = threadIdx.x; e < NL; e += blockDim.x) s_r[e] = r[4 * int64_t(groups[g * NPG + e / 4]) + e % 4];
+    __syncthreads();
+    const double* Ag = Ainv + g * NL * NL;
+    for (int i = threadIdx.x; i < NL; i += blockDim.x) {
+        double acc = 0.0;
+        for (int j = 0; j < NL; ++j) acc += Ag[j * NL + i] * s_r[j];
+        zloc[g * NL + i] = acc;
     }
-    for (int e = 0; e < NL; ++e) zloc[g * NL + e] = y[e];
 }
 
 // z_j = (1 / valence_j) sum of the groups' local solutions at node j
@@ -527,6 +549,35 @@ __global__ void __launch_bounds__(256) dot_final_kernel(const double* __restrict
     const double t = block_sum256(threadIdx.x < np ? part[threadIdx.x] : 0.0);
     if (threadIdx.x == 0) *out = t;
 }
+// Classical Gram-Schmidt pieces: part[i * gridDim.x + b] = the partial
+// <w, V_i> of block b for i = blockIdx.y; then out[i] = sum over blocks
+// (one block per i); then w -= sum_i h[i] V_i in order i = 0..cnt-1.
+__global__ void __launch_bounds__(256) multi_dot_partial_kernel(int64_t n, const double* __restrict__ w,
+                                                                const double* __restrict__ V,
+                                                                double* __restrict__ part) {
+    const double* v = V + int64_t(blockIdx.y) * n;
+    double acc = 0.0;
+    for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += int64_t(gridDim.x) * blockDim.x)
+        acc += w[k] * v[k];
+    acc = block_sum256(acc);
+    if (threadIdx.x == 0) part[int64_t(blockIdx.y) * gridDim.x + blockIdx.x] = acc;
+}
+__global__ void __launch_bounds__(256) multi_dot_final_kernel(const double* __restrict__ part, int nb,
+                                                              double* __restrict__ out) {
+    const double t = block_sum256(threadIdx.x < nb ? part[int64_t(blockIdx.x) * nb + threadIdx.x] : 0.0);
+    if (threadIdx.x == 0) out[blockIdx.x] = t;
+}
+__global__ void multi_axpy_kernel(int64_t n, int cnt, const double* __restrict__ h, const double* __restrict__ V,
+                                  double* __restrict__ w) {
+    for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += int64_t(gridDim.x) * blockDim.x) {
+        double acc = w[k];
+        for (int i = 0; i < cnt; ++i) acc -= h[i] * V[int64_t(i) * n + k];
+        w[k] = acc;
+    }
+}
+__global__ void add_vec_kernel(int cnt, const double* __restrict__ a, double* __restrict__ b) {
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) b[i] += a[i];
+}
 // y += sgn * coef[0] * x
 __global__ void axpy_dev_kernel(int64_t n, const double* __restrict__ coef, double sgn, const double* __restrict__ x,
                                 double* __restrict__ y) {
@@ -574,7 +625,7 @@ struct DeviceLevel {
     int32_t *blk_ptr = nullptr, *blk_src = nullptr, *grp_blk = nullptr;
     double* A = nullptr;        // BSR values [nnzb][4][4]
     double* Jloc = nullptr;     // [ng][4 npg][4 npg]
-    double* LU = nullptr;       // [ng][4 npg][4 npg]
+    double* LU = nullptr;       // [ng][4 npg][4 npg]: the inverse of each group block, column-major
     int32_t* piv = nullptr;     // [ng][4 npg]
     double* local = nullptr;    // [ng][npg][4]
     double* zloc = nullptr;     // [ng][4 npg]
@@ -667,8 +718,8 @@ cudaError_t create_level(const HostHierarchy& hh, bool fine, int krylov, DeviceL
     L->work = static_cast<double*>(p);
     if ((e = dalloc(L, size_t(krylov + 2) * size_t(krylov + 2) * 8 + 64 * 8, &p)) != cudaSuccess) return fail(e);
     L->scal = static_cast<double*>(p);
-    if ((e = dalloc(L, kRedBlocks * 8, &p)) != cudaSuccess) return fail(e);
-    L->part = static_cast<double*>(p);
+    if ((e = dalloc(L, size_t(kRedBlocks) * size_t(krylov + 1) * 8, &p)) != cudaSuccess) return fail(e);
+    L->part = static_cast<double*>(p);   // reduction partials, kRedBlocks per vector
     *out = L;
     return cudaSuccess;
 }
@@ -706,6 +757,14 @@ cudaError_t local_terms(DeviceLevel* L, const double* x, LvPrm p, cudaStream_t s
 cudaError_t dot(DeviceLevel* L, const double* a, const double* b, int64_t n, double* out_dev, cudaStream_t s) {
     dot_partial_kernel<<<kRedBlocks, 256, 0, s>>>(n, a, b, L->part);
     dot_final_kernel<<<1, 256, 0, s>>>(L->part, kRedBlocks, out_dev);
+    return cudaGetLastError();
+}
+
+// One classical Gram-Schmidt pass against V_0..V_{cnt-1}: h = V^T w, w -= V h.
+cudaError_t cgs_pass(DeviceLevel* L, double* w, const double* V, int cnt, int64_t n, double* h, cudaStream_t s) {
+    multi_dot_partial_kernel<<<dim3(kRedBlocks, unsigned(cnt)), 256, 0, s>>>(n, w, V, L->part);
+    multi_dot_final_kernel<<<unsigned(cnt), 256, 0, s>>>(L->part, kRedBlocks, h);
+    multi_axpy_kernel<<<256, 256, 0, s>>>(n, cnt, h, V, w);
     return cudaGetLastError();
 }
 
@@ -778,7 +837,7 @@ cudaError_t level_jacobian(DeviceLevel* L, const OpParams& op, const dnnmg_solve
     bsr_dirichlet_kernel<<<nblk(h.n, 128), 128, 0, s>>>(h.n, L->row_ptr, L->col_idx, L->dir, h.pin, L->A);
     CKE(cudaGetLastError());
     // group-Vanka factors
-    const size_t smem = size_t(nl) * nl * 8;
+    const size_t smem = 2 * size_t(nl) * nl * 8;   // the LU and the inverse
     if (h.npg == 27) {
         CKE(cudaFuncSetAttribute(vanka_factor_kernel<27>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
         vanka_factor_kernel<27><<<unsigned(h.ng), 256, smem, s>>>(h.ng, L->grp_blk, L->A, L->LU, L->piv);
@@ -810,9 +869,9 @@ namespace {
 cudaError_t precond(DeviceLevel* L, const double* r, double* z, cudaStream_t s) {
     const HostLevel& h = L->h;
     if (h.npg == 27)
-        vanka_solve_kernel<27><<<nblk(h.ng, 32), 32, 0, s>>>(h.ng, L->groups, L->LU, L->piv, r, L->zloc);
+        vanka_apply_kernel<27><<<unsigned(h.ng), 128, 0, s>>>(h.ng, L->groups, L->LU, r, L->zloc);
     else
-        vanka_solve_kernel<8><<<nblk(h.ng, 64), 64, 0, s>>>(h.ng, L->groups, L->LU, L->piv, r, L->zloc);
+        vanka_apply_kernel<8><<<unsigned(h.ng), 128, 0, s>>>(h.ng, L->groups, L->LU, r, L->zloc);
     CKE(cudaGetLastError());
     vanka_average_kernel<<<nblk(h.n, 256), 256, 0, s>>>(h.n, L->node_ptr, L->node_idx, L->zloc, z);
     return cudaGetLastError();
@@ -832,7 +891,7 @@ cudaError_t gmres(DeviceLevel* L, const double* r, double* dx, double rtol, int 
     double* z = L->work + 3 * n4;
     double* w = L->work + 5 * n4;
     double* V = L->work + 6 * n4;   // (m + 1) vectors
-    double* H = L->scal + 64;       // (m+1) x m column-major on the device: H[i + j*(m+1)]
+    double* H = L->scal + 64;       // (m+1) x m column-major on the device: H[i + j*(m+1)], then m+1 scratch
     std::vector<double> Hh(size_t(m + 1) * m), cs(m), sn(m), gvec(m + 1), y(m);
     cudaMemsetAsync(dx, 0, size_t(n4) * 8, s);
     double beta0 = 0.0;
@@ -861,11 +920,14 @@ cudaError_t gmres(DeviceLevel* L, const double* r, double* dx, double rtol, int 
             double* vn = V + int64_t(j + 1) * n4;
             CKE(precond(L, vj, z, s));
             CKE(spmv(L, z, w, s));
-            for (int i = 0; i <= j; ++i) {
-                double* hij = H + i + j * (m + 1);
-                CKE(dot(L, w, V + int64_t(i) * n4, n4, hij, s));
-                axpy_dev_kernel<<<256, 256, 0, s>>>(n4, hij, -1.0, V + int64_t(i) * n4, w);
-            }
+            // orthogonalise against V_0..V_j: classical Gram-Schmidt twice (as
+            // robust as the modified form, two multi-vector passes instead of
+            // 2 (j + 1) single ones); the column gets the sum of both passes
+            double* hcol = H + j * (m + 1);
+            double* h2 = H + size_t(m + 1) * m;   // scratch column after H
+            CKE(cgs_pass(L, w, V, j + 1, n4, hcol, s));
+            CKE(cgs_pass(L, w, V, j + 1, n4, h2, s));
+            add_vec_kernel<<<1, 64, 0, s>>>(j + 1, h2, hcol);
             double* hn = H + (j + 1) + j * (m + 1);
             CKE(dot(L, w, w, n4, hn, s));
             scale_inv_sqrt_kernel<<<256, 256, 0, s>>>(n4, hn, w, vn);
