@@ -9,7 +9,17 @@
 
 using namespace dnnmg;
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace {
+
+// An NVTX range over one entry point (a no-op unless a profiler is attached).
+struct Range {
+    explicit Range(const char* name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range&) = delete;
+    Range& operator=(const Range&) = delete;
+};
 
 const char* kStatusText[] = {"ok", "invalid argument", "out of memory", "CUDA error", "no convergence",
                              "NaN or Inf", "timeout", "call out of order", "unsupported"};
@@ -100,6 +110,7 @@ void dnnmg_destroy(dnnmg_ctx* ctx) {
 
 dnnmg_status dnnmg_create(const dnnmg_mesh_desc* mesh, const dnnmg_params* params, void* cuda_stream,
                           dnnmg_ctx** out) {
+    Range nvtx_range("dnnmg_create");
     if (!out) return DNNMG_EINVAL;
     *out = nullptr;
     if (!mesh || !params) return DNNMG_EINVAL;
@@ -239,6 +250,7 @@ dnnmg_status dnnmg_set_stream(dnnmg_ctx* ctx, void* cuda_stream) {
 
 dnnmg_status dnnmg_set_network(dnnmg_ctx* ctx, const dnnmg_net_desc* net, const double* const* W,
                                const double* const* scale, const double* const* shift) {
+    Range nvtx_range("dnnmg_set_network");
     if (!ctx || !net || !W || !net->widths || net->n_layers < 1 || net->n_layers > 64) return DNNMG_EINVAL;
     const int L = net->n_layers;
     if (net->widths[0] != n_in(ctx) || net->widths[L] != n_out(ctx))
@@ -339,6 +351,7 @@ dnnmg_status dnnmg_set_network(dnnmg_ctx* ctx, const dnnmg_net_desc* net, const 
 }
 
 dnnmg_status dnnmg_prolongate(dnnmg_ctx* ctx, const void* x_coarse_dev, void* x_fine_dev) {
+    Range nvtx_range("dnnmg_prolongate");
     if (!ctx || ctx->net_only || !x_coarse_dev || !x_fine_dev) return DNNMG_EINVAL;
     cudaError_t e = is_fp64(ctx) ? launch_prolongate(ctx->dm, (const double*)x_coarse_dev, (double*)x_fine_dev, ctx->stream)
                                  : launch_prolongate(ctx->dm, (const float*)x_coarse_dev, (float*)x_fine_dev, ctx->stream);
@@ -362,12 +375,14 @@ static dnnmg_status residual_impl(dnnmg_ctx* ctx, const void* x_coarse_dev, cons
 }
 
 dnnmg_status dnnmg_residual(dnnmg_ctx* ctx, const void* x_coarse_dev, const void* F_dev, void* r_dev) {
+    Range nvtx_range("dnnmg_residual");
     if (!ctx || ctx->net_only || !x_coarse_dev || !F_dev || !r_dev) return DNNMG_EINVAL;
     return residual_impl(ctx, x_coarse_dev, F_dev, r_dev, nullptr);
 }
 
 
 dnnmg_status dnnmg_local_restrict(dnnmg_ctx* ctx, const void* x_coarse_dev, const void* r_dev, void* X_dev) {
+    Range nvtx_range("dnnmg_local_restrict");
     if (!ctx || ctx->net_only || !x_coarse_dev || !r_dev || !X_dev) return DNNMG_EINVAL;
     cudaError_t e;
     if (ctx->precision == DNNMG_FP64)
@@ -383,6 +398,7 @@ dnnmg_status dnnmg_local_restrict(dnnmg_ctx* ctx, const void* x_coarse_dev, cons
 }
 
 dnnmg_status dnnmg_network(dnnmg_ctx* ctx, const void* X_dev, void* Y_dev, int64_t n_rows) {
+    Range nvtx_range("dnnmg_network");
     if (!ctx || !X_dev || !Y_dev || n_rows < 0) return DNNMG_EINVAL;
     if (!ctx->has_net) return fail(ctx, DNNMG_ESTATE, "dnnmg_network before dnnmg_set_network");
     if (n_rows > ctx->act_rows) return fail(ctx, DNNMG_EINVAL, "n_rows exceeds the activation capacity");
@@ -417,6 +433,7 @@ dnnmg_status dnnmg_network(dnnmg_ctx* ctx, const void* X_dev, void* Y_dev, int64
 }
 
 dnnmg_status dnnmg_extend(dnnmg_ctx* ctx, const void* Y_dev, void* d_dev) {
+    Range nvtx_range("dnnmg_extend");
     if (!ctx || ctx->net_only || !Y_dev || !d_dev) return DNNMG_EINVAL;
     cudaError_t e = is_fp64(ctx) ? launch_extend(ctx->dm, (const double*)Y_dev, (double*)d_dev, ctx->stream)
                                  : launch_extend(ctx->dm, (const float*)Y_dev, (float*)d_dev, ctx->stream);
@@ -427,6 +444,7 @@ dnnmg_status dnnmg_extend(dnnmg_ctx* ctx, const void* Y_dev, void* d_dev) {
 
 dnnmg_status dnnmg_rhs_restrict(dnnmg_ctx* ctx, const void* x_coarse_dev, const void* d_dev, void* b_fine_dev,
                                 void* b_coarse_dev) {
+    Range nvtx_range("dnnmg_rhs_restrict");
     if (!ctx || ctx->net_only || !x_coarse_dev || !d_dev) return DNNMG_EINVAL;
     int launches = 0;
     cudaError_t e =
@@ -443,6 +461,7 @@ dnnmg_status dnnmg_rhs_restrict(dnnmg_ctx* ctx, const void* x_coarse_dev, const 
 }
 
 dnnmg_status dnnmg_restrict(dnnmg_ctx* ctx, const void* b_fine_dev, void* b_coarse_dev) {
+    Range nvtx_range("dnnmg_restrict");
     if (!ctx || ctx->net_only || !b_fine_dev || !b_coarse_dev) return DNNMG_EINVAL;
     cudaError_t e = is_fp64(ctx) ? launch_restrict(ctx->dm, (const double*)b_fine_dev, (double*)b_coarse_dev,
                                                    (double*)ctx->partial_c, ctx->stream)
@@ -455,6 +474,7 @@ dnnmg_status dnnmg_restrict(dnnmg_ctx* ctx, const void* b_fine_dev, void* b_coar
 
 dnnmg_status dnnmg_patch_step(dnnmg_ctx* ctx, const void* x_coarse_dev, const void* F_dev, void* b_fine_dev,
                               void* b_coarse_dev) {
+    Range nvtx_range("dnnmg_patch_step");
     if (!ctx || ctx->net_only || !x_coarse_dev || !F_dev) return DNNMG_EINVAL;
     if (!ctx->has_net) return fail(ctx, DNNMG_ESTATE, "dnnmg_patch_step before dnnmg_set_network");
     dnnmg_status st;
@@ -467,6 +487,7 @@ dnnmg_status dnnmg_patch_step(dnnmg_ctx* ctx, const void* x_coarse_dev, const vo
 
 dnnmg_status dnnmg_patch_step_host(dnnmg_ctx* ctx, const void* x_coarse_host, const void* F_host,
                                    void* b_fine_host, void* b_coarse_host) {
+    Range nvtx_range("dnnmg_patch_step_host");
     if (!ctx || ctx->net_only || !x_coarse_host || !F_host) return DNNMG_EINVAL;
     if (!ctx->has_net) return fail(ctx, DNNMG_ESTATE, "dnnmg_patch_step_host before dnnmg_set_network");
     const size_t fe = field_elem(ctx->precision);
@@ -631,6 +652,7 @@ dnnmg_status dnnmg_level_jacobian(dnnmg_ctx* ctx, int32_t level, const dnnmg_sol
 
 dnnmg_status dnnmg_solve(dnnmg_ctx* ctx, int32_t level, const dnnmg_solver_params* prm, const double* b_dev,
                          double* x_dev, dnnmg_solve_stats* stats) {
+    Range nvtx_range("dnnmg_solve");
     if (!ctx || ctx->net_only || !b_dev || !x_dev) return DNNMG_EINVAL;
     dnnmg_solver_params d;
     dnnmg_solver_defaults(&d);
@@ -650,6 +672,7 @@ dnnmg_status dnnmg_solve(dnnmg_ctx* ctx, int32_t level, const dnnmg_solver_param
 
 dnnmg_status dnnmg_time_step(dnnmg_ctx* ctx, int32_t n_steps, const dnnmg_solver_params* prm, double* x_coarse_dev,
                              double* b_coarse_dev, void* F_dev, dnnmg_solve_stats* stats) {
+    Range nvtx_range("dnnmg_time_step");
     if (!ctx || ctx->net_only || !x_coarse_dev || !b_coarse_dev || !F_dev || n_steps < 0) return DNNMG_EINVAL;
     if (!ctx->has_net) return fail(ctx, DNNMG_ESTATE, "dnnmg_time_step before dnnmg_set_network");
     const int64_t nv = ctx->host.nv;
@@ -670,6 +693,7 @@ dnnmg_status dnnmg_time_step(dnnmg_ctx* ctx, int32_t n_steps, const dnnmg_solver
 
 dnnmg_status dnnmg_step_begin(dnnmg_ctx* ctx, const dnnmg_solver_params* prm, int32_t solve, double* x_coarse_dev,
                               const double* b_coarse_dev, const void* F_dev, void* X_dev, dnnmg_solve_stats* stats) {
+    Range nvtx_range("dnnmg_step_begin");
     if (!ctx || ctx->net_only || !x_coarse_dev || !F_dev || !X_dev || (solve && !b_coarse_dev)) return DNNMG_EINVAL;
     const int64_t nv = ctx->host.nv;
     dnnmg_status st = DNNMG_OK, solve_st = DNNMG_OK;
@@ -696,6 +720,7 @@ dnnmg_status dnnmg_step_begin(dnnmg_ctx* ctx, const dnnmg_solver_params* prm, in
 }
 
 dnnmg_status dnnmg_step_end(dnnmg_ctx* ctx, const void* Y_dev, void* F_dev, double* b_coarse_dev) {
+    Range nvtx_range("dnnmg_step_end");
     if (!ctx || ctx->net_only || !Y_dev || !F_dev || !b_coarse_dev) return DNNMG_EINVAL;
     if (!ctx->last_xc) return fail(ctx, DNNMG_ESTATE, "dnnmg_step_end before dnnmg_step_begin");
     const int64_t nv = ctx->host.nv;
@@ -746,6 +771,7 @@ dnnmg_status dnnmg_net_create(const dnnmg_net_desc* net, const double* const* W,
 
 dnnmg_status dnnmg_plain_step(dnnmg_ctx* ctx, int32_t level, int32_t n_steps, const dnnmg_solver_params* prm,
                               double* x_dev, dnnmg_solve_stats* stats) {
+    Range nvtx_range("dnnmg_plain_step");
     if (!ctx || ctx->net_only || !x_dev || n_steps < 0) return DNNMG_EINVAL;
     DeviceLevel* L;
     dnnmg_status st = get_level(ctx, level, prm, &L);

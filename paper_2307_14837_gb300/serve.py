@@ -124,6 +124,7 @@ class Server:
         self.reserved = 0
         self.rows_reserved = 0
         self.admission_s = 0.0       # host time the step loop spent admitting
+        self.failures = {}           # request name -> why its context could not be built
 
     # -- admission -----------------------------------------------------------
     def submit(self, req: Request):
@@ -162,20 +163,27 @@ class Server:
                 self.queue.popleft()
                 self.log.append(("rejected", req.name, now))
                 continue
-            if self.pool is not None:
-                entry = self.preparing.get(id(req))
-                if entry is None or not entry[0].done():
-                    break                                       # FIFO: the head is not ready yet
-                self.queue.popleft()
-                del self.preparing[id(req)]
-                sim = entry[0].result()
-                self.reserved -= mem
-                self.rows_reserved -= nc
-            else:
-                if self.used + mem > self.budget or self._rows() + nc > self.max_rows:
-                    break                                       # FIFO: wait for memory / rows
-                self.queue.popleft()
-                sim = self._start(req, mem, now)
+            try:
+                if self.pool is not None:
+                    entry = self.preparing.get(id(req))
+                    if entry is None or not entry[0].done():
+                        break                                   # FIFO: the head is not ready yet
+                    self.queue.popleft()
+                    del self.preparing[id(req)]
+                    self.reserved -= mem
+                    self.rows_reserved -= nc
+                    sim = entry[0].result()
+                else:
+                    if self.used + mem > self.budget or self._rows() + nc > self.max_rows:
+                        break                                   # FIFO: wait for memory / rows
+                    self.queue.popleft()
+                    sim = self._start(req, mem, now)
+            except (capi.DnnmgError, ValueError) as e:
+                # a request whose context cannot be built (an invalid mesh,
+                # no device memory) fails alone; the others go on
+                self.log.append(("failed", req.name, now))
+                self.failures[req.name] = str(e)
+                continue
             self.live.append(sim)
             self.used += mem
             self.log.append(("admitted", req.name, now))
@@ -279,7 +287,10 @@ class Server:
         if self.pool is not None:
             self.pool.shutdown(wait=True)
             for fut, _, _ in self.preparing.values():
-                fut.result().path.close()
+                try:
+                    fut.result().path.close()
+                except (capi.DnnmgError, ValueError):
+                    pass
             self.preparing = {}
         for s in self.live:
             s.path.close()

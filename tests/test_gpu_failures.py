@@ -1,0 +1,98 @@
+"""Checkpoint / resume and failure reporting:
+* a DNN-MG run saved after some steps and resumed in a new context gives
+  the uninterrupted run's next steps bit for bit (every stage is
+  deterministic);
+* a Newton iteration cap ends the solve with converged = 0 and the stats
+  filled (DNNMG_ENOCONV is a result, not an error);
+* a non-finite right-hand side is reported as DNNMG_ENAN;
+* a serving request whose context cannot be built fails alone while the
+  others are served."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2307_14837_gb300 import build, capi, inputs as I  # noqa: E402
+from paper_2307_14837_gb300.checkpoint import TimeLoop  # noqa: E402
+from paper_2307_14837_gb300.path import PatchPath  # noqa: E402
+from paper_2307_14837_gb300.serve import Request, Server  # noqa: E402
+
+WIDTHS = (228, 64, 64, 81)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    capi.load()
+
+
+def _net():
+    Ws, ss, ts = I.network_weights(WIDTHS, seed=5, scale_shift=True)
+    Ws[-1] = 0.05 * Ws[-1]
+    return Ws, ss, ts
+
+
+@pytest.mark.parametrize("precision", ["fp64", "bf16"])
+def test_resume_reproduces_the_next_steps_bit_exactly(precision, tmp_path):
+    m = I.cavity_mesh(4, jitter=0.1, seed=2)
+    Ws, ss, ts = _net()
+    a = TimeLoop(m, 0.01, 0.01, 0.5, precision, WIDTHS, Ws, ss, ts).start().advance(4)
+    b = TimeLoop(m, 0.01, 0.01, 0.5, precision, WIDTHS, Ws, ss, ts).start().advance(2)
+    ck = tmp_path / "run.npz"
+    b.save(ck)
+    b.close()
+    c = TimeLoop.load(ck).advance(2)
+    torch.cuda.synchronize()
+    assert c.step_count == 4
+    assert torch.equal(a.x, c.x) and torch.equal(a.b, c.b) and torch.equal(a.F, c.F)
+    assert np.abs(a.x.cpu().numpy()[:, 0:3]).max() > 0.1
+    a.close()
+    c.close()
+
+
+def test_iteration_cap_and_non_finite_input():
+    m = I.cavity_mesh(4)
+    p = PatchPath(m, 0.01, 0.01, 1.0, "fp64")
+    bc = I.dirichlet_values(m, m["xyz"], m["vertex_bc"])
+    dirc = (m["vertex_bc"] == 1) | (m["vertex_bc"] == 2)
+    x0 = np.zeros((p.n_coarse, 4))
+    x0[dirc, 0:3] = bc[dirc]
+    x = torch.as_tensor(x0, device="cuda")
+    b = torch.zeros_like(x)
+    capi.dnnmg_level_rhs(p.ctx, capi.LEVEL_COARSE, x, b)
+    prm = capi.dnnmg_solver_defaults(newton_max=1, newton_rtol=1e-15, newton_atol=1e-30)
+    st = capi.dnnmg_solve(p.ctx, capi.LEVEL_COARSE, b, x.clone(), prm=prm)
+    assert st["converged"] == 0 and st["newton_iterations"] == 1 and st["residual"] < st["residual0"]
+    bad = b.clone()
+    bad[int(np.flatnonzero(~dirc)[0]), 0] = float("nan")   # an interior row (Dirichlet rows are overwritten)
+    with pytest.raises(capi.DnnmgError) as e:
+        capi.dnnmg_solve(p.ctx, capi.LEVEL_COARSE, bad, x.clone())
+    assert e.value.status == -5
+    # the context stays usable
+    st = capi.dnnmg_solve(p.ctx, capi.LEVEL_COARSE, b, x)
+    assert st["converged"] == 1
+    p.close()
+
+
+@pytest.mark.parametrize("workers", [0, 2])
+def test_server_survives_a_request_that_cannot_be_built(workers):
+    Ws, ss, ts = _net()
+    bad_mesh = I.cavity_mesh(2)
+    bad_cells = np.array(bad_mesh["cells"]).copy()
+    bad_cells[0, 0] = 10 ** 6                   # vertex index out of range
+    bad = dict(xyz=bad_mesh["xyz"], cells=bad_cells, vertex_bc=bad_mesh["vertex_bc"])
+    reqs = [Request("a", I.cavity_mesh(4), 0.01, 0.01, 1.0, 2),
+            Request("bad", bad, 0.01, 0.01, 1.0, 2),
+            Request("c", I.cavity_mesh(2), 0.01, 0.01, 1.0, 3)]
+    srv = Server(WIDTHS, Ws, ss, ts, memory_budget=1 << 33, max_rows=4096, precision="bf16", prepare_workers=workers)
+    for r in reqs:
+        srv.submit(r)
+    while srv.live or srv.queue:
+        srv.step()
+    srv.close()
+    assert set(srv.results) == {"a", "c"} and "bad" in srv.failures
+    assert ("failed", "bad") in [(e, n) for e, n, _ in srv.log]
+    assert srv.results["c"]["steps"] == 3
