@@ -212,6 +212,15 @@ dnnmg_status dnnmg_local_restrict(dnnmg_ctx* ctx, const void* x_coarse_dev, cons
  * capacity fixed at dnnmg_set_network (max(n_patches, 1)). */
 dnnmg_status dnnmg_network(dnnmg_ctx* ctx, const void* X_dev, void* Y_dev, int64_t n_rows);
 
+/* Test of the failure path (the paper has no counterpart): dnnmg_network
+ * with the first operand stage of the first layer armed but never filled
+ * (BF16 tensor-core form only, else EUNSUPPORTED).  Every wait of the
+ * tensor-core kernel is bounded (about one second), so the kernel gives up,
+ * drains its copies, frees TMEM and returns; the following dnnmg_sync
+ * reports DNNMG_ETIMEOUT and clears the error, and the context stays usable.
+ * Takes a few seconds; Y holds no result. */
+dnnmg_status dnnmg_network_wait_test(dnnmg_ctx* ctx, const void* X_dev, void* Y_dev, int64_t n_rows);
+
 /* Extension d = mu . sum_P L(Y_P, P) of Eq. (15), mu = 1 / valence, summed
  * in patch order (deterministic, no atomics).  d_dev [n_fine_nodes][3];
  * zero at Dirichlet velocity nodes. */

@@ -66,6 +66,7 @@ _SIGS = {
     "dnnmg_residual": ([_VP, _VP, _VP, _VP], ctypes.c_int),
     "dnnmg_local_restrict": ([_VP, _VP, _VP, _VP], ctypes.c_int),
     "dnnmg_network": ([_VP, _VP, _VP, ctypes.c_int64], ctypes.c_int),
+    "dnnmg_network_wait_test": ([_VP, _VP, _VP, ctypes.c_int64], ctypes.c_int),
     "dnnmg_extend": ([_VP, _VP, _VP], ctypes.c_int),
     "dnnmg_rhs_restrict": ([_VP, _VP, _VP, _VP, _VP], ctypes.c_int),
     "dnnmg_patch_step": ([_VP, _VP, _VP, _VP, _VP], ctypes.c_int),
@@ -194,6 +195,10 @@ def dnnmg_local_restrict(ctx, x_coarse, r, X):
 
 def dnnmg_network(ctx, X, Y, n_rows):
     _check(ctx, load().dnnmg_network(ctx, _ptr(X), _ptr(Y), int(n_rows)))
+
+
+def dnnmg_network_wait_test(ctx, X, Y, n_rows):
+    _check(ctx, load().dnnmg_network_wait_test(ctx, _ptr(X), _ptr(Y), int(n_rows)))
 
 
 def dnnmg_extend(ctx, Y, d):

@@ -397,8 +397,10 @@ dnnmg_status dnnmg_local_restrict(dnnmg_ctx* ctx, const void* x_coarse_dev, cons
     return DNNMG_OK;
 }
 
-dnnmg_status dnnmg_network(dnnmg_ctx* ctx, const void* X_dev, void* Y_dev, int64_t n_rows) {
-    Range nvtx_range("dnnmg_network");
+// The network; withhold_first_load (tensor-core form only) arms the first
+// layer's first operand stage without filling it, to test the bounded waits.
+static dnnmg_status network_impl(dnnmg_ctx* ctx, const void* X_dev, void* Y_dev, int64_t n_rows,
+                                 int withhold_first_load) {
     if (!ctx || !X_dev || !Y_dev || n_rows < 0) return DNNMG_EINVAL;
     if (!ctx->has_net) return fail(ctx, DNNMG_ESTATE, "dnnmg_network before dnnmg_set_network");
     if (n_rows > ctx->act_rows) return fail(ctx, DNNMG_EINVAL, "n_rows exceeds the activation capacity");
@@ -424,12 +426,24 @@ dnnmg_status dnnmg_network(dnnmg_ctx* ctx, const void* X_dev, void* Y_dev, int64
         } else {
             e = launch_layer_tc((const __nv_bfloat16*)A, lda, (const __nv_bfloat16*)ctx->W[i], K, N,
                                 (const float*)ctx->scale[i], (const float*)ctx->shift[i], C, ldc, !last,
-                                (const __nv_bfloat16*)R, lda, n_rows, ctx->widths[i + 1], K, !last, ctx->stream);
+                                (const __nv_bfloat16*)R, lda, n_rows, ctx->widths[i + 1], K, !last, ctx->stream,
+                                i == 0 ? withhold_first_load : 0);
         }
         ctx->launches += 1;
         if (e != cudaSuccess) return cuda_fail(ctx, e, "network layer");
     }
     return DNNMG_OK;
+}
+
+dnnmg_status dnnmg_network(dnnmg_ctx* ctx, const void* X_dev, void* Y_dev, int64_t n_rows) {
+    Range nvtx_range("dnnmg_network");
+    return network_impl(ctx, X_dev, Y_dev, n_rows, 0);
+}
+
+dnnmg_status dnnmg_network_wait_test(dnnmg_ctx* ctx, const void* X_dev, void* Y_dev, int64_t n_rows) {
+    if (!ctx || ctx->precision != DNNMG_BF16) return DNNMG_EUNSUPPORTED;
+    Range nvtx_range("dnnmg_network_wait_test");
+    return network_impl(ctx, X_dev, Y_dev, n_rows, 1);
 }
 
 dnnmg_status dnnmg_extend(dnnmg_ctx* ctx, const void* Y_dev, void* d_dev) {

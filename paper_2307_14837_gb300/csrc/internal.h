@@ -192,7 +192,7 @@ namespace dnnmg {
 cudaError_t launch_layer_tc(const __nv_bfloat16* A, int64_t lda, const __nv_bfloat16* W, int64_t ldw, int n_rows_w,
                             const float* scale, const float* shift, void* C, int64_t ldc, bool out_bf16,
                             const __nv_bfloat16* R, int64_t ldr, int64_t M, int N, int K, bool relu,
-                            cudaStream_t s);
+                            cudaStream_t s, int withhold_first_load = 0);
 // Error code recorded by a tensor-core kernel whose bounded wait expired
 // (0 = none); reading clears it.  Synchronous.
 cudaError_t read_tc_error(int* code);

@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_layer_kernel(
     const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmW,
     const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmR,
     const float* __restrict__ scale, const float* __restrict__ shift, void* __restrict__ Cout, int64_t ldc,
-    const __nv_bfloat16* __restrict__ R, int64_t ldr, int M, int N, int K, int relu) {
+    const __nv_bfloat16* __restrict__ R, int64_t ldr, int M, int N, int K, int relu, int withhold_first_load) {
     using C = Cfg<BN>;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
@@ -268,8 +268,12 @@ __global__ void __launch_bounds__(kThreads, 1) tc_layer_kernel(
                 }
                 const uint32_t sa = base + stage * C::STAGE_BYTES;
                 mbar_arrive_expect_tx(full_bar(stage), C::STAGE_BYTES);
-                tma_load_2d(sa, &tmA, full_bar(stage), kb * BK, m0);
-                tma_load_2d(sa + C::A_BYTES, &tmW, full_bar(stage), kb * BK, n0);
+                // failure-path test: the first stage is armed but never
+                // filled, so every wait that depends on it runs out
+                if (!(withhold_first_load && t == int(blockIdx.x) && kb == 0)) {
+                    tma_load_2d(sa, &tmA, full_bar(stage), kb * BK, m0);
+                    tma_load_2d(sa + C::A_BYTES, &tmW, full_bar(stage), kb * BK, n0);
+                }
                 if (++stage == C::STAGES) {
                     stage = 0;
                     phase ^= 1u;
@@ -523,7 +527,7 @@ int sm_count() {
 template <int BN, bool OUT_BF16>
 cudaError_t launch_tc(const __nv_bfloat16* A, int64_t lda, const __nv_bfloat16* W, int64_t ldw, int n_rows_w,
                       const float* scale, const float* shift, void* C, int64_t ldc, const __nv_bfloat16* R,
-                      int64_t ldr, int64_t M, int N, int K, bool relu, cudaStream_t s) {
+                      int64_t ldr, int64_t M, int N, int K, bool relu, cudaStream_t s, int withhold) {
     using Cf = Cfg<BN>;
     static bool attr = false;
     if (!attr) {
@@ -541,7 +545,7 @@ cudaError_t launch_tc(const __nv_bfloat16* A, int64_t lda, const __nv_bfloat16* 
     const int64_t tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
     const int grid = int(std::min<int64_t>(tiles, sm_count()));
     tc_layer_kernel<BN, OUT_BF16><<<grid, kThreads, Cf::SMEM, s>>>(ta, tw, tc, tr, scale, shift, C, ldc, R, ldr, int(M),
-                                                                    N, K, relu ? 1 : 0);
+                                                                    N, K, relu ? 1 : 0, withhold);
     return cudaGetLastError();
 }
 
@@ -553,7 +557,7 @@ cudaError_t launch_tc(const __nv_bfloat16* A, int64_t lda, const __nv_bfloat16* 
 cudaError_t launch_layer_tc(const __nv_bfloat16* A, int64_t lda, const __nv_bfloat16* W, int64_t ldw, int n_rows_w,
                             const float* scale, const float* shift, void* C, int64_t ldc, bool out_bf16,
                             const __nv_bfloat16* R, int64_t ldr, int64_t M, int N, int K, bool relu,
-                            cudaStream_t s) {
+                            cudaStream_t s, int withhold_first_load) {
     if (M <= 0) return cudaSuccess;
     if (K % BK || lda % 8 || ldw % 8 || (reinterpret_cast<uintptr_t>(A) & 15) ||
         (reinterpret_cast<uintptr_t>(W) & 15) || M >= (int64_t(1) << 31) || n_rows_w < N)
@@ -561,10 +565,14 @@ cudaError_t launch_layer_tc(const __nv_bfloat16* A, int64_t lda, const __nv_bflo
     if (out_bf16 && (ldc % 8 || (reinterpret_cast<uintptr_t>(C) & 15) || (R && (ldr % 8 || (reinterpret_cast<uintptr_t>(R) & 15)))))
         return cudaErrorInvalidValue;
     if (N <= 96)
-        return out_bf16 ? launch_tc<96, true>(A, lda, W, ldw, n_rows_w, scale, shift, C, ldc, R, ldr, M, N, K, relu, s)
-                        : launch_tc<96, false>(A, lda, W, ldw, n_rows_w, scale, shift, C, ldc, R, ldr, M, N, K, relu, s);
-    return out_bf16 ? launch_tc<256, true>(A, lda, W, ldw, n_rows_w, scale, shift, C, ldc, R, ldr, M, N, K, relu, s)
-                    : launch_tc<256, false>(A, lda, W, ldw, n_rows_w, scale, shift, C, ldc, R, ldr, M, N, K, relu, s);
+        return out_bf16 ? launch_tc<96, true>(A, lda, W, ldw, n_rows_w, scale, shift, C, ldc, R, ldr, M, N, K, relu, s,
+                                              withhold_first_load)
+                        : launch_tc<96, false>(A, lda, W, ldw, n_rows_w, scale, shift, C, ldc, R, ldr, M, N, K, relu, s,
+                                               withhold_first_load);
+    return out_bf16 ? launch_tc<256, true>(A, lda, W, ldw, n_rows_w, scale, shift, C, ldc, R, ldr, M, N, K, relu, s,
+                                           withhold_first_load)
+                    : launch_tc<256, false>(A, lda, W, ldw, n_rows_w, scale, shift, C, ldc, R, ldr, M, N, K, relu, s,
+                                            withhold_first_load);
 }
 
 // Read and clear the error flag of the tensor-core kernels (synchronous).

@@ -96,3 +96,28 @@ def test_server_survives_a_request_that_cannot_be_built(workers):
     assert set(srv.results) == {"a", "c"} and "bad" in srv.failures
     assert ("failed", "bad") in [(e, n) for e, n, _ in srv.log]
     assert srv.results["c"]["steps"] == 3
+
+
+def test_tensor_core_wait_expiry_is_reported_and_recovered():
+    # the first operand stage of the first layer is armed but never filled:
+    # the kernel's bounded waits run out, it returns, dnnmg_sync reports
+    # DNNMG_ETIMEOUT, and the context then computes the network normally
+    m = I.cavity_mesh(4)
+    widths = (228, 256, 256, 81)
+    Ws, ss, ts = I.network_weights(widths, seed=1)
+    p = PatchPath(m, 0.01, 0.01, 1.0, "bf16")
+    p.set_network(widths, Ws, ss, ts)
+    X = torch.zeros((p.n_patches, 256), dtype=torch.bfloat16, device="cuda")
+    X[:, :228] = torch.as_tensor(I.splitmix_normal(4, p.n_patches * 228).reshape(p.n_patches, 228),
+                                 device="cuda").to(torch.bfloat16)
+    ref = p.network(X)
+    capi.dnnmg_sync(p.ctx, 10_000_000)
+    Y = torch.zeros_like(ref)
+    capi.dnnmg_network_wait_test(p.ctx, X, Y, p.n_patches)
+    with pytest.raises(capi.DnnmgError) as e:
+        capi.dnnmg_sync(p.ctx, 30_000_000)
+    assert e.value.status == -6
+    again = p.network(X)
+    capi.dnnmg_sync(p.ctx, 10_000_000)                  # the error was cleared
+    assert torch.equal(again, ref)
+    p.close()
