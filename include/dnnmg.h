@@ -44,6 +44,10 @@
  *       Y         [n_patches][n_out]: 27 x (u, v, w) (J = 2: 125 x 3 = 375)
  *     Patch node iota = a + 3b + 9c, (a,b,c) in {0,1,2}^3 along the coarse
  *     cell's reference axes (J = 2: a + 5b + 25c, (a,b,c) in {0..4}^3).
+   - Alignment of *_dev field pointers: [n][4] fields (x_coarse, x_fine,
+     F, r, b_fine, b_coarse) to 4 elements (16 bytes in float, 32 in
+     double), X to 16 bytes, d and Y to one element; DNNMG_EINVAL otherwise.
+     Fresh allocations of cudaMalloc or torch meet all of them.
  *   - Dirichlet velocity rows (fine node kinds 1 and 2) of r, d and b_fine,
  *     and coarse Dirichlet velocity rows of b_coarse are zero; pressure rows
  *     of b_fine and b_coarse are zero.
@@ -448,8 +452,8 @@ dnnmg_status dnnmg_adamw(int64_t n, float* w_dev, const float* g_dev, float* m_d
  * reads, so nothing has to be cleared, but calls that overlap on the GPU
  * (two streams, two threads) race on it.
  * Errors: DNNMG_EINVAL for a null pointer, non-positive size, bad
- * nu/dt/theta, or n_patches > DNNMG_NOALLOC_MAX_PATCHES (nothing is
- * launched); DNNMG_ECUDA if the address lookup or a launch fails. */
+ * nu/dt/theta, x_coarse_dev, F_dev or r_dev not 16-byte aligned, or
+ * n_patches > DNNMG_NOALLOC_MAX_PATCHES (nothing is launched); DNNMG_ECUDA if the address lookup or a launch fails. */
 dnnmg_status dnnmg_residual_noalloc(int64_t n_patches, int64_t n_fine_nodes, const int32_t* cells_dev,
                                     const float* xyz_dev, const int32_t* node_ptr_dev,
                                     const int32_t* node_idx_dev, const uint8_t* fine_dirichlet_dev,

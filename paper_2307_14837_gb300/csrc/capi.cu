@@ -2,6 +2,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <initializer_list>
 #include <new>
 #include <thread>
 
@@ -66,6 +67,21 @@ dnnmg_status alloc(dnnmg_ctx* ctx, size_t bytes, void** dev) {
 size_t field_elem(int precision) { return precision == DNNMG_FP64 ? sizeof(double) : sizeof(float); }
 
 bool is_fp64(const dnnmg_ctx* c) { return c->precision == DNNMG_FP64; }
+
+// Fields of [n][4] values are read and written 4 values at a time (16 bytes
+// in float, 32 in double) and rows of X in 16-byte pieces; d and Y are read
+// by the element.  Pointers that break this are refused before any launch.
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+bool node_fields_aligned(const dnnmg_ctx* c, std::initializer_list<const void*> ps) {
+    for (const void* p : ps)
+        if (p && !aligned(p, 4 * field_elem(c->precision))) return false;
+    return true;
+}
+bool elem_aligned(const dnnmg_ctx* c, std::initializer_list<const void*> ps) {
+    for (const void* p : ps)
+        if (p && !aligned(p, field_elem(c->precision))) return false;
+    return true;
+}
 
 // network inputs per patch: 2 x nodes x 4 values + the geometry features;
 // the row stride of X; outputs per patch (3 per node)
@@ -353,6 +369,7 @@ dnnmg_status dnnmg_set_network(dnnmg_ctx* ctx, const dnnmg_net_desc* net, const 
 dnnmg_status dnnmg_prolongate(dnnmg_ctx* ctx, const void* x_coarse_dev, void* x_fine_dev) {
     Range nvtx_range("dnnmg_prolongate");
     if (!ctx || ctx->net_only || !x_coarse_dev || !x_fine_dev) return DNNMG_EINVAL;
+    if (!node_fields_aligned(ctx, {x_coarse_dev, x_fine_dev})) return fail(ctx, DNNMG_EINVAL, "misaligned field");
     cudaError_t e = is_fp64(ctx) ? launch_prolongate(ctx->dm, (const double*)x_coarse_dev, (double*)x_fine_dev, ctx->stream)
                                  : launch_prolongate(ctx->dm, (const float*)x_coarse_dev, (float*)x_fine_dev, ctx->stream);
     ctx->launches += 1;
@@ -377,6 +394,7 @@ static dnnmg_status residual_impl(dnnmg_ctx* ctx, const void* x_coarse_dev, cons
 dnnmg_status dnnmg_residual(dnnmg_ctx* ctx, const void* x_coarse_dev, const void* F_dev, void* r_dev) {
     Range nvtx_range("dnnmg_residual");
     if (!ctx || ctx->net_only || !x_coarse_dev || !F_dev || !r_dev) return DNNMG_EINVAL;
+    if (!node_fields_aligned(ctx, {x_coarse_dev, F_dev, r_dev})) return fail(ctx, DNNMG_EINVAL, "misaligned field");
     return residual_impl(ctx, x_coarse_dev, F_dev, r_dev, nullptr);
 }
 
@@ -384,6 +402,8 @@ dnnmg_status dnnmg_residual(dnnmg_ctx* ctx, const void* x_coarse_dev, const void
 dnnmg_status dnnmg_local_restrict(dnnmg_ctx* ctx, const void* x_coarse_dev, const void* r_dev, void* X_dev) {
     Range nvtx_range("dnnmg_local_restrict");
     if (!ctx || ctx->net_only || !x_coarse_dev || !r_dev || !X_dev) return DNNMG_EINVAL;
+    if (!node_fields_aligned(ctx, {x_coarse_dev, r_dev}) || !aligned(X_dev, 16))
+        return fail(ctx, DNNMG_EINVAL, "misaligned field");
     cudaError_t e;
     if (ctx->precision == DNNMG_FP64)
         e = launch_local_restrict(ctx->dm, (const double*)x_coarse_dev, (const double*)r_dev, (double*)X_dev, ctx->stream);
@@ -402,6 +422,7 @@ dnnmg_status dnnmg_local_restrict(dnnmg_ctx* ctx, const void* x_coarse_dev, cons
 static dnnmg_status network_impl(dnnmg_ctx* ctx, const void* X_dev, void* Y_dev, int64_t n_rows,
                                  int withhold_first_load) {
     if (!ctx || !X_dev || !Y_dev || n_rows < 0) return DNNMG_EINVAL;
+    if (!aligned(X_dev, 16) || !elem_aligned(ctx, {Y_dev})) return fail(ctx, DNNMG_EINVAL, "misaligned field");
     if (!ctx->has_net) return fail(ctx, DNNMG_ESTATE, "dnnmg_network before dnnmg_set_network");
     if (n_rows > ctx->act_rows) return fail(ctx, DNNMG_EINVAL, "n_rows exceeds the activation capacity");
     const int L = ctx->n_layers;
@@ -449,6 +470,7 @@ dnnmg_status dnnmg_network_wait_test(dnnmg_ctx* ctx, const void* X_dev, void* Y_
 dnnmg_status dnnmg_extend(dnnmg_ctx* ctx, const void* Y_dev, void* d_dev) {
     Range nvtx_range("dnnmg_extend");
     if (!ctx || ctx->net_only || !Y_dev || !d_dev) return DNNMG_EINVAL;
+    if (!elem_aligned(ctx, {Y_dev, d_dev})) return fail(ctx, DNNMG_EINVAL, "misaligned field");
     cudaError_t e = is_fp64(ctx) ? launch_extend(ctx->dm, (const double*)Y_dev, (double*)d_dev, ctx->stream)
                                  : launch_extend(ctx->dm, (const float*)Y_dev, (float*)d_dev, ctx->stream);
     ctx->launches += 1;
@@ -460,6 +482,8 @@ dnnmg_status dnnmg_rhs_restrict(dnnmg_ctx* ctx, const void* x_coarse_dev, const 
                                 void* b_coarse_dev) {
     Range nvtx_range("dnnmg_rhs_restrict");
     if (!ctx || ctx->net_only || !x_coarse_dev || !d_dev) return DNNMG_EINVAL;
+    if (!node_fields_aligned(ctx, {x_coarse_dev, b_fine_dev, b_coarse_dev}) || !elem_aligned(ctx, {d_dev}))
+        return fail(ctx, DNNMG_EINVAL, "misaligned field");
     int launches = 0;
     cudaError_t e =
         is_fp64(ctx)
@@ -477,6 +501,7 @@ dnnmg_status dnnmg_rhs_restrict(dnnmg_ctx* ctx, const void* x_coarse_dev, const 
 dnnmg_status dnnmg_restrict(dnnmg_ctx* ctx, const void* b_fine_dev, void* b_coarse_dev) {
     Range nvtx_range("dnnmg_restrict");
     if (!ctx || ctx->net_only || !b_fine_dev || !b_coarse_dev) return DNNMG_EINVAL;
+    if (!node_fields_aligned(ctx, {b_fine_dev, b_coarse_dev})) return fail(ctx, DNNMG_EINVAL, "misaligned field");
     cudaError_t e = is_fp64(ctx) ? launch_restrict(ctx->dm, (const double*)b_fine_dev, (double*)b_coarse_dev,
                                                    (double*)ctx->partial_c, ctx->stream)
                                  : launch_restrict(ctx->dm, (const float*)b_fine_dev, (float*)b_coarse_dev,

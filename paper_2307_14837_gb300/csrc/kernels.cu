@@ -929,6 +929,9 @@ extern "C" dnnmg_status dnnmg_residual_noalloc(int64_t n_patches, int64_t n_fine
         !(theta >= 0.0 && theta <= 1.0))
         return DNNMG_EINVAL;
     if (n_patches > DNNMG_NOALLOC_MAX_PATCHES) return DNNMG_EINVAL;   // beyond the fixed scratch
+    for (const void* f : {static_cast<const void*>(x_coarse_dev), static_cast<const void*>(F_dev),
+                          static_cast<const void*>(r_dev)})
+        if (reinterpret_cast<uintptr_t>(f) % 16) return DNNMG_EINVAL;   // [n][4] rows move as 16 bytes
     float* partial = nullptr;
     if (noalloc_scratch(&partial) != cudaSuccess) return DNNMG_ECUDA;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);

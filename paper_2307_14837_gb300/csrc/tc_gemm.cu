@@ -122,6 +122,10 @@ __device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, uint32_t sr
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 // the source shared memory of every committed store has been read
 __device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// ... of every committed store but the most recent one
+__device__ __forceinline__ void bulk_wait_read_all_but_last() {
+    asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+}
 // every committed store is complete
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 // generic-proxy writes to shared memory become visible to the async proxy (TMA)
@@ -328,10 +332,14 @@ __global__ void __launch_bounds__(kThreads, 1) tc_layer_kernel(
         const int half = (warp - 2) >> 2;
         const int ew = warp - 2;
         float* stage = ep_stage + ew * (C::EP_WARP_BYTES / 4);          // fp32 output
-        const uint32_t obox = ep_base + uint32_t(ew * C::EP_WARP_BYTES);   // bf16 output box
-        const uint32_t rbox = obox + 2048u;                               // skip input box
+        const uint32_t obox0 = ep_base + uint32_t(ew * C::EP_WARP_BYTES);  // bf16 output box
+        const uint32_t rbox = obox0 + 2048u;                              // skip input box
         const uint32_t rbar = skip_bar(ew);
         const bool has_r = OUT_BF16 && R != nullptr;
+        // without a skip input its box is a second output box: consecutive
+        // chunks alternate between the two, so a chunk's box writes wait
+        // only for the store before the previous one
+        uint32_t n_stored = 0;
         uint32_t rphase = 0;
         bool r_pending = false;
         // TMA load of the skip box of chunk c0 of the tile at (m0, n0)
@@ -415,8 +423,14 @@ __global__ void __launch_bounds__(kThreads, 1) tc_layer_kernel(
                         __syncwarp();                      // every lane has read the skip box
                         if (c0 + 64 < BN && n_base + 64 < N) issue_skip(m0, n0, c0 + 64);
                     }
-                    // the previous store must have read the output box
-                    if (lane == 0) bulk_wait_read();
+                    const uint32_t obox = has_r ? obox0 : obox0 + ((n_stored & 1u) << 11);
+                    // the last store from this box must have read it
+                    if (lane == 0) {
+                        if (has_r)
+                            bulk_wait_read();
+                        else
+                            bulk_wait_read_all_but_last();
+                    }
                     __syncwarp();
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
@@ -437,6 +451,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_layer_kernel(
                         tma_store_2d(&tmC, obox, n_base, int(row0));
                         bulk_commit();
                     }
+                    ++n_stored;
                 } else {
                     // fp32 rows of arbitrary stride: through a 32 x 32 block in
                     // shared memory (row r's float4 number q at q ^ (r & 7),

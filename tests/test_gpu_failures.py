@@ -121,3 +121,42 @@ def test_tensor_core_wait_expiry_is_reported_and_recovered():
     capi.dnnmg_sync(p.ctx, 10_000_000)                  # the error was cleared
     assert torch.equal(again, ref)
     p.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_misaligned_fields_are_refused_and_element_aligned_slices_read_alike(precision):
+    # [n][4] fields move 4 values at a time and X rows in 16-byte pieces: a
+    # view starting inside a row is refused with DNNMG_EINVAL before any
+    # launch.  Y and d need only element alignment (serving hands over row
+    # slices of one Y): the extension of a slice that starts one element into
+    # an array equals that of an aligned copy bit for bit.
+    m = I.cavity_mesh(4, jitter=0.1, seed=4)
+    p = PatchPath(m, 0.01, 0.01, 1.0, precision)
+    es = 8 if precision == "fp64" else 4
+    xc = torch.zeros((p.n_coarse + 1, 4), dtype=p.dtype, device="cuda")
+    F = torch.zeros((p.n_fine + 1, 4), dtype=p.dtype, device="cuda")
+    r = p.field(p.n_fine, 4)
+    X = torch.zeros((p.n_patches + 1) * p.sizes["n_in_padded"], dtype=p.x_dtype, device="cuda")
+    d = p.field(p.n_fine, 3)
+    n0 = p.launches()
+    refused = [
+        lambda: capi.dnnmg_prolongate(p.ctx, xc.data_ptr() + es, F),
+        lambda: capi.dnnmg_residual(p.ctx, xc.data_ptr() + es, F, r),
+        lambda: capi.dnnmg_residual(p.ctx, xc, F.data_ptr() + 2 * es, r),
+        lambda: capi.dnnmg_local_restrict(p.ctx, xc, r, X.data_ptr() + 8),
+        lambda: capi.dnnmg_rhs_restrict(p.ctx, xc, d, F.data_ptr() + es, None),
+        lambda: capi.dnnmg_extend(p.ctx, p.field(p.n_patches * 81 + 1, 1).data_ptr() + 2, d),
+    ]
+    for call in refused:
+        with pytest.raises(capi.DnnmgError) as e:
+            call()
+        assert e.value.status == -1
+    assert p.launches() == n0
+    rng = np.random.default_rng(7)
+    Y_big = torch.as_tensor(rng.standard_normal(p.n_patches * 81 + 1), device="cuda").to(p.dtype)
+    d_copy = p.extend(Y_big[1:].clone().reshape(p.n_patches, 81))
+    d_slice = p.field(p.n_fine, 3)
+    capi.dnnmg_extend(p.ctx, Y_big.data_ptr() + es, d_slice)
+    torch.cuda.synchronize()
+    assert torch.equal(d_slice, d_copy)
+    p.close()
