@@ -13,6 +13,7 @@
 // Every reduction is a gather over a CSR list sorted by patch index, so the
 // results are bitwise reproducible run to run (no floating-point atomics).
 #include <cstdio>
+#include <limits>
 #include <mutex>
 
 #include "internal.h"
@@ -120,9 +121,12 @@ __device__ __forceinline__ void from_moments(T (&c)[8]) {
 // Dv_c . g_k - p (g_k)_c = sum_e dN_k/dxi_e Fhat_ce / w with
 // Fhat_ce = w sum_d Jinv_ed (coef Dv_cd - p delta_cd), and the test
 // functions enter through the moments of the monomials.
+//
+// affine: the cell is a parallelepiped (its patch's corners are), so J is
+// constant; it is then formed at the first Gauss point only and reused.
 template <typename T, int MODE>
 __device__ __forceinline__ void element(const T* const (&xs)[8], const T* const (&us)[8], T (&R)[8][4],
-                                        T m, T th, T nu) {
+                                        T m, T th, T nu, bool affine) {
     T X[3][8], U[4][8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
@@ -140,6 +144,7 @@ __device__ __forceinline__ void element(const T* const (&xs)[8], const T* const 
     for (int c = 0; c < 4; ++c)
 #pragma unroll
         for (int S = 0; S < 8; ++S) M[c][S] = T(0);
+    T Ji[3][3], w;   // Jinv[e][d] = d xi_e / d x_d and the weight det J / 8 at the point
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
         const T x0 = (q & 1) ? T(0.5 + kGaussOff) : T(0.5 - kGaussOff);
@@ -152,34 +157,39 @@ __device__ __forceinline__ void element(const T* const (&xs)[8], const T* const 
         auto d0 = [&](const T (&c)[8]) { return c[1] + c[3] * x1 + c[5] * x2 + c[7] * (x1 * x2); };
         auto d1 = [&](const T (&c)[8]) { return c[2] + c[3] * x0 + c[6] * x2 + c[7] * (x0 * x2); };
         auto d2 = [&](const T (&c)[8]) { return c[4] + c[5] * x0 + c[6] * x1 + c[7] * (x0 * x1); };
-        T J[3][3], Dr[3][3], v[3];   // J[d][e] = dx_d/dxi_e, Dr[c][e] = dv_c/dxi_e
+        T Dr[3][3], v[3];   // Dr[c][e] = dv_c/dxi_e
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            J[d][0] = d0(X[d]);
-            J[d][1] = d1(X[d]);
-            J[d][2] = d2(X[d]);
             Dr[d][0] = d0(U[d]);
             Dr[d][1] = d1(U[d]);
             Dr[d][2] = d2(U[d]);
             v[d] = val(U[d]);
         }
         const T p = MODE == MODE_RESIDUAL ? val(U[3]) : T(0);
-        const T c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
-        const T c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
-        const T c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
-        const T det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
-        const T idet = T(1) / det;
-        T Ji[3][3];   // Jinv[e][d] = d xi_e / d x_d
-        Ji[0][0] = c00 * idet;
-        Ji[1][0] = c01 * idet;
-        Ji[2][0] = c02 * idet;
-        Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) * idet;
-        Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) * idet;
-        Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) * idet;
-        Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) * idet;
-        Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) * idet;
-        Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) * idet;
-        const T w = det * T(0.125);
+        if (q == 0 || !affine) {   // warp-uniform: the patches of a warp share the test's outcome but rarely
+            T J[3][3];             // J[d][e] = dx_d/dxi_e
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                J[d][0] = d0(X[d]);
+                J[d][1] = d1(X[d]);
+                J[d][2] = d2(X[d]);
+            }
+            const T c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+            const T c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+            const T c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+            const T det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+            const T idet = T(1) / det;
+            Ji[0][0] = c00 * idet;
+            Ji[1][0] = c01 * idet;
+            Ji[2][0] = c02 * idet;
+            Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) * idet;
+            Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) * idet;
+            Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) * idet;
+            Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) * idet;
+            Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) * idet;
+            Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) * idet;
+            w = det * T(0.125);
+        }
         T Dv[3][3];   // d v_c / d x_d
 #pragma unroll
         for (int c = 0; c < 3; ++c)
@@ -227,6 +237,26 @@ __device__ __forceinline__ void element(const T* const (&xs)[8], const T* const 
     }
 }
 
+// Corners cr[d][k] relative to corner 0 (cr[d][0] = 0) span a
+// parallelepiped when the bilinear and trilinear monomial coefficients of
+// the trilinear map vanish; "vanish" allows 16 rounding units of the edge
+// vectors, far below any tolerance the results are held to.  Then every
+// fine cell of the patch is a parallelepiped too, with a constant Jacobian.
+template <typename T>
+__device__ __forceinline__ bool is_parallelepiped(const T (&cr)[3][8]) {
+    T edge = T(0), bend = T(0);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const T c3 = cr[d][3] - cr[d][2] - cr[d][1];
+        const T c5 = cr[d][5] - cr[d][4] - cr[d][1];
+        const T c6 = cr[d][6] - cr[d][4] - cr[d][2];
+        const T c7 = cr[d][7] - cr[d][6] - cr[d][5] + cr[d][4] - c3;
+        edge = fmax(edge, fmax(fabs(cr[d][1]), fmax(fabs(cr[d][2]), fabs(cr[d][4]))));
+        bend = fmax(bend, fmax(fmax(fabs(c3), fabs(c5)), fmax(fabs(c6), fabs(c7))));
+    }
+    return bend <= T(16) * std::numeric_limits<T>::epsilon() * edge;
+}
+
 constexpr int kPatchThreads = 64;   // threads per block of the patch operator
 template <int J>
 constexpr int patches_per_block() { return kPatchThreads / PatchGeom<J>::NCELL; }   // 8 (J = 1), 1 (J = 2)
@@ -271,6 +301,7 @@ __global__ void __launch_bounds__(kPatchThreads, patch_min_blocks<T>()) patch_op
         s_cu[lp][t][3] = u.w;
     }
     __syncthreads();
+    bool affine = false;
     if (active) {
         // the 8 corners in registers once (coordinates relative to corner 0:
         // the element needs only differences, which stay exact in float)
@@ -282,6 +313,7 @@ __global__ void __launch_bounds__(kPatchThreads, patch_min_blocks<T>()) patch_op
 #pragma unroll
             for (int d = 0; d < 4; ++d) cv[k][d] = s_cu[lp][k][d];
         }
+        affine = is_parallelepiped(cr);
         for (int iota = t; iota < G::NPN; iota += TPP) {
             const int a = iota % G::NS, b = (iota / G::NS) % G::NS, c = iota / (G::NS * G::NS);
 #pragma unroll
@@ -312,7 +344,7 @@ __global__ void __launch_bounds__(kPatchThreads, patch_min_blocks<T>()) patch_op
         for (int k = 0; k < 8; ++k)
 #pragma unroll
             for (int c = 0; c < 4; ++c) R[k][c] = T(0);
-        element<T, MODE>(xs, us, R, m, th, nu);
+        element<T, MODE>(xs, us, R, m, th, nu, affine);
 #pragma unroll
         for (int k = 0; k < 8; ++k)
 #pragma unroll
