@@ -314,16 +314,34 @@ __global__ void __launch_bounds__(kPatchThreads, patch_min_blocks<T>()) patch_op
             for (int d = 0; d < 4; ++d) cv[k][d] = s_cu[lp][k][d];
         }
         affine = is_parallelepiped(cr);
-        for (int iota = t; iota < G::NPN; iota += TPP) {
+        // RHS: the correction d at this thread's nodes, every load issued
+        // before the first is used (node ids, then their values)
+        constexpr int NPT = (G::NPN + TPP - 1) / TPP;   // nodes per thread (4, 2)
+        T dn[NPT][3];
+        if (MODE == MODE_RHS) {
+            int64_t jn[NPT];
+#pragma unroll
+            for (int i = 0; i < NPT; ++i) {
+                const int iota = t + i * TPP;
+                jn[i] = iota < G::NPN ? int64_t(patch_map[G::NPN * P + iota]) : 0;
+            }
+#pragma unroll
+            for (int i = 0; i < NPT; ++i)
+#pragma unroll
+                for (int d = 0; d < 3; ++d) dn[i][d] = t + i * TPP < G::NPN ? dfine[3 * jn[i] + d] : T(0);
+        }
+#pragma unroll
+        for (int i = 0; i < NPT; ++i) {
+            const int iota = t + i * TPP;
+            if (iota >= G::NPN) break;
             const int a = iota % G::NS, b = (iota / G::NS) % G::NS, c = iota / (G::NS * G::NS);
 #pragma unroll
             for (int d = 0; d < 3; ++d) s_nx[lp][iota][d] = interp27<T, 1, G::NS>(cr[d], 0, a, b, c);
 #pragma unroll
             for (int d = 0; d < 4; ++d) s_nu[lp][iota][d] = interp27<T, 4, G::NS>(&cv[0][0], d, a, b, c);
             if (MODE == MODE_RHS) {   // corrected velocity x~ + d
-                const int64_t j = patch_map[G::NPN * P + iota];
 #pragma unroll
-                for (int d = 0; d < 3; ++d) s_nu[lp][iota][d] += dfine[3 * j + d];
+                for (int d = 0; d < 3; ++d) s_nu[lp][iota][d] += dn[i][d];
             }
         }
     }
