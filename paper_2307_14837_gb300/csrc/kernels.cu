@@ -98,6 +98,26 @@ __device__ __forceinline__ void to_monomials(T (&c)[8]) {
         for (int S = 0; S < 8; ++S)
             if (!(S & (1 << d))) c[S | (1 << d)] -= c[S];
 }
+// Monomial coefficients over a patch (its coarse cell, reference cube
+// [0,1]^3) to those over the patch's fine cell (ci, cj, ck) of NC per axis:
+// the substitution xi_d = (i_d + xi'_d) / NC, one axis at a time (c_S gains
+// i_d / NC times c_{S+d}, which then scales by 1 / NC).  Exact up to
+// rounding: the trilinear function restricted to a sub-box is trilinear.
+template <int NC, typename T>
+__device__ __forceinline__ void to_cell(T (&c)[8], int ci, int cj, int ck) {
+    const int id[3] = {ci, cj, ck};
+    constexpr double inv = 1.0 / NC;   // NC = 2 or 4: exact
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const T o = T(id[d]) * T(inv);
+#pragma unroll
+        for (int S = 0; S < 8; ++S)
+            if (!(S & (1 << d))) {
+                c[S] += o * c[S | (1 << d)];
+                c[S | (1 << d)] *= T(inv);
+            }
+    }
+}
 template <typename T>
 __device__ __forceinline__ void from_moments(T (&c)[8]) {
 #pragma unroll
@@ -107,9 +127,10 @@ __device__ __forceinline__ void from_moments(T (&c)[8]) {
             if (!(S & (1 << d))) c[S] -= c[S | (1 << d)];
 }
 
-// Element integrals of one fine cell with vertex coordinates x[k] and nodal
-// values u[k] (smem pointers with per-vertex strides 3 and 4), accumulated
-// into R[8][4], with the 2x2x2 Gauss rule:
+// Element integrals of one fine cell whose geometry X[d] and fields U[c]
+// (u, v, w, p) are given as monomial coefficients over the cell's own
+// reference cube, accumulated into R[8][4] (the cell's 8 vertices), with the
+// 2x2x2 Gauss rule:
 //   MODE_RESIDUAL: Galerkin part of A_h (Eq. (6) left-hand side):
 //     R_kc += w [ (m v_c + th conv_c) N_k + th nu Dv_c . g_k - p (g_k)_c ]
 //     R_k3 += w div(v) N_k
@@ -125,20 +146,8 @@ __device__ __forceinline__ void from_moments(T (&c)[8]) {
 // affine: the cell is a parallelepiped (its patch's corners are), so J is
 // constant; it is then formed at the first Gauss point only and reused.
 template <typename T, int MODE>
-__device__ __forceinline__ void element(const T* const (&xs)[8], const T* const (&us)[8], T (&R)[8][4],
-                                        T m, T th, T nu, bool affine) {
-    T X[3][8], U[4][8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-#pragma unroll
-        for (int d = 0; d < 3; ++d) X[d][k] = xs[k][d];
-#pragma unroll
-        for (int c = 0; c < 4; ++c) U[c][k] = (MODE == MODE_RESIDUAL || c < 3) ? us[k][c] : T(0);
-    }
-#pragma unroll
-    for (int d = 0; d < 3; ++d) to_monomials(X[d]);
-#pragma unroll
-    for (int c = 0; c < 4; ++c) to_monomials(U[c]);
+__device__ __forceinline__ void element(const T (&X)[3][8], const T (&U)[4][8], T (&R)[8][4], T m, T th, T nu,
+                                        bool affine) {
     T M[4][8];
 #pragma unroll
     for (int c = 0; c < 4; ++c)
@@ -262,7 +271,8 @@ template <int J>
 constexpr int patches_per_block() { return kPatchThreads / PatchGeom<J>::NCELL; }   // 8 (J = 1), 1 (J = 2)
 
 // One thread per fine cell; the NCELL consecutive threads of a patch share
-// its nodes in shared memory.
+// its corners (and, for the rhs, the correction at its nodes) in shared
+// memory, and each forms its own cell's monomial coefficients from them.
 // 128 registers (8 blocks of 64 threads per SM) for float: the element's
 // arithmetic is latency-bound at fewer warps
 template <typename T>
@@ -278,9 +288,9 @@ __global__ void __launch_bounds__(kPatchThreads, patch_min_blocks<T>()) patch_op
     constexpr int TPP = G::NCELL;                 // threads per patch
     __shared__ T s_cx[PPB][8][3];                 // corner coordinates
     __shared__ T s_cu[PPB][8][4];                 // corner values
-    __shared__ T s_nx[PPB][G::NPN][3];            // patch node coordinates
-    __shared__ T s_nu[PPB][G::NPN][5];            // patch node values (u, v, w, p; stride 5 spreads
-                                                  // the 8 nodes a cell reads over distinct banks)
+    // RHS: the correction d at the patch nodes, later the node sums of the
+    // partial rhs (stride 5 spreads the 8 nodes a cell reads over banks)
+    __shared__ T s_node[PPB][G::NPN][5];
     // per-cell contributions, one padded row of 8 x 4 per cell: the cells'
     // threads store with a stride of 33 words (no bank conflicts)
     __shared__ T s_R[PPB][G::NCELL][33];
@@ -300,69 +310,73 @@ __global__ void __launch_bounds__(kPatchThreads, patch_min_blocks<T>()) patch_op
         s_cu[lp][t][2] = u.z;
         s_cu[lp][t][3] = u.w;
     }
-    __syncthreads();
-    bool affine = false;
-    if (active) {
-        // the 8 corners in registers once (coordinates relative to corner 0:
-        // the element needs only differences, which stay exact in float)
-        T cr[3][8], cv[8][4];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-#pragma unroll
-            for (int d = 0; d < 3; ++d) cr[d][k] = s_cx[lp][k][d] - s_cx[lp][0][d];
-#pragma unroll
-            for (int d = 0; d < 4; ++d) cv[k][d] = s_cu[lp][k][d];
-        }
-        affine = is_parallelepiped(cr);
-        // RHS: the correction d at this thread's nodes, every load issued
-        // before the first is used (node ids, then their values)
+    if (MODE == MODE_RHS && active) {
+        // the correction at this thread's nodes, every load issued before
+        // the first is used (node ids, then their values)
         constexpr int NPT = (G::NPN + TPP - 1) / TPP;   // nodes per thread (4, 2)
+        int64_t jn[NPT];
         T dn[NPT][3];
-        if (MODE == MODE_RHS) {
-            int64_t jn[NPT];
-#pragma unroll
-            for (int i = 0; i < NPT; ++i) {
-                const int iota = t + i * TPP;
-                jn[i] = iota < G::NPN ? int64_t(patch_map[G::NPN * P + iota]) : 0;
-            }
-#pragma unroll
-            for (int i = 0; i < NPT; ++i)
-#pragma unroll
-                for (int d = 0; d < 3; ++d) dn[i][d] = t + i * TPP < G::NPN ? dfine[3 * jn[i] + d] : T(0);
-        }
 #pragma unroll
         for (int i = 0; i < NPT; ++i) {
             const int iota = t + i * TPP;
-            if (iota >= G::NPN) break;
-            const int a = iota % G::NS, b = (iota / G::NS) % G::NS, c = iota / (G::NS * G::NS);
-#pragma unroll
-            for (int d = 0; d < 3; ++d) s_nx[lp][iota][d] = interp27<T, 1, G::NS>(cr[d], 0, a, b, c);
-#pragma unroll
-            for (int d = 0; d < 4; ++d) s_nu[lp][iota][d] = interp27<T, 4, G::NS>(&cv[0][0], d, a, b, c);
-            if (MODE == MODE_RHS) {   // corrected velocity x~ + d
-#pragma unroll
-                for (int d = 0; d < 3; ++d) s_nu[lp][iota][d] += dn[i][d];
-            }
+            jn[i] = iota < G::NPN ? int64_t(patch_map[G::NPN * P + iota]) : 0;
         }
+#pragma unroll
+        for (int i = 0; i < NPT; ++i)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) dn[i][d] = t + i * TPP < G::NPN ? dfine[3 * jn[i] + d] : T(0);
+#pragma unroll
+        for (int i = 0; i < NPT; ++i)
+            if (t + i * TPP < G::NPN)
+#pragma unroll
+                for (int d = 0; d < 3; ++d) s_node[lp][t + i * TPP][d] = dn[i][d];
     }
     __syncthreads();
     if (active) {
-        const int ci = t % G::NC, cj = (t / G::NC) % G::NC, ck = t / (G::NC * G::NC);
-        const T* xs[8];
-        const T* us[8];
+        // the coarse cell's corners (coordinates relative to corner 0: the
+        // element needs only differences) as monomial coefficients over the
+        // patch, then over this thread's fine cell
+        T X[3][8], U[4][8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-            const int node =
-                (ci + (k & 1)) + G::NS * (cj + ((k >> 1) & 1)) + G::NS * G::NS * (ck + ((k >> 2) & 1));
-            xs[k] = &s_nx[lp][node][0];
-            us[k] = &s_nu[lp][node][0];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) X[d][k] = s_cx[lp][k][d] - s_cx[lp][0][d];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) U[c][k] = s_cu[lp][k][c];
+        }
+        const bool affine = is_parallelepiped(X);
+        const int ci = t % G::NC, cj = (t / G::NC) % G::NC, ck = t / (G::NC * G::NC);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            to_monomials(X[d]);
+            to_cell<G::NC>(X[d], ci, cj, ck);
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            to_monomials(U[c]);
+            to_cell<G::NC>(U[c], ci, cj, ck);
+        }
+        if (MODE == MODE_RHS) {   // corrected velocity x~ + d, d nodal on the fine nodes
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                T dc[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const int node =
+                        (ci + (k & 1)) + G::NS * (cj + ((k >> 1) & 1)) + G::NS * G::NS * (ck + ((k >> 2) & 1));
+                    dc[k] = s_node[lp][node][c];
+                }
+                to_monomials(dc);
+#pragma unroll
+                for (int S = 0; S < 8; ++S) U[c][S] += dc[S];
+            }
         }
         T R[8][4];
 #pragma unroll
         for (int k = 0; k < 8; ++k)
 #pragma unroll
             for (int c = 0; c < 4; ++c) R[k][c] = T(0);
-        element<T, MODE>(xs, us, R, m, th, nu, affine);
+        element<T, MODE>(X, U, R, m, th, nu, affine);
 #pragma unroll
         for (int k = 0; k < 8; ++k)
 #pragma unroll
@@ -394,7 +408,7 @@ __global__ void __launch_bounds__(kPatchThreads, patch_min_blocks<T>()) patch_op
         if (MODE == MODE_RHS) {
             // keep the node sums for the restriction below
 #pragma unroll
-            for (int d = 0; d < 4; ++d) s_nu[lp][iota][d] = acc[d];
+            for (int d = 0; d < 4; ++d) s_node[lp][iota][d] = acc[d];
         }
     }
     if (MODE == MODE_RHS) {
@@ -411,7 +425,7 @@ __global__ void __launch_bounds__(kPatchThreads, patch_min_blocks<T>()) patch_op
                           corner_weight<T, G::NS>(c, kz);
             if (wgt != T(0)) {
 #pragma unroll
-                for (int d = 0; d < 3; ++d) acc[d] += wgt * s_nu[lp][iota][d];
+                for (int d = 0; d < 3; ++d) acc[d] += wgt * s_node[lp][iota][d];
             }
         }
         st4(partial_c + (8 * P + k) * 4, V4<T>{acc[0], acc[1], acc[2], T(0)});
