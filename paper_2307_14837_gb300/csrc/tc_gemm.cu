@@ -77,20 +77,6 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
-// AND of `ok` over the epilogue threads (named barrier 1); also a barrier.
-__device__ __forceinline__ bool epilogue_all(bool ok) {
-    uint32_t r;
-    asm volatile(
-        "{\n\t.reg .pred p, q;\n\t"
-        "setp.ne.u32 q, %1, 0;\n\t"
-        "bar.red.and.pred p, 1, 256, q;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(r)
-        : "r"(uint32_t(ok))
-        : "memory");
-    return r != 0;
-}
-
 // Bounded wait for the phase with the given parity; false on expiry (the
 // error code is recorded once).
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int code) {
@@ -358,11 +344,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_layer_kernel(
             const int64_t row0 = int64_t(m0) + quarter * 32;
             const bool rows_live = row0 < M;                 // warp-uniform
             if (has_r && rows_live && n0 + half * 32 < N) issue_skip(m0, n0, half * 32);   // in flight during the wait
-            // the wait result is voted on so that all epilogue warps leave
-            // the loop together (the named barrier must never be left
-            // waiting for a warp that has gone)
-            const bool ok = mbar_wait(tfull_bar(buf), use & 1u, kErrTmemFull);
-            if (!epilogue_all(ok)) break;
+            // the wait result is made warp-uniform (the TMEM loads below are
+            // warp-collective); a warp whose wait expired leaves on its own,
+            // and the others' waits for it are bounded too
+            const bool ok = __all_sync(0xffffffffu, mbar_wait(tfull_bar(buf), use & 1u, kErrTmemFull));
+            if (!ok) break;
             fence_after();
 #pragma unroll 1
             for (int c0 = half * 32; c0 < BN; c0 += 64) {
