@@ -15,6 +15,7 @@
 #include <cstdio>
 #include <limits>
 #include <mutex>
+#include <type_traits>
 
 #include "internal.h"
 
@@ -904,12 +905,106 @@ cudaError_t launch_rhs_restrict(const DeviceMesh& dm, OpParams p, const T* xc, c
     return cudaGetLastError();
 }
 
+// FP32 form of the layer for 16-byte aligned operands with row strides that
+// are multiples of 4: 128 x 128 tiles of C, 256 threads of 8 x 8 outputs
+// (rows 4 ty .. 4 ty + 3 and 64 + 4 ty .. 64 + 4 ty + 3, columns likewise
+// with tx), K in steps of 8 through two shared-memory buffers (the next
+// step's operands are loaded into registers while the current one
+// multiplies).  Every output sums over k in increasing order, as
+// layer_simt_kernel does.
+constexpr int kSgTile = 128, kSgK = 8;
+__global__ void __launch_bounds__(256, 2) layer_sgemm_kernel(
+    const float* __restrict__ A, int64_t lda, const float* __restrict__ W, int64_t ldw,
+    const float* __restrict__ scale, const float* __restrict__ shift, float* __restrict__ C, int64_t ldc,
+    const float* __restrict__ R, int64_t ldr, int64_t M, int N, int K, int relu) {
+    __shared__ alignas(16) float sA[2][kSgK][kSgTile];
+    __shared__ alignas(16) float sW[2][kSgK][kSgTile];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int64_t m0 = int64_t(blockIdx.x) * kSgTile;
+    const int n0 = blockIdx.y * kSgTile;
+    // this thread's share of a step's operands: row lr, columns 4 lq .. 4 lq + 3
+    const int lr = threadIdx.x >> 1, lq = threadIdx.x & 1;
+    const bool a_ok = m0 + lr < M, w_ok = n0 + lr < N;
+    const float* a_src = A + (a_ok ? (m0 + lr) * lda : 0) + 4 * lq;
+    const float* w_src = W + (w_ok ? int64_t(n0 + lr) * ldw : 0) + 4 * lq;
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 ra = a_ok ? __ldg(reinterpret_cast<const float4*>(a_src)) : zero4;
+    float4 rw = w_ok ? __ldg(reinterpret_cast<const float4*>(w_src)) : zero4;
+    auto stage = [&](int buf) {
+        sA[buf][4 * lq + 0][lr] = ra.x;
+        sA[buf][4 * lq + 1][lr] = ra.y;
+        sA[buf][4 * lq + 2][lr] = ra.z;
+        sA[buf][4 * lq + 3][lr] = ra.w;
+        sW[buf][4 * lq + 0][lr] = rw.x;
+        sW[buf][4 * lq + 1][lr] = rw.y;
+        sW[buf][4 * lq + 2][lr] = rw.z;
+        sW[buf][4 * lq + 3][lr] = rw.w;
+    };
+    stage(0);
+    __syncthreads();
+    float acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+    const int steps = K / kSgK;
+    for (int st = 0; st < steps; ++st) {
+        const int buf = st & 1;
+        if (st + 1 < steps) {   // next step's operands in flight during this one
+            const int k1 = (st + 1) * kSgK;
+            ra = a_ok ? __ldg(reinterpret_cast<const float4*>(a_src + k1)) : zero4;
+            rw = w_ok ? __ldg(reinterpret_cast<const float4*>(w_src + k1)) : zero4;
+        }
+#pragma unroll
+        for (int kk = 0; kk < kSgK; ++kk) {
+            const float4 a0 = *reinterpret_cast<const float4*>(&sA[buf][kk][4 * ty]);
+            const float4 a1 = *reinterpret_cast<const float4*>(&sA[buf][kk][64 + 4 * ty]);
+            const float4 b0 = *reinterpret_cast<const float4*>(&sW[buf][kk][4 * tx]);
+            const float4 b1 = *reinterpret_cast<const float4*>(&sW[buf][kk][64 + 4 * tx]);
+            const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] += a[i] * b[j];
+        }
+        if (st + 1 < steps) {
+            stage(buf ^ 1);   // the other buffer was last read before the previous barrier
+            __syncthreads();
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int64_t gm = m0 + (i < 4 ? 4 * ty + i : 64 + 4 * ty + i - 4);
+        if (gm >= M) continue;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int gn = n0 + (j < 4 ? 4 * tx + j : 64 + 4 * tx + j - 4);
+            if (gn >= N) continue;
+            float z = scale[gn] * acc[i][j] + shift[gn];
+            if (relu) z = z > 0.f ? z : 0.f;
+            if (R) z += R[gm * ldr + gn];
+            C[gm * ldc + gn] = z;
+        }
+    }
+}
+
 template <typename TA, typename TW, typename TC, typename TS>
 cudaError_t launch_layer_simt(const TA* A, int64_t lda, const TW* W, int64_t ldw, const TS* scale,
                               const TS* shift, TC* C, int64_t ldc, const TA* R, int64_t ldr, int64_t M,
                               int N, int K, bool relu, cudaStream_t s) {
     if (K % 16) return cudaErrorInvalidValue;
     if (M == 0) return cudaSuccess;
+    if constexpr (std::is_same<TA, float>::value && std::is_same<TW, float>::value &&
+                  std::is_same<TC, float>::value && std::is_same<TS, float>::value) {
+        if (lda % 4 == 0 && ldw % 4 == 0 && (reinterpret_cast<uintptr_t>(A) & 15) == 0 &&
+            (reinterpret_cast<uintptr_t>(W) & 15) == 0) {
+            dim3 grid(unsigned((M + kSgTile - 1) / kSgTile), unsigned((N + kSgTile - 1) / kSgTile));
+            layer_sgemm_kernel<<<grid, 256, 0, s>>>(A, lda, W, ldw, scale, shift, C, ldc, R, ldr, M, N, K,
+                                                    relu ? 1 : 0);
+            return cudaGetLastError();
+        }
+    }
     using TACC = typename AccOf<TS>::type;
     dim3 grid(unsigned((M + 63) / 64), unsigned((N + 63) / 64));
     layer_simt_kernel<TA, TW, TC, TS, TACC><<<grid, 256, 0, s>>>(A, lda, W, ldw, scale, shift, C, ldc, R, ldr,
