@@ -45,6 +45,20 @@ __device__ __forceinline__ void st4(T* p, V4<T> v) {
     *reinterpret_cast<V4<T>*>(p) = v;
 }
 
+// Three consecutive values p[0..2] of an array that is only element-aligned,
+// as one aligned pair and one scalar: the pair starts at p when p is aligned
+// to two elements, else at p + 1.
+template <typename T>
+__device__ __forceinline__ void ld3(const T* p, T (&o)[3]) {
+    using P2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
+    const bool even = (reinterpret_cast<uintptr_t>(p) & (2 * sizeof(T) - 1)) == 0;
+    const P2 q = *reinterpret_cast<const P2*>(p + (even ? 0 : 1));
+    const T single = p[even ? 2 : 0];
+    o[0] = even ? T(q.x) : single;
+    o[1] = even ? T(q.y) : T(q.x);
+    o[2] = even ? single : T(q.y);
+}
+
 // Patches of J levels (Sec. 5.2): a coarse cell refined J times, NC = 2^J
 // cells and NS = NC + 1 nodes per axis; node iota = a + NS b + NS^2 c.
 template <int J>
@@ -648,11 +662,25 @@ __global__ void __launch_bounds__(256) local_restrict_kernel(
     for (int p = 0; p < PPW; ++p) {
         const int64_t P = P0 + p;
         if (P >= nc) break;   // warp-uniform
-        T corner[8][4];
+        // J = 1: x~ at this lane's node as the weighted sum of the corners,
+        // fetched one corner at a time (J = 2: all corners held, 4 nodes per lane)
+        T xt[4] = {T(0), T(0), T(0), T(0)};
+        T corner[J == 1 ? 1 : 8][4];
+        if constexpr (J == 1) {
+            const int a = lane % 3, b = (lane / 3) % 3, c = lane / 9;
 #pragma unroll
-        for (int k = 0; k < 8; ++k)
+            for (int k = 0; k < 8; ++k) {
+                const T wk = corner_weight<T, 3>(a, k & 1) * corner_weight<T, 3>(b, (k >> 1) & 1) *
+                             corner_weight<T, 3>(c, (k >> 2) & 1);
 #pragma unroll
-            for (int d = 0; d < 4; ++d) corner[k][d] = __shfl_sync(0xffffffffu, cu[p][d], k);
+                for (int d = 0; d < 4; ++d) xt[d] += wk * __shfl_sync(0xffffffffu, cu[p][d], k);
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+#pragma unroll
+                for (int d = 0; d < 4; ++d) corner[k][d] = __shfl_sync(0xffffffffu, cu[p][d], k);
+        }
         // geometry features 4 lane .. 4 lane + 3 (zero past n_geo)
         T e[4];
 #pragma unroll
@@ -665,11 +693,15 @@ __global__ void __launch_bounds__(256) local_restrict_kernel(
         for (int i = 0; i < NPL; ++i) {
             const int iota = lane + 32 * i;
             if (iota >= G::NPN) continue;
-            const int a = iota % G::NS, b = (iota / G::NS) % G::NS, c = iota / (G::NS * G::NS);
-            store4<TX>(row + 4 * iota, interp27<T, 4, G::NS>(&corner[0][0], 0, a, b, c),
-                       interp27<T, 4, G::NS>(&corner[0][0], 1, a, b, c),
-                       interp27<T, 4, G::NS>(&corner[0][0], 2, a, b, c),
-                       interp27<T, 4, G::NS>(&corner[0][0], 3, a, b, c));
+            if constexpr (J == 1) {
+                store4<TX>(row + 4 * iota, xt[0], xt[1], xt[2], xt[3]);
+            } else {
+                const int a = iota % G::NS, b = (iota / G::NS) % G::NS, c = iota / (G::NS * G::NS);
+                store4<TX>(row + 4 * iota, interp27<T, 4, G::NS>(&corner[0][0], 0, a, b, c),
+                           interp27<T, 4, G::NS>(&corner[0][0], 1, a, b, c),
+                           interp27<T, 4, G::NS>(&corner[0][0], 2, a, b, c),
+                           interp27<T, 4, G::NS>(&corner[0][0], 3, a, b, c));
+            }
             store4<TX>(row + 4 * G::NPN + 4 * iota, rv[p][i].x, rv[p][i].y, rv[p][i].z, rv[p][i].w);
         }
         constexpr int GEO0 = 8 * G::NPN;              // first geometry column (216, 1000)
@@ -690,8 +722,8 @@ __global__ void __launch_bounds__(256) extend_kernel(
     T acc[3] = {T(0), T(0), T(0)};
     const int32_t e0 = ptr[j], e1 = ptr[j + 1];
     for (int32_t e = e0; e < e1; ++e) {
-        const int32_t pe = idx[e];
-        const T* y = Y + 3 * int64_t(pe);   // Y[P][3 iota]: rows of 3 x nodes per patch
+        T y[3];
+        ld3(Y + 3 * int64_t(idx[e]), y);   // Y[P][3 iota]: rows of 3 x nodes per patch
         acc[0] += y[0];
         acc[1] += y[1];
         acc[2] += y[2];
