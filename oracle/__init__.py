@@ -19,6 +19,8 @@ Modules
   mlp       the patch network with skips and folded normalisation (Sec. 4)
   dnnmg     local restriction Q, extension L, one DNN-MG step   (Alg. 1)
   solve     Newton solve of A_h(x) = F on one level      (Sec. 3.4)
+  q2        the paper's Q2/Q2 element with one-level local projection,
+            its levels and the nested prolongation        (Sec. 3.2, Eqs. (5), (8))
 
 Parity status of each function is stated in its docstring ("pinned by ..."),
 with the pins in tests/test_oracle_*.py.

@@ -1,0 +1,192 @@
+"""Pins of the Q2/Q2 oracle (the paper's own element, Sec. 3.2) against
+closed forms, exactness properties and manufactured-solution rates."""
+import numpy as np
+import pytest
+
+from oracle import mesh, q2, solve
+from oracle.fem import q1_basis
+from paper_2307_14837_gb300 import inputs as I
+
+import mms
+
+
+def _levels(n, jitter=0.0, seed=0):
+    m = I.cavity_mesh(n, grouped=False, jitter=jitter, seed=seed)
+    h = mesh.Hierarchy(m["xyz"], m["cells"], m["vertex_bc"])
+    return m, h, q2.coarse_level(h)
+
+
+PRM0 = dict(m=0.0, theta=1.0, nu=0.0, alpha0=0.02, delta0=0.1, lps=False)
+
+
+def test_basis_lagrange_property_and_triquadratic_exactness():
+    nodes = [(a / 2.0, b / 2.0, c / 2.0) for c in range(3) for b in range(3) for a in range(3)]
+    V = np.array([q2.q2_basis(x)[0] for x in nodes])
+    assert np.allclose(V, np.eye(27), rtol=0, atol=1e-15)
+    rng = np.random.default_rng(0)
+    C = rng.standard_normal((3, 3, 3))            # a random triquadratic sum C_abc x^a y^b z^c
+
+    def f(x):
+        return sum(C[a, b, c] * x[0] ** a * x[1] ** b * x[2] ** c
+                   for a in range(3) for b in range(3) for c in range(3))
+    fn = np.array([f(x) for x in nodes])
+    for x in rng.random((10, 3)):
+        phi, dphi = q2.q2_basis(x)
+        assert abs(phi @ fn - f(x)) < 1e-13
+        eps = 1e-6                                # derivatives against central differences
+        for d in range(3):
+            e = np.zeros(3)
+            e[d] = eps
+            fd = (q2.q2_basis(x + e)[0] - q2.q2_basis(x - e)[0]) / (2 * eps)
+            assert np.allclose(dphi[:, d], fd, rtol=0, atol=1e-8)
+
+
+def test_mass_rows_sum_to_volume_and_one_dimensional_weights():
+    _, _, lev = _levels(3, jitter=0.2, seed=4)
+    assert abs(lev.lumped_mass().sum() - 1.0) < 1e-13     # interior jitter keeps the unit cube
+    # on one unit cell the integrals of the basis are products of (1/6, 2/3, 1/6)
+    X8 = np.array([[(k & 1), (k >> 1) & 1, (k >> 2) & 1] for k in range(8)], dtype=float)
+    cell = q2.LevelQ2(q2_nodes_of(X8), np.arange(27)[None, :], np.zeros(27, dtype=int))
+    w1 = np.array([1 / 6, 2 / 3, 1 / 6])
+    ref = np.array([w1[i % 3] * w1[(i // 3) % 3] * w1[i // 9] for i in range(27)])
+    assert np.allclose(cell.lumped_mass(), ref, rtol=0, atol=1e-15)
+
+
+def q2_nodes_of(X8):
+    """Trilinear images of the 27 reference nodes of one cell."""
+    return np.array([q1_basis((a / 2.0, b / 2.0, c / 2.0))[0] @ X8
+                     for c in range(3) for b in range(3) for a in range(3)])
+
+
+def _sheared(n):
+    m, h, _ = _levels(n)
+    A = np.array([[1.0, 0.3, 0.0], [0.0, 1.2, 0.1], [0.2, 0.0, 0.8]])
+    h2 = mesh.Hierarchy(m["xyz"] @ A.T, m["cells"], m["vertex_bc"])
+    return A, q2.coarse_level(h2)
+
+
+def test_divergence_and_viscous_rows_exact_for_quadratic_fields():
+    # parallelepiped cells: every term below is a polynomial the 3-point rule
+    # integrates exactly.  v quadratic with div v = 2 x + 3 and Lap v = (2, 0, 4)
+    A, lev = _sheared(2)
+    x, y, z = lev.xyz.T
+    v = np.stack([x ** 2 + 3 * x, y * z, 2 * z ** 2 + x * y], axis=1)
+    U = np.zeros((lev.n, 4))
+    U[:, 0:3] = v
+    R = lev.operator(U, PRM0)
+    mass = lev.lumped_mass()
+    # continuity rows: (div v, phi_i); their sum is the integral of div v
+    vol = abs(np.linalg.det(A))
+    cen = A @ np.array([0.5, 0.5, 0.5])
+    assert abs(R[:, 3].sum() - vol * (2 * cen[0] + 3 + 5 * cen[2])) < 1e-12
+    # viscous rows at interior nodes: nu (grad v_c, grad phi_i) = -nu (Lap v_c, phi_i)
+    Rv = lev.operator(U, dict(PRM0, nu=1.0)) - R
+    interior = lev.bc == 0
+    lap = np.array([2.0, 0.0, 4.0])
+    assert np.allclose(Rv[interior, 0:3], -lap[None, :] * mass[interior, None], rtol=0, atol=1e-13)
+
+
+def test_stabilisation_vanishes_on_q1_fields_only():
+    m, h, lev = _levels(3)                          # axis-aligned boxes
+    x, y, z = lev.xyz.T
+    U = np.stack([1 + x * y * z, x - 2 * y * z, 3 * x * y + z, 0.5 * x * z - y], axis=1)   # trilinear
+    prm = dict(m=10.0, theta=0.5, nu=0.01, alpha0=0.02, delta0=0.1)
+    R_lps = lev.operator(U, prm) - lev.operator(U, dict(prm, lps=False))
+    assert np.abs(R_lps).max() <= 1e-14 * np.abs(lev.operator(U, prm)).max()
+    U2 = U.copy()
+    U2[:, 0] += x ** 2
+    U2[:, 3] += y ** 2
+    R2 = lev.operator(U2, prm) - lev.operator(U2, dict(prm, lps=False))
+    assert np.abs(R2[:, 0]).max() > 1e-6 and np.abs(R2[:, 3]).max() > 1e-6
+
+
+def test_prolongation_is_exact_for_coarse_q2_fields():
+    # nested trilinear geometry: a coarse Q2 function evaluated through the
+    # fine cells is the same function, on a jittered (non-affine) mesh
+    m = I.cavity_mesh(2, grouped=False, jitter=0.2, seed=5)
+    h = mesh.Hierarchy(m["xyz"], m["cells"], m["vertex_bc"])
+    h2 = mesh.Hierarchy2(m["xyz"], m["cells"], m["vertex_bc"])
+    rng = np.random.default_rng(1)
+    xc = rng.standard_normal((h.n_fine, 4))
+    xf = q2.prolongate(h, h2, xc)
+    coarse, fine = q2.coarse_level(h), q2.fine_level(h2)
+    for t in range(8):                              # fine cell t of every coarse cell
+        i, j, k = t & 1, (t >> 1) & 1, (t >> 2) & 1
+        for xi in rng.random((3, 3)):
+            vf, pf = fine.evaluate(xf, xi)
+            vf, pf = vf[t::8], pf[t::8]
+            vc, pc = coarse.evaluate(xc, ((i + xi[0]) / 2, (j + xi[1]) / 2, (k + xi[2]) / 2))
+            assert np.allclose(pf, pc, rtol=0, atol=1e-14)
+            assert np.allclose(vf, vc, rtol=0, atol=1e-12)
+    # the matrix form agrees and its transpose is the restriction
+    Pm = q2.prolongation_matrix(h, h2)
+    assert np.allclose(Pm @ xc, xf, rtol=0, atol=1e-13)
+    yf = rng.standard_normal(h2.n_fine)
+    assert abs(yf @ (Pm @ xc[:, 0]) - (Pm.T @ yf) @ xc[:, 0]) < 1e-10
+
+
+def test_complex_step_jacobian_matches_finite_differences():
+    _, _, lev = _levels(2, jitter=0.15, seed=2)
+    rng = np.random.default_rng(3)
+    x = 0.3 * rng.standard_normal((lev.n, 4))
+    prm = dict(m=5.0, theta=0.5, nu=0.05, alpha0=0.02, delta0=0.1)
+    J = lev.jacobian(x, prm).toarray()
+    frozen = dict(prm, vref=x)                      # parameters frozen, as in the Jacobian
+    eps = 1e-6
+    Jfd = np.empty_like(J)
+    for k in range(4 * lev.n):
+        dx = np.zeros(4 * lev.n)
+        dx[k] = eps
+        Jfd[:, k] = (lev.operator(x + dx.reshape(-1, 4), frozen).ravel()
+                     - lev.operator(x - dx.reshape(-1, 4), frozen).ravel()) / (2 * eps)
+    assert np.abs(J - Jfd).max() <= 1e-7 * np.abs(J).max()
+
+
+def _errors(lev, x):
+    """Velocity L2, H1-seminorm and pressure L2 errors against mms.exact
+    (3x3x3 Gauss on every cell)."""
+    det, G = q2.cell_geometry(lev.X8)
+    U = x[lev.cells]
+    ev = eg = ep = 0.0
+    for q in range(27):
+        phi = q2.PHI2[q]
+        xq = np.einsum("k,nkd->nd", q1_basis(q2._QP[q])[0], lev.X8)
+        v, p = mms.exact(xq)
+        vh = np.einsum("i,nic->nc", phi, U[:, :, 0:3])
+        ph = np.einsum("i,ni->n", phi, U[:, :, 3])
+        Gh = np.einsum("nic,nid->ncd", U[:, :, 0:3], G[:, q])
+        w = q2.QW[q] * det[:, q]
+        ev += np.sum(w * np.sum((vh - v) ** 2, axis=1))
+        eg += np.sum(w * np.sum((Gh - mms.grad_v(xq)) ** 2, axis=(1, 2)))
+        ep += np.sum(w * (ph - p) ** 2)
+    return np.sqrt(ev), np.sqrt(eg), np.sqrt(ep)
+
+
+def test_manufactured_solution_convergence():
+    # viscous-dominated (nu = 1): alpha_T and delta_T of Eq. (8) scale like
+    # h^2 / nu on these meshes, so the stabilisation is consistent to the
+    # element's order and the rates are the Q2 ones; the errors stay within
+    # 10% of those of the nodal Q2 interpolant of the exact solution.  (At
+    # nu = 0.1 with m = 10 the parameters stay near alpha0 / m over n = 2..8
+    # and the measured rates are 2.7 / 1.7 / 2.5: the stabilisation's own
+    # consistency error, which decays like h while alpha_T does not shrink.)
+    nu = 1.0
+    errs, interp = [], []
+    for n in (2, 4):
+        _, _, lev = _levels(n)
+        prm = dict(m=1.0, theta=0.5, nu=nu, alpha0=0.02, delta0=0.1)
+        v, p = mms.exact(lev.xyz)
+        f = mms.force(lev.xyz, nu)
+        F = lev.rhs(v, prm, f_new=f, f_old=f)
+        x0 = np.zeros((lev.n, 4))
+        x0[lev.dirichlet, 0:3] = v[lev.dirichlet]
+        x, info = solve.newton(lev, x0, F, prm)
+        assert info["residuals"][-1] < 1e-10
+        errs.append(_errors(lev, x))
+        interp.append(_errors(lev, np.concatenate([v, p[:, None]], axis=1)))
+    rates = np.log2(np.array(errs[0]) / np.array(errs[1]))
+    assert rates[0] > 2.9, rates      # velocity L2 ~ h^3   (measured 3.07)
+    assert rates[1] > 1.9, rates      # velocity H1 ~ h^2   (2.04)
+    assert rates[2] > 1.9, rates      # pressure L2 ~ h^2   (2.81)
+    for e, ei in zip(errs[1][:2], interp[1][:2]):
+        assert e <= 1.1 * ei, (errs[1], interp[1])
