@@ -303,3 +303,73 @@ def prolongation_matrix(hier, hier2):
                 cols.append(hier.patch_map[P, i])
                 vals.append(phi[i])
     return sp.csr_matrix((vals, (rows, cols)), shape=(nf, ncq))
+
+
+# ---- DNN-MG with Q2 elements (Alg. 1 on the paper's element) ----------------
+#
+# The coarse level is Q2 on the mesh (nodes: the mesh refined once, hier);
+# the fine level L+1 is Q2 on the refined mesh (nodes: the mesh refined
+# twice, hier2).  A patch is a coarse cell with its 125 fine Q2 nodes, the
+# node set and order of a two-level patch, so the local restriction Q and
+# the extension L are those of oracle.dnnmg applied to hier2.
+
+def restrict(hier, hier2, b_fine):
+    """R b = P^T b, then zero velocity rows at coarse Dirichlet nodes."""
+    P = prolongation_matrix(hier, hier2)
+    out = np.asarray(P.T @ b_fine)
+    dirc = (hier.bc_f == 1) | (hier.bc_f == 2)
+    out[dirc, 0:3] = 0.0
+    return out
+
+
+def hot_path_step(hier, hier2, net, x_coarse, F, prm, fine=None, features=12):
+    """The patch-correction steps of Alg. 1 with Q2 elements: x~ = P x^L,
+    r = F - A_{L+1}(x~), X = Q(x~) | Q(r) | geometry, Y = N(X),
+    d = L(Y), b = Rhs(v~ + d), b^L = R b.  Every intermediate as a dict."""
+    from . import dnnmg, mlp
+    lev = fine if fine is not None else fine_level(hier2)
+    x_f = prolongate(hier, hier2, x_coarse)
+    r = lev.residual(x_f, F, prm)
+    X = dnnmg.gather(hier2, x_f, r, features)
+    Ws, ss, ts, skip = net
+    Y = mlp.forward(X, Ws, ss, ts, skip=skip)
+    d = dnnmg.extend(hier2, Y)
+    b_f = lev.rhs(x_f[:, 0:3] + d, prm)
+    return dict(x_fine=x_f, r=r, X=X, Y=Y, d=d, b_fine=b_f, b_coarse=restrict(hier, hier2, b_f))
+
+
+def run(hier, hier2, net, x0, n_steps, prm, bc_values, newton_tol=1e-13, features=12):
+    """DNN-MG time stepping with Q2 elements: Newton on the coarse Q2 level,
+    then the patch correction on the fine one.  x0 [n_coarse_q2, 4];
+    bc_values(t) -> [n_coarse_q2, 3].  Returns the coarse states."""
+    from .solve import newton
+    coarse, fine = coarse_level(hier), fine_level(hier2)
+    x = np.array(x0, dtype=np.float64)
+    F = fine.rhs(prolongate(hier, hier2, x[:, 0:3]), prm)
+    b = restrict(hier, hier2, F)
+    states = []
+    for n in range(1, n_steps + 1):
+        t = n / prm["m"] if prm["m"] > 0 else float(n)
+        xi = x.copy()
+        xi[coarse.dirichlet, 0:3] = bc_values(t)[coarse.dirichlet]
+        x, _ = newton(coarse, xi, b, prm, tol=newton_tol)
+        states.append(x.copy())
+        last = hot_path_step(hier, hier2, net, x, F, prm, fine=fine, features=features)
+        F, b = last["b_fine"], last["b_coarse"]
+    return states
+
+
+def run_plain(hier, x0, n_steps, prm, bc_values, newton_tol=1e-13):
+    """The plain Q2 scheme on the coarse level: rhs b_L(v_{n-1}) each step."""
+    from .solve import newton
+    coarse = coarse_level(hier)
+    x = np.array(x0, dtype=np.float64)
+    states = []
+    for n in range(1, n_steps + 1):
+        t = n / prm["m"] if prm["m"] > 0 else float(n)
+        b = coarse.rhs(x[:, 0:3], prm)
+        xi = x.copy()
+        xi[coarse.dirichlet, 0:3] = bc_values(t)[coarse.dirichlet]
+        x, _ = newton(coarse, xi, b, prm, tol=newton_tol)
+        states.append(x.copy())
+    return states

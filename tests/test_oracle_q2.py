@@ -190,3 +190,65 @@ def test_manufactured_solution_convergence():
     assert rates[2] > 1.9, rates      # pressure L2 ~ h^2   (2.81)
     for e, ei in zip(errs[1][:2], interp[1][:2]):
         assert e <= 1.1 * ei, (errs[1], interp[1])
+
+
+def _q2_hierarchies(n, shear=False):
+    m = I.cavity_mesh(n, grouped=False)
+    xyz = m["xyz"] @ np.array([[1.0, 0.3, 0.0], [0.0, 1.2, 0.1], [0.2, 0.0, 0.8]]).T if shear else m["xyz"]
+    h = mesh.Hierarchy(xyz, m["cells"], m["vertex_bc"])
+    h2 = mesh.Hierarchy2(xyz, m["cells"], m["vertex_bc"])
+    return m, h, h2
+
+
+@pytest.mark.parametrize("shear", [False, True])
+def test_restricted_fine_rhs_equals_coarse_rhs(shear):
+    # nested Q2 spaces and a mass term the 3-point rule integrates exactly on
+    # parallelepipeds (theta = 1: the rhs is m (v_old, phi) + force terms)
+    _, h, h2 = _q2_hierarchies(2, shear)
+    coarse, fine = q2.coarse_level(h), q2.fine_level(h2)
+    rng = np.random.default_rng(6)
+    v = rng.standard_normal((h.n_fine, 3))
+    f = rng.standard_normal((h.n_fine, 3))
+    prm = dict(m=7.0, theta=1.0, nu=0.01)
+    bc = coarse.rhs(v, prm, f_new=f)
+    bf = fine.rhs(q2.prolongate(h, h2, v), prm, f_new=q2.prolongate(h, h2, f))
+    Rb = q2.restrict(h, h2, bf)
+    assert np.abs(Rb - bc).max() <= 1e-13 * np.abs(bc).max()
+
+
+def test_zero_network_dnnmg_equals_plain_q2_scheme():
+    m, h, h2 = _q2_hierarchies(2)
+    widths = (1012, 16, 375)                        # 125-node patches: 1000 + 12 inputs, 375 outputs
+    Ws, ss, ts = I.network_weights(widths, seed=0)
+    Ws[-1] = np.zeros_like(Ws[-1])
+    coarse = q2.coarse_level(h)
+    prm = dict(m=100.0, theta=1.0, nu=0.01, alpha0=0.02, delta0=0.1)
+
+    def bcv(t):
+        return I.dirichlet_values(m, coarse.xyz, coarse.bc)
+    x0 = np.zeros((coarse.n, 4))
+    x0[coarse.dirichlet, 0:3] = bcv(0.0)[coarse.dirichlet]
+    a = q2.run(h, h2, (Ws, ss, ts, True), x0, 3, prm, bcv)
+    b = q2.run_plain(h, x0, 3, prm, bcv)
+    for xa, xb in zip(a, b):
+        assert np.abs(xa - xb).max() <= 1e-11 * np.abs(xb).max()
+    assert np.abs(b[-1][:, 0:3]).max() > 0.1       # the lid drives a flow
+
+
+def test_q2_patch_step_shapes_and_gather_positions():
+    _, h, h2 = _q2_hierarchies(2)
+    widths = (1012, 8, 375)
+    Ws, ss, ts = I.network_weights(widths, seed=1)
+    rng = np.random.default_rng(2)
+    xc = rng.standard_normal((h.n_fine, 4))
+    prm = dict(m=10.0, theta=0.5, nu=0.01, alpha0=0.02, delta0=0.1)
+    F = rng.standard_normal((h2.n_fine, 4))
+    out = q2.hot_path_step(h, h2, (Ws, ss, ts, True), xc, F, prm)
+    assert out["X"].shape == (h.n_patches, 1012) and out["Y"].shape == (h.n_patches, 375)
+    assert out["b_coarse"].shape == (h.n_fine, 4)
+    # x~ columns of patch P at node iota: the coarse Q2 field at (a/4, b/4, c/4) of cell P
+    lev = q2.coarse_level(h)
+    for iota in (0, 31, 62, 124):
+        a, b, c = iota % 5, (iota // 5) % 5, iota // 25
+        val, _ = lev.evaluate(xc, (a / 4.0, b / 4.0, c / 4.0))
+        assert np.allclose(out["X"][:, 4 * iota:4 * iota + 4], val, rtol=0, atol=1e-13)
