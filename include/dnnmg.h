@@ -66,7 +66,7 @@
 extern "C" {
 #endif
 
-#define DNNMG_ABI_VERSION 2
+#define DNNMG_ABI_VERSION 3
 
 typedef struct dnnmg_ctx dnnmg_ctx;
 
@@ -176,6 +176,26 @@ dnnmg_status dnnmg_get_sizes(const dnnmg_ctx* ctx, dnnmg_sizes* out);
 /* Copy mesh data to host memory `host_buf` of `bytes` bytes (EINVAL if too
  * small). */
 dnnmg_status dnnmg_get_mesh_data(const dnnmg_ctx* ctx, int32_t item, void* host_buf, size_t bytes);
+
+/* The mesh hierarchy alone, built on the host with no CUDA call: the same
+ * refinement, hierarchical fine numbering, patch map dof(P, iota) (Sec. 5.2),
+ * valences mult_j (Eq. (15)), boundary kinds and geometry features that
+ * dnnmg_create builds for its context.  It serves inspection and tests on
+ * machines without a GPU.
+ *   dnnmg_hierarchy_build    mesh as for dnnmg_create (copied); features
+ *                            0 or 12 (edge lengths) or 24; patch_levels 0 or
+ *                            1 (J = 1) or 2 (J = 2).  EINVAL for bad
+ *                            arguments or an invalid mesh, ENOMEM.
+ *   dnnmg_hierarchy_sizes    as dnnmg_get_sizes, precision = -1
+ *   dnnmg_hierarchy_data     as dnnmg_get_mesh_data (items dnnmg_mesh_item)
+ *   dnnmg_hierarchy_destroy  frees the handle (NULL is ignored)
+ * The handle is immutable after build; concurrent reads are safe. */
+typedef struct dnnmg_hierarchy dnnmg_hierarchy;
+dnnmg_status dnnmg_hierarchy_build(const dnnmg_mesh_desc* mesh, int32_t features, int32_t patch_levels,
+                                   dnnmg_hierarchy** out);
+dnnmg_status dnnmg_hierarchy_sizes(const dnnmg_hierarchy* h, dnnmg_sizes* out);
+dnnmg_status dnnmg_hierarchy_data(const dnnmg_hierarchy* h, int32_t item, void* host_buf, size_t bytes);
+void dnnmg_hierarchy_destroy(dnnmg_hierarchy* h);
 
 dnnmg_status dnnmg_set_stream(dnnmg_ctx* ctx, void* cuda_stream);
 

@@ -59,6 +59,11 @@ _SIGS = {
     "dnnmg_last_error": ([_VP], ctypes.c_char_p),
     "dnnmg_get_sizes": ([_VP, ctypes.POINTER(Sizes)], ctypes.c_int),
     "dnnmg_get_mesh_data": ([_VP, ctypes.c_int32, _VP, ctypes.c_size_t], ctypes.c_int),
+    "dnnmg_hierarchy_build": ([ctypes.POINTER(MeshDesc), ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(_VP)],
+                              ctypes.c_int),
+    "dnnmg_hierarchy_sizes": ([_VP, ctypes.POINTER(Sizes)], ctypes.c_int),
+    "dnnmg_hierarchy_data": ([_VP, ctypes.c_int32, _VP, ctypes.c_size_t], ctypes.c_int),
+    "dnnmg_hierarchy_destroy": ([_VP], None),
     "dnnmg_set_stream": ([_VP, _VP], ctypes.c_int),
     "dnnmg_set_network": ([_VP, ctypes.POINTER(NetDesc), ctypes.POINTER(_VP), ctypes.POINTER(_VP),
                            ctypes.POINTER(_VP)], ctypes.c_int),
@@ -126,22 +131,71 @@ def _check(ctx, status):
 
 # -- thin wrappers with the C names ------------------------------------------
 
-def dnnmg_create(mesh, nu, dt, theta, precision, stream=None, features=12, patch_levels=1):
-    """mesh: dict with xyz [nv,3] float64, cells [nc,8] int32, vertex_bc [nv] int32.
-    stream: a torch.cuda.Stream, an int handle, or None (default stream).
-    features: geometry features per patch, 12 (edge lengths) or 24.
-    patch_levels: J of the patches, 1 (27 nodes) or 2 (125 nodes)."""
-    lib = load()
+def _mesh_desc(mesh):
+    """A MeshDesc over contiguous copies of the mesh arrays (returned with
+    them, so they outlive the call)."""
     xyz = np.ascontiguousarray(mesh["xyz"], dtype=np.float64)
     cells = np.ascontiguousarray(mesh["cells"], dtype=np.int32)
     bc = np.ascontiguousarray(mesh["vertex_bc"], dtype=np.int32)
     desc = MeshDesc(int(xyz.shape[0]), xyz.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                     int(cells.shape[0]), cells.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                     bc.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+    return desc, (xyz, cells, bc)
+
+
+def _mesh_item(sz, item):
+    """Shape and dtype of a mesh item for the sizes sz."""
+    return {PATCH_MAP: ((sz["n_patches"], sz["n_out"] // 3), np.int32), VALENCE: ((sz["n_fine_nodes"],), np.int32),
+            FINE_KIND: ((sz["n_fine_nodes"],), np.int32), FINE_XYZ: ((sz["n_fine_nodes"], 3), np.float64),
+            EDGE_LENGTHS: ((sz["n_patches"], 12), np.float64),
+            GEOMETRY: ((sz["n_patches"], sz["n_in"] - 8 * (sz["n_out"] // 3)), np.float64)}[item]
+
+
+class HostHierarchy:
+    """The library's mesh hierarchy built on the host alone (no GPU):
+    ``data(item)`` returns the items dnnmg_get_mesh_data gives for a context."""
+
+    def __init__(self, mesh, features=12, patch_levels=1):
+        desc, keep = _mesh_desc(mesh)
+        handle = _VP()
+        _check(None, load().dnnmg_hierarchy_build(ctypes.byref(desc), int(features), int(patch_levels),
+                                                  ctypes.byref(handle)))
+        del keep
+        self.handle = handle.value
+        s = Sizes()
+        _check(None, load().dnnmg_hierarchy_sizes(self.handle, ctypes.byref(s)))
+        self.sizes = {k: getattr(s, k) for k, _ in Sizes._fields_}
+
+    def data(self, item):
+        shape, dt = _mesh_item(self.sizes, item)
+        out = np.empty(shape, dtype=dt)
+        _check(None, load().dnnmg_hierarchy_data(self.handle, item, out.ctypes.data, out.nbytes))
+        return out
+
+    def close(self):
+        if self.handle:
+            load().dnnmg_hierarchy_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def dnnmg_create(mesh, nu, dt, theta, precision, stream=None, features=12, patch_levels=1):
+    """mesh: dict with xyz [nv,3] float64, cells [nc,8] int32, vertex_bc [nv] int32.
+    stream: a torch.cuda.Stream, an int handle, or None (default stream).
+    features: geometry features per patch, 12 (edge lengths) or 24.
+    patch_levels: J of the patches, 1 (27 nodes) or 2 (125 nodes)."""
+    lib = load()
+    desc, keep = _mesh_desc(mesh)
     prm = Params(float(nu), float(dt), float(theta), int(precision), int(features), int(patch_levels), 0)
     handle = _VP()
     s = getattr(stream, "cuda_stream", stream)
     _check(None, lib.dnnmg_create(ctypes.byref(desc), ctypes.byref(prm), s, ctypes.byref(handle)))
+    del keep
     return handle.value
 
 
@@ -156,11 +210,7 @@ def dnnmg_get_sizes(ctx) -> dict:
 
 
 def dnnmg_get_mesh_data(ctx, item):
-    sz = dnnmg_get_sizes(ctx)
-    shape, dt = {PATCH_MAP: ((sz["n_patches"], sz["n_out"] // 3), np.int32), VALENCE: ((sz["n_fine_nodes"],), np.int32),
-                 FINE_KIND: ((sz["n_fine_nodes"],), np.int32), FINE_XYZ: ((sz["n_fine_nodes"], 3), np.float64),
-                 EDGE_LENGTHS: ((sz["n_patches"], 12), np.float64),
-                 GEOMETRY: ((sz["n_patches"], sz["n_in"] - 8 * (sz["n_out"] // 3)), np.float64)}[item]
+    shape, dt = _mesh_item(dnnmg_get_sizes(ctx), item)
     out = np.empty(shape, dtype=dt)
     _check(ctx, load().dnnmg_get_mesh_data(ctx, item, out.ctypes.data, out.nbytes))
     return out

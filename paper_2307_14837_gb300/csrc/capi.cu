@@ -85,9 +85,49 @@ bool elem_aligned(const dnnmg_ctx* c, std::initializer_list<const void*> ps) {
 
 // network inputs per patch: 2 x nodes x 4 values + the geometry features;
 // the row stride of X; outputs per patch (3 per node)
-int n_in(const dnnmg_ctx* c) { return 8 * c->host.npn + c->host.n_geo; }
-int n_in_pad(const dnnmg_ctx* c) { return c->host.J == 2 ? kNInPadJ2 : kNInPad; }
-int n_out(const dnnmg_ctx* c) { return 3 * c->host.npn; }
+int n_in(const HostHierarchy& h) { return 8 * h.npn + h.n_geo; }
+int n_in_pad(const HostHierarchy& h) { return h.J == 2 ? kNInPadJ2 : kNInPad; }
+int n_out(const HostHierarchy& h) { return 3 * h.npn; }
+int n_in(const dnnmg_ctx* c) { return n_in(c->host); }
+int n_in_pad(const dnnmg_ctx* c) { return n_in_pad(c->host); }
+int n_out(const dnnmg_ctx* c) { return n_out(c->host); }
+
+void fill_sizes(const HostHierarchy& h, int32_t precision, dnnmg_sizes* out) {
+    out->n_coarse_vertices = h.nv;
+    out->n_patches = h.nc;
+    out->n_fine_nodes = h.n_fine;
+    out->n_coarse_edges = h.ne;
+    out->n_coarse_faces = h.nf;
+    out->n_in = n_in(h);
+    out->n_in_padded = n_in_pad(h);
+    out->n_out = n_out(h);
+    out->precision = precision;
+}
+
+// one item of a host hierarchy into a caller buffer of `bytes` bytes
+dnnmg_status copy_mesh_item(const HostHierarchy& h, int32_t item, void* host_buf, size_t bytes) {
+    const void* src = nullptr;
+    size_t n = 0;
+    switch (item) {
+        case DNNMG_PATCH_MAP: src = h.patch_map.data(); n = h.patch_map.size() * 4; break;
+        case DNNMG_VALENCE: src = h.valence.data(); n = h.valence.size() * 4; break;
+        case DNNMG_FINE_KIND: src = h.kind_f.data(); n = h.kind_f.size() * 4; break;
+        case DNNMG_FINE_XYZ: src = h.xyz_f.data(); n = h.xyz_f.size() * 8; break;
+        case DNNMG_EDGE_LENGTHS: {   // the first 12 of each patch's geometry features
+            n = size_t(h.nc) * 12 * 8;
+            if (bytes < n) return DNNMG_EINVAL;
+            double* dst = static_cast<double*>(host_buf);
+            for (int64_t c = 0; c < h.nc; ++c)
+                std::memcpy(dst + 12 * c, h.geo.data() + size_t(h.n_geo) * size_t(c), 12 * 8);
+            return DNNMG_OK;
+        }
+        case DNNMG_GEOMETRY: src = h.geo.data(); n = h.geo.size() * 8; break;
+        default: return DNNMG_EINVAL;
+    }
+    if (bytes < n) return DNNMG_EINVAL;
+    std::memcpy(host_buf, src, n);
+    return DNNMG_OK;
+}
 
 }  // namespace
 
@@ -220,43 +260,50 @@ dnnmg_status dnnmg_create(const dnnmg_mesh_desc* mesh, const dnnmg_params* param
 
 dnnmg_status dnnmg_get_sizes(const dnnmg_ctx* ctx, dnnmg_sizes* out) {
     if (!ctx || !out) return DNNMG_EINVAL;
-    out->n_coarse_vertices = ctx->host.nv;
-    out->n_patches = ctx->host.nc;
-    out->n_fine_nodes = ctx->host.n_fine;
-    out->n_coarse_edges = ctx->host.ne;
-    out->n_coarse_faces = ctx->host.nf;
-    out->n_in = n_in(ctx);
-    out->n_in_padded = n_in_pad(ctx);
-    out->n_out = n_out(ctx);
-    out->precision = ctx->precision;
+    fill_sizes(ctx->host, ctx->precision, out);
     return DNNMG_OK;
 }
 
 dnnmg_status dnnmg_get_mesh_data(const dnnmg_ctx* ctx, int32_t item, void* host_buf, size_t bytes) {
     if (!ctx || ctx->net_only || !host_buf) return DNNMG_EINVAL;
-    const HostHierarchy& h = ctx->host;
-    const void* src = nullptr;
-    size_t n = 0;
-    switch (item) {
-        case DNNMG_PATCH_MAP: src = h.patch_map.data(); n = h.patch_map.size() * 4; break;
-        case DNNMG_VALENCE: src = h.valence.data(); n = h.valence.size() * 4; break;
-        case DNNMG_FINE_KIND: src = h.kind_f.data(); n = h.kind_f.size() * 4; break;
-        case DNNMG_FINE_XYZ: src = h.xyz_f.data(); n = h.xyz_f.size() * 8; break;
-        case DNNMG_EDGE_LENGTHS: {   // the first 12 of each patch's geometry features
-            n = size_t(h.nc) * 12 * 8;
-            if (bytes < n) return DNNMG_EINVAL;
-            double* dst = static_cast<double*>(host_buf);
-            for (int64_t c = 0; c < h.nc; ++c)
-                std::memcpy(dst + 12 * c, h.geo.data() + size_t(h.n_geo) * size_t(c), 12 * 8);
-            return DNNMG_OK;
-        }
-        case DNNMG_GEOMETRY: src = h.geo.data(); n = h.geo.size() * 8; break;
-        default: return DNNMG_EINVAL;
+    return copy_mesh_item(ctx->host, item, host_buf, bytes);
+}
+
+// ---- the hierarchy alone, on the host -------------------------------------------
+struct dnnmg_hierarchy {
+    HostHierarchy host;
+};
+
+dnnmg_status dnnmg_hierarchy_build(const dnnmg_mesh_desc* mesh, int32_t features, int32_t patch_levels,
+                                   dnnmg_hierarchy** out) {
+    if (!out) return DNNMG_EINVAL;
+    *out = nullptr;
+    if (!mesh || (features != 0 && features != 12 && features != 24) || patch_levels < 0 || patch_levels > 2)
+        return DNNMG_EINVAL;
+    dnnmg_hierarchy* h = new (std::nothrow) dnnmg_hierarchy();
+    if (!h) return DNNMG_ENOMEM;
+    std::string err;
+    const dnnmg_status st = build_hierarchy(mesh, features == 24 ? 24 : 12, patch_levels == 2 ? 2 : 1, &h->host, &err);
+    if (st != DNNMG_OK) {
+        delete h;
+        return st;
     }
-    if (bytes < n) return DNNMG_EINVAL;
-    std::memcpy(host_buf, src, n);
+    *out = h;
     return DNNMG_OK;
 }
+
+dnnmg_status dnnmg_hierarchy_sizes(const dnnmg_hierarchy* h, dnnmg_sizes* out) {
+    if (!h || !out) return DNNMG_EINVAL;
+    fill_sizes(h->host, -1, out);
+    return DNNMG_OK;
+}
+
+dnnmg_status dnnmg_hierarchy_data(const dnnmg_hierarchy* h, int32_t item, void* host_buf, size_t bytes) {
+    if (!h || !host_buf) return DNNMG_EINVAL;
+    return copy_mesh_item(h->host, item, host_buf, bytes);
+}
+
+void dnnmg_hierarchy_destroy(dnnmg_hierarchy* h) { delete h; }
 
 dnnmg_status dnnmg_set_stream(dnnmg_ctx* ctx, void* cuda_stream) {
     if (!ctx) return DNNMG_EINVAL;

@@ -1,0 +1,71 @@
+"""The library's C++ mesh hierarchy, built on the host alone
+(dnnmg_hierarchy_build, no GPU), against the oracle's: patch maps and
+valences bit for bit, boundary kinds, node coordinates and the geometry
+features, for one- and two-level patches on the cavity and the channel."""
+import numpy as np
+import pytest
+
+from oracle import mesh as omesh
+from paper_2307_14837_gb300 import build, capi, inputs as I
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+    capi.load()
+
+
+CASES = {
+    "cavity4_jitter": lambda: I.cavity_mesh(4, jitter=0.2, seed=3),
+    "cavity3": lambda: I.cavity_mesh(3, grouped=False),
+    "channel4": lambda: I.channel_mesh(4, seed=1),
+}
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+@pytest.mark.parametrize("features", [12, 24])
+def test_one_level_hierarchy_matches_oracle(case, features):
+    m = CASES[case]()
+    h = omesh.Hierarchy(m["xyz"], m["cells"], m["vertex_bc"])
+    lib = capi.HostHierarchy(m, features=features, patch_levels=1)
+    assert lib.sizes["n_patches"] == h.n_patches and lib.sizes["n_fine_nodes"] == h.n_fine
+    assert lib.sizes["n_in"] == 216 + features and lib.sizes["n_out"] == 81 and lib.sizes["precision"] == -1
+    assert np.array_equal(lib.data(capi.PATCH_MAP), h.patch_map)
+    assert np.array_equal(lib.data(capi.VALENCE), h.mult)
+    assert np.array_equal(lib.data(capi.FINE_KIND), h.bc_f)
+    assert np.allclose(lib.data(capi.FINE_XYZ), h.xyz_f, rtol=0, atol=1e-15)
+    g = h.geometry(features)
+    assert np.allclose(lib.data(capi.GEOMETRY), g, rtol=1e-13, atol=1e-14)
+    assert np.allclose(lib.data(capi.EDGE_LENGTHS), g[:, :12], rtol=1e-13, atol=1e-14)
+    lib.close()
+
+
+@pytest.mark.parametrize("case", ["cavity4_jitter", "channel4"])
+def test_two_level_hierarchy_matches_oracle(case):
+    m = CASES[case]()
+    h2 = omesh.Hierarchy2(m["xyz"], m["cells"], m["vertex_bc"])
+    lib = capi.HostHierarchy(m, features=24, patch_levels=2)
+    assert lib.sizes["n_in"] == 1024 and lib.sizes["n_out"] == 375 and lib.sizes["n_in_padded"] == 1024
+    assert np.array_equal(lib.data(capi.PATCH_MAP), h2.patch_map)
+    assert np.array_equal(lib.data(capi.VALENCE), h2.mult)
+    assert np.array_equal(lib.data(capi.FINE_KIND), h2.bc_f)
+    assert np.allclose(lib.data(capi.FINE_XYZ), h2.xyz_f, rtol=0, atol=1e-15)
+    assert np.allclose(lib.data(capi.GEOMETRY), h2.geometry(24), rtol=1e-13, atol=1e-14)
+    lib.close()
+
+
+def test_invalid_meshes_and_arguments_are_refused():
+    m = I.cavity_mesh(2)
+    with pytest.raises(capi.DnnmgError) as e:
+        capi.HostHierarchy(m, features=13)
+    assert e.value.status == -1
+    with pytest.raises(capi.DnnmgError):
+        capi.HostHierarchy(m, patch_levels=3)
+    bad = dict(m, cells=np.array(m["cells"]).copy())
+    bad["cells"][0, 0] = len(m["xyz"])                  # a vertex index past the end
+    with pytest.raises(capi.DnnmgError):
+        capi.HostHierarchy(bad)
+    twice = dict(m, cells=np.array(m["cells"]).copy())
+    twice["cells"][0, 1] = twice["cells"][0, 0]         # a repeated vertex
+    with pytest.raises(capi.DnnmgError):
+        capi.HostHierarchy(twice)
