@@ -651,6 +651,26 @@ def main():
     if rank != 0:
         torch.distributed.destroy_process_group()
         return
+    line = result_line(res, args, world, el)
+    if not args.no_fp64:
+        line["equal_error"] = equal_error()
+    if not args.no_cpu_baseline:
+        o = OracleSample(nz=10)
+        secs, n = 0.0, 0
+        while n < 2 or (secs < 10.0 and n < 5):
+            secs += o.step()
+            n += 1
+        pps = o.h.n_patches * n / secs
+        line["cpu_baseline"] = {"value": pps / res["nc"], "unit": UNIT, "cores": o.threads(), "kind": "oracle",
+                                "sample": f"{o.desc}; {n} timed steps", "patches_per_s": pps}
+    print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def result_line(res, args, world, el):
+    """The JSON line of the device arm from run_ours' result ``res`` and the
+    slowest rank's elapsed time ``el`` (ms for args.steps steps)."""
     K = args.steps
     ms = el / K
     value = whole_job_rate(K, el, world)
@@ -684,20 +704,7 @@ def main():
         "clocks": res["clocks"],
         "fp64_plain": res["fp64"],
     }
-    if not args.no_fp64:
-        line["equal_error"] = equal_error()
-    if not args.no_cpu_baseline:
-        o = OracleSample(nz=10)
-        secs, n = 0.0, 0
-        while n < 2 or (secs < 10.0 and n < 5):
-            secs += o.step()
-            n += 1
-        pps = o.h.n_patches * n / secs
-        line["cpu_baseline"] = {"value": pps / nc, "unit": UNIT, "cores": o.threads(), "kind": "oracle",
-                                "sample": f"{o.desc}; {n} timed steps", "patches_per_s": pps}
-    print(json.dumps(line))
-    if world > 1:
-        torch.distributed.destroy_process_group()
+    return line
 
 
 if __name__ == "__main__":
