@@ -48,3 +48,23 @@ def test_create_rejects_bad_arguments_without_a_gpu(lib):
     with pytest.raises(capi.DnnmgError):
         capi.dnnmg_create(mesh, 0.01, -1.0, 1.0, capi.FP64)     # dt <= 0
 
+
+
+def test_missing_library_fails_loudly(tmp_path, monkeypatch):
+    # no CPU fallback: without the built library the binding raises
+    monkeypatch.setattr(capi, "_lib", None)
+    with pytest.raises(RuntimeError, match="not built"):
+        capi.load(str(tmp_path / "libdnnmg.so"))
+
+
+def test_product_package_does_not_import_the_oracle():
+    # the oracle is test infrastructure: no module of the package imports it
+    pkg = os.path.join(ROOT, "paper_2307_14837_gb300")
+    for name in os.listdir(pkg):
+        if name.endswith(".py"):
+            src = open(os.path.join(pkg, name)).read()
+            assert not re.search(r"^\s*(from|import)\s+oracle\b", src, flags=re.M), name
+
+
+def test_build_targets_sm103a_only():
+    assert build.ARCH_FLAGS == ["-gencode", "arch=compute_103a,code=sm_103a"]
