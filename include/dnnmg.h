@@ -272,8 +272,12 @@ dnnmg_status dnnmg_patch_step(dnnmg_ctx* ctx, const void* x_coarse_dev, const vo
                               void* b_fine_dev, void* b_coarse_dev);
 
 /* dnnmg_patch_step on host buffers: copies x_coarse and F to the device,
- * runs the step, copies b_fine and b_coarse back, and synchronises.  For
- * pinned host memory the copies are asynchronous on the context's stream. */
+ * runs the step, copies b_fine and b_coarse back, and synchronises.  With
+ * pinned host memory the copies are asynchronous: x_coarse goes on the
+ * context's stream, F on a second stream of the context while the
+ * residual's element kernel (which needs only x_coarse) runs, and the
+ * gather that reads F waits for it.  b_fine_host or b_coarse_host may be
+ * NULL (not copied back). */
 dnnmg_status dnnmg_patch_step_host(dnnmg_ctx* ctx, const void* x_coarse_host, const void* F_host,
                                    void* b_fine_host, void* b_coarse_host);
 
