@@ -371,7 +371,7 @@ dnnmg_status dnnmg_set_network(dnnmg_ctx* ctx, const dnnmg_net_desc* net, const 
         void* ds;
         void* dt;
         if (ctx->precision == DNNMG_FP64) {
-            double* p;
+            double* p = nullptr;
             if ((st = upload(ctx, w.data(), w.size(), &p)) != DNNMG_OK) return st;
             dw = p;
             if ((st = upload(ctx, s.data(), s.size(), &p)) != DNNMG_OK) return st;
@@ -380,7 +380,7 @@ dnnmg_status dnnmg_set_network(dnnmg_ctx* ctx, const dnnmg_net_desc* net, const 
             dt = p;
         } else {
             std::vector<float> sf(s.begin(), s.end()), tf(t.begin(), t.end());
-            float* p;
+            float* p = nullptr;
             if (ctx->precision == DNNMG_FP32) {
                 std::vector<float> wf(w.begin(), w.end());
                 if ((st = upload(ctx, wf.data(), wf.size(), &p)) != DNNMG_OK) return st;
@@ -388,7 +388,7 @@ dnnmg_status dnnmg_set_network(dnnmg_ctx* ctx, const dnnmg_net_desc* net, const 
             } else {
                 std::vector<__nv_bfloat16> wb(w.size());
                 for (size_t e = 0; e < w.size(); ++e) wb[e] = __float2bfloat16_rn(float(w[e]));
-                __nv_bfloat16* pb;
+                __nv_bfloat16* pb = nullptr;
                 if ((st = upload(ctx, wb.data(), wb.size(), &pb)) != DNNMG_OK) return st;
                 dw = pb;
             }
