@@ -2,6 +2,8 @@
 method arithmetic): the SplitMix64 stream against its published definition,
 the derived uniform and normal draws, the weight distribution, and the
 meshes' structural promises."""
+import os
+
 import numpy as np
 
 from paper_2307_14837_gb300 import inputs as I
@@ -51,3 +53,16 @@ def test_cavity_jitter_keeps_the_boundary_and_stays_bounded():
     assert np.all(d[on_b] == 0.0)
     assert np.abs(d).max() <= jit / n and np.abs(d[~on_b]).max() > 0.5 * jit / n
     assert np.array_equal(m0["cells"], m1["cells"])
+
+
+def test_smooth_fields_take_the_papers_training_statistics():
+    path = os.path.join(os.path.dirname(__file__), "golden", "training_field_statistics.txt")
+    rows = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
+    mean = np.array([float(r[2]) for r in rows])
+    sigma = np.array([float(r[4]) for r in rows])
+    assert np.allclose(I.PAPER_FIELD_MEAN, mean, rtol=0, atol=1e-10)
+    assert np.allclose(I.PAPER_FIELD_STD, sigma, rtol=0, atol=0)
+    m = I.channel_mesh(6, seed=2)
+    f = I.smooth_field(m["xyz"], seed=4)
+    assert np.allclose(f.mean(axis=0), mean, rtol=0, atol=1e-9)
+    assert np.allclose(f.std(axis=0), sigma, rtol=1e-12)
