@@ -44,10 +44,10 @@
  *       Y         [n_patches][n_out]: 27 x (u, v, w) (J = 2: 125 x 3 = 375)
  *     Patch node iota = a + 3b + 9c, (a,b,c) in {0,1,2}^3 along the coarse
  *     cell's reference axes (J = 2: a + 5b + 25c, (a,b,c) in {0..4}^3).
-   - Alignment of *_dev field pointers: [n][4] fields (x_coarse, x_fine,
-     F, r, b_fine, b_coarse) to 4 elements (16 bytes in float, 32 in
-     double), X to 16 bytes, d and Y to one element; DNNMG_EINVAL otherwise.
-     Fresh allocations of cudaMalloc or torch meet all of them.
+ *   - Alignment of *_dev field pointers: [n][4] fields (x_coarse, x_fine,
+ *     F, r, b_fine, b_coarse) to 4 elements (16 bytes in float, 32 in
+ *     double), X to 16 bytes, d and Y to one element; DNNMG_EINVAL otherwise.
+ *     Fresh allocations of cudaMalloc or torch meet all of them.
  *   - Dirichlet velocity rows (fine node kinds 1 and 2) of r, d and b_fine,
  *     and coarse Dirichlet velocity rows of b_coarse are zero; pressure rows
  *     of b_fine and b_coarse are zero.
@@ -245,6 +245,16 @@ dnnmg_status dnnmg_network(dnnmg_ctx* ctx, const void* X_dev, void* Y_dev, int64
  * Takes a few seconds; Y holds no result. */
 dnnmg_status dnnmg_network_wait_test(dnnmg_ctx* ctx, const void* X_dev, void* Y_dev, int64_t n_rows);
 
+/* The same failure-path test through any entry point (the paper has no
+ * counterpart): the next network launch of this context, whichever call
+ * makes it (dnnmg_network, dnnmg_patch_step, dnnmg_patch_step_host,
+ * dnnmg_time_step), withholds its first operand stage.  The calls that
+ * synchronise (dnnmg_patch_step_host, dnnmg_time_step) then return
+ * DNNMG_ETIMEOUT themselves; after an asynchronous call dnnmg_sync does.
+ * The expiry is recorded in this context's own error word, so other
+ * contexts on the device are not affected.  BF16 only, else EUNSUPPORTED. */
+dnnmg_status dnnmg_arm_wait_test(dnnmg_ctx* ctx);
+
 /* Extension d = mu . sum_P L(Y_P, P) of Eq. (15), mu = 1 / valence, summed
  * in patch order (deterministic, no atomics).  d_dev [n_fine_nodes][3];
  * zero at Dirichlet velocity nodes. */
@@ -267,7 +277,9 @@ dnnmg_status dnnmg_restrict(dnnmg_ctx* ctx, const void* b_fine_dev, void* b_coar
 /* The whole patch correction of one time step: prolongate, residual with
  * F_dev, local restriction, network, extension, rhs and restriction.  r, X,
  * Y and d live in context buffers (readable with dnnmg_get_buffer).
- * b_fine_dev may alias F_dev (the step reads F before writing b). */
+ * b_fine_dev may alias F_dev (the step reads F before writing b).
+ * Asynchronous: an expired bounded wait of the network (BF16) is reported
+ * by the next dnnmg_sync as DNNMG_ETIMEOUT. */
 dnnmg_status dnnmg_patch_step(dnnmg_ctx* ctx, const void* x_coarse_dev, const void* F_dev,
                               void* b_fine_dev, void* b_coarse_dev);
 
@@ -277,7 +289,9 @@ dnnmg_status dnnmg_patch_step(dnnmg_ctx* ctx, const void* x_coarse_dev, const vo
  * context's stream, F on a second stream of the context while the
  * residual's element kernel (which needs only x_coarse) runs, and the
  * gather that reads F waits for it.  b_fine_host or b_coarse_host may be
- * NULL (not copied back). */
+ * NULL (not copied back).  Returns DNNMG_ETIMEOUT if a bounded wait of the
+ * network expired (the outputs are then not valid).  On any error the call
+ * first waits for its copies, so the host buffers are free on return. */
 dnnmg_status dnnmg_patch_step_host(dnnmg_ctx* ctx, const void* x_coarse_host, const void* F_host,
                                    void* b_fine_host, void* b_coarse_host);
 
@@ -367,7 +381,9 @@ dnnmg_status dnnmg_solve(dnnmg_ctx* ctx, int32_t level, const dnnmg_solver_param
  *   x_coarse_dev double [n_coarse][4] (Dirichlet values set by the caller),
  *   b_coarse_dev double [n_coarse][4],
  *   F_dev        [n_fine][4] in the context's field type.
- * Requires dnnmg_set_network.  stats (may be NULL) are the last coarse solve's. */
+ * Requires dnnmg_set_network.  stats (may be NULL) are the last coarse solve's.
+ * Synchronises after every step; returns DNNMG_ETIMEOUT at once if a bounded
+ * wait of the network expired in that step (its correction is not valid). */
 dnnmg_status dnnmg_time_step(dnnmg_ctx* ctx, int32_t n_steps, const dnnmg_solver_params* prm,
                              double* x_coarse_dev, double* b_coarse_dev, void* F_dev, dnnmg_solve_stats* stats);
 
@@ -445,7 +461,9 @@ dnnmg_status dnnmg_mse_loss(int64_t batch, const float* Y_dev, const float* T_de
 dnnmg_status dnnmg_adamw(int64_t n, float* w_dev, const float* g_dev, float* m_dev, float* v_dev, double lr,
                          double beta1, double beta2, double eps, double weight_decay, int32_t step, void* cuda_stream);
 
-/* Largest mesh dnnmg_residual_noalloc accepts (coarse cells = patches). */
+/* Largest mesh dnnmg_residual_noalloc accepts (coarse cells = patches);
+ * the Python binding's NOALLOC_MAX_PATCHES must equal it (a CPU test reads
+ * this line). */
 #define DNNMG_NOALLOC_MAX_PATCHES 16384
 
 /* dnnmg_residual without any allocation, for callers that may not allocate
@@ -469,9 +487,18 @@ dnnmg_status dnnmg_adamw(int64_t n, float* w_dev, const float* g_dev, float* m_d
  *   x_coarse_dev       float [n_coarse_vertices][4], F_dev float [n_fine_nodes][4]
  *   r_dev              float [n_fine_nodes][4] (output)
  *   nu, dt, theta      as in dnnmg_params; cuda_stream a cudaStream_t (NULL = default)
+ * The index arrays are trusted as given: nothing checks them (unlike
+ * dnnmg_create, which validates a mesh).  cells_dev entries must be vertex
+ * ids in [0, n_coarse_vertices), node_ptr_dev must be non-decreasing from 0
+ * to 27 n_patches, and node_idx_dev entries must lie in [0, 27 n_patches);
+ * an entry outside these ranges reads partial sums of an earlier call or
+ * memory outside the arrays.
  * The first call on a device looks up the fixed array's device address
- * (cudaGetSymbolAddress, once per device, under a lock); make that first
- * call before any stream capture.  Every call uses the same array, whose
+ * (cudaGetSymbolAddress, once per device, under a lock) and keeps it for
+ * the life of the process; make that first call before any stream capture.
+ * A cudaDeviceReset reloads the library's device image at a possibly
+ * different address, so after one this entry point must not be called on
+ * that device again in the same process.  Every call uses the same array, whose
  * contents persist between calls; each call overwrites all partial sums it
  * reads, so nothing has to be cleared, but calls that overlap on the GPU
  * (two streams, two threads) race on it.

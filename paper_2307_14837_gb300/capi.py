@@ -72,6 +72,7 @@ _SIGS = {
     "dnnmg_local_restrict": ([_VP, _VP, _VP, _VP], ctypes.c_int),
     "dnnmg_network": ([_VP, _VP, _VP, ctypes.c_int64], ctypes.c_int),
     "dnnmg_network_wait_test": ([_VP, _VP, _VP, ctypes.c_int64], ctypes.c_int),
+    "dnnmg_arm_wait_test": ([_VP], ctypes.c_int),
     "dnnmg_extend": ([_VP, _VP, _VP], ctypes.c_int),
     "dnnmg_rhs_restrict": ([_VP, _VP, _VP, _VP, _VP], ctypes.c_int),
     "dnnmg_patch_step": ([_VP, _VP, _VP, _VP, _VP], ctypes.c_int),
@@ -249,6 +250,10 @@ def dnnmg_network(ctx, X, Y, n_rows):
 
 def dnnmg_network_wait_test(ctx, X, Y, n_rows):
     _check(ctx, load().dnnmg_network_wait_test(ctx, _ptr(X), _ptr(Y), int(n_rows)))
+
+
+def dnnmg_arm_wait_test(ctx):
+    _check(ctx, load().dnnmg_arm_wait_test(ctx))
 
 
 def dnnmg_extend(ctx, Y, d):

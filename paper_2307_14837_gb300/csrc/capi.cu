@@ -83,6 +83,18 @@ bool elem_aligned(const dnnmg_ctx* c, std::initializer_list<const void*> ps) {
     return true;
 }
 
+// Wait for the context's stream, then report an expired bounded wait of
+// this context's tensor-core kernels (and clear it) as ETIMEOUT.
+dnnmg_status sync_and_check(dnnmg_ctx* ctx) {
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    int code = 0;
+    CK(ctx, read_tc_error(ctx->tc_err, ctx->stream, &code));
+    if (code)
+        return fail(ctx, DNNMG_ETIMEOUT,
+                    "tensor-core kernel: a bounded wait expired (code " + std::to_string(code) + ")");
+    return DNNMG_OK;
+}
+
 // network inputs per patch: 2 x nodes x 4 values + the geometry features;
 // the row stride of X; outputs per patch (3 per node)
 int n_in(const HostHierarchy& h) { return 8 * h.npn + h.n_geo; }
@@ -343,6 +355,13 @@ dnnmg_status dnnmg_set_network(dnnmg_ctx* ctx, const dnnmg_net_desc* net, const 
     ctx->scale.clear();
     ctx->shift.clear();
     ctx->has_net = false;
+    if (!ctx->tc_err) {
+        void* p = nullptr;
+        dnnmg_status sa = alloc(ctx, sizeof(int), &p);
+        if (sa != DNNMG_OK) return sa;
+        CK(ctx, cudaMemset(p, 0, sizeof(int)));
+        ctx->tc_err = static_cast<int*>(p);
+    }
     ctx->n_layers = L;
     ctx->skip = net->skip;
     ctx->widths.assign(net->widths, net->widths + L + 1);
@@ -472,6 +491,10 @@ static dnnmg_status network_impl(dnnmg_ctx* ctx, const void* X_dev, void* Y_dev,
     if (!aligned(X_dev, 16) || !elem_aligned(ctx, {Y_dev})) return fail(ctx, DNNMG_EINVAL, "misaligned field");
     if (!ctx->has_net) return fail(ctx, DNNMG_ESTATE, "dnnmg_network before dnnmg_set_network");
     if (n_rows > ctx->act_rows) return fail(ctx, DNNMG_EINVAL, "n_rows exceeds the activation capacity");
+    if (ctx->wait_test_armed && ctx->precision == DNNMG_BF16) {
+        withhold_first_load = 1;
+        ctx->wait_test_armed = 0;
+    }
     const int L = ctx->n_layers;
     for (int i = 0; i < L; ++i) {
         const bool last = i == L - 1;
@@ -495,7 +518,7 @@ static dnnmg_status network_impl(dnnmg_ctx* ctx, const void* X_dev, void* Y_dev,
             e = launch_layer_tc((const __nv_bfloat16*)A, lda, (const __nv_bfloat16*)ctx->W[i], K, N,
                                 (const float*)ctx->scale[i], (const float*)ctx->shift[i], C, ldc, !last,
                                 (const __nv_bfloat16*)R, lda, n_rows, ctx->widths[i + 1], K, !last, ctx->stream,
-                                i == 0 ? withhold_first_load : 0);
+                                ctx->tc_err, i == 0 ? withhold_first_load : 0);
         }
         ctx->launches += 1;
         if (e != cudaSuccess) return cuda_fail(ctx, e, "network layer");
@@ -512,6 +535,12 @@ dnnmg_status dnnmg_network_wait_test(dnnmg_ctx* ctx, const void* X_dev, void* Y_
     if (!ctx || ctx->precision != DNNMG_BF16) return DNNMG_EUNSUPPORTED;
     Range nvtx_range("dnnmg_network_wait_test");
     return network_impl(ctx, X_dev, Y_dev, n_rows, 1);
+}
+
+dnnmg_status dnnmg_arm_wait_test(dnnmg_ctx* ctx) {
+    if (!ctx || ctx->precision != DNNMG_BF16) return DNNMG_EUNSUPPORTED;
+    ctx->wait_test_armed = 1;
+    return DNNMG_OK;
 }
 
 dnnmg_status dnnmg_extend(dnnmg_ctx* ctx, const void* Y_dev, void* d_dev) {
@@ -588,21 +617,29 @@ dnnmg_status dnnmg_patch_step_host(dnnmg_ctx* ctx, const void* x_coarse_host, co
     // element kernel of the residual (which needs only x^L) runs
     CK(ctx, cudaEventRecord(ctx->ev_ready, ctx->stream));
     CK(ctx, cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_ready, 0));
-    CK(ctx, cudaMemcpyAsync(ctx->buf_xc, x_coarse_host, nv * 4 * fe, cudaMemcpyHostToDevice, ctx->stream));
-    CK(ctx, cudaMemcpyAsync(ctx->buf_F, F_host, nf * 4 * fe, cudaMemcpyHostToDevice, ctx->copy_stream));
-    CK(ctx, cudaEventRecord(ctx->ev_input, ctx->copy_stream));
+    // from the first copy on, an error return first waits for both streams,
+    // so that no copy still reads the caller's host buffers afterwards
+    auto drain = [&](dnnmg_status st) {
+        cudaStreamSynchronize(ctx->copy_stream);
+        cudaStreamSynchronize(ctx->stream);
+        return st;
+    };
+    cudaError_t ce = cudaMemcpyAsync(ctx->buf_xc, x_coarse_host, nv * 4 * fe, cudaMemcpyHostToDevice, ctx->stream);
+    if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(ctx->buf_F, F_host, nf * 4 * fe, cudaMemcpyHostToDevice, ctx->copy_stream);
+    if (ce == cudaSuccess) ce = cudaEventRecord(ctx->ev_input, ctx->copy_stream);
+    if (ce != cudaSuccess) return drain(cuda_fail(ctx, ce, "input upload"));
     dnnmg_status st;
-    if ((st = residual_impl(ctx, ctx->buf_xc, ctx->buf_F, ctx->buf_r, ctx->ev_input)) != DNNMG_OK) return st;
-    if ((st = dnnmg_local_restrict(ctx, ctx->buf_xc, ctx->buf_r, ctx->buf_X)) != DNNMG_OK) return st;
-    if ((st = dnnmg_network(ctx, ctx->buf_X, ctx->buf_Y, ctx->host.nc)) != DNNMG_OK) return st;
-    if ((st = dnnmg_extend(ctx, ctx->buf_Y, ctx->buf_d)) != DNNMG_OK) return st;
-    if ((st = dnnmg_rhs_restrict(ctx, ctx->buf_xc, ctx->buf_d, ctx->buf_F, ctx->buf_bc)) != DNNMG_OK) return st;
-    if (b_fine_host)
-        CK(ctx, cudaMemcpyAsync(b_fine_host, ctx->buf_F, nf * 4 * fe, cudaMemcpyDeviceToHost, ctx->stream));
-    if (b_coarse_host)
-        CK(ctx, cudaMemcpyAsync(b_coarse_host, ctx->buf_bc, nv * 4 * fe, cudaMemcpyDeviceToHost, ctx->stream));
-    CK(ctx, cudaStreamSynchronize(ctx->stream));
-    return DNNMG_OK;
+    if ((st = residual_impl(ctx, ctx->buf_xc, ctx->buf_F, ctx->buf_r, ctx->ev_input)) != DNNMG_OK) return drain(st);
+    if ((st = dnnmg_local_restrict(ctx, ctx->buf_xc, ctx->buf_r, ctx->buf_X)) != DNNMG_OK) return drain(st);
+    if ((st = dnnmg_network(ctx, ctx->buf_X, ctx->buf_Y, ctx->host.nc)) != DNNMG_OK) return drain(st);
+    if ((st = dnnmg_extend(ctx, ctx->buf_Y, ctx->buf_d)) != DNNMG_OK) return drain(st);
+    if ((st = dnnmg_rhs_restrict(ctx, ctx->buf_xc, ctx->buf_d, ctx->buf_F, ctx->buf_bc)) != DNNMG_OK) return drain(st);
+    if (b_fine_host) ce = cudaMemcpyAsync(b_fine_host, ctx->buf_F, nf * 4 * fe, cudaMemcpyDeviceToHost, ctx->stream);
+    if (ce == cudaSuccess && b_coarse_host)
+        ce = cudaMemcpyAsync(b_coarse_host, ctx->buf_bc, nv * 4 * fe, cudaMemcpyDeviceToHost, ctx->stream);
+    if (ce != cudaSuccess) return drain(cuda_fail(ctx, ce, "output download"));
+    return drain(sync_and_check(ctx));
 }
 
 dnnmg_status dnnmg_get_buffer(dnnmg_ctx* ctx, int32_t which, void** dev_ptr) {
@@ -622,13 +659,7 @@ dnnmg_status dnnmg_sync(dnnmg_ctx* ctx, int64_t timeout_us) {
     const auto t0 = std::chrono::steady_clock::now();
     for (;;) {
         cudaError_t e = cudaStreamQuery(ctx->stream);
-        if (e == cudaSuccess) {
-            int code = 0;
-            CK(ctx, read_tc_error(&code));
-            if (code) return fail(ctx, DNNMG_ETIMEOUT, "tensor-core kernel: a bounded wait expired (code " +
-                                                          std::to_string(code) + ")");
-            return DNNMG_OK;
-        }
+        if (e == cudaSuccess) return sync_and_check(ctx);
         if (e != cudaErrorNotReady) return cuda_fail(ctx, e, "cudaStreamQuery");
         if (timeout_us >= 0) {
             const auto us = std::chrono::duration_cast<std::chrono::microseconds>(
@@ -772,9 +803,11 @@ dnnmg_status dnnmg_time_step(dnnmg_ctx* ctx, int32_t n_steps, const dnnmg_solver
         if (st != DNNMG_OK && st != DNNMG_ENOCONV) return st;
         if ((st = dnnmg_network(ctx, ctx->buf_X, ctx->buf_Y, ctx->host.nc)) != DNNMG_OK) return st;
         if ((st = dnnmg_step_end(ctx, ctx->buf_Y, F_dev, b_coarse_dev)) != DNNMG_OK) return st;
+        // the next coarse solve reads b_coarse, which the network fed: stop
+        // at once if one of its bounded waits expired
+        if ((st = sync_and_check(ctx)) != DNNMG_OK) return st;
     }
-    CK(ctx, cudaStreamSynchronize(ctx->stream));
-    return DNNMG_OK;
+    return sync_and_check(ctx);
 }
 
 dnnmg_status dnnmg_step_begin(dnnmg_ctx* ctx, const dnnmg_solver_params* prm, int32_t solve, double* x_coarse_dev,
@@ -862,14 +895,14 @@ dnnmg_status dnnmg_plain_step(dnnmg_ctx* ctx, int32_t level, int32_t n_steps, co
     DeviceLevel* L;
     dnnmg_status st = get_level(ctx, level, prm, &L);
     if (st != DNNMG_OK) return st;
-    void* b = nullptr;
-    if ((st = alloc(ctx, size_t(level_nodes(L)) * 4 * 8, &b)) != DNNMG_OK) return st;
+    if (!ctx->plain_b[level] && (st = alloc(ctx, size_t(level_nodes(L)) * 4 * 8, &ctx->plain_b[level])) != DNNMG_OK)
+        return st;
+    void* b = ctx->plain_b[level];
     for (int32_t k = 0; k < n_steps; ++k) {
         if ((st = dnnmg_level_rhs(ctx, level, x_dev, (double*)b)) != DNNMG_OK) return st;
         st = dnnmg_solve(ctx, level, prm, (const double*)b, x_dev, stats);
         if (st != DNNMG_OK && st != DNNMG_ENOCONV) return st;
     }
-    // the scratch rhs is released with the context
     return DNNMG_OK;
 }
 

@@ -180,11 +180,14 @@ struct dnnmg_ctx {
     int64_t net_capacity = 0;    // rows of a network-only context (no mesh)
     bool net_only = false;
     const void* last_xc = nullptr;   // coarse state (field type) of the last dnnmg_step_begin
+    int* tc_err = nullptr;           // device word: a tensor-core wait of this context expired
+    int wait_test_armed = 0;         // the next network launch withholds its first operand stage
 
     // Newton solver levels (0: L, 1: L+1), created on first use
     dnnmg::DeviceLevel* level[2] = {nullptr, nullptr};
     void* xc_field = nullptr;   // [nv][4] x^L in the field type (time stepping)
     void* bc_field = nullptr;   // [nv][4] b^L in the field type
+    void* plain_b[2] = {nullptr, nullptr};   // [n][4] double rhs of dnnmg_plain_step per level
 };
 
 namespace dnnmg {
@@ -192,8 +195,8 @@ namespace dnnmg {
 cudaError_t launch_layer_tc(const __nv_bfloat16* A, int64_t lda, const __nv_bfloat16* W, int64_t ldw, int n_rows_w,
                             const float* scale, const float* shift, void* C, int64_t ldc, bool out_bf16,
                             const __nv_bfloat16* R, int64_t ldr, int64_t M, int N, int K, bool relu,
-                            cudaStream_t s, int withhold_first_load = 0);
-// Error code recorded by a tensor-core kernel whose bounded wait expired
-// (0 = none); reading clears it.  Synchronous.
-cudaError_t read_tc_error(int* code);
+                            cudaStream_t s, int* err, int withhold_first_load = 0);
+// Error code that a tensor-core kernel whose bounded wait expired recorded
+// in the device word err (0 = none); reading clears it.  Synchronises s.
+cudaError_t read_tc_error(int* err, cudaStream_t s, int* code);
 }  // namespace dnnmg

@@ -19,8 +19,10 @@
 //               load, so no lane issues global loads or stores per element
 // Two TMEM accumulators let the epilogue of one tile overlap the MMAs of
 // the next.  Every mbarrier wait is bounded (~1 s of %globaltimer); on
-// expiry the thread records an error code in tc_error, stops issuing work,
-// and the CTA still meets at the final barrier, frees TMEM and returns.
+// expiry the thread records an error code in the caller's error word (one
+// per context, so simulations sharing a device do not see each other's
+// expiries), stops issuing work, and the CTA still meets at the final
+// barrier, frees TMEM and returns.
 #include <cuda.h>
 
 #include <cstdio>
@@ -29,8 +31,6 @@
 #include "internal.h"
 
 namespace dnnmg {
-
-__device__ int tc_error = 0;   // 0 ok; otherwise which wait expired (see TcErr)
 
 namespace {
 
@@ -79,13 +79,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
 
 // Bounded wait for the phase with the given parity; false on expiry (the
 // error code is recorded once).
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int code) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int code, int* err) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = globaltimer();
     for (uint32_t i = 0;; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
         if ((i & 255) == 255 && globaltimer() - t0 > kWaitNs) {
-            atomicCAS(&tc_error, 0, code);
+            atomicCAS(err, 0, code);
             return false;
         }
     }
@@ -193,7 +193,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_layer_kernel(
     const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmW,
     const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmR,
     const float* __restrict__ scale, const float* __restrict__ shift, void* __restrict__ Cout, int64_t ldc,
-    const __nv_bfloat16* __restrict__ R, int64_t ldr, int M, int N, int K, int relu, int withhold_first_load) {
+    const __nv_bfloat16* __restrict__ R, int64_t ldr, int M, int N, int K, int relu, int withhold_first_load,
+    int* __restrict__ err) {
     using C = Cfg<BN>;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
@@ -252,7 +253,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_layer_kernel(
         for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
             const int m0 = (t / tiles_n) * BM, n0 = (t % tiles_n) * BN;
             for (int kb = 0; kb < kblocks; ++kb) {
-                if (!mbar_wait(empty_bar(stage), phase ^ 1u, kErrEmpty)) {
+                if (!mbar_wait(empty_bar(stage), phase ^ 1u, kErrEmpty, err)) {
                     ok = false;
                     break;
                 }
@@ -275,7 +276,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_layer_kernel(
         // with parity `phase` if s was filled in the current lap (s < stage),
         // else parity phase ^ 1 (a never-filled stage passes at once).
         for (int s = 0; s < C::STAGES; ++s)
-            mbar_wait(full_bar(s), s < stage ? phase : (phase ^ 1u), kErrDrain);
+            mbar_wait(full_bar(s), s < stage ? phase : (phase ^ 1u), kErrDrain, err);
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issuer
         constexpr uint32_t idesc = mma_idesc(BN);
@@ -286,11 +287,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_layer_kernel(
         for (int t = blockIdx.x; t < total && ok; t += gridDim.x, ++it) {
             const int buf = it & 1;
             const uint32_t use = uint32_t(it >> 1);
-            if (!mbar_wait(tempty_bar(buf), (use & 1u) ^ 1u, kErrTmemEmpty)) break;
+            if (!mbar_wait(tempty_bar(buf), (use & 1u) ^ 1u, kErrTmemEmpty, err)) break;
             fence_after();
             const uint32_t d = tmem_base + uint32_t(buf * C::ACC_COLS);
             for (int kb = 0; kb < kblocks; ++kb) {
-                if (!mbar_wait(full_bar(stage), phase, kErrFull)) {
+                if (!mbar_wait(full_bar(stage), phase, kErrFull, err)) {
                     ok = false;
                     break;
                 }
@@ -310,7 +311,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_layer_kernel(
         }
         // all MMAs this thread issued must finish before TMEM is freed
         mma_commit(done_bar);
-        mbar_wait(done_bar, 0, kErrDrain);
+        mbar_wait(done_bar, 0, kErrDrain, err);
     } else if (warp >= 2) {
         // ---------------- epilogue: warp w reads TMEM lanes 32 (w % 4) ..
         // (its 32 rows) and the 32-column chunks c0 = 32 half, 32 half + 64, ...
@@ -347,7 +348,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_layer_kernel(
             // the wait result is made warp-uniform (the TMEM loads below are
             // warp-collective); a warp whose wait expired leaves on its own,
             // and the others' waits for it are bounded too
-            const bool ok = __all_sync(0xffffffffu, mbar_wait(tfull_bar(buf), use & 1u, kErrTmemFull));
+            const bool ok = __all_sync(0xffffffffu, mbar_wait(tfull_bar(buf), use & 1u, kErrTmemFull, err));
             if (!ok) break;
             fence_after();
 #pragma unroll 1
@@ -389,7 +390,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_layer_kernel(
                     const uint32_t row_off = uint32_t(lane) * 64u;
                     const uint32_t sw = uint32_t((lane >> 1) & 3);
                     if (has_r) {
-                        if (!mbar_wait(rbar, rphase, kErrSkip)) { /* recorded; values are garbage */ }
+                        if (!mbar_wait(rbar, rphase, kErrSkip, err)) { /* recorded; values are garbage */ }
                         rphase ^= 1u;
                         r_pending = false;
 #pragma unroll
@@ -463,7 +464,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_layer_kernel(
         }
         // drain: a skip load still in flight (only after an early exit) and
         // every output store must complete before the CTA exits
-        if (r_pending) mbar_wait(rbar, rphase, kErrDrain);
+        if (r_pending) mbar_wait(rbar, rphase, kErrDrain, err);
         if constexpr (OUT_BF16) {
             if (lane == 0) bulk_wait_all();
         }
@@ -528,7 +529,7 @@ int sm_count() {
 template <int BN, bool OUT_BF16>
 cudaError_t launch_tc(const __nv_bfloat16* A, int64_t lda, const __nv_bfloat16* W, int64_t ldw, int n_rows_w,
                       const float* scale, const float* shift, void* C, int64_t ldc, const __nv_bfloat16* R,
-                      int64_t ldr, int64_t M, int N, int K, bool relu, cudaStream_t s, int withhold) {
+                      int64_t ldr, int64_t M, int N, int K, bool relu, cudaStream_t s, int withhold, int* err) {
     using Cf = Cfg<BN>;
     static bool attr = false;
     if (!attr) {
@@ -546,7 +547,7 @@ cudaError_t launch_tc(const __nv_bfloat16* A, int64_t lda, const __nv_bfloat16* 
     const int64_t tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
     const int grid = int(std::min<int64_t>(tiles, sm_count()));
     tc_layer_kernel<BN, OUT_BF16><<<grid, kThreads, Cf::SMEM, s>>>(ta, tw, tc, tr, scale, shift, C, ldc, R, ldr, int(M),
-                                                                    N, K, relu ? 1 : 0, withhold);
+                                                                    N, K, relu ? 1 : 0, withhold, err);
     return cudaGetLastError();
 }
 
@@ -554,12 +555,14 @@ cudaError_t launch_tc(const __nv_bfloat16* A, int64_t lda, const __nv_bfloat16* 
 
 // Hidden layer (bf16 out) or last layer (fp32 out) of the BF16 network.
 // Requirements (checked): K % 64 == 0, lda/ldw multiples of 8, 16-byte
-// aligned A and W, M < 2^31.  n_rows_w = rows stored in W (>= N).
+// aligned A and W, M < 2^31, err a device int.  n_rows_w = rows stored in W
+// (>= N).
 cudaError_t launch_layer_tc(const __nv_bfloat16* A, int64_t lda, const __nv_bfloat16* W, int64_t ldw, int n_rows_w,
                             const float* scale, const float* shift, void* C, int64_t ldc, bool out_bf16,
                             const __nv_bfloat16* R, int64_t ldr, int64_t M, int N, int K, bool relu,
-                            cudaStream_t s, int withhold_first_load) {
+                            cudaStream_t s, int* err, int withhold_first_load) {
     if (M <= 0) return cudaSuccess;
+    if (!err) return cudaErrorInvalidValue;
     if (K % BK || lda % 8 || ldw % 8 || (reinterpret_cast<uintptr_t>(A) & 15) ||
         (reinterpret_cast<uintptr_t>(W) & 15) || M >= (int64_t(1) << 31) || n_rows_w < N)
         return cudaErrorInvalidValue;
@@ -567,21 +570,27 @@ cudaError_t launch_layer_tc(const __nv_bfloat16* A, int64_t lda, const __nv_bflo
         return cudaErrorInvalidValue;
     if (N <= 96)
         return out_bf16 ? launch_tc<96, true>(A, lda, W, ldw, n_rows_w, scale, shift, C, ldc, R, ldr, M, N, K, relu, s,
-                                              withhold_first_load)
+                                              withhold_first_load, err)
                         : launch_tc<96, false>(A, lda, W, ldw, n_rows_w, scale, shift, C, ldc, R, ldr, M, N, K, relu, s,
-                                               withhold_first_load);
+                                               withhold_first_load, err);
     return out_bf16 ? launch_tc<256, true>(A, lda, W, ldw, n_rows_w, scale, shift, C, ldc, R, ldr, M, N, K, relu, s,
-                                           withhold_first_load)
+                                           withhold_first_load, err)
                     : launch_tc<256, false>(A, lda, W, ldw, n_rows_w, scale, shift, C, ldc, R, ldr, M, N, K, relu, s,
-                                            withhold_first_load);
+                                            withhold_first_load, err);
 }
 
-// Read and clear the error flag of the tensor-core kernels (synchronous).
-cudaError_t read_tc_error(int* code) {
-    int zero = 0;
-    cudaError_t e = cudaMemcpyFromSymbol(code, tc_error, sizeof(int));
+// Read and clear an error word of the tensor-core kernels, in order on
+// stream s (synchronises s).
+cudaError_t read_tc_error(int* err, cudaStream_t s, int* code) {
+    *code = 0;
+    if (!err) return cudaSuccess;
+    cudaError_t e = cudaMemcpyAsync(code, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return e;
-    if (*code) e = cudaMemcpyToSymbol(tc_error, &zero, sizeof(int));
+    if (*code) {
+        e = cudaMemsetAsync(err, 0, sizeof(int), s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
     return e;
 }
 

@@ -166,6 +166,7 @@ struct dnnmg_trainer {
     std::vector<const float*> bias;   // bias pointers of the last forward
     void *dZ = nullptr, *dH[2] = {nullptr, nullptr}, *T1 = nullptr, *T2 = nullptr;
     float *ones = nullptr, *zeros = nullptr, *part = nullptr;
+    int* tc_err = nullptr;            // device word of the tensor-core kernels' bounded waits
     int maxpad = 0;
     std::vector<void*> allocs;
     size_t es() const { return precision == DNNMG_BF16 ? 2 : 4; }
@@ -188,7 +189,7 @@ cudaError_t gemm(dnnmg_trainer* t, const void* A, int64_t lda, const void* W, in
                  int64_t M, int N, int K, bool relu) {
     if (t->precision == DNNMG_BF16)
         return launch_layer_tc((const __nv_bfloat16*)A, lda, (const __nv_bfloat16*)W, ldw, n_rows_w, scale, shift, C,
-                               ldc, out_act, (const __nv_bfloat16*)R, ldr, M, N, K, relu, t->stream);
+                               ldc, out_act, (const __nv_bfloat16*)R, ldr, M, N, K, relu, t->stream, t->tc_err);
     // FP32: activations and gradients all float
     return launch_layer_simt((const float*)A, lda, (const float*)W, ldw, scale, shift, (float*)C, ldc, (const float*)R,
                              ldr, M, N, K, relu, t->stream);
@@ -316,6 +317,8 @@ dnnmg_status dnnmg_trainer_create(const dnnmg_net_desc* net, int32_t precision, 
     };
     void* p;
     dnnmg_status st;
+    if ((st = talloc(t, sizeof(int), &p, true)) != DNNMG_OK) return fail(st);
+    t->tc_err = static_cast<int*>(p);
     t->Wb.resize(L);
     t->WT.resize(L);
     t->H.assign(L, nullptr);

@@ -124,7 +124,7 @@ class Server:
         self.reserved = 0
         self.rows_reserved = 0
         self.admission_s = 0.0       # host time the step loop spent admitting
-        self.failures = {}           # request name -> why its context could not be built
+        self.failures = {}           # request name -> why it failed (context build, network wait)
 
     # -- admission -----------------------------------------------------------
     def submit(self, req: Request):
@@ -239,6 +239,20 @@ class Server:
                 s.ev_end.record(s.stream)
         for s in self.live:
             s.ev_end.synchronize()
+        try:
+            capi.dnnmg_sync(self.net)               # the shared network's bounded waits (stream done)
+        except capi.DnnmgError as e:
+            if e.status != -6:
+                raise
+            # an expired wait left Y invalid: every simulation of this step
+            # took a wrong correction, so all of them fail
+            for s in list(self.live):
+                self.live.remove(s)
+                self.used -= s.mem
+                s.path.close()
+                self.log.append(("failed", s.req.name, now))
+                self.failures[s.req.name] = str(e)
+            return 0
         dt = time.perf_counter() - t0
         self.step_latencies.append(dt)
         self.patches += off

@@ -68,3 +68,9 @@ def test_product_package_does_not_import_the_oracle():
 
 def test_build_targets_sm103a_only():
     assert build.ARCH_FLAGS == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_noalloc_limit_matches_header():
+    src = open(os.path.join(ROOT, "include", "dnnmg.h")).read()
+    m = re.search(r"#define\s+DNNMG_NOALLOC_MAX_PATCHES\s+(\d+)", src)
+    assert m and int(m.group(1)) == capi.NOALLOC_MAX_PATCHES

@@ -123,6 +123,55 @@ def test_tensor_core_wait_expiry_is_reported_and_recovered():
     p.close()
 
 
+def test_wait_expiry_in_a_whole_time_step_is_reported_by_that_step_only():
+    # an expiry inside dnnmg_time_step is returned by that call (its
+    # correction feeds the next coarse solve), and recorded in the context's
+    # own error word: a second simulation on the same device that runs its
+    # network meanwhile reports nothing and computes what it computes alone
+    m = I.cavity_mesh(4)
+    widths = (228, 256, 256, 81)
+    Ws, ss, ts = I.network_weights(widths, seed=1)
+    Ws[-1] = 0.05 * Ws[-1]
+    prm = capi.dnnmg_solver_defaults(newton_rtol=1e-9, newton_atol=1e-10)
+    ref = TimeLoop(m, 0.01, 0.01, 1.0, "bf16", widths, Ws, ss, ts, solver=prm).start().advance(2)
+    a = TimeLoop(m, 0.01, 0.01, 1.0, "bf16", widths, Ws, ss, ts, solver=prm).start()
+    b = TimeLoop(m, 0.01, 0.01, 1.0, "bf16", widths, Ws, ss, ts, solver=prm).start()
+    a.advance(1)
+    capi.dnnmg_arm_wait_test(a.path.ctx)
+    with pytest.raises(capi.DnnmgError) as e:
+        a.advance(1)
+    assert e.value.status == -6
+    b.advance(2)
+    capi.dnnmg_sync(b.path.ctx, 10_000_000)
+    assert torch.equal(b.x, ref.x) and torch.equal(b.F, ref.F)
+    # the failed context still works: restart it and repeat the reference
+    a.start().advance(2)
+    assert torch.equal(a.x, ref.x) and torch.equal(a.F, ref.F)
+    for t in (ref, a, b):
+        t.close()
+
+
+def test_host_step_reports_a_wait_expiry():
+    m = I.cavity_mesh(4)
+    widths = (228, 256, 256, 81)
+    Ws, ss, ts = I.network_weights(widths, seed=1)
+    p = PatchPath(m, 0.01, 0.01, 1.0, "bf16")
+    p.set_network(widths, Ws, ss, ts)
+    xc = torch.as_tensor(I.coarse_state(m, seed=1), dtype=torch.float32).pin_memory()
+    F = torch.zeros((p.n_fine, 4), dtype=torch.float32).pin_memory()
+    bf = torch.zeros_like(F)
+    bc = torch.zeros((p.n_coarse, 4), dtype=torch.float32).pin_memory()
+    capi.dnnmg_patch_step_host(p.ctx, xc, F, bf, bc)
+    ok_bf = bf.clone()
+    capi.dnnmg_arm_wait_test(p.ctx)
+    with pytest.raises(capi.DnnmgError) as e:
+        capi.dnnmg_patch_step_host(p.ctx, xc, F, bf, bc)
+    assert e.value.status == -6
+    capi.dnnmg_patch_step_host(p.ctx, xc, F, bf, bc)
+    assert torch.equal(bf, ok_bf)
+    p.close()
+
+
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 def test_misaligned_fields_are_refused_and_element_aligned_slices_read_alike(precision):
     # [n][4] fields move 4 values at a time and X rows in 16-byte pieces: a

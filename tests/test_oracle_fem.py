@@ -1,6 +1,8 @@
 """Pins of the oracle's Q1/Q1-LPS operator, right-hand side and transfer
 against closed forms, a manufactured solution, finite differences and the
 Galerkin identities of nested spaces."""
+import math
+
 import numpy as np
 import pytest
 
@@ -237,3 +239,87 @@ def test_brute_force_assembled_matrix_matches_matrix_free_operator():
     xp[:, 3] = rng.standard_normal(lev.n)
     Ao = lev.operator(xp, prm).ravel()
     assert np.abs(Ao - Jb @ xp.ravel()).max() <= 1e-12 * np.abs(Ao).max()
+
+
+# ---- closed-form values of the local projection terms (Eqs. (5), (8)) ------
+# One group: the unit cube split into 8 children of side 1/2; group node
+# iota = a + 3b + 9c sits at (a, b, c) / 2.  Every child has diameter
+# h_T = sqrt(3)/2, so nu / h_T^2 = 4 nu / 3.  The fields below are piecewise
+# linear in each child with integrands of degree <= 3 per direction, so the
+# 2 x 2 x 2 Gauss rule integrates them exactly and the values follow by hand.
+_NU, _M, _A0, _D0 = 0.3, 2.0, 0.02, 0.1
+_HT = math.sqrt(3.0) / 2.0
+
+
+def _unit_group():
+    a, b, c = np.meshgrid(np.arange(3), np.arange(3), np.arange(3), indexing="ij")
+    pos = np.stack([a.T.ravel(), b.T.ravel(), c.T.ravel()], axis=1) / 2.0   # iota = a + 3b + 9c
+    return pos[None]
+
+
+def test_lps_pressure_term_closed_form():
+    # v = 0, p = 1 at the centre node (iota 13), 0 elsewhere: pi p = 0, so
+    # p - pi p is the centre's fine hat function.  With v = 0 every child has
+    # alpha_T = alpha0 / (nu / h_T^2 + m).  Rows of the pressure test
+    # functions xi_i - pi xi_i (Q1 stiffness on a cube of side s: diagonal
+    # s/3, face diagonal -s/12, edge neighbour 0; the parent-trilinear part
+    # of a corner's test function is orthogonal to the centre hat):
+    #   centre        8 children x (1/2)/3            =  4/3  alpha_T
+    #   face centre   edge neighbours in 4 children    =  0
+    #   edge midpoint face diagonals in 2 children     = -1/12 alpha_T
+    #   corner        space diagonal in 1 child        = -1/24 alpha_T
+    X = _unit_group()
+    U = np.zeros((1, 27, 4))
+    U[0, 13, 3] = 1.0
+    R = fem.group_lps(X, U, _M, _NU, _A0, _D0)[0]
+    aT = _A0 / (_NU / _HT ** 2 + _M)
+    want = np.zeros(27)
+    for i in range(27):
+        ones = sum(1 for v in (i % 3, (i // 3) % 3, i // 9) if v == 1)   # coordinates at 1/2
+        want[i] = {3: 4.0 / 3.0, 2: 0.0, 1: -1.0 / 12.0, 0: -1.0 / 24.0}[ones] * aT
+    np.testing.assert_allclose(R[:, 3], want, rtol=1e-13, atol=1e-16)
+    np.testing.assert_array_equal(R[:, 0:3], 0.0)
+    assert abs(R[:, 3].sum()) < 1e-15          # test functions xi - pi xi sum to 0
+
+
+def test_lps_convection_term_closed_form():
+    # v = (f(x), 0, 0), f piecewise linear with nodal values f(0) = 0,
+    # f(1/2) = 3/2, f(1) = 1, i.e. f = x + 2 psi(x) with psi the hat at 1/2;
+    # p = 0.  Then pi v = (x, 0, 0) and
+    #   g = v.grad v - pi v.grad pi v = (f f' - x) e_x = 8x e_x (x < 1/2),
+    #                                                   -2 e_x (x > 1/2).
+    # |v|_inf = 3/2 in every child, so delta_T = delta0 / (nu/h^2 + 1.5/h + m).
+    # The velocity rows tested against a nodal vector q give
+    # delta_T (g, v.grad q - pi v.grad pi q):
+    #   q = f: (g, g)                          = 64/24 + 2   = 14/3
+    #   q = x: (g, f - x) = (g, 2 psi)         = 2/3 - 1/2   = 1/6
+    # and the v, w rows vanish.
+    X = _unit_group()
+    x = X[0, :, 0]
+    f = np.where(x == 0.5, 1.5, np.where(x == 1.0, 1.0, 0.0))
+    U = np.zeros((1, 27, 4))
+    U[0, :, 0] = f
+    R = fem.group_lps(X, U, _M, _NU, _A0, _D0)[0]
+    dT = _D0 / (_NU / _HT ** 2 + 1.5 / _HT + _M)
+    assert f @ R[:, 0] == pytest.approx(dT * 14.0 / 3.0, rel=1e-13)
+    assert x @ R[:, 0] == pytest.approx(dT / 6.0, rel=1e-12)
+    np.testing.assert_allclose(R[:, 1:4], 0.0, atol=1e-16)
+
+
+def test_lps_parameters_scale_as_eq8():
+    # alpha_T and delta_T of Eq. (8) as functions of nu, m and |v|: the term
+    # is linear in alpha0 / delta0 and every other factor is fixed by the
+    # fields, so the ratio of two evaluations is the ratio of the
+    # denominators nu / h_T^2 + |v|_inf / h_T + m
+    X = _unit_group()
+    x = X[0, :, 0]
+    U = np.zeros((1, 27, 4))
+    U[0, :, 0] = np.where(x == 0.5, 1.5, np.where(x == 1.0, 1.0, 0.0))
+    U[0, 13, 3] = 1.0
+    for (nu1, m1), (nu2, m2) in [((0.3, 2.0), (0.03, 2.0)), ((0.3, 2.0), (0.3, 50.0))]:
+        R1 = fem.group_lps(X, U, m1, nu1, _A0, _D0)[0]
+        R2 = fem.group_lps(X, U, m2, nu2, _A0, _D0)[0]
+        den = lambda nu, m: nu / _HT ** 2 + 1.5 / _HT + m   # noqa: E731
+        ratio = den(nu2, m2) / den(nu1, m1)
+        np.testing.assert_allclose(R2[:, 0] * ratio, R1[:, 0], rtol=1e-12, atol=1e-18)
+        np.testing.assert_allclose(R2[:, 3] * ratio, R1[:, 3], rtol=1e-12, atol=1e-18)
