@@ -318,12 +318,13 @@ def run_ours(args, rank, world, local_rank):
             torch.cuda.synchronize(dev)
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            q.step(xq, Fq, bfq, bcq)
+            for _ in range(3):
+                q.step(xq, Fq, bfq, bcq)
             b.record(stream)
             torch.cuda.synchronize(dev)
-        ms = a.elapsed_time(b)
+        ms = a.elapsed_time(b) / 3
         fp64 = {"ms_per_step": round(ms, 3), "steps_per_s": round(1000.0 / ms, 4),
-                "patches_per_s": round(nc * 1000.0 / ms, 1), "timed_steps": 1}
+                "patches_per_s": round(nc * 1000.0 / ms, 1), "timed_steps": 3}
         q.close()
 
     # the FP32 form (FP32 fields, FP32 SIMT network) of the same step
@@ -485,73 +486,217 @@ def run_serving(args):
     print(json.dumps(line))
 
 
-def equal_error(steps=20):
-    """Velocity error of the DNN-MG time loop in the BF16 form and in the plain
-    FP64 form against a fine-level reference (the plain scheme on level L+1),
-    on the cavity workload (8^3 -> 16^3, Re 100, backward Euler dt 0.01,
-    20 steps, network 228-256-256-81 from seed 0 with the last layer scaled by
-    0.05 as a stand-in for a trained network's small corrections).  Errors are
-    l2 norms over the fine nodes after `steps` steps (E_v of Sec. 6.5 at one
-    time).  Also the rate of whole DNN-MG time steps (GPU Newton-GMRES coarse
-    solve + patch correction) of each form, steps 2..steps timed with CUDA
-    events, beside the plain coarse scheme and the fine-level scheme."""
+def _fine_initial(p, m, x0):
+    """The prolongated initial coarse state with the fine Dirichlet data."""
+    import numpy as np
+    import torch
+    from paper_2307_14837_gb300 import capi, inputs as I
+    kind = p.mesh_data(capi.FINE_KIND)
+    dirf = (kind == 1) | (kind == 2)
+    xr = p.prolongate(torch.as_tensor(x0, device="cuda")).cpu().numpy()
+    xr[dirf, 0:3] = I.dirichlet_values(m, p.mesh_data(capi.FINE_XYZ), kind)[dirf]
+    return torch.as_tensor(xr, device="cuda")
+
+
+def equal_error(steps=20, train_steps=8, epochs=300):
+    """Velocity error against the fine-mesh solution of the plain coarse
+    scheme and of DNN-MG in the FP64 and BF16 forms, with a network trained
+    on the project's own fine solves (the learned part, Sec. 6.4), on the
+    cavity workload: 8^3 -> 16^3, Re 100 (nu = 0.01), backward Euler
+    dt = 0.01, 20 steps, network 228-256-256-81.
+
+    Training: fine-level (L+1) trajectories at nu = 0.008 and 0.0125
+    (train_steps steps each) by the GPU Newton-GMRES-multigrid solver, BF16
+    training kernels, AdamW (lr 1e-3, weight decay 1e-5), `epochs` epochs of
+    batches of 1024.  Evaluation at the held-out nu = 0.01.
+
+    Errors (Sec. 6.5-6.6): e_v(n) = |v~_n + d_n - v_n| / |v_n| over the fine
+    nodes' velocities (d = 0 for the plain scheme) and the time-integrated
+    E_v = (sum_n |v~_n + d_n - v_n|^2 dt / sum_n |v_n|^2 dt)^(1/2).
+    Rates: whole time steps (coarse Newton-GMRES-multigrid solve + patch
+    correction), steps 2..steps timed with CUDA events."""
+    import numpy as np
+    import torch
+
+    from paper_2307_14837_gb300 import capi, inputs as I
+    from paper_2307_14837_gb300 import train as T
+    from paper_2307_14837_gb300.path import PatchPath
+
+    t0 = time.perf_counter()
+    m = I.cavity_mesh(8, levels=2)
+    dt, nu = 0.01, 0.01
+    widths = (228, 256, 256, 81)
+    solver = lambda: capi.dnnmg_solver_defaults(mg_levels=3)   # noqa: E731
+    Xs, Ts = [], []
+    for nu_t in (0.008, 0.0125):
+        X, Tg, _ = T.make_samples(m, nu_t, dt, 1.0, train_steps, solver=solver())
+        Xs.append(X)
+        Ts.append(Tg)
+    X, Tg = torch.cat(Xs), torch.cat(Ts)
+    norm = T.fit_normalization(X, Tg)
+    Xn, Tn = T.normalize(X, norm, Tg)
+    net = T.PatchNet(widths, precision="bf16", max_batch=4096, seed=0)
+    hist = T.train(net, Xn, Tn, epochs=epochs, batch=1024, lr=1e-3, weight_decay=1e-5)
+    Ws, ss, ts = net.export(norm)
+    net.close()
+    t_train = time.perf_counter() - t0
+
+    dirc = (m["vertex_bc"] == 1) | (m["vertex_bc"] == 2)
+    x0 = np.zeros((m.n_vertices, 4))
+    x0[dirc, 0:3] = I.dirichlet_values(m, m["xyz"], m["vertex_bc"])[dirc]
+    ev = torch.cuda.Event
+
+    def timed_steps(step):
+        """run `steps` steps, record the fine velocity after each; time 2.."""
+        out, ms = [], 0.0
+        for k in range(steps):
+            a, b = ev(enable_timing=True), ev(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record()
+            v = step()
+            b.record()
+            torch.cuda.synchronize()
+            if k > 0:
+                ms += a.elapsed_time(b)
+            out.append(v().double().cpu().numpy())
+        return out, round(1000.0 * (steps - 1) / ms, 2)
+
+    vel, rate, stats = {}, {}, {}
+    # fine reference: the plain scheme on level L+1
+    p = PatchPath(m, nu, dt, 1.0, "fp64")
+    xr = _fine_initial(p, m, x0)
+    prm = solver()
+
+    def fine_step():
+        stats.setdefault("fine", []).append(capi.dnnmg_plain_step(p.ctx, capi.LEVEL_FINE, 1, xr, prm))
+        return lambda: xr[:, 0:3]
+
+    vel["fine"], rate["plain_fine_fp64"] = timed_steps(fine_step)
+    xp = torch.as_tensor(x0, device="cuda")
+
+    def coarse_step():
+        stats.setdefault("plain_coarse", []).append(capi.dnnmg_plain_step(p.ctx, capi.LEVEL_COARSE, 1, xp, prm))
+        return lambda: p.prolongate(xp)[:, 0:3]
+
+    vel["plain_coarse"], rate["plain_coarse_fp64"] = timed_steps(coarse_step)
+    p.close()
+    for prec in ("fp64", "bf16"):
+        p = PatchPath(m, nu, dt, 1.0, prec)
+        p.set_network(widths, Ws, ss, ts)
+        x = torch.as_tensor(x0, device="cuda")
+        bf, bcf = p.rhs_restrict(x.to(p.dtype), torch.zeros((p.n_fine, 3), dtype=p.dtype, device="cuda"))
+        bc = bcf.double().contiguous()
+        prm = solver()
+
+        def dnnmg_step():
+            stats.setdefault(f"dnnmg_{prec}", []).append(capi.dnnmg_time_step(p.ctx, 1, x, bc, bf, prm))
+
+            def corrected():          # P x^L + d, evaluated after the timed step
+                d = p.field(p.n_fine, 3)
+                capi.dnnmg_extend(p.ctx, capi.dnnmg_get_buffer(p.ctx, capi.BUF_Y), d)
+                return p.prolongate(x.to(p.dtype))[:, 0:3] + d
+            return corrected
+
+        vel[f"dnnmg_{prec}"], rate[f"dnnmg_{prec}"] = timed_steps(dnnmg_step)
+        p.close()
+    ref = vel["fine"]
+    out = {"workload": "cavity 8^3->16^3 (nested: multigrid 8^3, 4^3, 2^3), Re 100, BE dt 0.01, "
+                       f"{steps} steps; network 228-256-256-81 trained on the GPU (BF16 kernels, AdamW) on "
+                       f"fine-level solves at nu 0.008 and 0.0125 ({train_steps} steps each, "
+                       f"{X.shape[0]} samples, {epochs} epochs), evaluated at nu 0.01",
+           "reference": "plain scheme on level L+1 (GPU Newton-GMRES-multigrid, FP64)",
+           "train_loss_first_last": [hist[0], hist[-1]], "train_seconds": round(t_train, 2)}
+    den = sum(float(np.sum(r ** 2)) for r in ref)
+    for k in ("plain_coarse", "dnnmg_fp64", "dnnmg_bf16"):
+        err = [float(np.linalg.norm(v - r)) for v, r in zip(vel[k], ref)]
+        out[k] = {"e_v_last": err[-1] / float(np.linalg.norm(ref[-1])),
+                  "e_v": [round(e / float(np.linalg.norm(r)), 6) for e, r in zip(err, ref)],
+                  "E_v": (sum(e * e for e in err) / den) ** 0.5,
+                  "newton_gmres_per_step": [round(sum(s["newton_iterations"] for s in stats[k]) / steps, 2),
+                                            round(sum(s["gmres_iterations"] for s in stats[k]) / steps, 2)]}
+    e64, e16, epl = out["dnnmg_fp64"]["E_v"], out["dnnmg_bf16"]["E_v"], out["plain_coarse"]["E_v"]
+    out["E_v_bf16_vs_fp64_relative_difference"] = abs(e16 - e64) / e64
+    out["E_v_dnnmg_over_plain_coarse"] = {"fp64": e64 / epl, "bf16": e16 / epl}
+    out["time_steps_per_s"] = rate
+    out["seconds"] = round(time.perf_counter() - t0, 2)
+    return out
+
+
+WHOLE_NZ, WHOLE_LEVELS = 16, 3
+
+
+def whole_steps(steps=10, nz=WHOLE_NZ, levels=WHOLE_LEVELS):
+    """Whole DNN-MG time steps (Alg. 1: the coarse Newton-GMRES-multigrid
+    solve, then the patch correction) on the nested channel: nz = 16 layers
+    as the 3rd refinement of the nz = 2 channel, 65,536 coarse hex (level L)
+    and 524,288 fine hex (level L+1), seeded cylinder, Re 200, Crank-Nicolson
+    dt = 0.005, an impulsive start from rest with the full inflow.  Forms: FP32
+    fields with the FP32 SIMT network 228-512x3-81, and FP32 fields with the
+    BF16 tensor-core network 228-1024x4-81; random-init weights of those
+    architectures (seed 0, last layer x 0.05).  Beside them the plain coarse
+    scheme (the same solver, no correction).  The multigrid V-cycle runs
+    over levels L, L-1, L-2 and the base (nz = 2, 128 hex) with 4 + 4 Vanka
+    sweeps damped by 0.8; the first step (which builds the solver) is not timed; `steps`
+    steps are timed with CUDA events."""
     import numpy as np
     import torch
 
     from paper_2307_14837_gb300 import capi, inputs as I
     from paper_2307_14837_gb300.path import PatchPath
 
-    m = I.cavity_mesh(8)
-    widths = (228, 256, 256, 81)
-    Ws, ss, ts = I.network_weights(widths, seed=0)
-    Ws[-1] = 0.05 * Ws[-1]
-    bcv = I.dirichlet_values(m, m["xyz"], m["vertex_bc"])
+    t_start = time.perf_counter()
+    m = I.channel_mesh(nz, seed=0, levels=levels)
+    nu = m["meta"]["nu_re200"]
     dirc = (m["vertex_bc"] == 1) | (m["vertex_bc"] == 2)
-    x0 = np.zeros((m.n_vertices, 4))
-    x0[dirc, 0:3] = bcv[dirc]
-    res, rate, t0 = {}, {}, time.perf_counter()
-    ref = None
 
-    def timed(fn):
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    def initial(t):
+        x0 = np.zeros((m.n_vertices, 4))
+        x0[dirc, 0:3] = I.dirichlet_values(m, m["xyz"], m["vertex_bc"], t)[dirc]
+        return x0
+
+    prm = lambda: capi.dnnmg_solver_defaults(mg_levels=levels, mg_pre=4, mg_post=4, mg_omega=0.8,  # noqa: E731
+                                             newton_rtol=1e-9, newton_atol=1e-10, gmres_rtol=1e-8)
+    out = {"workload": f"channel nz={nz} nested ({levels} refinements of nz={nz >> levels}): "
+                       f"{m.n_cells} coarse hex, {8 * m.n_cells} fine hex; Re 200, CN dt={DT}; "
+                       f"{steps} timed whole time steps after 1 untimed",
+           "forms": {}}
+    for name, prec, widths in (("fp32_228_512x3_81", "fp32", (228, 512, 512, 512, 81)),
+                               ("bf16_228_1024x4_81", "bf16", WIDTHS), ("plain_coarse", "fp32", None)):
+        p = PatchPath(m, nu, DT, THETA, prec)
+        x = torch.as_tensor(initial(1.0), device="cuda")
+        sp = prm()
+        stats = []
+        if widths is not None:
+            Ws, ss, ts = I.network_weights(widths, seed=0)
+            Ws[-1] = 0.05 * Ws[-1]
+            p.set_network(widths, Ws, ss, ts, skip=True)
+            bf, bcf = p.rhs_restrict(x.to(p.dtype), torch.zeros((p.n_fine, 3), dtype=p.dtype, device="cuda"))
+            bc = bcf.double().contiguous()
+            step = lambda: stats.append(capi.dnnmg_time_step(p.ctx, 1, x, bc, bf, sp))   # noqa: E731
+        else:
+            step = lambda: stats.append(capi.dnnmg_plain_step(p.ctx, capi.LEVEL_COARSE, 1, x, sp))  # noqa: E731
+        step()
         torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
-        fn()
+        for _ in range(steps):
+            step()
         b.record()
         torch.cuda.synchronize()
-        return a.elapsed_time(b)
-
-    for prec in ("fp64", "bf16"):
-        p = PatchPath(m, 0.01, 0.01, 1.0, prec)
-        p.set_network(widths, Ws, ss, ts)
-        x = torch.as_tensor(x0, device="cuda")
-        bf, bcf = p.rhs_restrict(x.to(p.dtype), torch.zeros((p.n_fine, 3), dtype=p.dtype, device="cuda"))
-        bc = bcf.double().contiguous()
-        capi.dnnmg_time_step(p.ctx, 1, x, bc, bf)          # first step: builds the coarse solver level
-        ms = timed(lambda: capi.dnnmg_time_step(p.ctx, steps - 1, x, bc, bf))
-        rate[f"dnnmg_{prec}"] = round(1000.0 * (steps - 1) / ms, 2)
-        res[prec] = p.prolongate(x.to(p.dtype)).double().cpu().numpy()
-        if ref is None:
-            kind = p.mesh_data(capi.FINE_KIND)
-            dirf = (kind == 1) | (kind == 2)
-            xr = p.prolongate(torch.as_tensor(x0, device="cuda")).cpu().numpy()
-            xr[dirf, 0:3] = I.dirichlet_values(m, p.mesh_data(capi.FINE_XYZ), kind)[dirf]
-            xr = torch.as_tensor(xr, device="cuda")
-            capi.dnnmg_plain_step(p.ctx, capi.LEVEL_FINE, 1, xr)
-            ms = timed(lambda: capi.dnnmg_plain_step(p.ctx, capi.LEVEL_FINE, steps - 1, xr))
-            rate["plain_fine_fp64"] = round(1000.0 * (steps - 1) / ms, 2)
-            ref = xr.cpu().numpy()
-            xp = torch.as_tensor(x0, device="cuda")
-            capi.dnnmg_plain_step(p.ctx, capi.LEVEL_COARSE, 1, xp)
-            ms = timed(lambda: capi.dnnmg_plain_step(p.ctx, capi.LEVEL_COARSE, steps - 1, xp))
-            rate["plain_coarse_fp64"] = round(1000.0 * (steps - 1) / ms, 2)
+        ms = a.elapsed_time(b) / steps
+        timed = stats[1:]
+        out["forms"][name] = {
+            "ms_per_step": round(ms, 2), "steps_per_s": round(1000.0 / ms, 3),
+            "patches_per_s": round(m.n_cells * 1000.0 / ms, 1) if widths is not None else None,
+            "newton_per_step": round(sum(s_["newton_iterations"] for s_ in timed) / steps, 2),
+            "gmres_per_newton": round(sum(s_["gmres_iterations"] for s_ in timed) /
+                                      max(1, sum(s_["newton_iterations"] for s_ in timed)), 2),
+            "jacobians_per_step": round(sum(s_["jacobian_assemblies"] for s_ in timed) / steps, 2),
+            "converged": all(s_["converged"] for s_ in timed)}
+        out["multigrid_nodes"] = capi.dnnmg_level_mg(p.ctx, capi.LEVEL_COARSE, sp)
         p.close()
-    e = {k: float(np.linalg.norm(v[:, 0:3] - ref[:, 0:3])) for k, v in res.items()}
-    return {"workload": "cavity 8^3->16^3, Re 100, BE dt 0.01, 228-256-256-81 (last layer x0.05), "
-                        f"{steps} DNN-MG steps vs plain scheme on level L+1",
-            "e_v_fp64": e["fp64"], "e_v_bf16": e["bf16"],
-            "relative_difference": abs(e["bf16"] - e["fp64"]) / e["fp64"],
-            "time_steps_per_s": rate, "seconds": time.perf_counter() - t0}
+    out["seconds"] = round(time.perf_counter() - t_start, 2)
+    return out
 
 
 class OracleSample:
@@ -654,6 +799,7 @@ def main():
     line = result_line(res, args, world, el)
     if not args.no_fp64:
         line["equal_error"] = equal_error()
+        line["whole_time_steps"] = whole_steps()
     if not args.no_cpu_baseline:
         o = OracleSample(nz=10)
         secs, n = 0.0, 0

@@ -66,7 +66,7 @@
 extern "C" {
 #endif
 
-#define DNNMG_ABI_VERSION 3
+#define DNNMG_ABI_VERSION 4
 
 typedef struct dnnmg_ctx dnnmg_ctx;
 
@@ -320,12 +320,25 @@ int64_t dnnmg_launch_count(const dnnmg_ctx* ctx);
  * patches are its groups), used as the fine-mesh reference.  Level fields are
  * double [n_nodes][4] (u, v, w, p) device arrays in every precision form.
  *
- * The solver (FP64): Newton with the exact Jacobian of A_h (stabilisation
+ * The solver: Newton with the exact Jacobian of A_h (stabilisation
  * parameters frozen, Sec. 3.4), re-assembled when the residual rate exceeds
- * rho_max; restarted GMRES, right-preconditioned by additive group-Vanka (the
- * 108 x 108 local problems of the 27-node groups, LU-factorised).  The paper
- * uses GMRES with geometric multigrid and a Vanka smoother and allows any
- * coarse solver (Sec. 3). */
+ * rho_max; flexible restarted GMRES in FP64 (vectors, Gram-Schmidt, norms
+ * and Givens rotations on the device), right-preconditioned by geometric
+ * multigrid as in Sec. 3.4: a V-cycle over coarser levels with damped
+ * additive group-Vanka smoothing (the 108 x 108 local problems of the
+ * 27-node groups, LU-factorised) in FP32, and a dense LU with partial
+ * pivoting in FP64 on the coarsest level.  The Jacobian is assembled in FP32
+ * on the solve and smoothing levels and in FP64 on the coarsest.
+ * Multigrid levels: each coarser level is made of the parents of the groups
+ * of the level above, which needs a mesh whose cells come in groups of 8
+ * children recursively and whose vertices are numbered coarsest level first
+ * (level L+1 over level L always qualifies); mg_levels caps the depth, and
+ * the hierarchy stops where a level cannot be coarsened or where the next
+ * coarser level would have fewer than 8 nodes of free velocity (its
+ * continuity rows would then see almost no velocity).  A coarsest level
+ * without parents takes the stabilisation terms with full fluctuations (the
+ * projection taken as zero).  With mg_levels = 0 the preconditioner is one
+ * group-Vanka application. */
 enum { DNNMG_LEVEL_COARSE = 0, DNNMG_LEVEL_FINE = 1 };
 
 typedef struct {
@@ -335,9 +348,17 @@ typedef struct {
     int32_t newton_max;
     int32_t gmres_restart;   /* Krylov dimension per cycle (fixed at first use of a level) */
     int32_t gmres_max;       /* GMRES iterations per Newton step */
-    int32_t reserved;        /* must be 0 */
+    int32_t mg_levels;       /* coarser multigrid levels below the solve level, at most
+                              * (fixed at first use of a level); 0 = one-level Vanka */
     double gmres_rtol;
     double rho_max;          /* Jacobian re-assembly threshold, 0.1 or 0.05 in the paper */
+    int32_t mg_pre, mg_post; /* Vanka sweeps before and after the coarse-grid correction */
+    double mg_omega;         /* damping of the Vanka sweeps */
+    int32_t mg_smoother;     /* 0 additive group-Vanka (local solutions averaged over the
+                              * groups sharing a node); 1 multiplicative: groups in colours
+                              * sharing no node, updated colour after colour (forward before,
+                              * backward after the coarse-grid correction) */
+    int32_t reserved;        /* must be 0 */
 } dnnmg_solver_params;
 
 typedef struct {
@@ -346,11 +367,24 @@ typedef struct {
 } dnnmg_solve_stats;
 
 /* Defaults: alpha0 0.02, delta0 0.1, atol 1e-11, rtol 1e-12, 25 Newton steps,
- * restart 40, 400 GMRES iterations, gmres_rtol 1e-10, rho_max 0.1. */
+ * restart 40, 400 GMRES iterations, gmres_rtol 1e-10, rho_max 0.1,
+ * mg_levels 0, 2 + 2 additive Vanka sweeps, damping 0.7. */
 void dnnmg_solver_defaults(dnnmg_solver_params* p);
 
 /* Number of nodes of a level and whether it uses the local projection. */
 dnnmg_status dnnmg_level_info(dnnmg_ctx* ctx, int32_t level, int64_t* n_nodes, int32_t* grouped);
+
+/* The multigrid hierarchy of a level as its solver built it (created with
+ * prm's gmres_restart and mg_levels on first use): *n_levels = levels
+ * including the solve level, nodes[k] = nodes of level k (0 = the solve
+ * level, then coarser) for k < max_levels. */
+dnnmg_status dnnmg_level_mg(dnnmg_ctx* ctx, int32_t level, const dnnmg_solver_params* prm, int32_t max_levels,
+                            int32_t* n_levels, int64_t* nodes);
+
+/* The same hierarchy on the host with no CUDA call (inspection and tests):
+ * level 0 or 1 as above, at most mg_levels coarser levels. */
+dnnmg_status dnnmg_hierarchy_mg(const dnnmg_hierarchy* h, int32_t level, int32_t mg_levels, int32_t max_levels,
+                                int32_t* n_levels, int64_t* nodes);
 
 /* A_h(x) of Eqs. (6), (9) on a level (no row modified).  x_dev, Ax_dev
  * double [n][4].  prm may be NULL (defaults). */
@@ -460,6 +494,15 @@ dnnmg_status dnnmg_mse_loss(int64_t batch, const float* Y_dev, const float* T_de
  * are formed in double and rounded once to fp32 for the update. */
 dnnmg_status dnnmg_adamw(int64_t n, float* w_dev, const float* g_dev, float* m_dev, float* v_dev, double lr,
                          double beta1, double beta2, double eps, double weight_decay, int32_t step, void* cuda_stream);
+
+/* Measured peak of the SIMT fused multiply-add pipe on the current device
+ * (the paper has no counterpart: a roofline denominator for the kernels
+ * bound by FP32 or FP64 arithmetic).  Every thread of blocks_per_sm x (SM
+ * count) blocks of 256 threads runs 8 independent FMA chains for `iters`
+ * rounds; the best of 3 timed launches after a warm-up, 2 flop per FMA,
+ * is returned in *tflops.  precision DNNMG_FP32 or DNNMG_FP64.  Allocates a
+ * small device buffer, a stream and two events, and synchronises. */
+dnnmg_status dnnmg_probe_fma(int32_t precision, int32_t iters, int32_t blocks_per_sm, double* tflops);
 
 /* Largest mesh dnnmg_residual_noalloc accepts (coarse cells = patches);
  * the Python binding's NOALLOC_MAX_PATCHES must equal it (a CPU test reads

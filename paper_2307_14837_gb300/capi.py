@@ -73,6 +73,8 @@ _SIGS = {
     "dnnmg_network": ([_VP, _VP, _VP, ctypes.c_int64], ctypes.c_int),
     "dnnmg_network_wait_test": ([_VP, _VP, _VP, ctypes.c_int64], ctypes.c_int),
     "dnnmg_arm_wait_test": ([_VP], ctypes.c_int),
+    "dnnmg_probe_fma": ([ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)],
+                        ctypes.c_int),
     "dnnmg_extend": ([_VP, _VP, _VP], ctypes.c_int),
     "dnnmg_rhs_restrict": ([_VP, _VP, _VP, _VP, _VP], ctypes.c_int),
     "dnnmg_patch_step": ([_VP, _VP, _VP, _VP, _VP], ctypes.c_int),
@@ -173,6 +175,16 @@ class HostHierarchy:
         _check(None, load().dnnmg_hierarchy_data(self.handle, item, out.ctypes.data, out.nbytes))
         return out
 
+    def mg_nodes(self, level=0, mg_levels=16, max_levels=32):
+        """Nodes of every level of the multigrid hierarchy the solver would
+        build on `level` (0 coarse, 1 fine) with at most mg_levels coarser
+        levels (solve level first)."""
+        n = ctypes.c_int32()
+        nodes = np.zeros(max_levels, dtype=np.int64)
+        _check(None, load().dnnmg_hierarchy_mg(self.handle, int(level), int(mg_levels), int(max_levels),
+                                               ctypes.byref(n), nodes.ctypes.data))
+        return [int(v) for v in nodes[:min(n.value, max_levels)]]
+
     def close(self):
         if self.handle:
             load().dnnmg_hierarchy_destroy(self.handle)
@@ -252,6 +264,13 @@ def dnnmg_network_wait_test(ctx, X, Y, n_rows):
     _check(ctx, load().dnnmg_network_wait_test(ctx, _ptr(X), _ptr(Y), int(n_rows)))
 
 
+def dnnmg_probe_fma(precision, iters=4096, blocks_per_sm=8) -> float:
+    """Measured FMA throughput (TFLOP/s) of the SIMT pipe in FP32 or FP64."""
+    t = ctypes.c_double()
+    _check(None, load().dnnmg_probe_fma(int(precision), int(iters), int(blocks_per_sm), ctypes.byref(t)))
+    return t.value
+
+
 def dnnmg_arm_wait_test(ctx):
     _check(ctx, load().dnnmg_arm_wait_test(ctx))
 
@@ -306,8 +325,9 @@ LEVEL_COARSE, LEVEL_FINE = 0, 1
 class SolverParams(ctypes.Structure):
     _fields_ = [("alpha0", ctypes.c_double), ("delta0", ctypes.c_double), ("newton_atol", ctypes.c_double),
                 ("newton_rtol", ctypes.c_double), ("newton_max", ctypes.c_int32), ("gmres_restart", ctypes.c_int32),
-                ("gmres_max", ctypes.c_int32), ("reserved", ctypes.c_int32), ("gmres_rtol", ctypes.c_double),
-                ("rho_max", ctypes.c_double)]
+                ("gmres_max", ctypes.c_int32), ("mg_levels", ctypes.c_int32), ("gmres_rtol", ctypes.c_double),
+                ("rho_max", ctypes.c_double), ("mg_pre", ctypes.c_int32), ("mg_post", ctypes.c_int32),
+                ("mg_omega", ctypes.c_double), ("mg_smoother", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class SolveStats(ctypes.Structure):
@@ -330,6 +350,10 @@ _SIGS.update({
                          ctypes.POINTER(SolveStats)], ctypes.c_int),
     "dnnmg_plain_step": ([_VP, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(SolverParams), _VP,
                           ctypes.POINTER(SolveStats)], ctypes.c_int),
+    "dnnmg_level_mg": ([_VP, ctypes.c_int32, ctypes.POINTER(SolverParams), ctypes.c_int32,
+                        ctypes.POINTER(ctypes.c_int32), _VP], ctypes.c_int),
+    "dnnmg_hierarchy_mg": ([_VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                            _VP], ctypes.c_int),
 })
 ENOCONV = -4
 
@@ -344,6 +368,15 @@ def dnnmg_solver_defaults(**overrides) -> SolverParams:
 
 def _stats(s):
     return {k: getattr(s, k) for k, _ in SolveStats._fields_}
+
+
+def dnnmg_level_mg(ctx, level, prm=None, max_levels=32):
+    """Nodes of every level of the level's multigrid hierarchy (solve level first)."""
+    n = ctypes.c_int32()
+    nodes = np.zeros(max_levels, dtype=np.int64)
+    _check(ctx, load().dnnmg_level_mg(ctx, int(level), ctypes.byref(prm) if prm else None, int(max_levels),
+                                      ctypes.byref(n), nodes.ctypes.data))
+    return [int(v) for v in nodes[:min(n.value, max_levels)]]
 
 
 def dnnmg_level_info(ctx, level):

@@ -682,9 +682,33 @@ void dnnmg_solver_defaults(dnnmg_solver_params* p) {
     p->newton_max = 25;
     p->gmres_restart = 40;
     p->gmres_max = 400;
-    p->reserved = 0;
+    p->mg_levels = 0;
     p->gmres_rtol = 1e-10;
     p->rho_max = 0.1;
+    p->mg_pre = 2;
+    p->mg_post = 2;
+    p->mg_omega = 0.7;
+    p->mg_smoother = 0;
+    p->reserved = 0;
+}
+
+dnnmg_status dnnmg_hierarchy_mg(const dnnmg_hierarchy* h, int32_t level, int32_t mg_levels, int32_t max_levels,
+                                int32_t* n_levels, int64_t* nodes) {
+    if (!h || !n_levels || (level != DNNMG_LEVEL_COARSE && level != DNNMG_LEVEL_FINE) || mg_levels < 0 ||
+        max_levels < 0 || (max_levels > 0 && !nodes))
+        return DNNMG_EINVAL;
+    if (level == DNNMG_LEVEL_FINE && h->host.J != 1) return DNNMG_EUNSUPPORTED;
+    std::vector<HostLevel> lv(1);
+    build_level(h->host, level == DNNMG_LEVEL_FINE, &lv[0]);
+    for (int k = 0; k < mg_levels; ++k) {
+        HostLevel c;
+        MgTransfer t;
+        if (!coarsen_level(lv.back(), &c, &t)) break;
+        lv.push_back(std::move(c));
+    }
+    *n_levels = int32_t(lv.size());
+    for (int k = 0; k < max_levels && k < int(lv.size()); ++k) nodes[k] = lv[size_t(k)].n;
+    return DNNMG_OK;
 }
 
 }  // extern "C"
@@ -698,7 +722,12 @@ dnnmg_status get_level(dnnmg_ctx* ctx, int32_t level, const dnnmg_solver_params*
     if (!ctx->level[level]) {
         const int krylov = prm && prm->gmres_restart > 0 ? prm->gmres_restart : 40;
         if (krylov > 200) return fail(ctx, DNNMG_EINVAL, "gmres_restart > 200");
-        cudaError_t e = create_level(ctx->host, level == DNNMG_LEVEL_FINE, krylov, &ctx->level[level]);
+        const int mg = prm ? prm->mg_levels : 0;
+        if (mg < 0 || mg > 16) return fail(ctx, DNNMG_EINVAL, "mg_levels outside [0, 16]");
+        cudaError_t e = create_level(ctx->host, level == DNNMG_LEVEL_FINE, krylov, mg, &ctx->level[level]);
+        if (e == cudaErrorInvalidValue)
+            return fail(ctx, DNNMG_EINVAL, "the coarsest multigrid level is too large for the dense solve "
+                                           "(more than 8192 unknowns): allow more levels");
         if (e != cudaSuccess) return cuda_fail(ctx, e, "create_level");
     }
     *out = ctx->level[level];
@@ -761,9 +790,18 @@ dnnmg_status dnnmg_level_jacobian(dnnmg_ctx* ctx, int32_t level, const dnnmg_sol
     if (st != DNNMG_OK) return st;
     const int64_t N = 4 * level_nodes(L);
     if (N > 8192 || bytes < size_t(N) * size_t(N) * 8) return fail(ctx, DNNMG_EINVAL, "level too large for a dense Jacobian");
-    CK(ctx, level_jacobian(L, ctx->op, prm ? prm : &d, x_dev, ctx->stream));
-    CK(ctx, cudaStreamSynchronize(ctx->stream));
-    CK(ctx, level_dense_jacobian(L, dense_host));
+    CK(ctx, level_dense_jacobian(L, ctx->op, prm ? prm : &d, x_dev, dense_host, ctx->stream));
+    return DNNMG_OK;
+}
+
+dnnmg_status dnnmg_level_mg(dnnmg_ctx* ctx, int32_t level, const dnnmg_solver_params* prm, int32_t max_levels,
+                            int32_t* n_levels, int64_t* nodes) {
+    if (!ctx || ctx->net_only || !n_levels || max_levels < 0 || (max_levels > 0 && !nodes)) return DNNMG_EINVAL;
+    DeviceLevel* L;
+    dnnmg_status st = get_level(ctx, level, prm, &L);
+    if (st != DNNMG_OK) return st;
+    *n_levels = 1 + level_mg_depth(L);
+    for (int k = 0; k < max_levels && k < *n_levels; ++k) nodes[k] = level_mg_nodes(L, k);
     return DNNMG_OK;
 }
 
@@ -774,7 +812,10 @@ dnnmg_status dnnmg_solve(dnnmg_ctx* ctx, int32_t level, const dnnmg_solver_param
     dnnmg_solver_params d;
     dnnmg_solver_defaults(&d);
     if (!prm) prm = &d;
-    if (prm->reserved != 0 || prm->newton_max < 0 || prm->gmres_max < 1) return DNNMG_EINVAL;
+    if (prm->reserved != 0 || prm->mg_smoother < 0 || prm->mg_smoother > 1 || prm->newton_max < 0 || prm->gmres_max < 1 ||
+        prm->mg_pre < 0 || prm->mg_post < 0 || prm->mg_pre + prm->mg_post > 64 || !(prm->mg_omega > 0.0) ||
+        prm->mg_omega > 2.0)
+        return DNNMG_EINVAL;
     DeviceLevel* L;
     dnnmg_status st = get_level(ctx, level, prm, &L);
     if (st != DNNMG_OK) return st;

@@ -395,64 +395,32 @@ dnnmg_status build_hierarchy(const dnnmg_mesh_desc* mesh, int n_geo, int J, Host
 
 namespace dnnmg {
 
-void build_level(const HostHierarchy& h, bool fine, HostLevel* lv) {
-    if (fine) {
-        lv->n = h.n_fine;
-        lv->ng = h.nc;
-        lv->npg = 27;
-        lv->lps = true;
-        lv->groups = h.patch_map;
-        lv->xyz = h.xyz_f;
-        lv->dir.resize(size_t(h.n_fine));
-        bool outflow = false;
-        for (int64_t j = 0; j < h.n_fine; ++j) {
-            lv->dir[j] = (h.kind_f[j] == 1 || h.kind_f[j] == 2) ? 1 : 0;
-            outflow |= h.kind_f[j] == 3;
-        }
-        lv->mean_zero_pressure = !outflow;
-    } else {
-        lv->n = h.nv;
-        lv->xyz = h.xyz_c;
-        lv->dir.resize(size_t(h.nv));
-        bool outflow = false;
-        for (int64_t v = 0; v < h.nv; ++v) {
-            lv->dir[v] = (h.bc_c[v] == 1 || h.bc_c[v] == 2) ? 1 : 0;
-            outflow |= h.bc_c[v] == 3;
-        }
-        lv->mean_zero_pressure = !outflow;
-        // cells in consecutive groups of 8 children (i + 2j + 4k) of a parent?
-        bool grouped = h.nc % 8 == 0;
-        std::vector<int32_t> g27;
-        if (grouped) {
-            const int64_t ng = h.nc / 8;
-            g27.assign(size_t(27 * ng), -1);
-            for (int64_t g = 0; g < ng && grouped; ++g)
-                for (int t = 0; t < 8 && grouped; ++t)
-                    for (int k = 0; k < 8; ++k) {
-                        const int a = (t & 1) + (k & 1), b = ((t >> 1) & 1) + ((k >> 1) & 1),
-                                  c = ((t >> 2) & 1) + ((k >> 2) & 1);
-                        int32_t& slot = g27[size_t(27 * g + a + 3 * b + 9 * c)];
-                        const int32_t v = h.cells[size_t(8 * (8 * g + t) + k)];
-                        if (slot < 0)
-                            slot = v;
-                        else if (slot != v) {
-                            grouped = false;
-                            break;
-                        }
-                    }
-        }
-        if (grouped) {
-            lv->ng = h.nc / 8;
-            lv->npg = 27;
-            lv->lps = true;
-            lv->groups = g27;
-        } else {
-            lv->ng = h.nc;
-            lv->npg = 8;
-            lv->lps = false;
-            lv->groups = h.cells;
-        }
-    }
+namespace {
+
+// Cells in consecutive groups of 8 children (i + 2j + 4k) of a parent?  On
+// success g27 holds the 27 nodes of each group (iota = a + 3b + 9c).
+bool group_cells(const std::vector<int32_t>& cells, int64_t nc, std::vector<int32_t>* g27) {
+    if (nc % 8 != 0 || nc == 0) return false;
+    const int64_t ng = nc / 8;
+    g27->assign(size_t(27 * ng), -1);
+    for (int64_t g = 0; g < ng; ++g)
+        for (int t = 0; t < 8; ++t)
+            for (int k = 0; k < 8; ++k) {
+                const int a = (t & 1) + (k & 1), b = ((t >> 1) & 1) + ((k >> 1) & 1),
+                          c = ((t >> 2) & 1) + ((k >> 2) & 1);
+                int32_t& slot = (*g27)[size_t(27 * g + a + 3 * b + 9 * c)];
+                const int32_t v = cells[size_t(8 * (8 * g + t) + k)];
+                if (slot < 0)
+                    slot = v;
+                else if (slot != v)
+                    return false;
+            }
+    return true;
+}
+
+// Pinned pressure node, node CSR, block sparsity and block maps of a level
+// whose groups, nodes and Dirichlet flags are set.
+void finish_level(HostLevel* lv) {
     const int npg = lv->npg;
     const int64_t n = lv->n, ng = lv->ng;
     lv->pin = -1;
@@ -505,6 +473,160 @@ void build_level(const HostHierarchy& h, bool fine, HostLevel* lv) {
     lv->blk_ptr = cnt;
     lv->blk_src.assign(size_t(ng * npg * npg), 0);
     for (int64_t e = 0; e < ng * npg * npg; ++e) lv->blk_src[cnt[lv->grp_blk[e]]++] = int32_t(e);
+    // greedy colouring of the groups in group order: the smallest colour that
+    // no earlier group sharing a node has
+    std::vector<int32_t> color(size_t(ng), -1);
+    int ncol = 0;
+    std::vector<int64_t> seen_at;   // colour -> last group that marked it
+    for (int64_t g = 0; g < ng; ++g) {
+        for (int i = 0; i < npg; ++i) {
+            const int32_t j = lv->groups[size_t(g * npg + i)];
+            for (int32_t e = lv->node_ptr[j]; e < lv->node_ptr[j + 1]; ++e) {
+                const int32_t c = color[size_t(lv->node_idx[e] / npg)];
+                if (c >= 0) seen_at[size_t(c)] = g;
+            }
+        }
+        int c = 0;
+        while (c < ncol && seen_at[size_t(c)] == g) ++c;
+        if (c == ncol) {
+            ++ncol;
+            seen_at.push_back(-1);
+        }
+        color[size_t(g)] = c;
+    }
+    lv->color_ptr.assign(size_t(ncol + 1), 0);
+    for (int32_t c : color) lv->color_ptr[size_t(c) + 1]++;
+    for (int c = 0; c < ncol; ++c) lv->color_ptr[c + 1] += lv->color_ptr[c];
+    lv->color_groups.assign(size_t(ng), 0);
+    std::vector<int32_t> fill(lv->color_ptr.begin(), lv->color_ptr.end() - 1);
+    for (int64_t g = 0; g < ng; ++g) lv->color_groups[size_t(fill[size_t(color[size_t(g)])]++)] = int32_t(g);
+}
+
+// A level from cells: grouped (27-node groups, local projection) when its
+// cells come in groups of 8 children, else one 8-node "group" per cell.
+void level_from_cells(int64_t n, std::vector<double> xyz, std::vector<uint8_t> dir, bool mean_zero,
+                      const std::vector<int32_t>& cells, HostLevel* lv) {
+    const int64_t nc = int64_t(cells.size() / 8);
+    lv->n = n;
+    lv->xyz = std::move(xyz);
+    lv->dir = std::move(dir);
+    lv->mean_zero_pressure = mean_zero;
+    std::vector<int32_t> g27;
+    if (group_cells(cells, nc, &g27)) {
+        lv->ng = nc / 8;
+        lv->npg = 27;
+        lv->lps = true;
+        lv->groups = std::move(g27);
+    } else {
+        lv->ng = nc;
+        lv->npg = 8;
+        lv->lps = false;
+        lv->groups = cells;
+    }
+    finish_level(lv);
+}
+
+// trilinear weight of parent corner K at group node iota (reference point iota / 2)
+double corner_weight(int iota, int K) {
+    const int c[3] = {iota % 3, (iota / 3) % 3, iota / 9};
+    double w = 1.0;
+    for (int d = 0; d < 3; ++d) {
+        const double x = 0.5 * c[d];
+        w *= ((K >> d) & 1) ? x : 1.0 - x;
+    }
+    return w;
+}
+
+}  // namespace
+
+void build_level(const HostHierarchy& h, bool fine, HostLevel* lv) {
+    if (fine) {
+        lv->n = h.n_fine;
+        lv->ng = h.nc;
+        lv->npg = 27;
+        lv->lps = true;
+        lv->groups = h.patch_map;
+        lv->xyz = h.xyz_f;
+        lv->dir.resize(size_t(h.n_fine));
+        bool outflow = false;
+        for (int64_t j = 0; j < h.n_fine; ++j) {
+            lv->dir[j] = (h.kind_f[j] == 1 || h.kind_f[j] == 2) ? 1 : 0;
+            outflow |= h.kind_f[j] == 3;
+        }
+        lv->mean_zero_pressure = !outflow;
+        finish_level(lv);
+        return;
+    }
+    std::vector<uint8_t> dir(size_t(h.nv));
+    bool outflow = false;
+    for (int64_t v = 0; v < h.nv; ++v) {
+        dir[v] = (h.bc_c[v] == 1 || h.bc_c[v] == 2) ? 1 : 0;
+        outflow |= h.bc_c[v] == 3;
+    }
+    level_from_cells(h.nv, h.xyz_c, std::move(dir), !outflow, h.cells, lv);
+}
+
+bool coarsen_level(const HostLevel& f, HostLevel* c, MgTransfer* t) {
+    if (f.npg != 27 || f.ng == 0) return false;
+    const int64_t ng = f.ng;
+    // parent cells: the 8 corners of each group; they must be the nodes
+    // 0 .. nc - 1 of the level (numbered coarsest level first)
+    std::vector<int32_t> cells(size_t(8 * ng));
+    int32_t nmax = -1;
+    for (int64_t g = 0; g < ng; ++g)
+        for (int K = 0; K < 8; ++K) {
+            const int iota = 2 * (K & 1) + 6 * ((K >> 1) & 1) + 18 * ((K >> 2) & 1);
+            const int32_t v = f.groups[size_t(27 * g + iota)];
+            cells[size_t(8 * g + K)] = v;
+            nmax = std::max(nmax, v);
+        }
+    const int64_t nc = int64_t(nmax) + 1;
+    if (nc >= f.n) return false;
+    std::vector<uint8_t> seen(size_t(nc), 0);
+    for (int32_t v : cells) seen[size_t(v)] = 1;
+    for (uint8_t s : seen)
+        if (!s) return false;
+    std::vector<double> xyz(f.xyz.begin(), f.xyz.begin() + 3 * nc);
+    std::vector<uint8_t> dir(f.dir.begin(), f.dir.begin() + nc);
+    // a level with almost no free velocity nodes cannot carry the coarse
+    // pressure modes (the continuity rows then see hardly any velocity, and
+    // only the stabilisation would fix the pressure): stop above it
+    int64_t free_nodes = 0;
+    for (uint8_t d : dir) free_nodes += d ? 0 : 1;
+    if (free_nodes < kMinFreeCoarseNodes) return false;
+    level_from_cells(nc, std::move(xyz), std::move(dir), f.mean_zero_pressure, cells, c);
+    // prolongation rows: fine node j takes the trilinear weights of the
+    // corners of the first group (in group order) that contains it
+    const int64_t n = f.n;
+    t->P_ptr.assign(size_t(n + 1), 0);
+    t->P_idx.clear();
+    t->P_w.clear();
+    for (int64_t j = 0; j < n; ++j) {
+        const int32_t e = f.node_idx[size_t(f.node_ptr[j])];
+        const int64_t g = e / 27;
+        const int iota = int(e % 27);
+        for (int K = 0; K < 8; ++K) {
+            const double w = corner_weight(iota, K);
+            if (w == 0.0) continue;
+            t->P_idx.push_back(cells[size_t(8 * g + K)]);
+            t->P_w.push_back(w);
+        }
+        t->P_ptr[j + 1] = int32_t(t->P_idx.size());
+    }
+    // restriction = transpose, rows in increasing fine node order
+    t->R_ptr.assign(size_t(nc + 1), 0);
+    for (int32_t v : t->P_idx) t->R_ptr[size_t(v) + 1]++;
+    for (int64_t i = 0; i < nc; ++i) t->R_ptr[i + 1] += t->R_ptr[i];
+    t->R_idx.assign(t->P_idx.size(), 0);
+    t->R_w.assign(t->P_idx.size(), 0.0);
+    std::vector<int32_t> fill(t->R_ptr.begin(), t->R_ptr.end() - 1);
+    for (int64_t j = 0; j < n; ++j)
+        for (int32_t e = t->P_ptr[j]; e < t->P_ptr[j + 1]; ++e) {
+            const int32_t at = fill[size_t(t->P_idx[e])]++;
+            t->R_idx[size_t(at)] = int32_t(j);
+            t->R_w[size_t(at)] = t->P_w[size_t(e)];
+        }
+    return true;
 }
 
 }  // namespace dnnmg

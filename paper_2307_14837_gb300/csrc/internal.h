@@ -61,18 +61,40 @@ struct HostLevel {
     std::vector<int32_t> row_ptr, col_idx;     // node-node block sparsity (BSR, 4x4 blocks)
     std::vector<int32_t> blk_ptr, blk_src;     // block -> local entries g*npg*npg + i*npg + j
     std::vector<int32_t> grp_blk;              // [ng][npg][npg] block index
+    std::vector<int32_t> color_ptr, color_groups;  // groups by colour: no two of a colour share a node
 };
 
 // Level L from the coarse mesh (grouped if its cells come in consistent
 // groups of 8) or level L+1 from the hierarchy.
 void build_level(const HostHierarchy& h, bool fine, HostLevel* lv);
 
+// Grid transfer between a level and the next coarser one: P (rows = fine
+// nodes, trilinear weights of the parent's corners) and R = P^T (rows =
+// coarse nodes, entries in increasing fine node order).
+constexpr int64_t kMinFreeCoarseNodes = 8;
+
+struct MgTransfer {
+    std::vector<int32_t> P_ptr, P_idx, R_ptr, R_idx;
+    std::vector<double> P_w, R_w;
+};
+
+// The next coarser level of a grouped level for geometric multigrid: the
+// parents of its groups, whose corners must be nodes 0 .. n_c - 1 (meshes
+// numbered coarsest level first; level L+1 of a hierarchy always is), with
+// at least kMinFreeCoarseNodes nodes of free velocity.  False if the level
+// cannot be coarsened.
+bool coarsen_level(const HostLevel& fine, HostLevel* coarse, MgTransfer* t);
+
 struct OpParams;
 struct DeviceLevel;   // solver.cu
-cudaError_t create_level(const HostHierarchy& hh, bool fine, int krylov, DeviceLevel** out);
+// The level solved on (level L, or L+1 when fine) with up to mg_levels
+// coarser multigrid levels below it and a Krylov dimension of krylov.
+cudaError_t create_level(const HostHierarchy& hh, bool fine, int krylov, int mg_levels, DeviceLevel** out);
 void destroy_level(DeviceLevel* L);
 int64_t level_nodes(const DeviceLevel* L);
 bool level_lps(const DeviceLevel* L);
+int level_mg_depth(const DeviceLevel* L);                // coarser levels in use
+int64_t level_mg_nodes(const DeviceLevel* L, int k);     // nodes of level k (0 = the solve level)
 cudaError_t level_operator(DeviceLevel* L, const OpParams& op, const dnnmg_solver_params* sp, const double* x,
                            double* Ax, cudaStream_t s);
 cudaError_t level_residual(DeviceLevel* L, const OpParams& op, const dnnmg_solver_params* sp, const double* x,
@@ -80,7 +102,8 @@ cudaError_t level_residual(DeviceLevel* L, const OpParams& op, const dnnmg_solve
 cudaError_t level_rhs(DeviceLevel* L, const OpParams& op, const double* x_old, double* b, cudaStream_t s);
 cudaError_t level_jacobian(DeviceLevel* L, const OpParams& op, const dnnmg_solver_params* sp, const double* x,
                            cudaStream_t s);
-cudaError_t level_dense_jacobian(DeviceLevel* L, double* dense_host);
+cudaError_t level_dense_jacobian(DeviceLevel* L, const OpParams& op, const dnnmg_solver_params* sp, const double* x,
+                                 double* dense_host, cudaStream_t s);
 cudaError_t level_solve(DeviceLevel* L, const OpParams& op, const dnnmg_solver_params* sp, const double* b, double* x,
                         cudaStream_t s, dnnmg_solve_stats* st);
 

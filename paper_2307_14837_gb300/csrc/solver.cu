@@ -1,24 +1,33 @@
-// Newton-Krylov solve of A_h(x) = b on one mesh level (Sec. 3.4), FP64.
+// Newton-Krylov-multigrid solve of A_h(x) = b on one mesh level (Sec. 3.4).
 //
 // The paper solves each time step's nonlinear system on the coarse level
 // with Newton's method (stabilisation parameters frozen in the Jacobian),
 // GMRES and a geometric multigrid preconditioner with a Vanka smoother whose
-// local problems are the 108 x 108 matrices of one Q2 cell; it notes that any
-// coarse solver can take its place.  Here:
+// local problems are the 108 x 108 matrices of one Q2 cell.  Here:
 //   * the operator A_h is the Q1/Q1 form of Eqs. (5)-(6) with the two-level
 //     local projection on groups of 8 child cells (27 nodes = one Q2 cell's
-//     nodes), evaluated per group;
-//   * the Jacobian is exact: forward-mode dual numbers, one direction per
-//     local unknown of a group (108), with alpha_T, delta_T from the value
-//     part (frozen, Eq. (8)); local 108 x 108 matrices are summed into a
-//     4 x 4-block CSR matrix by a gather in group order (deterministic);
-//   * the preconditioner is additive group-Vanka: the global matrix
-//     restricted to each group's 108 unknowns, LU-factorised and inverted
-//     once per assembly, the inverse applied to the group's residual as a
-//     dense product and averaged over the groups sharing a node;
-//   * right-preconditioned restarted GMRES with classical Gram-Schmidt
-//     applied twice; all vectors, dot products (warp shuffles, then a second
-//     pass over the blocks: fixed order) and norms in FP64;
+//     nodes), evaluated per group in FP64; Newton residual norms are FP64;
+//   * the Jacobian is the exact derivative of A_h (alpha_T, delta_T frozen,
+//     Eq. (8)), formed column by column per group from closed-form
+//     derivatives of every term (FP32 on the solve and smoothing levels,
+//     FP64 on the coarsest level); the local 108 x 108 matrices are summed
+//     into a 4 x 4-block CSR matrix by a gather in group order
+//     (deterministic);
+//   * the preconditioner is a geometric multigrid V-cycle over the levels
+//     below (each the parents of the groups of the next finer one), with
+//     additive group-Vanka smoothing in FP32: the matrix restricted to each
+//     group's 108 unknowns, LU-factorised and inverted once per assembly,
+//     applied as a dense product, averaged over the groups sharing a node and
+//     damped; restriction R = P^T and trilinear prolongation P between
+//     levels; on the coarsest level a dense LU with partial pivoting and its
+//     explicit inverse in FP64.  Without coarser levels the preconditioner
+//     is one group-Vanka application;
+//   * flexible restarted GMRES (the preconditioned vectors are kept, so an
+//     FP32 preconditioner does not limit the FP64 solution) with classical
+//     Gram-Schmidt applied twice; vectors, dot products (warp shuffles, then
+//     a second pass over the blocks: fixed order), norms and the Givens
+//     rotations in FP64, on the device; the host reads the residual estimate
+//     every few iterations only;
 //   * Newton re-assembles the Jacobian when the residual rate
 //     rho = |r_{j+1}| / |r_j| exceeds rho_max (Sec. 3.4).
 // Dirichlet velocity unknowns keep the values given in x; where no boundary
@@ -31,36 +40,24 @@
 #include "internal.h"
 
 namespace dnnmg {
+
+// largest coarsest multigrid level for the dense FP64 LU (unknowns): 8192^2
+// doubles = 512 MiB per buffer
+constexpr int64_t kMaxCoarsestUnknowns = 8192;
+
 namespace {
 
 constexpr double kGaussOff = 0.28867513459481288225457439025098;
 
-struct Dual {
-    double v, d;
-};
-__device__ __forceinline__ Dual operator+(Dual a, Dual b) { return {a.v + b.v, a.d + b.d}; }
-__device__ __forceinline__ Dual operator-(Dual a, Dual b) { return {a.v - b.v, a.d - b.d}; }
-__device__ __forceinline__ Dual operator-(Dual a) { return {-a.v, -a.d}; }
-__device__ __forceinline__ Dual operator*(Dual a, Dual b) { return {a.v * b.v, a.d * b.v + a.v * b.d}; }
-__device__ __forceinline__ Dual operator*(double s, Dual a) { return {s * a.v, s * a.d}; }
-__device__ __forceinline__ Dual operator*(Dual a, double s) { return {s * a.v, s * a.d}; }
-__device__ __forceinline__ Dual operator+(Dual a, double s) { return {a.v + s, a.d}; }
-__device__ __forceinline__ Dual& operator+=(Dual& a, Dual b) { a.v += b.v; a.d += b.d; return a; }
-__device__ __forceinline__ Dual& operator-=(Dual& a, Dual b) { a.v -= b.v; a.d -= b.d; return a; }
 __device__ __forceinline__ double val(double x) { return x; }
-__device__ __forceinline__ double val(Dual x) { return x.v; }
 template <typename T>
 __device__ __forceinline__ T zero() { return T{}; }
 template <>
 __device__ __forceinline__ double zero<double>() { return 0.0; }
-template <>
-__device__ __forceinline__ Dual zero<Dual>() { return Dual{0.0, 0.0}; }
 template <typename T>
 __device__ __forceinline__ T lift(double x);
 template <>
 __device__ __forceinline__ double lift<double>(double x) { return x; }
-template <>
-__device__ __forceinline__ Dual lift<Dual>(double x) { return Dual{x, 0.0}; }
 
 __device__ __forceinline__ double gpt(int i) { return i ? 0.5 + kGaussOff : 0.5 - kGaussOff; }
 __device__ __forceinline__ double basis(int k, int q) {
@@ -289,42 +286,59 @@ __global__ void __launch_bounds__(64) level_local_kernel(int64_t ng, const int32
         for (int c = 0; c < 4; ++c) out[(g * NPG + i) * 4 + c] = R[i][c];
 }
 
-// Column j (local unknown 4 i + c) of each group's local Jacobian:
-// one thread per (group, j), forward-mode derivative of the local residual.
-template <int NPG>
-__global__ void __launch_bounds__(128) level_jacobian_kernel(int64_t ng, const int32_t* __restrict__ groups,
-                                                             const double* __restrict__ xyz,
-                                                             const double* __restrict__ x, LvPrm p,
-                                                             double* __restrict__ Jloc) {
-    constexpr int NL = 4 * NPG;
-    const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (tid >= ng * NL) return;
-    const int64_t g = tid / NL;
-    const int j = int(tid % NL);
-    const int jn = j / 4;
-    double X[NPG][3];
-    Dual U[NPG][4], PU[NPG][4], R[NPG][4];
-    for (int i = 0; i < NPG; ++i) {
-        const int64_t n = groups[g * NPG + i];
-        for (int d = 0; d < 3; ++d) X[i][d] = xyz[3 * n + d];
-        for (int c = 0; c < 4; ++c) {
-            U[i][c] = Dual{x[4 * n + c], (4 * i + c == j) ? 1.0 : 0.0};
-            R[i][c] = Dual{0.0, 0.0};
+
+// Local residual / rhs / mass of 27-node groups with one thread per child
+// cell: a block takes 8 groups (their coordinates, values and projected
+// values in shared memory), each thread adds its child's terms into its own
+// slice, and the 8 slices of a group are summed in child order.
+constexpr int kChildGroups = 8;
+constexpr size_t kChildSmem = size_t(kChildGroups) * (27 * 3 + 2 * 27 * 4 + 8 * 27 * 4) * sizeof(double);
+
+template <int MODE>
+__global__ void __launch_bounds__(64) level_local_child_kernel(int64_t ng, const int32_t* __restrict__ groups,
+                                                               const double* __restrict__ xyz,
+                                                               const double* __restrict__ x, LvPrm p,
+                                                               double* __restrict__ out) {
+    extern __shared__ __align__(16) double lc_smem[];
+    auto X = reinterpret_cast<double (*)[27][3]>(lc_smem);
+    auto U = reinterpret_cast<double (*)[27][4]>(lc_smem + kChildGroups * 81);
+    auto PU = reinterpret_cast<double (*)[27][4]>(lc_smem + kChildGroups * (81 + 108));
+    auto R = reinterpret_cast<double (*)[8][27][4]>(lc_smem + kChildGroups * (81 + 216));
+    const int64_t g0 = int64_t(blockIdx.x) * kChildGroups;
+    for (int e = threadIdx.x; e < kChildGroups * 27; e += blockDim.x) {
+        const int gg = e / 27, i = e % 27;
+        const int64_t g = g0 + gg;
+        if (g >= ng) continue;
+        const int64_t n = groups[g * 27 + i];
+        for (int d = 0; d < 3; ++d) X[gg][i][d] = xyz[3 * n + d];
+        for (int c = 0; c < 4; ++c) U[gg][i][c] = MODE == LV_MASS ? 0.0 : x[4 * n + c];
+    }
+    for (int e = threadIdx.x; e < kChildGroups * 8 * 108; e += blockDim.x) (&R[0][0][0][0])[e] = 0.0;
+    __syncthreads();
+    if (MODE == LV_OPERATOR)
+        for (int e = threadIdx.x; e < kChildGroups * 27; e += blockDim.x) {
+            const int gg = e / 27, i = e % 27;
+            for (int c = 0; c < 4; ++c) {
+                double a = 0.0;
+                for (int K = 0; K < 8; ++K) {
+                    const double wk = wpi(i, K);
+                    if (wk != 0.0) a += wk * U[gg][corner_node(K)][c];
+                }
+                PU[gg][i][c] = a;
+            }
         }
+    __syncthreads();
+    const int gl = threadIdx.x >> 3, t = threadIdx.x & 7;
+    if (g0 + gl < ng) child_terms<double, 27, MODE>(X[gl], U[gl], PU[gl], t, p, R[gl][t]);
+    __syncthreads();
+    for (int e = threadIdx.x; e < kChildGroups * 108; e += blockDim.x) {
+        const int gg = e / 108, k = e % 108;
+        const int64_t g = g0 + gg;
+        if (g >= ng) continue;
+        double a = 0.0;
+        for (int c = 0; c < 8; ++c) a += R[gg][c][k >> 2][k & 3];
+        out[g * 108 + k] = a;
     }
-    project_group<Dual, NPG>(U, PU);
-    bool is_corner = false;
-    if (NPG == 27)
-        for (int K = 0; K < 8; ++K) is_corner |= corner_node(K) == jn;
-    const int children = NPG == 27 ? 8 : 1;
-    for (int t = 0; t < children; ++t) {
-        bool touches = is_corner && p.lps;
-        for (int k = 0; k < 8; ++k) touches |= child_node<NPG>(t, k) == jn;
-        if (touches) child_terms<Dual, NPG, LV_OPERATOR>(X, U, PU, t, p, R);
-    }
-    double* col = Jloc + g * NL * NL + j;
-    for (int i = 0; i < NPG; ++i)
-        for (int c = 0; c < 4; ++c) col[int64_t(4 * i + c) * NL] = R[i][c].d;
 }
 
 // out_j = sum over (g, local) containing node j of local[g*NPG + local][0..3]
@@ -352,16 +366,252 @@ __global__ void finish_rows_kernel(int64_t n, const double* __restrict__ b, doub
     }
 }
 
-// BSR block b = sum of its local entries; 16 threads per block
-template <int NPG>
+// ---- Jacobian from closed-form derivatives ------------------------------------
+//
+// Column (b, e) of a group's local matrix is the derivative of the group's
+// local residual with respect to unknown e of group node b.  With phi_b the
+// child basis function of b, Pi_b the parent (group) trilinear function of b
+// when b is a group corner (zero otherwise), and the frozen parameters:
+//   velocity e: mass m phi_a phi_b delta_ce; convection theta phi_a
+//     (phi_b d_e v_c + delta_ce v.grad phi_b); viscosity theta nu delta_ce
+//     grad phi_a.grad phi_b; continuity phi_a d_e phi_b; projection term
+//     delta_T [g'_c (v.grad phi_a) + g_c phi_b d_e phi_a] on child nodes and
+//     -delta_T [g'_c (pi v.grad Pi_K) + g_c Pi_b d_e Pi_K] on corners K, with
+//     g = v.grad v - pi v.grad pi v and g'_c = phi_b d_e v_c + delta_ce
+//     v.grad phi_b - Pi_b d_e (pi v)_c - delta_ce pi v.grad Pi_b;
+//   pressure: -d_c phi_a phi_b; alpha_T grad(phi_b - Pi_b).grad phi_a on
+//     child nodes and -alpha_T grad(phi_b - Pi_b).grad Pi_K on corners.
+// On a level without parents used as the coarsest multigrid level (8-node
+// cells, stab != 0) the projection is taken as zero, which leaves the
+// stabilisation terms with full fluctuations.
+
+// per quadrature point of a child: everything the columns read
+template <typename T>
+struct QPoint {
+    T w, N[8], G[8][3];      // weight x det J, child basis values, physical gradients
+    T Pi[8], dPi[8][3];      // parent trilinear basis of the 8 group corners
+    T v[3], Dv[3][3];        // velocity and gradient (Dv[c][d] = d v_c / d x_d)
+    T pv[3], Dpv[3][3];      // projected velocity pi v and its gradient
+    T gv[3];                 // v.grad v - pi v.grad pi v
+};
+
+template <typename T, int NPG>
+constexpr size_t jac_smem_bytes() {
+    return size_t(NPG == 27 ? 64 : 8) * sizeof(QPoint<T>) + size_t(4 * NPG) * size_t(4 * NPG) * sizeof(T);
+}
+
+template <typename T, int NPG>
+__global__ void __launch_bounds__(128) jacobian_kernel(int64_t ng, const int32_t* __restrict__ groups,
+                                                       const double* __restrict__ xyz,
+                                                       const double* __restrict__ x, LvPrm p, int stab,
+                                                       T* __restrict__ Jloc) {
+    constexpr int NL = 4 * NPG;
+    constexpr int NCH = NPG == 27 ? 8 : 1;
+    constexpr int NQ = 8 * NCH;
+    extern __shared__ __align__(16) unsigned char jac_smem[];
+    QPoint<T>* P = reinterpret_cast<QPoint<T>*>(jac_smem);
+    T* M = reinterpret_cast<T*>(jac_smem + size_t(NQ) * sizeof(QPoint<T>));   // [NL][NL]
+    __shared__ double Xs[NPG][3];
+    __shared__ T Us[NPG][4];
+    __shared__ T prm_s[NCH][2];
+    const int64_t g = blockIdx.x;
+    for (int i = threadIdx.x; i < NPG; i += blockDim.x) {
+        const int64_t n = groups[g * NPG + i];
+        for (int d = 0; d < 3; ++d) Xs[i][d] = xyz[3 * n + d];
+        for (int c = 0; c < 4; ++c) Us[i][c] = T(x[4 * n + c]);
+    }
+    for (int e = threadIdx.x; e < NL * NL; e += blockDim.x) M[e] = T(0);
+    __syncthreads();
+    if (threadIdx.x < NQ) {
+        const int t = threadIdx.x >> 3, q = threadIdx.x & 7;
+        QPoint<T>& Q = P[threadIdx.x];
+        int nd[8];
+        for (int k = 0; k < 8; ++k) nd[k] = child_node<NPG>(t, k);
+        T J[3][3];
+        for (int d = 0; d < 3; ++d)
+            for (int e = 0; e < 3; ++e) {
+                T s = T(0);
+                for (int k = 1; k < 8; ++k) s += T(Xs[nd[k]][d] - Xs[nd[0]][d]) * T(dbasis(k, q, e));
+                J[d][e] = s;
+            }
+        const T c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+        const T c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+        const T c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+        const T det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+        const T idet = T(1) / det;
+        T Ji[3][3];
+        Ji[0][0] = c00 * idet;
+        Ji[1][0] = c01 * idet;
+        Ji[2][0] = c02 * idet;
+        Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) * idet;
+        Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) * idet;
+        Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) * idet;
+        Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) * idet;
+        Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) * idet;
+        Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) * idet;
+        Q.w = T(0.125) * det;
+        for (int k = 0; k < 8; ++k) {
+            Q.N[k] = T(basis(k, q));
+            for (int d = 0; d < 3; ++d)
+                Q.G[k][d] = T(dbasis(k, q, 0)) * Ji[0][d] + T(dbasis(k, q, 1)) * Ji[1][d] + T(dbasis(k, q, 2)) * Ji[2][d];
+        }
+        // parent basis at the point's parent reference coordinates (t_d + xi_d) / 2
+        const bool par = NPG == 27 && stab;
+        for (int K = 0; K < 8; ++K) {
+            T val = T(par ? 1 : 0), dr[3] = {T(par ? 0.5 : 0), T(par ? 0.5 : 0), T(par ? 0.5 : 0)};
+            if (par)
+                for (int d = 0; d < 3; ++d) {
+                    const T xp = T(0.5 * (((t >> d) & 1) + gpt((q >> d) & 1)));
+                    const T f = ((K >> d) & 1) ? xp : T(1) - xp;
+                    const T df = ((K >> d) & 1) ? T(1) : T(-1);
+                    val *= f;
+                    for (int e = 0; e < 3; ++e) dr[e] *= (e == d) ? df : f;
+                }
+            Q.Pi[K] = val;
+            for (int d = 0; d < 3; ++d) Q.dPi[K][d] = dr[0] * Ji[0][d] + dr[1] * Ji[1][d] + dr[2] * Ji[2][d];
+        }
+        for (int c = 0; c < 3; ++c) {
+            T v = T(0), pv = T(0);
+            T Dv[3] = {T(0), T(0), T(0)}, Dp[3] = {T(0), T(0), T(0)};
+            for (int k = 0; k < 8; ++k) {
+                const T u = Us[nd[k]][c];
+                v += Q.N[k] * u;
+                for (int d = 0; d < 3; ++d) Dv[d] += Q.G[k][d] * u;
+                const T uc = Us[corner_node(k) < NPG ? corner_node(k) : 0][c];
+                if (par) {
+                    pv += Q.Pi[k] * uc;
+                    for (int d = 0; d < 3; ++d) Dp[d] += Q.dPi[k][d] * uc;
+                }
+            }
+            Q.v[c] = v;
+            Q.pv[c] = pv;
+            for (int d = 0; d < 3; ++d) {
+                Q.Dv[c][d] = Dv[d];
+                Q.Dpv[c][d] = Dp[d];
+            }
+        }
+        for (int c = 0; c < 3; ++c)
+            Q.gv[c] = Q.v[0] * Q.Dv[c][0] + Q.v[1] * Q.Dv[c][1] + Q.v[2] * Q.Dv[c][2] -
+                      (Q.pv[0] * Q.Dpv[c][0] + Q.pv[1] * Q.Dpv[c][1] + Q.pv[2] * Q.Dpv[c][2]);
+    }
+    if (threadIdx.x < NCH) {
+        // frozen alpha_T, delta_T of child t (Eq. (8)) from the iterate's values
+        const int t = threadIdx.x;
+        double h = 0.0, vmax = 0.0;
+        for (int a = 0; a < 8; ++a) {
+            const int na = child_node<NPG>(t, a);
+            for (int b = a + 1; b < 8; ++b) {
+                const int nb = child_node<NPG>(t, b);
+                double s = 0.0;
+                for (int d = 0; d < 3; ++d) {
+                    const double t0 = Xs[na][d] - Xs[nb][d];
+                    s += t0 * t0;
+                }
+                h = fmax(h, sqrt(s));
+            }
+            double s = 0.0;
+            for (int d = 0; d < 3; ++d) s += double(Us[na][d]) * double(Us[na][d]);
+            vmax = fmax(vmax, sqrt(s));
+        }
+        const double den = p.nu / (h * h) + vmax / h + p.m;
+        prm_s[t][0] = T(stab ? p.a0 / den : 0.0);
+        prm_s[t][1] = T(stab ? p.d0 / den : 0.0);
+    }
+    __syncthreads();
+    const int j = threadIdx.x;
+    if (j < NL) {
+        const int b = j >> 2, e = j & 3;
+        int Kb = -1;
+        if (NPG == 27 && stab)
+            for (int K = 0; K < 8; ++K)
+                if (corner_node(K) == b) Kb = K;
+        const T m = T(p.m), th = T(p.th), nu = T(p.nu);
+        for (int t = 0; t < NCH; ++t) {
+            int bl = -1, nd[8];
+            for (int k = 0; k < 8; ++k) {
+                nd[k] = child_node<NPG>(t, k);
+                if (nd[k] == b) bl = k;
+            }
+            if (bl < 0 && Kb < 0) continue;
+            const T aT = prm_s[t][0], dT = prm_s[t][1];
+            for (int q = 0; q < 8; ++q) {
+                const QPoint<T>& Q = P[t * 8 + q];
+                const T w = Q.w;
+                const T phib = bl >= 0 ? Q.N[bl] : T(0);
+                T gb[3], gP[3];
+                for (int d = 0; d < 3; ++d) {
+                    gb[d] = bl >= 0 ? Q.G[bl][d] : T(0);
+                    gP[d] = Kb >= 0 ? Q.dPi[Kb][d] : T(0);
+                }
+                const T Pib = Kb >= 0 ? Q.Pi[Kb] : T(0);
+                if (e < 3) {
+                    const T vgb = Q.v[0] * gb[0] + Q.v[1] * gb[1] + Q.v[2] * gb[2];
+                    if (bl >= 0)
+                        for (int a = 0; a < 8; ++a) {
+                            const T Na = Q.N[a];
+                            const T ggb = Q.G[a][0] * gb[0] + Q.G[a][1] * gb[1] + Q.G[a][2] * gb[2];
+                            T* row = M + (4 * nd[a]) * NL + j;
+                            for (int c = 0; c < 3; ++c) {
+                                T val = th * Na * phib * Q.Dv[c][e];
+                                if (c == e) val += m * Na * phib + th * Na * vgb + th * nu * ggb;
+                                row[c * NL] += w * val;
+                            }
+                            row[3 * NL] += w * Na * gb[e];
+                        }
+                    if (stab) {
+                        const T pvgP = Q.pv[0] * gP[0] + Q.pv[1] * gP[1] + Q.pv[2] * gP[2];
+                        T gvp[3];
+                        for (int c = 0; c < 3; ++c) {
+                            gvp[c] = phib * Q.Dv[c][e] - Pib * Q.Dpv[c][e];
+                            if (c == e) gvp[c] += vgb - pvgP;
+                        }
+                        for (int a = 0; a < 8; ++a) {
+                            const T vGa = Q.v[0] * Q.G[a][0] + Q.v[1] * Q.G[a][1] + Q.v[2] * Q.G[a][2];
+                            T* row = M + (4 * nd[a]) * NL + j;
+                            for (int c = 0; c < 3; ++c) row[c * NL] += dT * w * (gvp[c] * vGa + Q.gv[c] * phib * Q.G[a][e]);
+                        }
+                        if (NPG == 27)
+                            for (int K = 0; K < 8; ++K) {
+                                const T pvdP = Q.pv[0] * Q.dPi[K][0] + Q.pv[1] * Q.dPi[K][1] + Q.pv[2] * Q.dPi[K][2];
+                                T* row = M + (4 * corner_node(K)) * NL + j;
+                                for (int c = 0; c < 3; ++c)
+                                    row[c * NL] -= dT * w * (gvp[c] * pvdP + Q.gv[c] * Pib * Q.dPi[K][e]);
+                            }
+                    }
+                } else {
+                    if (bl >= 0)
+                        for (int a = 0; a < 8; ++a) {
+                            T* row = M + (4 * nd[a]) * NL + j;
+                            for (int c = 0; c < 3; ++c) row[c * NL] -= w * Q.G[a][c] * phib;
+                        }
+                    if (stab) {
+                        const T gq[3] = {gb[0] - gP[0], gb[1] - gP[1], gb[2] - gP[2]};
+                        for (int a = 0; a < 8; ++a)
+                            M[(4 * nd[a] + 3) * NL + j] += aT * w * (gq[0] * Q.G[a][0] + gq[1] * Q.G[a][1] + gq[2] * Q.G[a][2]);
+                        if (NPG == 27)
+                            for (int K = 0; K < 8; ++K)
+                                M[(4 * corner_node(K) + 3) * NL + j] -=
+                                    aT * w * (gq[0] * Q.dPi[K][0] + gq[1] * Q.dPi[K][1] + gq[2] * Q.dPi[K][2]);
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+    T* out = Jloc + g * NL * NL;
+    for (int e = threadIdx.x; e < NL * NL; e += blockDim.x) out[e] = M[e];
+}
+
+// BSR block b = sum of its local entries in group order; 16 threads per block
+template <typename T, int NPG>
 __global__ void bsr_assemble_kernel(int64_t nnzb, const int32_t* __restrict__ bptr, const int32_t* __restrict__ bsrc,
-                                    const double* __restrict__ Jloc, double* __restrict__ A) {
+                                    const T* __restrict__ Jloc, T* __restrict__ A) {
     constexpr int NL = 4 * NPG;
     const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (tid >= nnzb * 16) return;
     const int64_t b = tid >> 4;
     const int r = int(tid & 15) >> 2, s = int(tid & 3);
-    double acc = 0.0;
+    T acc = T(0);
     for (int32_t e = bptr[b]; e < bptr[b + 1]; ++e) {
         const int32_t src = bsrc[e];
         const int64_t g = src / (NPG * NPG);
@@ -372,31 +622,51 @@ __global__ void bsr_assemble_kernel(int64_t nnzb, const int32_t* __restrict__ bp
 }
 
 // identity rows for Dirichlet velocity unknowns and the pinned pressure
+template <typename T>
 __global__ void bsr_dirichlet_kernel(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                                     const uint8_t* __restrict__ dir, int32_t pin, double* __restrict__ A) {
+                                     const uint8_t* __restrict__ dir, int32_t pin, T* __restrict__ A) {
     const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= n) return;
     for (int r = 0; r < 4; ++r) {
         const bool fix = (r < 3 && dir[i]) || (r == 3 && i == pin);
         if (!fix) continue;
         for (int32_t b = rp[i]; b < rp[i + 1]; ++b)
-            for (int s = 0; s < 4; ++s) A[16 * int64_t(b) + 4 * r + s] = (ci[b] == i && s == r) ? 1.0 : 0.0;
+            for (int s = 0; s < 4; ++s) A[16 * int64_t(b) + 4 * r + s] = T((ci[b] == i && s == r) ? 1 : 0);
     }
 }
 
-__global__ void bsr_spmv_kernel(int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                                const double* __restrict__ A, const double* __restrict__ x, double* __restrict__ y) {
-    const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (tid >= 4 * n) return;
-    const int64_t i = tid >> 2;
-    const int r = int(tid & 3);
-    double acc = 0.0;
-    for (int32_t b = rp[i]; b < rp[i + 1]; ++b) {
-        const double* blk = A + 16 * int64_t(b) + 4 * r;
-        const double* xv = x + 4 * int64_t(ci[b]);
-        acc += blk[0] * xv[0] + blk[1] * xv[1] + blk[2] * xv[2] + blk[3] * xv[3];
+template <typename TA, typename TB>
+__global__ void convert_kernel(int64_t n, const TA* __restrict__ a, TB* __restrict__ b) {
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+        b[i] = TB(a[i]);
+}
+
+// y = A x (r == null) or y = r - A x; one warp per node row: four lanes take
+// one 4 x 4 block, lane 4k + rr its row rr (one 16-byte load), so a warp
+// reads 8 consecutive blocks (512 bytes) per step; the row sums of the lanes
+// with the same rr are reduced by a fixed shuffle tree (deterministic)
+template <typename T>
+__global__ void __launch_bounds__(256) bsr_spmv_kernel(int64_t n, const int32_t* __restrict__ rp,
+                                                       const int32_t* __restrict__ ci, const T* __restrict__ A,
+                                                       const T* __restrict__ x, const T* __restrict__ r,
+                                                       T* __restrict__ y) {
+    static_assert(sizeof(T) == 4, "FP32 blocks");
+    const int64_t i = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (i >= n) return;
+    const int rr = lane & 3;
+    const float4* A4 = reinterpret_cast<const float4*>(A);
+    const float4* x4 = reinterpret_cast<const float4*>(x);
+    float acc = 0.f;
+    for (int32_t b = rp[i] + (lane >> 2); b < rp[i + 1]; b += 8) {
+        const float4 a = A4[4 * int64_t(b) + rr];
+        const float4 v = x4[ci[b]];
+        acc += a.x * v.x + a.y * v.y + a.z * v.z + a.w * v.w;
     }
-    y[tid] = acc;
+    acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 8);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 16);
+    if (lane < 4) y[4 * i + rr] = r ? r[4 * i + rr] - acc : acc;
 }
 
 // Group block of the global matrix: LU with partial pivoting in shared
@@ -404,13 +674,13 @@ __global__ void bsr_spmv_kernel(int64_t n, const int32_t* __restrict__ rp, const
 // a back substitution of a unit vector), stored column-major in Ainv so that
 // applying it is a coalesced dense product.  A zero pivot gives a zero
 // component, as a triangular solve with that convention would.
-template <int NPG>
-__global__ void vanka_factor_kernel(int64_t ng, const int32_t* __restrict__ grp_blk, const double* __restrict__ A,
-                                    double* __restrict__ Ainv, int32_t* __restrict__ piv) {
+template <typename T, int NPG>
+__global__ void vanka_factor_kernel(int64_t ng, const int32_t* __restrict__ grp_blk, const T* __restrict__ A,
+                                    T* __restrict__ Ainv) {
     constexpr int NL = 4 * NPG;
-    extern __shared__ double sm[];
-    double* M = sm;                          // NL x NL
-    double* X = sm + NL * NL;                // NL x NL: X[i * NL + c] = (A^{-1})_{ic}
+    extern __shared__ __align__(16) unsigned char vf_smem[];
+    T* M = reinterpret_cast<T*>(vf_smem);   // NL x NL
+    T* X = M + NL * NL;                     // NL x NL: X[i * NL + c] = (A^{-1})_{ic}
     __shared__ int s_p;
     __shared__ int s_piv[NL];
     const int64_t g = blockIdx.x;
@@ -421,29 +691,41 @@ __global__ void vanka_factor_kernel(int64_t ng, const int32_t* __restrict__ grp_
     }
     __syncthreads();
     for (int k = 0; k < NL; ++k) {
-        if (threadIdx.x == 0) {
-            int best = k;
-            double bv = fabs(M[k * NL + k]);
-            for (int i = k + 1; i < NL; ++i)
-                if (fabs(M[i * NL + k]) > bv) {
-                    bv = fabs(M[i * NL + k]);
-                    best = i;
+        if (threadIdx.x < 32) {
+            // pivot: largest |M[i][k]|, i >= k, smallest i on ties (warp argmax)
+            T bv = T(-1);
+            int bi = k;
+            for (int i = k + threadIdx.x; i < NL; i += 32) {
+                const T a = fabs(M[i * NL + k]);
+                if (a > bv) {
+                    bv = a;
+                    bi = i;
                 }
-            s_p = best;
-            s_piv[k] = best;
-            piv[g * NL + k] = best;
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const T ov = __shfl_down_sync(0xffffffffu, bv, o);
+                const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+                if (ov > bv || (ov == bv && oi < bi)) {
+                    bv = ov;
+                    bi = oi;
+                }
+            }
+            if (threadIdx.x == 0) {
+                s_p = bi;
+                s_piv[k] = bi;
+            }
         }
         __syncthreads();
         const int pr = s_p;
         if (pr != k)
             for (int j = threadIdx.x; j < NL; j += blockDim.x) {
-                const double t = M[k * NL + j];
+                const T t = M[k * NL + j];
                 M[k * NL + j] = M[pr * NL + j];
                 M[pr * NL + j] = t;
             }
         __syncthreads();
-        const double d = M[k * NL + k];
-        const double inv = d != 0.0 ? 1.0 / d : 0.0;
+        const T d = M[k * NL + k];
+        const T inv = d != T(0) ? T(1) / d : T(0);
         for (int i = k + 1 + threadIdx.x; i < NL; i += blockDim.x) M[i * NL + k] *= inv;
         __syncthreads();
         const int rem = NL - k - 1;
@@ -455,25 +737,25 @@ __global__ void vanka_factor_kernel(int64_t ng, const int32_t* __restrict__ grp_
     }
     const int c = threadIdx.x;
     if (c < NL) {
-        for (int i = 0; i < NL; ++i) X[i * NL + c] = i == c ? 1.0 : 0.0;
+        for (int i = 0; i < NL; ++i) X[i * NL + c] = i == c ? T(1) : T(0);
         for (int k = 0; k < NL; ++k) {
             const int pr = s_piv[k];
             if (pr != k) {
-                const double t = X[k * NL + c];
+                const T t = X[k * NL + c];
                 X[k * NL + c] = X[pr * NL + c];
                 X[pr * NL + c] = t;
             }
         }
         for (int i = 1; i < NL; ++i) {
-            double acc = X[i * NL + c];
+            T acc = X[i * NL + c];
             for (int j = 0; j < i; ++j) acc -= M[i * NL + j] * X[j * NL + c];
             X[i * NL + c] = acc;
         }
         for (int i = NL - 1; i >= 0; --i) {
-            double acc = X[i * NL + c];
+            T acc = X[i * NL + c];
             for (int j = i + 1; j < NL; ++j) acc -= M[i * NL + j] * X[j * NL + c];
-            const double d = M[i * NL + i];
-            X[i * NL + c] = d != 0.0 ? acc / d : 0.0;
+            const T d = M[i * NL + i];
+            X[i * NL + c] = d != T(0) ? acc / d : T(0);
         }
     }
     __syncthreads();
@@ -486,34 +768,271 @@ __global__ void vanka_factor_kernel(int64_t ng, const int32_t* __restrict__ grp_
 
 // z_g = A_g^{-1} r restricted to group g: one block per group, thread i
 // computes row i of the dense product (column-major inverse: coalesced).
-template <int NPG>
+template <typename T, int NPG>
 __global__ void __launch_bounds__(128) vanka_apply_kernel(int64_t ng, const int32_t* __restrict__ groups,
-                                                          const double* __restrict__ Ainv,
-                                                          const double* __restrict__ r, double* __restrict__ zloc) {
+                                                          const T* __restrict__ Ainv, const T* __restrict__ r,
+                                                          T* __restrict__ zloc) {
     constexpr int NL = 4 * NPG;
-    __shared__ double s_r[NL];
+    __shared__ T s_r[NL];
     const int64_t g = blockIdx.x;
     for (int e = threadIdx.x; e < NL; e += blockDim.x) s_r[e] = r[4 * int64_t(groups[g * NPG + e / 4]) + e % 4];
     __syncthreads();
-    const double* Ag = Ainv + g * NL * NL;
+    const T* Ag = Ainv + g * NL * NL;
     for (int i = threadIdx.x; i < NL; i += blockDim.x) {
-        double acc = 0.0;
+        T acc = T(0);
         for (int j = 0; j < NL; ++j) acc += Ag[j * NL + i] * s_r[j];
         zloc[g * NL + i] = acc;
     }
 }
 
-// z_j = (1 / valence_j) sum of the groups' local solutions at node j
-__global__ void vanka_average_kernel(int64_t n, const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
-                                     const double* __restrict__ zloc, double* __restrict__ z) {
+// e_j = (first ? 0 : e_j) + omega / valence_j * (sum of the groups' local
+// solutions at node j), in group order
+template <typename T>
+__global__ void vanka_update_kernel(int64_t n, const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
+                                    const T* __restrict__ zloc, T omega, int first, T* __restrict__ e) {
     const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (j >= n) return;
-    double a[4] = {0, 0, 0, 0};
+    T a[4] = {T(0), T(0), T(0), T(0)};
     const int32_t e0 = ptr[j], e1 = ptr[j + 1];
-    for (int32_t e = e0; e < e1; ++e)
-        for (int c = 0; c < 4; ++c) a[c] += zloc[4 * int64_t(idx[e]) + c];
-    const double mu = 1.0 / double(e1 - e0);
-    for (int c = 0; c < 4; ++c) z[4 * j + c] = a[c] * mu;
+    for (int32_t k = e0; k < e1; ++k)
+        for (int c = 0; c < 4; ++c) a[c] += zloc[4 * int64_t(idx[k]) + c];
+    const T mu = omega / T(e1 - e0);
+    for (int c = 0; c < 4; ++c) e[4 * j + c] = (first ? T(0) : e[4 * j + c]) + a[c] * mu;
+}
+
+// One colour of a multiplicative group-Vanka sweep, in two launches so that
+// every group of the colour sees the same e (no two groups of a colour share
+// a node, but their rows reach each other's nodes): first the residual of
+// each group's 4 NPG rows at the current e into dloc[g], then the local
+// solve with the group inverse and e += omega z on the group's unknowns.
+// Colours run one after another, so later colours see the earlier ones'
+// updates (multiplicative between colours, fixed order: deterministic).
+template <int NPG>
+__global__ void __launch_bounds__(128) vanka_colour_residual_kernel(const int32_t* __restrict__ cgroups,
+                                                                    const int32_t* __restrict__ groups,
+                                                                    const int32_t* __restrict__ rp,
+                                                                    const int32_t* __restrict__ ci,
+                                                                    const float* __restrict__ A,
+                                                                    const float* __restrict__ r,
+                                                                    const float* __restrict__ e,
+                                                                    float* __restrict__ dloc) {
+    constexpr int NL = 4 * NPG;
+    const int64_t g = cgroups[blockIdx.x];
+    const float4* A4 = reinterpret_cast<const float4*>(A);
+    const float4* e4 = reinterpret_cast<const float4*>(e);
+    for (int i = threadIdx.x; i < NL; i += blockDim.x) {
+        const int64_t node = groups[g * NPG + i / 4];
+        const int rr = i & 3;
+        float acc = 0.f;
+        for (int32_t b = rp[node]; b < rp[node + 1]; ++b) {
+            const float4 a = A4[4 * int64_t(b) + rr];
+            const float4 v = e4[ci[b]];
+            acc += a.x * v.x + a.y * v.y + a.z * v.z + a.w * v.w;
+        }
+        dloc[g * NL + i] = r[4 * node + rr] - acc;
+    }
+}
+
+template <int NPG>
+__global__ void __launch_bounds__(128) vanka_colour_update_kernel(const int32_t* __restrict__ cgroups,
+                                                                  const int32_t* __restrict__ groups,
+                                                                  const float* __restrict__ Ainv,
+                                                                  const float* __restrict__ dloc, float omega,
+                                                                  float* __restrict__ e) {
+    constexpr int NL = 4 * NPG;
+    __shared__ float s_d[NL];
+    const int64_t g = cgroups[blockIdx.x];
+    for (int i = threadIdx.x; i < NL; i += blockDim.x) s_d[i] = dloc[g * NL + i];
+    __syncthreads();
+    const float* Ag = Ainv + g * NL * NL;
+    for (int i = threadIdx.x; i < NL; i += blockDim.x) {
+        float z = 0.f;
+        for (int j = 0; j < NL; ++j) z += Ag[j * NL + i] * s_d[j];
+        e[4 * int64_t(groups[g * NPG + i / 4]) + (i & 3)] += omega * z;
+    }
+}
+
+// coarse residual r_c = R d (rows of R = P^T in fine node order), with
+// Dirichlet velocity rows and the pinned pressure row of the coarse level 0
+template <typename T>
+__global__ void mg_restrict_kernel(int64_t nc, const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
+                                   const float* __restrict__ w, const T* __restrict__ d,
+                                   const uint8_t* __restrict__ dir, int32_t pin, T* __restrict__ rc) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= nc) return;
+    T a[4] = {T(0), T(0), T(0), T(0)};
+    for (int32_t k = ptr[i]; k < ptr[i + 1]; ++k) {
+        const T wk = T(w[k]);
+        const T* dv = d + 4 * int64_t(idx[k]);
+        for (int c = 0; c < 4; ++c) a[c] += wk * dv[c];
+    }
+    for (int c = 0; c < 4; ++c) rc[4 * i + c] = ((c < 3 && dir[i]) || (c == 3 && i == pin)) ? T(0) : a[c];
+}
+
+// e += P e_c, with the fine level's Dirichlet velocity rows and pinned
+// pressure row left alone
+template <typename T>
+__global__ void mg_prolong_add_kernel(int64_t nf, const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
+                                      const float* __restrict__ w, const T* __restrict__ ec,
+                                      const uint8_t* __restrict__ dir, int32_t pin, T* __restrict__ e) {
+    const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (j >= nf) return;
+    T a[4] = {T(0), T(0), T(0), T(0)};
+    for (int32_t k = ptr[j]; k < ptr[j + 1]; ++k) {
+        const T wk = T(w[k]);
+        const T* ev = ec + 4 * int64_t(idx[k]);
+        for (int c = 0; c < 4; ++c) a[c] += wk * ev[c];
+    }
+    for (int c = 0; c < 4; ++c)
+        if (!((c < 3 && dir[j]) || (c == 3 && j == pin))) e[4 * j + c] += a[c];
+}
+
+// ---- coarsest level: dense LU with partial pivoting and explicit inverse (FP64)
+
+// Dense row-major copy of a BSR matrix restricted to the free unknowns:
+// cidx[4 node + c] = the compact index of unknown (node, c), -1 for a
+// Dirichlet velocity or the pinned pressure (their rows are identity rows
+// with zero right-hand side, so they and their columns drop out).  D (nf x
+// nf) zeroed beforehand.
+__global__ void dense_from_bsr_kernel(int64_t n, int nf, const int32_t* __restrict__ rp,
+                                      const int32_t* __restrict__ ci, const int32_t* __restrict__ cidx,
+                                      const double* __restrict__ A, double* __restrict__ D) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int r = 0; r < 4; ++r) {
+        const int row = cidx[4 * i + r];
+        if (row < 0) continue;
+        for (int32_t b = rp[i]; b < rp[i + 1]; ++b)
+            for (int c = 0; c < 4; ++c) {
+                const int col = cidx[4 * int64_t(ci[b]) + c];
+                if (col >= 0) D[int64_t(row) * nf + col] = A[16 * int64_t(b) + 4 * r + c];
+            }
+    }
+}
+
+// Elimination step k: reads the factorisation so far from Ain and writes it
+// to Aout with rows k and p (the pivot: largest |A[i][k]|, i >= k, smallest
+// i on ties, found by every block alike) exchanged, the multipliers of
+// column k below the diagonal and the updated trailing rows; row k - 1 (final
+// since the previous step) is copied, so that both buffers hold every final
+// row.  A zero pivot leaves zero multipliers.
+__global__ void __launch_bounds__(256) lu_step_kernel(int N, int k, const double* __restrict__ Ain,
+                                                      double* __restrict__ Aout, int32_t* __restrict__ piv) {
+    __shared__ double sv[8];
+    __shared__ int si[8];
+    double bv = -1.0;
+    int bi = k;
+    for (int i = k + int(threadIdx.x); i < N; i += blockDim.x) {
+        const double a = fabs(Ain[int64_t(i) * N + k]);
+        if (a > bv) {
+            bv = a;
+            bi = i;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_down_sync(0xffffffffu, bv, o);
+        const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+        if (ov > bv || (ov == bv && oi < bi)) {
+            bv = ov;
+            bi = oi;
+        }
+    }
+    if ((threadIdx.x & 31) == 0) {
+        sv[threadIdx.x >> 5] = bv;
+        si[threadIdx.x >> 5] = bi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < int(blockDim.x >> 5); ++w)
+            if (sv[w] > sv[0] || (sv[w] == sv[0] && si[w] < si[0])) {
+                sv[0] = sv[w];
+                si[0] = si[w];
+            }
+        if (blockIdx.x == 0) piv[k] = si[0];
+    }
+    __syncthreads();
+    const int p = si[0];
+    const double pv = Ain[int64_t(p) * N + k];
+    const int r0 = k > 0 ? k - 1 : 0;
+    const int64_t total = int64_t(N - r0) * N;
+    for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < total; t += int64_t(gridDim.x) * blockDim.x) {
+        const int i = r0 + int(t / N), j = int(t % N);
+        double out;
+        if (i < k) {
+            out = Ain[int64_t(i) * N + j];
+        } else {
+            const int src = i == k ? p : (i == p ? k : i);
+            const double a = Ain[int64_t(src) * N + j];
+            if (i == k || j < k) {
+                out = a;
+            } else {
+                const double l = pv != 0.0 ? Ain[int64_t(src) * N + k] / pv : 0.0;
+                out = j == k ? l : a - l * Ain[int64_t(p) * N + j];
+            }
+        }
+        Aout[int64_t(i) * N + j] = out;
+    }
+}
+
+// Column c of A^{-1} from P A = L U, one warp per column held in shared
+// memory: the row exchanges, then the unit-lower forward and the upper back
+// substitution; each row's sum is split over the lanes and reduced by a
+// fixed shuffle tree.  A zero diagonal gives a zero component.  The result
+// is stored row-major, X[i][c].
+__global__ void __launch_bounds__(128) lu_inverse_kernel(int N, const double* __restrict__ LU,
+                                                         const int32_t* __restrict__ piv, double* __restrict__ X) {
+    extern __shared__ double inv_col[];                 // [warps][N]
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c = int(blockIdx.x) * int(blockDim.x >> 5) + w;
+    if (c >= N) return;
+    double* x = inv_col + size_t(w) * N;
+    for (int i = lane; i < N; i += 32) x[i] = i == c ? 1.0 : 0.0;
+    __syncwarp();
+    if (lane == 0)
+        for (int k = 0; k < N; ++k) {
+            const int p = piv[k];
+            if (p != k) {
+                const double t = x[k];
+                x[k] = x[p];
+                x[p] = t;
+            }
+        }
+    __syncwarp();
+    for (int i = 1; i < N; ++i) {
+        double acc = 0.0;
+        const double* Li = LU + int64_t(i) * N;
+        for (int j = lane; j < i; j += 32) acc += Li[j] * x[j];
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if (lane == 0) x[i] -= acc;
+        __syncwarp();
+    }
+    for (int i = N - 1; i >= 0; --i) {
+        double acc = 0.0;
+        const double* Ui = LU + int64_t(i) * N;
+        for (int j = i + 1 + lane; j < N; j += 32) acc += Ui[j] * x[j];
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if (lane == 0) {
+            const double d = Ui[i];
+            x[i] = d != 0.0 ? (x[i] - acc) / d : 0.0;
+        }
+        __syncwarp();
+    }
+    for (int i = lane; i < N; i += 32) X[int64_t(i) * N + c] = x[i];
+}
+
+// e = Ainv r on the free unknowns in FP64 (one warp per row, fixed shuffle
+// tree); fixed unknowns of e are 0.  fidx[k] = the unknown 4 node + c of
+// compact index k.
+template <typename T>
+__global__ void dense_matvec_kernel(int nf, const int32_t* __restrict__ fidx, const double* __restrict__ Ainv,
+                                    const T* __restrict__ r, T* __restrict__ e) {
+    const int row = int((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (row >= nf) return;
+    double acc = 0.0;
+    for (int j = lane; j < nf; j += 32) acc += Ainv[int64_t(row) * nf + j] * double(r[fidx[j]]);
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) e[fidx[row]] = T(acc);
 }
 
 // ---- vector kernels (FP64, deterministic reductions) -------------------------
@@ -612,40 +1131,124 @@ __global__ void mean_ratio_kernel(const double* __restrict__ num, const double* 
 
 inline unsigned nblk(int64_t n, int per) { return unsigned((n + per - 1) / per); }
 
+// ---- flexible GMRES state on the device ----------------------------------------
+// st[0] = beta0 (initial residual norm), st[1] = residual estimate |g[j+1]|,
+// st[2] = the iteration count at which the estimate first met the tolerance
+// (-1 before)
+__global__ void set_beta0_kernel(const double* __restrict__ nrm2, double* __restrict__ st) {
+    st[0] = sqrt(fmax(nrm2[0], 0.0));
+    st[1] = st[0];
+    st[2] = -1.0;
+}
+__global__ void cycle_init_kernel(int m, const double* __restrict__ nrm2, double* __restrict__ g,
+                                  double* __restrict__ st) {
+    for (int i = threadIdx.x; i <= m; i += blockDim.x) g[i] = 0.0;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        g[0] = sqrt(fmax(nrm2[0], 0.0));
+        st[2] = -1.0;
+    }
+}
+// Givens rotations on column j of H (column-major, leading dimension m + 1;
+// H[j+1][j] holds |w|^2): the earlier rotations, then one that zeroes
+// H[j+1][j]; g follows, and |g[j+1]| is the residual norm of the iterate.
+__global__ void givens_kernel(int j, int m, double* __restrict__ H, double* __restrict__ cs,
+                              double* __restrict__ sn, double* __restrict__ g, double rtol,
+                              double* __restrict__ st) {
+    double* col = H + size_t(j) * (m + 1);
+    col[j + 1] = sqrt(fmax(col[j + 1], 0.0));
+    for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * col[i] + sn[i] * col[i + 1];
+        col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+        col[i] = t;
+    }
+    const double den = hypot(col[j], col[j + 1]);
+    cs[j] = den > 0.0 ? col[j] / den : 1.0;
+    sn[j] = den > 0.0 ? col[j + 1] / den : 0.0;
+    col[j] = den;
+    col[j + 1] = 0.0;
+    g[j + 1] = -sn[j] * g[j];
+    g[j] = cs[j] * g[j];
+    const double r = fabs(g[j + 1]);
+    st[1] = r;
+    if (st[2] < 0.0 && r <= rtol * st[0]) st[2] = double(j + 1);
+}
+// y = R^{-1} g for the first jn columns (back substitution, one thread)
+__global__ void ls_solve_kernel(int jn, int m, const double* __restrict__ H, const double* __restrict__ g,
+                                double* __restrict__ y) {
+    for (int i = jn - 1; i >= 0; --i) {
+        double t = g[i];
+        for (int k = i + 1; k < jn; ++k) t -= H[i + size_t(k) * (m + 1)] * y[k];
+        const double d = H[i + size_t(i) * (m + 1)];
+        y[i] = d != 0.0 ? t / d : 0.0;
+    }
+}
+// x += sum_i y[i] Z_i, i = 0 .. cnt - 1 in order
+__global__ void multi_axpy_add_kernel(int64_t n, int cnt, const double* __restrict__ y, const double* __restrict__ Z,
+                                      double* __restrict__ x) {
+    for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += int64_t(gridDim.x) * blockDim.x) {
+        double acc = x[k];
+        for (int i = 0; i < cnt; ++i) acc += y[i] * Z[int64_t(i) * n + k];
+        x[k] = acc;
+    }
+}
+
 }  // namespace
 
-// ---- device level + host drivers -------------------------------------------------
+// ---- device levels ------------------------------------------------------------
 
-struct DeviceLevel {
+// One mesh level on the device: its structure, FP32 matrix and smoother,
+// multigrid vectors, the transfer to the next coarser level, and (coarsest
+// level) the FP64 matrix with its dense LU and inverse.
+struct LevelData {
     HostLevel h;
-    int32_t* groups = nullptr;
+    int32_t *groups = nullptr, *node_ptr = nullptr, *node_idx = nullptr, *row_ptr = nullptr, *col_idx = nullptr;
+    int32_t *blk_ptr = nullptr, *blk_src = nullptr, *grp_blk = nullptr;
     double* xyz = nullptr;
     uint8_t* dir = nullptr;
-    int32_t *node_ptr = nullptr, *node_idx = nullptr, *row_ptr = nullptr, *col_idx = nullptr;
-    int32_t *blk_ptr = nullptr, *blk_src = nullptr, *grp_blk = nullptr;
-    double* A = nullptr;        // BSR values [nnzb][4][4]
-    double* Jloc = nullptr;     // [ng][4 npg][4 npg]
-    double* LU = nullptr;       // [ng][4 npg][4 npg]: the inverse of each group block, column-major
-    int32_t* piv = nullptr;     // [ng][4 npg]
-    double* local = nullptr;    // [ng][npg][4]
-    double* zloc = nullptr;     // [ng][4 npg]
+    float* A = nullptr;       // BSR values [nnzb][4][4]
+    float* G = nullptr;       // [ng][nl][nl]: local Jacobians, then the group inverses (column-major)
+    float* zloc = nullptr;    // [ng][nl]
+    float *r = nullptr, *e = nullptr, *d = nullptr;   // [n][4]
+    float *r2 = nullptr, *e2 = nullptr, *d2 = nullptr;  // [n][4] operands of the Krylov products (solve level)
+    int32_t *P_ptr = nullptr, *P_idx = nullptr, *R_ptr = nullptr, *R_idx = nullptr;
+    float *P_w = nullptr, *R_w = nullptr;
+    double *J64 = nullptr, *A64 = nullptr, *D0 = nullptr, *D1 = nullptr, *Dinv = nullptr;
+    int32_t* piv = nullptr;
+    int32_t *cidx = nullptr, *fidx = nullptr;   // unknown -> compact free index (-1 fixed), and back
+    int32_t* cgroups = nullptr;                 // groups by colour (multiplicative smoothing)
+    int nfree = 0;
+    bool coarsest = false;
+    int stab = 0;             // stabilisation terms in the Jacobian (see jacobian_kernel)
+    std::vector<void*> allocs;
+};
+
+struct DeviceLevel {
+    LevelData top;                   // the level solved on
+    std::vector<LevelData*> mg;      // coarser levels, mg[0] the next coarser
+    int mg_pre = 2, mg_post = 2;
+    int mg_smoother = 0;        // 0 additive, 1 multiplicative (coloured) group-Vanka
+    float omega = 0.7f;
+    double* local = nullptr;    // [ng][npg][4] FP64 local residuals
     double* mass = nullptr;     // [n] lumped mass
-    double* work = nullptr;     // scratch vectors
-    double* scal = nullptr;     // device scalars
+    double* work = nullptr;     // r, dx, tmp, rr, w: [5][n][4]
+    double* V = nullptr;        // (krylov + 1) x [n][4]
+    double* Z = nullptr;        // krylov x [n][4]
+    double* scal = nullptr;     // device scalars and the small GMRES arrays
     double* part = nullptr;     // reduction partials
     int krylov = 0;
+    bool has_jacobian = false, mass_ready = false;
     std::vector<void*> allocs;
-    bool has_jacobian = false;
 };
 
 namespace {
 
 template <typename T>
-cudaError_t up(DeviceLevel* L, const std::vector<T>& v, T** out) {
+cudaError_t up(std::vector<void*>& allocs, const std::vector<T>& v, T** out) {
     void* p = nullptr;
     cudaError_t e = cudaMalloc(&p, std::max<size_t>(v.size() * sizeof(T), 1));
     if (e != cudaSuccess) return e;
-    L->allocs.push_back(p);
+    allocs.push_back(p);
     if (!v.empty()) {
         e = cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return e;
@@ -653,12 +1256,13 @@ cudaError_t up(DeviceLevel* L, const std::vector<T>& v, T** out) {
     *out = static_cast<T*>(p);
     return cudaSuccess;
 }
-cudaError_t dalloc(DeviceLevel* L, size_t bytes, void** out) {
+template <typename T>
+cudaError_t dalloc(std::vector<void*>& allocs, size_t count, T** out) {
     void* p = nullptr;
-    cudaError_t e = cudaMalloc(&p, std::max<size_t>(bytes, 1));
+    cudaError_t e = cudaMalloc(&p, std::max<size_t>(count * sizeof(T), 1));
     if (e != cudaSuccess) return e;
-    L->allocs.push_back(p);
-    *out = p;
+    allocs.push_back(p);
+    *out = static_cast<T*>(p);
     return cudaSuccess;
 }
 
@@ -668,64 +1272,153 @@ cudaError_t dalloc(DeviceLevel* L, size_t bytes, void** out) {
         if (e_ != cudaSuccess) return e_;       \
     } while (0)
 
-}  // namespace
-
-void destroy_level(DeviceLevel* L) {
-    if (!L) return;
-    for (void* p : L->allocs) cudaFree(p);
-    delete L;
-}
-
-cudaError_t create_level(const HostHierarchy& hh, bool fine, int krylov, DeviceLevel** out) {
-    DeviceLevel* L = new DeviceLevel();
-    build_level(hh, fine, &L->h);
+cudaError_t upload_level(LevelData* L) {
     const HostLevel& h = L->h;
-    auto fail = [&](cudaError_t e) {
-        destroy_level(L);
-        return e;
-    };
-    cudaError_t e;
-    if ((e = up(L, h.groups, &L->groups)) != cudaSuccess) return fail(e);
-    if ((e = up(L, h.xyz, &L->xyz)) != cudaSuccess) return fail(e);
-    if ((e = up(L, h.dir, &L->dir)) != cudaSuccess) return fail(e);
-    if ((e = up(L, h.node_ptr, &L->node_ptr)) != cudaSuccess) return fail(e);
-    if ((e = up(L, h.node_idx, &L->node_idx)) != cudaSuccess) return fail(e);
-    if ((e = up(L, h.row_ptr, &L->row_ptr)) != cudaSuccess) return fail(e);
-    if ((e = up(L, h.col_idx, &L->col_idx)) != cudaSuccess) return fail(e);
-    if ((e = up(L, h.blk_ptr, &L->blk_ptr)) != cudaSuccess) return fail(e);
-    if ((e = up(L, h.blk_src, &L->blk_src)) != cudaSuccess) return fail(e);
-    if ((e = up(L, h.grp_blk, &L->grp_blk)) != cudaSuccess) return fail(e);
-    const size_t nl = size_t(4 * h.npg);
-    const size_t nnzb = h.col_idx.size();
-    void* p;
-    if ((e = dalloc(L, nnzb * 16 * 8, &p)) != cudaSuccess) return fail(e);
-    L->A = static_cast<double*>(p);
-    if ((e = dalloc(L, size_t(h.ng) * nl * nl * 8, &p)) != cudaSuccess) return fail(e);
-    L->Jloc = static_cast<double*>(p);
-    if ((e = dalloc(L, size_t(h.ng) * nl * nl * 8, &p)) != cudaSuccess) return fail(e);
-    L->LU = static_cast<double*>(p);
-    if ((e = dalloc(L, size_t(h.ng) * nl * 4, &p)) != cudaSuccess) return fail(e);
-    L->piv = static_cast<int32_t*>(p);
-    if ((e = dalloc(L, size_t(h.ng) * nl * 8, &p)) != cudaSuccess) return fail(e);
-    L->local = static_cast<double*>(p);
-    if ((e = dalloc(L, size_t(h.ng) * nl * 8, &p)) != cudaSuccess) return fail(e);
-    L->zloc = static_cast<double*>(p);
-    if ((e = dalloc(L, size_t(h.n) * 8, &p)) != cudaSuccess) return fail(e);
-    L->mass = static_cast<double*>(p);
-    L->krylov = krylov;
-    // work vectors: r, dx, tmp, z, p, + (krylov + 1) basis vectors
-    if ((e = dalloc(L, size_t(4 * h.n) * 8 * size_t(6 + krylov + 1), &p)) != cudaSuccess) return fail(e);
-    L->work = static_cast<double*>(p);
-    if ((e = dalloc(L, size_t(krylov + 2) * size_t(krylov + 2) * 8 + 64 * 8, &p)) != cudaSuccess) return fail(e);
-    L->scal = static_cast<double*>(p);
-    if ((e = dalloc(L, size_t(kRedBlocks) * size_t(krylov + 1) * 8, &p)) != cudaSuccess) return fail(e);
-    L->part = static_cast<double*>(p);   // reduction partials, kRedBlocks per vector
-    *out = L;
+    auto& a = L->allocs;
+    CKE(up(a, h.groups, &L->groups));
+    CKE(up(a, h.xyz, &L->xyz));
+    CKE(up(a, h.dir, &L->dir));
+    CKE(up(a, h.node_ptr, &L->node_ptr));
+    CKE(up(a, h.node_idx, &L->node_idx));
+    CKE(up(a, h.row_ptr, &L->row_ptr));
+    CKE(up(a, h.col_idx, &L->col_idx));
+    CKE(up(a, h.blk_ptr, &L->blk_ptr));
+    CKE(up(a, h.blk_src, &L->blk_src));
+    CKE(up(a, h.grp_blk, &L->grp_blk));
+    CKE(up(a, h.color_groups, &L->cgroups));
     return cudaSuccess;
 }
 
-int64_t level_nodes(const DeviceLevel* L) { return L->h.n; }
-bool level_lps(const DeviceLevel* L) { return L->h.lps; }
+// FP32 matrix, group inverses and multigrid vectors of a smoothing level
+cudaError_t alloc_smoother(LevelData* L) {
+    const HostLevel& h = L->h;
+    const size_t nl = size_t(4 * h.npg);
+    CKE(dalloc(L->allocs, h.col_idx.size() * 16, &L->A));
+    CKE(dalloc(L->allocs, size_t(h.ng) * nl * nl, &L->G));
+    CKE(dalloc(L->allocs, size_t(h.ng) * nl, &L->zloc));
+    CKE(dalloc(L->allocs, size_t(4 * h.n), &L->r));
+    CKE(dalloc(L->allocs, size_t(4 * h.n), &L->e));
+    CKE(dalloc(L->allocs, size_t(4 * h.n), &L->d));
+    return cudaSuccess;
+}
+
+cudaError_t alloc_fp64_matrix(LevelData* L) {
+    if (L->A64) return cudaSuccess;
+    const HostLevel& h = L->h;
+    const size_t nl = size_t(4 * h.npg);
+    CKE(dalloc(L->allocs, size_t(h.ng) * nl * nl, &L->J64));
+    CKE(dalloc(L->allocs, h.col_idx.size() * 16, &L->A64));
+    return cudaSuccess;
+}
+
+cudaError_t upload_transfer(LevelData* L, const MgTransfer& t) {
+    std::vector<float> pw(t.P_w.begin(), t.P_w.end()), rw(t.R_w.begin(), t.R_w.end());   // dyadic: exact
+    CKE(up(L->allocs, t.P_ptr, &L->P_ptr));
+    CKE(up(L->allocs, t.P_idx, &L->P_idx));
+    CKE(up(L->allocs, pw, &L->P_w));
+    CKE(up(L->allocs, t.R_ptr, &L->R_ptr));
+    CKE(up(L->allocs, t.R_idx, &L->R_idx));
+    CKE(up(L->allocs, rw, &L->R_w));
+    return cudaSuccess;
+}
+
+void free_level_data(LevelData* L) {
+    for (void* p : L->allocs) cudaFree(p);
+    L->allocs.clear();
+}
+
+}  // namespace
+
+void destroy_level(DeviceLevel* D) {
+    if (!D) return;
+    free_level_data(&D->top);
+    for (LevelData* L : D->mg) {
+        free_level_data(L);
+        delete L;
+    }
+    for (void* p : D->allocs) cudaFree(p);
+    delete D;
+}
+
+cudaError_t create_level(const HostHierarchy& hh, bool fine, int krylov, int mg_levels, DeviceLevel** out) {
+    DeviceLevel* D = new DeviceLevel();
+    auto fail = [&](cudaError_t e) {
+        destroy_level(D);
+        return e;
+    };
+    build_level(hh, fine, &D->top.h);
+    LevelData* cur = &D->top;
+    for (int k = 0; k < mg_levels; ++k) {
+        LevelData* c = new LevelData();
+        MgTransfer t;
+        if (!coarsen_level(cur->h, &c->h, &t)) {
+            delete c;
+            break;
+        }
+        cudaError_t e = upload_transfer(cur, t);
+        D->mg.push_back(c);
+        if (e != cudaSuccess) return fail(e);
+        cur = c;
+    }
+    if (!D->mg.empty()) {
+        LevelData* c = D->mg.back();
+        c->coarsest = true;
+        if (4 * c->h.n > kMaxCoarsestUnknowns) return fail(cudaErrorInvalidValue);
+    }
+    // stabilisation in the Jacobian: the local projection on grouped levels;
+    // full fluctuations on an ungrouped coarsest multigrid level
+    D->top.stab = D->top.h.npg == 27 && D->top.h.lps ? 1 : 0;
+    for (LevelData* L : D->mg) L->stab = L->h.npg == 27 ? (L->h.lps ? 1 : 0) : (L->coarsest ? 1 : 0);
+    cudaError_t e;
+    if ((e = upload_level(&D->top)) != cudaSuccess) return fail(e);
+    if ((e = alloc_smoother(&D->top)) != cudaSuccess) return fail(e);
+    for (float** v : {&D->top.r2, &D->top.e2, &D->top.d2})
+        if ((e = dalloc(D->top.allocs, size_t(4 * D->top.h.n), v)) != cudaSuccess) return fail(e);
+    for (LevelData* L : D->mg) {
+        if ((e = upload_level(L)) != cudaSuccess) return fail(e);
+        if (L->coarsest) {
+            // the dense system on the free unknowns only
+            std::vector<int32_t> cidx(size_t(4 * L->h.n), -1), fidx;
+            for (int64_t j = 0; j < L->h.n; ++j)
+                for (int c = 0; c < 4; ++c)
+                    if (!((c < 3 && L->h.dir[size_t(j)]) || (c == 3 && j == L->h.pin))) {
+                        cidx[size_t(4 * j + c)] = int32_t(fidx.size());
+                        fidx.push_back(int32_t(4 * j + c));
+                    }
+            L->nfree = int(fidx.size());
+            if ((e = up(L->allocs, cidx, &L->cidx)) != cudaSuccess) return fail(e);
+            if ((e = up(L->allocs, fidx, &L->fidx)) != cudaSuccess) return fail(e);
+            const size_t N = size_t(std::max(L->nfree, 1));
+            if ((e = alloc_fp64_matrix(L)) != cudaSuccess) return fail(e);
+            if ((e = dalloc(L->allocs, N * N, &L->D0)) != cudaSuccess) return fail(e);
+            if ((e = dalloc(L->allocs, N * N, &L->D1)) != cudaSuccess) return fail(e);
+            if ((e = dalloc(L->allocs, N * N, &L->Dinv)) != cudaSuccess) return fail(e);
+            if ((e = dalloc(L->allocs, N, &L->piv)) != cudaSuccess) return fail(e);
+            if ((e = dalloc(L->allocs, size_t(4 * L->h.n), &L->r)) != cudaSuccess) return fail(e);
+            if ((e = dalloc(L->allocs, size_t(4 * L->h.n), &L->e)) != cudaSuccess) return fail(e);
+        } else if ((e = alloc_smoother(L)) != cudaSuccess) {
+            return fail(e);
+        }
+    }
+    const HostLevel& h = D->top.h;
+    const size_t n4 = size_t(4 * h.n);
+    const size_t nl = size_t(4 * h.npg);
+    if ((e = dalloc(D->allocs, size_t(h.ng) * nl, &D->local)) != cudaSuccess) return fail(e);
+    if ((e = dalloc(D->allocs, size_t(h.n), &D->mass)) != cudaSuccess) return fail(e);
+    if ((e = dalloc(D->allocs, 5 * n4, &D->work)) != cudaSuccess) return fail(e);
+    if ((e = dalloc(D->allocs, size_t(krylov + 1) * n4, &D->V)) != cudaSuccess) return fail(e);
+    if ((e = dalloc(D->allocs, size_t(krylov) * n4, &D->Z)) != cudaSuccess) return fail(e);
+    if ((e = dalloc(D->allocs, size_t(krylov + 2) * size_t(krylov + 6) + 64, &D->scal)) != cudaSuccess) return fail(e);
+    if ((e = dalloc(D->allocs, size_t(kRedBlocks) * size_t(krylov + 1), &D->part)) != cudaSuccess) return fail(e);
+    D->krylov = krylov;
+    *out = D;
+    return cudaSuccess;
+}
+
+int64_t level_nodes(const DeviceLevel* D) { return D->top.h.n; }
+bool level_lps(const DeviceLevel* D) { return D->top.h.lps; }
+int level_mg_depth(const DeviceLevel* D) { return int(D->mg.size()); }
+int64_t level_mg_nodes(const DeviceLevel* D, int k) { return k == 0 ? D->top.h.n : D->mg[size_t(k - 1)]->h.n; }
 
 namespace {
 
@@ -741,29 +1434,37 @@ LvPrm make_prm(const OpParams& op, const dnnmg_solver_params* sp) {
 }
 
 template <int MODE>
-cudaError_t local_terms(DeviceLevel* L, const double* x, LvPrm p, cudaStream_t s) {
-    const HostLevel& h = L->h;
+cudaError_t local_terms(DeviceLevel* D, const double* x, LvPrm p, cudaStream_t s) {
+    const LevelData& L = D->top;
+    const HostLevel& h = L.h;
     p.lps = h.lps ? p.lps : 0;
-    if (h.npg == 27)
-        level_local_kernel<27, MODE><<<nblk(h.ng, 64), 64, 0, s>>>(h.ng, L->groups, L->xyz, x, p, L->local);
-    else
-        level_local_kernel<8, MODE><<<nblk(h.ng, 64), 64, 0, s>>>(h.ng, L->groups, L->xyz, x, p, L->local);
+    if (h.npg == 27) {
+        static bool attr = false;
+        if (!attr) {
+            CKE(cudaFuncSetAttribute(level_local_child_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     int(kChildSmem)));
+            attr = true;
+        }
+        level_local_child_kernel<MODE><<<nblk(h.ng, kChildGroups), 64, kChildSmem, s>>>(h.ng, L.groups, L.xyz, x, p,
+                                                                                       D->local);
+    } else
+        level_local_kernel<8, MODE><<<nblk(h.ng, 64), 64, 0, s>>>(h.ng, L.groups, L.xyz, x, p, D->local);
     CKE(cudaGetLastError());
-    node_gather_kernel<<<nblk(h.n, 256), 256, 0, s>>>(h.n, L->node_ptr, L->node_idx, L->local,
-                                                        L->work + 2 * 4 * h.n);   // tmp
+    node_gather_kernel<<<nblk(h.n, 256), 256, 0, s>>>(h.n, L.node_ptr, L.node_idx, D->local,
+                                                        D->work + 2 * 4 * h.n);   // tmp
     return cudaGetLastError();
 }
 
-cudaError_t dot(DeviceLevel* L, const double* a, const double* b, int64_t n, double* out_dev, cudaStream_t s) {
-    dot_partial_kernel<<<kRedBlocks, 256, 0, s>>>(n, a, b, L->part);
-    dot_final_kernel<<<1, 256, 0, s>>>(L->part, kRedBlocks, out_dev);
+cudaError_t dot(DeviceLevel* D, const double* a, const double* b, int64_t n, double* out_dev, cudaStream_t s) {
+    dot_partial_kernel<<<kRedBlocks, 256, 0, s>>>(n, a, b, D->part);
+    dot_final_kernel<<<1, 256, 0, s>>>(D->part, kRedBlocks, out_dev);
     return cudaGetLastError();
 }
 
 // One classical Gram-Schmidt pass against V_0..V_{cnt-1}: h = V^T w, w -= V h.
-cudaError_t cgs_pass(DeviceLevel* L, double* w, const double* V, int cnt, int64_t n, double* h, cudaStream_t s) {
-    multi_dot_partial_kernel<<<dim3(kRedBlocks, unsigned(cnt)), 256, 0, s>>>(n, w, V, L->part);
-    multi_dot_final_kernel<<<unsigned(cnt), 256, 0, s>>>(L->part, kRedBlocks, h);
+cudaError_t cgs_pass(DeviceLevel* D, double* w, const double* V, int cnt, int64_t n, double* h, cudaStream_t s) {
+    multi_dot_partial_kernel<<<dim3(kRedBlocks, unsigned(cnt)), 256, 0, s>>>(n, w, V, D->part);
+    multi_dot_final_kernel<<<unsigned(cnt), 256, 0, s>>>(D->part, kRedBlocks, h);
     multi_axpy_kernel<<<256, 256, 0, s>>>(n, cnt, h, V, w);
     return cudaGetLastError();
 }
@@ -773,87 +1474,152 @@ cudaError_t fetch(double* host, const double* dev, size_t n, cudaStream_t s) {
     return cudaStreamSynchronize(s);
 }
 
-// Lumped mass (integral of each basis function) into L->mass and its sum
-// into the device scalar L->scal[2].
-cudaError_t compute_mass(DeviceLevel* L, const OpParams& op, cudaStream_t s) {
-    CKE(local_terms<LV_MASS>(L, nullptr, make_prm(op, nullptr), s));
-    const int64_t n = L->h.n;
-    extract_component_kernel<<<nblk(n, 256), 256, 0, s>>>(n, L->work + 2 * 4 * n, 0, L->mass);
+// Lumped mass (integral of each basis function) into D->mass and its sum
+// into the device scalar D->scal[2] (once per level).
+cudaError_t compute_mass(DeviceLevel* D, const OpParams& op, cudaStream_t s) {
+    if (D->mass_ready) return cudaSuccess;
+    CKE(local_terms<LV_MASS>(D, nullptr, make_prm(op, nullptr), s));
+    const int64_t n = D->top.h.n;
+    extract_component_kernel<<<nblk(n, 256), 256, 0, s>>>(n, D->work + 2 * 4 * n, 0, D->mass);
     CKE(cudaGetLastError());
     std::vector<double> mh(static_cast<size_t>(n));
-    CKE(fetch(mh.data(), L->mass, static_cast<size_t>(n), s));
+    CKE(fetch(mh.data(), D->mass, static_cast<size_t>(n), s));
     double sum = 0.0;
     for (double v : mh) sum += v;
-    CKE(cudaMemcpyAsync(L->scal + 2, &sum, 8, cudaMemcpyHostToDevice, s));
-    return cudaStreamSynchronize(s);
+    CKE(cudaMemcpyAsync(D->scal + 2, &sum, 8, cudaMemcpyHostToDevice, s));
+    CKE(cudaStreamSynchronize(s));
+    D->mass_ready = true;
+    return cudaSuccess;
+}
+
+template <typename T, int NPG>
+cudaError_t launch_jacobian(const LevelData& L, const double* x, const LvPrm& p, T* Jloc, cudaStream_t s) {
+    constexpr size_t smem = jac_smem_bytes<T, NPG>();
+    static bool attr = false;
+    if (!attr) {
+        CKE(cudaFuncSetAttribute(jacobian_kernel<T, NPG>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+        attr = true;
+    }
+    jacobian_kernel<T, NPG><<<unsigned(L.h.ng), 128, smem, s>>>(L.h.ng, L.groups, L.xyz, x, p, L.stab, Jloc);
+    return cudaGetLastError();
+}
+
+// Jacobian at x (the first n nodes of x are this level's nodes) into the
+// level's BSR matrix of element type T, Dirichlet and pinned rows identity
+template <typename T>
+cudaError_t assemble(const LevelData& L, const double* x, const LvPrm& p, T* Jloc, T* A, cudaStream_t s) {
+    const HostLevel& h = L.h;
+    if (h.npg == 27)
+        CKE((launch_jacobian<T, 27>(L, x, p, Jloc, s)));
+    else
+        CKE((launch_jacobian<T, 8>(L, x, p, Jloc, s)));
+    const int64_t nnzb = int64_t(h.col_idx.size());
+    if (h.npg == 27)
+        bsr_assemble_kernel<T, 27><<<nblk(nnzb * 16, 256), 256, 0, s>>>(nnzb, L.blk_ptr, L.blk_src, Jloc, A);
+    else
+        bsr_assemble_kernel<T, 8><<<nblk(nnzb * 16, 256), 256, 0, s>>>(nnzb, L.blk_ptr, L.blk_src, Jloc, A);
+    CKE(cudaGetLastError());
+    bsr_dirichlet_kernel<T><<<nblk(h.n, 128), 128, 0, s>>>(h.n, L.row_ptr, L.col_idx, L.dir, h.pin, A);
+    return cudaGetLastError();
+}
+
+template <int NPG>
+cudaError_t launch_vanka_factor(const LevelData& L, cudaStream_t s) {
+    constexpr int NL = 4 * NPG;
+    constexpr size_t smem = 2 * size_t(NL) * NL * sizeof(float);
+    static bool attr = false;
+    if (!attr) {
+        CKE(cudaFuncSetAttribute(vanka_factor_kernel<float, NPG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 int(smem)));
+        attr = true;
+    }
+    vanka_factor_kernel<float, NPG><<<unsigned(L.h.ng), 256, smem, s>>>(L.h.ng, L.grp_blk, L.A, L.G);
+    return cudaGetLastError();
+}
+
+// FP32 matrix and group inverses of a smoothing level
+cudaError_t setup_smoother(LevelData& L, const double* x, const LvPrm& p, cudaStream_t s) {
+    CKE(assemble<float>(L, x, p, L.G, L.A, s));
+    return L.h.npg == 27 ? launch_vanka_factor<27>(L, s) : launch_vanka_factor<8>(L, s);
+}
+
+// FP64 matrix, its dense LU and inverse on the coarsest level
+cudaError_t setup_coarsest(LevelData& L, const double* x, const LvPrm& p, cudaStream_t s) {
+    CKE(assemble<double>(L, x, p, L.J64, L.A64, s));
+    const int N = L.nfree;
+    if (N == 0) return cudaSuccess;
+    CKE(cudaMemsetAsync(L.D0, 0, size_t(N) * N * 8, s));
+    dense_from_bsr_kernel<<<nblk(L.h.n, 128), 128, 0, s>>>(L.h.n, N, L.row_ptr, L.col_idx, L.cidx, L.A64, L.D0);
+    CKE(cudaGetLastError());
+    double* buf[2] = {L.D0, L.D1};
+    const int grid = std::max(1, std::min(1024, int((int64_t(N) * N + 1023) / 1024)));
+    for (int k = 0; k < N; ++k) {
+        lu_step_kernel<<<grid, 256, 0, s>>>(N, k, buf[k & 1], buf[(k + 1) & 1], L.piv);
+        CKE(cudaGetLastError());
+    }
+    // one warp per column of the inverse, its column in shared memory
+    const int warps = std::max(1, std::min(4, int((160 * 1024) / (size_t(N) * 8))));
+    const size_t smem = size_t(warps) * N * 8;
+    static bool attr = false;
+    if (!attr) {
+        CKE(cudaFuncSetAttribute(lu_inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        attr = true;
+    }
+    lu_inverse_kernel<<<nblk(N, warps), 32 * warps, smem, s>>>(N, buf[N & 1], L.piv, L.Dinv);
+    return cudaGetLastError();
 }
 
 }  // namespace
 
 // r = b - A(x) with Dirichlet / pin rows zero
-cudaError_t level_residual(DeviceLevel* L, const OpParams& op, const dnnmg_solver_params* sp, const double* x,
+cudaError_t level_residual(DeviceLevel* D, const OpParams& op, const dnnmg_solver_params* sp, const double* x,
                            const double* b, double* r, cudaStream_t s) {
-    CKE(local_terms<LV_OPERATOR>(L, x, make_prm(op, sp), s));
-    const int64_t n = L->h.n;
-    CKE(cudaMemcpyAsync(r, L->work + 2 * 4 * n, size_t(4 * n) * 8, cudaMemcpyDeviceToDevice, s));
-    finish_rows_kernel<<<nblk(n, 256), 256, 0, s>>>(n, b, r, L->dir, L->h.pin, 1, 0);
+    CKE(local_terms<LV_OPERATOR>(D, x, make_prm(op, sp), s));
+    const int64_t n = D->top.h.n;
+    CKE(cudaMemcpyAsync(r, D->work + 2 * 4 * n, size_t(4 * n) * 8, cudaMemcpyDeviceToDevice, s));
+    finish_rows_kernel<<<nblk(n, 256), 256, 0, s>>>(n, b, r, D->top.dir, D->top.h.pin, 1, 0);
     return cudaGetLastError();
 }
 
 // A(x) as assembled (no row modification)
-cudaError_t level_operator(DeviceLevel* L, const OpParams& op, const dnnmg_solver_params* sp, const double* x,
+cudaError_t level_operator(DeviceLevel* D, const OpParams& op, const dnnmg_solver_params* sp, const double* x,
                            double* Ax, cudaStream_t s) {
-    CKE(local_terms<LV_OPERATOR>(L, x, make_prm(op, sp), s));
-    return cudaMemcpyAsync(Ax, L->work + 2 * 4 * L->h.n, size_t(4 * L->h.n) * 8, cudaMemcpyDeviceToDevice, s);
+    CKE(local_terms<LV_OPERATOR>(D, x, make_prm(op, sp), s));
+    return cudaMemcpyAsync(Ax, D->work + 2 * 4 * D->top.h.n, size_t(4 * D->top.h.n) * 8, cudaMemcpyDeviceToDevice, s);
 }
 
 // b(x_old): rhs of Eq. (6), Dirichlet velocity rows and pressure rows zero
-cudaError_t level_rhs(DeviceLevel* L, const OpParams& op, const double* x_old, double* b, cudaStream_t s) {
-    CKE(local_terms<LV_RHS>(L, x_old, make_prm(op, nullptr), s));
-    const int64_t n = L->h.n;
-    CKE(cudaMemcpyAsync(b, L->work + 2 * 4 * n, size_t(4 * n) * 8, cudaMemcpyDeviceToDevice, s));
-    finish_rows_kernel<<<nblk(n, 256), 256, 0, s>>>(n, nullptr, b, L->dir, -1, 0, 1);
+cudaError_t level_rhs(DeviceLevel* D, const OpParams& op, const double* x_old, double* b, cudaStream_t s) {
+    CKE(local_terms<LV_RHS>(D, x_old, make_prm(op, nullptr), s));
+    const int64_t n = D->top.h.n;
+    CKE(cudaMemcpyAsync(b, D->work + 2 * 4 * n, size_t(4 * n) * 8, cudaMemcpyDeviceToDevice, s));
+    finish_rows_kernel<<<nblk(n, 256), 256, 0, s>>>(n, nullptr, b, D->top.dir, -1, 0, 1);
     return cudaGetLastError();
 }
 
-// Jacobian dA/dx at x into the BSR matrix (rows of fixed unknowns = identity)
-cudaError_t level_jacobian(DeviceLevel* L, const OpParams& op, const dnnmg_solver_params* sp, const double* x,
+// Jacobians at x on every level (coarser levels at the injected iterate:
+// their nodes are the first nodes of the finer level), the smoothers, and
+// the coarsest level's dense inverse
+cudaError_t level_jacobian(DeviceLevel* D, const OpParams& op, const dnnmg_solver_params* sp, const double* x,
                            cudaStream_t s) {
-    const HostLevel& h = L->h;
-    LvPrm p = make_prm(op, sp);
-    p.lps = h.lps ? 1 : 0;
-    const int nl = 4 * h.npg;
-    if (h.npg == 27)
-        level_jacobian_kernel<27><<<nblk(h.ng * nl, 128), 128, 0, s>>>(h.ng, L->groups, L->xyz, x, p, L->Jloc);
-    else
-        level_jacobian_kernel<8><<<nblk(h.ng * nl, 128), 128, 0, s>>>(h.ng, L->groups, L->xyz, x, p, L->Jloc);
-    CKE(cudaGetLastError());
-    const int64_t nnzb = int64_t(h.col_idx.size());
-    if (h.npg == 27)
-        bsr_assemble_kernel<27><<<nblk(nnzb * 16, 256), 256, 0, s>>>(nnzb, L->blk_ptr, L->blk_src, L->Jloc, L->A);
-    else
-        bsr_assemble_kernel<8><<<nblk(nnzb * 16, 256), 256, 0, s>>>(nnzb, L->blk_ptr, L->blk_src, L->Jloc, L->A);
-    CKE(cudaGetLastError());
-    bsr_dirichlet_kernel<<<nblk(h.n, 128), 128, 0, s>>>(h.n, L->row_ptr, L->col_idx, L->dir, h.pin, L->A);
-    CKE(cudaGetLastError());
-    // group-Vanka factors
-    const size_t smem = 2 * size_t(nl) * nl * 8;   // the LU and the inverse
-    if (h.npg == 27) {
-        CKE(cudaFuncSetAttribute(vanka_factor_kernel<27>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
-        vanka_factor_kernel<27><<<unsigned(h.ng), 256, smem, s>>>(h.ng, L->grp_blk, L->A, L->LU, L->piv);
-    } else {
-        vanka_factor_kernel<8><<<unsigned(h.ng), 256, smem, s>>>(h.ng, L->grp_blk, L->A, L->LU, L->piv);
-    }
-    L->has_jacobian = true;
-    return cudaGetLastError();
+    const LvPrm p = make_prm(op, sp);
+    CKE(setup_smoother(D->top, x, p, s));
+    for (LevelData* L : D->mg) CKE(L->coarsest ? setup_coarsest(*L, x, p, s) : setup_smoother(*L, x, p, s));
+    D->has_jacobian = true;
+    return cudaSuccess;
 }
 
-// dense copy of the assembled matrix (small levels; tests)
-cudaError_t level_dense_jacobian(DeviceLevel* L, double* dense_host) {
-    const HostLevel& h = L->h;
+// dense copy of the FP64 Jacobian of the solve level at x (small levels; tests)
+cudaError_t level_dense_jacobian(DeviceLevel* D, const OpParams& op, const dnnmg_solver_params* sp, const double* x,
+                                 double* dense_host, cudaStream_t s) {
+    LevelData& L = D->top;
+    CKE(alloc_fp64_matrix(&L));
+    CKE(assemble<double>(L, x, make_prm(op, sp), L.J64, L.A64, s));
+    const HostLevel& h = L.h;
     const size_t nnzb = h.col_idx.size();
     std::vector<double> A(nnzb * 16);
-    CKE(cudaMemcpy(A.data(), L->A, A.size() * 8, cudaMemcpyDeviceToHost));
+    CKE(cudaMemcpyAsync(A.data(), L.A64, A.size() * 8, cudaMemcpyDeviceToHost, s));
+    CKE(cudaStreamSynchronize(s));
     const int64_t N = 4 * h.n;
     std::fill(dense_host, dense_host + N * N, 0.0);
     for (int64_t i = 0; i < h.n; ++i)
@@ -866,139 +1632,202 @@ cudaError_t level_dense_jacobian(DeviceLevel* L, double* dense_host) {
 
 namespace {
 
-cudaError_t precond(DeviceLevel* L, const double* r, double* z, cudaStream_t s) {
-    const HostLevel& h = L->h;
-    if (h.npg == 27)
-        vanka_apply_kernel<27><<<unsigned(h.ng), 128, 0, s>>>(h.ng, L->groups, L->LU, r, L->zloc);
-    else
-        vanka_apply_kernel<8><<<unsigned(h.ng), 128, 0, s>>>(h.ng, L->groups, L->LU, r, L->zloc);
+// `sweeps` multiplicative group-Vanka sweeps on L, colours in increasing
+// order (reverse = decreasing, for the sweeps after the coarse correction)
+cudaError_t smooth_mult(LevelData& L, int sweeps, bool e_zero, float omega, bool reverse, cudaStream_t s) {
+    const HostLevel& h = L.h;
+    if (e_zero) CKE(cudaMemsetAsync(L.e, 0, size_t(4 * h.n) * 4, s));
+    const int nc = int(h.color_ptr.size()) - 1;
+    for (int it = 0; it < sweeps; ++it)
+        for (int k = 0; k < nc; ++k) {
+            const int c = reverse ? nc - 1 - k : k;
+            const int32_t c0 = h.color_ptr[size_t(c)], cnt = h.color_ptr[size_t(c) + 1] - c0;
+            if (cnt == 0) continue;
+            if (h.npg == 27) {
+                vanka_colour_residual_kernel<27><<<unsigned(cnt), 128, 0, s>>>(L.cgroups + c0, L.groups, L.row_ptr,
+                                                                               L.col_idx, L.A, L.r, L.e, L.zloc);
+                vanka_colour_update_kernel<27><<<unsigned(cnt), 128, 0, s>>>(L.cgroups + c0, L.groups, L.G, L.zloc,
+                                                                             omega, L.e);
+            } else {
+                vanka_colour_residual_kernel<8><<<unsigned(cnt), 32, 0, s>>>(L.cgroups + c0, L.groups, L.row_ptr,
+                                                                             L.col_idx, L.A, L.r, L.e, L.zloc);
+                vanka_colour_update_kernel<8><<<unsigned(cnt), 32, 0, s>>>(L.cgroups + c0, L.groups, L.G, L.zloc,
+                                                                           omega, L.e);
+            }
+        }
+    return cudaGetLastError();
+}
+
+// `sweeps` damped additive group-Vanka sweeps on L: e += omega V(r - A e)
+// (e = omega V(r) first when e_zero)
+cudaError_t smooth(LevelData& L, int sweeps, bool e_zero, float omega, cudaStream_t s) {
+    const HostLevel& h = L.h;
+    for (int it = 0; it < sweeps; ++it) {
+        const bool first = it == 0 && e_zero;
+        const float* d = L.r;
+        if (!first) {
+            bsr_spmv_kernel<float><<<nblk(32 * h.n, 256), 256, 0, s>>>(h.n, L.row_ptr, L.col_idx, L.A, L.e,
+                                                                              L.r, L.d);
+            d = L.d;
+        }
+        if (h.npg == 27)
+            vanka_apply_kernel<float, 27><<<unsigned(h.ng), 128, 0, s>>>(h.ng, L.groups, L.G, d, L.zloc);
+        else
+            vanka_apply_kernel<float, 8><<<unsigned(h.ng), 32, 0, s>>>(h.ng, L.groups, L.G, d, L.zloc);
+        vanka_update_kernel<float><<<nblk(h.n, 256), 256, 0, s>>>(h.n, L.node_ptr, L.node_idx, L.zloc, omega,
+                                                                   first ? 1 : 0, L.e);
+    }
+    return cudaGetLastError();
+}
+
+// e ~ A^{-1} r on level k (0 = the solve level) by one V-cycle
+cudaError_t vcycle(DeviceLevel* D, int k, cudaStream_t s) {
+    LevelData& L = k == 0 ? D->top : *D->mg[size_t(k - 1)];
+    const HostLevel& h = L.h;
+    if (L.coarsest) {
+        CKE(cudaMemsetAsync(L.e, 0, size_t(4 * h.n) * 4, s));
+        if (L.nfree == 0) return cudaSuccess;
+        dense_matvec_kernel<float><<<nblk(int64_t(L.nfree) * 32, 256), 256, 0, s>>>(L.nfree, L.fidx, L.Dinv, L.r, L.e);
+        return cudaGetLastError();
+    }
+    if (size_t(k) == D->mg.size()) return smooth(L, 1, true, 1.0f, s);   // one-level: one Vanka application
+    const bool mult = D->mg_smoother == 1;
+    bool e_zero = true;
+    if (D->mg_pre > 0) {
+        CKE(mult ? smooth_mult(L, D->mg_pre, true, D->omega, false, s) : smooth(L, D->mg_pre, true, D->omega, s));
+        e_zero = false;
+    }
+    if (e_zero) CKE(cudaMemsetAsync(L.e, 0, size_t(4 * h.n) * 4, s));
+    bsr_spmv_kernel<float><<<nblk(32 * h.n, 256), 256, 0, s>>>(h.n, L.row_ptr, L.col_idx, L.A, L.e, L.r, L.d);
+    LevelData& C = *D->mg[size_t(k)];
+    mg_restrict_kernel<float><<<nblk(C.h.n, 256), 256, 0, s>>>(C.h.n, L.R_ptr, L.R_idx, L.R_w, L.d, C.dir, C.h.pin,
+                                                                C.r);
     CKE(cudaGetLastError());
-    vanka_average_kernel<<<nblk(h.n, 256), 256, 0, s>>>(h.n, L->node_ptr, L->node_idx, L->zloc, z);
+    CKE(vcycle(D, k + 1, s));
+    mg_prolong_add_kernel<float><<<nblk(h.n, 256), 256, 0, s>>>(h.n, L.P_ptr, L.P_idx, L.P_w, C.e, L.dir, h.pin, L.e);
+    CKE(cudaGetLastError());
+    return mult ? smooth_mult(L, D->mg_post, false, D->omega, true, s) : smooth(L, D->mg_post, false, D->omega, s);
+}
+
+// z = M^{-1} v (FP64 in and out, FP32 inside)
+cudaError_t precond(DeviceLevel* D, const double* v, double* z, cudaStream_t s) {
+    const int64_t n4 = 4 * D->top.h.n;
+    convert_kernel<double, float><<<nblk(n4, 256), 256, 0, s>>>(n4, v, D->top.r);
+    CKE(vcycle(D, 0, s));
+    convert_kernel<float, double><<<nblk(n4, 256), 256, 0, s>>>(n4, D->top.e, z);
     return cudaGetLastError();
 }
 
-cudaError_t spmv(DeviceLevel* L, const double* x, double* y, cudaStream_t s) {
-    const int64_t n = L->h.n;
-    bsr_spmv_kernel<<<nblk(4 * n, 256), 256, 0, s>>>(n, L->row_ptr, L->col_idx, L->A, x, y);
+// y = J x (r == null) or y = r - J x with the FP32 Jacobian: x (and r)
+// rounded to FP32, the product in FP32, the result widened to FP64.  The
+// matrix is itself the Jacobian rounded to FP32, so this adds an error of
+// the same order; Newton's FP64 residual decides convergence.
+cudaError_t spmv64(DeviceLevel* D, const double* x, const double* r, double* y, cudaStream_t s) {
+    LevelData& L = D->top;
+    const int64_t n4 = 4 * L.h.n;
+    convert_kernel<double, float><<<nblk(n4, 256), 256, 0, s>>>(n4, x, L.e2);
+    if (r) convert_kernel<double, float><<<nblk(n4, 256), 256, 0, s>>>(n4, r, L.r2);
+    bsr_spmv_kernel<float><<<nblk(32 * L.h.n, 256), 256, 0, s>>>(L.h.n, L.row_ptr, L.col_idx, L.A, L.e2,
+                                                                  r ? L.r2 : nullptr, L.d2);
+    convert_kernel<float, double><<<nblk(n4, 256), 256, 0, s>>>(n4, L.d2, y);
     return cudaGetLastError();
 }
 
-// Right-preconditioned restarted GMRES for J dx = r (dx zero on entry).
-cudaError_t gmres(DeviceLevel* L, const double* r, double* dx, double rtol, int max_it, cudaStream_t s,
-                  int* iters, double* res_out) {
-    const int64_t n4 = 4 * L->h.n;
-    const int m = L->krylov;
-    double* z = L->work + 3 * n4;
-    double* w = L->work + 5 * n4;
-    double* V = L->work + 6 * n4;   // (m + 1) vectors
-    double* H = L->scal + 64;       // (m+1) x m column-major on the device: H[i + j*(m+1)], then m+1 scratch
-    std::vector<double> Hh(size_t(m + 1) * m), cs(m), sn(m), gvec(m + 1), y(m);
-    cudaMemsetAsync(dx, 0, size_t(n4) * 8, s);
-    double beta0 = 0.0;
-    {
-        CKE(dot(L, r, r, n4, L->scal, s));
-        double t;
-        CKE(fetch(&t, L->scal, 1, s));
-        beta0 = std::sqrt(t);
-    }
+// Flexible right-preconditioned restarted GMRES for J dx = r (dx zero on
+// entry).  The host reads the residual estimate every `check` iterations.
+cudaError_t fgmres(DeviceLevel* D, const double* r, double* dx, double rtol, int max_it, cudaStream_t s,
+                   int* iters, double* res_out) {
+    const int64_t n4 = 4 * D->top.h.n;
+    const int m = D->krylov;
+    double* w = D->work + 4 * n4;
+    double* rr = D->work + 3 * n4;
+    double* V = D->V;
+    double* Z = D->Z;
+    double* st = D->scal + 8;               // beta0, residual estimate, stop
+    double* nrm = D->scal + 12;
+    double* h2 = D->scal + 16;              // second CGS pass: m + 1
+    double* cs = h2 + (m + 1);
+    double* sn = cs + m;
+    double* g = sn + m;                     // m + 1
+    double* y = g + (m + 1);                // m
+    double* H = y + m;                      // (m + 1) x m, column-major
+    const int check = D->mg.empty() ? 8 : 2;
+    CKE(cudaMemsetAsync(dx, 0, size_t(n4) * 8, s));
+    CKE(dot(D, r, r, n4, nrm, s));
+    set_beta0_kernel<<<1, 1, 0, s>>>(nrm, st);
+    double hs[3];
+    CKE(fetch(hs, st, 3, s));
     *iters = 0;
-    *res_out = beta0;
-    if (beta0 == 0.0) return cudaSuccess;
-    // residual of the current iterate: r - J dx; start from r
-    double* rr = L->work + 4 * n4;   // shares the pressure scratch: not used concurrently
+    *res_out = hs[0];
+    if (hs[0] == 0.0) return cudaSuccess;
     CKE(cudaMemcpyAsync(rr, r, size_t(n4) * 8, cudaMemcpyDeviceToDevice, s));
-    double beta = beta0;
-    while (*iters < max_it) {
-        // v0 = rr / beta
-        CKE(dot(L, rr, rr, n4, L->scal, s));
-        scale_inv_sqrt_kernel<<<256, 256, 0, s>>>(n4, L->scal, rr, V);
-        std::fill(gvec.begin(), gvec.end(), 0.0);
-        gvec[0] = beta;
-        int j = 0;
-        for (; j < m && *iters < max_it; ++j, ++(*iters)) {
-            double* vj = V + int64_t(j) * n4;
-            double* vn = V + int64_t(j + 1) * n4;
-            CKE(precond(L, vj, z, s));
-            CKE(spmv(L, z, w, s));
-            // orthogonalise against V_0..V_j: classical Gram-Schmidt twice (as
-            // robust as the modified form, two multi-vector passes instead of
-            // 2 (j + 1) single ones); the column gets the sum of both passes
-            double* hcol = H + j * (m + 1);
-            double* h2 = H + size_t(m + 1) * m;   // scratch column after H
-            CKE(cgs_pass(L, w, V, j + 1, n4, hcol, s));
-            CKE(cgs_pass(L, w, V, j + 1, n4, h2, s));
-            add_vec_kernel<<<1, 64, 0, s>>>(j + 1, h2, hcol);
-            double* hn = H + (j + 1) + j * (m + 1);
-            CKE(dot(L, w, w, n4, hn, s));
-            scale_inv_sqrt_kernel<<<256, 256, 0, s>>>(n4, hn, w, vn);
-            CKE(fetch(Hh.data() + size_t(j) * (m + 1), H + j * (m + 1), size_t(j + 2), s));
-            double* col = Hh.data() + size_t(j) * (m + 1);
-            col[j + 1] = std::sqrt(std::max(col[j + 1], 0.0));
-            for (int i = 0; i < j; ++i) {
-                const double t = cs[i] * col[i] + sn[i] * col[i + 1];
-                col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
-                col[i] = t;
-            }
-            const double den = std::hypot(col[j], col[j + 1]);
-            cs[j] = den > 0 ? col[j] / den : 1.0;
-            sn[j] = den > 0 ? col[j + 1] / den : 0.0;
-            col[j] = den;
-            col[j + 1] = 0.0;
-            gvec[j + 1] = -sn[j] * gvec[j];
-            gvec[j] = cs[j] * gvec[j];
-            beta = std::fabs(gvec[j + 1]);
-            if (beta <= rtol * beta0) {
-                ++j;
-                ++(*iters);
-                break;
-            }
-        }
-        // y = R^{-1} g; dx += M^{-1} V y
-        for (int i = j - 1; i >= 0; --i) {
-            double t = gvec[i];
-            for (int k = i + 1; k < j; ++k) t -= Hh[size_t(k) * (m + 1) + i] * y[k];
-            y[i] = t / Hh[size_t(i) * (m + 1) + i];
-        }
-        double* comb = w;
-        CKE(cudaMemsetAsync(comb, 0, size_t(n4) * 8, s));
-        for (int i = 0; i < j; ++i) axpy_kernel<<<256, 256, 0, s>>>(n4, y[i], V + int64_t(i) * n4, comb);
-        CKE(precond(L, comb, z, s));
-        axpy_kernel<<<256, 256, 0, s>>>(n4, 1.0, z, dx);
+    for (;;) {
+        CKE(dot(D, rr, rr, n4, nrm, s));
+        scale_inv_sqrt_kernel<<<256, 256, 0, s>>>(n4, nrm, rr, V);
+        cycle_init_kernel<<<1, 256, 0, s>>>(m, nrm, g, st);
         CKE(cudaGetLastError());
-        if (beta <= rtol * beta0 || *iters >= max_it) break;
-        // true residual for the restart: rr = r - J dx
-        CKE(spmv(L, dx, rr, s));
-        CKE(cudaMemcpyAsync(w, r, size_t(n4) * 8, cudaMemcpyDeviceToDevice, s));
-        axpy_kernel<<<256, 256, 0, s>>>(n4, -1.0, rr, w);
-        CKE(cudaMemcpyAsync(rr, w, size_t(n4) * 8, cudaMemcpyDeviceToDevice, s));
-        CKE(dot(L, rr, rr, n4, L->scal, s));
-        double t;
-        CKE(fetch(&t, L->scal, 1, s));
-        beta = std::sqrt(t);
-        if (beta <= rtol * beta0) break;
+        int j = 0, jn = -1;
+        while (j < m && *iters < max_it) {
+            double* vj = V + int64_t(j) * n4;
+            double* zj = Z + int64_t(j) * n4;
+            double* vn = V + int64_t(j + 1) * n4;
+            CKE(precond(D, vj, zj, s));
+            CKE(spmv64(D, zj, nullptr, w, s));
+            // orthogonalise against V_0..V_j: classical Gram-Schmidt twice;
+            // the column gets the sum of both passes
+            double* hcol = H + size_t(j) * (m + 1);
+            CKE(cgs_pass(D, w, V, j + 1, n4, hcol, s));
+            CKE(cgs_pass(D, w, V, j + 1, n4, h2, s));
+            add_vec_kernel<<<1, 64, 0, s>>>(j + 1, h2, hcol);
+            double* hn = hcol + (j + 1);
+            CKE(dot(D, w, w, n4, hn, s));
+            scale_inv_sqrt_kernel<<<256, 256, 0, s>>>(n4, hn, w, vn);
+            givens_kernel<<<1, 1, 0, s>>>(j, m, H, cs, sn, g, rtol, st);
+            CKE(cudaGetLastError());
+            ++j;
+            ++(*iters);
+            if (j % check == 0 || j == m || *iters >= max_it) {
+                CKE(fetch(hs, st, 3, s));
+                if (hs[2] >= 0.0) {
+                    jn = int(hs[2]);
+                    break;
+                }
+            }
+        }
+        const bool converged = jn >= 0;
+        if (jn < 0) jn = j;
+        ls_solve_kernel<<<1, 1, 0, s>>>(jn, m, H, g, y);
+        multi_axpy_add_kernel<<<256, 256, 0, s>>>(n4, jn, y, Z, dx);
+        CKE(cudaGetLastError());
+        *res_out = hs[1];
+        if (converged || *iters >= max_it) break;
+        CKE(spmv64(D, dx, r, rr, s));   // true residual for the restart: rr = r - J dx
     }
-    *res_out = beta;
     return cudaSuccess;
 }
 
 }  // namespace
 
-// Newton solve of A(x) = b on level L; x holds the Dirichlet values (and the
-// initial guess) on entry.
-cudaError_t level_solve(DeviceLevel* L, const OpParams& op, const dnnmg_solver_params* sp, const double* b, double* x,
+// Newton solve of A(x) = b on the level; x holds the Dirichlet values (and
+// the initial guess) on entry.
+cudaError_t level_solve(DeviceLevel* D, const OpParams& op, const dnnmg_solver_params* sp, const double* b, double* x,
                         cudaStream_t s, dnnmg_solve_stats* st) {
-    const int64_t n = L->h.n, n4 = 4 * n;
-    double* r = L->work;
-    double* dx = L->work + n4;
+    const int64_t n = D->top.h.n, n4 = 4 * n;
+    double* r = D->work;
+    double* dx = D->work + n4;
     dnnmg_solve_stats stats{};
-    if (L->h.mean_zero_pressure) CKE(compute_mass(L, op, s));
+    D->mg_pre = sp->mg_pre;
+    D->mg_post = sp->mg_post;
+    D->mg_smoother = sp->mg_smoother;
+    D->omega = float(sp->mg_omega);
+    if (D->top.h.mean_zero_pressure) CKE(compute_mass(D, op, s));
     double r0 = -1.0, rprev = -1.0;
     bool reassemble = true;
     for (int it = 0;; ++it) {
-        CKE(level_residual(L, op, sp, x, b, r, s));
-        CKE(dot(L, r, r, n4, L->scal, s));
+        CKE(level_residual(D, op, sp, x, b, r, s));
+        CKE(dot(D, r, r, n4, D->scal, s));
         double t;
-        CKE(fetch(&t, L->scal, 1, s));
+        CKE(fetch(&t, D->scal, 1, s));
         const double rn = std::sqrt(t);
         if (!std::isfinite(rn)) {
             stats.residual = rn;
@@ -1015,29 +1844,29 @@ cudaError_t level_solve(DeviceLevel* L, const OpParams& op, const dnnmg_solver_p
         }
         if (it >= sp->newton_max) break;
         if (rprev > 0 && rn / rprev > sp->rho_max) reassemble = true;
-        if (reassemble || !L->has_jacobian) {
-            CKE(level_jacobian(L, op, sp, x, s));
+        if (reassemble || !D->has_jacobian) {
+            CKE(level_jacobian(D, op, sp, x, s));
             stats.jacobian_assemblies++;
             reassemble = false;
         }
         rprev = rn;
         int gi = 0;
         double gres = 0.0;
-        CKE(gmres(L, r, dx, sp->gmres_rtol, sp->gmres_max, s, &gi, &gres));
+        CKE(fgmres(D, r, dx, sp->gmres_rtol, sp->gmres_max, s, &gi, &gres));
         stats.gmres_iterations += gi;
         axpy_kernel<<<256, 256, 0, s>>>(n4, 1.0, dx, x);
         CKE(cudaGetLastError());
-        if (L->h.mean_zero_pressure) {
+        if (D->top.h.mean_zero_pressure) {
             // p -= (mass . p) / (mass . 1)
-            double* pv = L->work + 2 * n4;   // tmp (n entries used)
+            double* pv = D->work + 2 * n4;   // tmp (n entries used)
             extract_component_kernel<<<nblk(n, 256), 256, 0, s>>>(n, x, 3, pv);
-            CKE(dot(L, L->mass, pv, n, L->scal + 1, s));
-            mean_ratio_kernel<<<1, 1, 0, s>>>(L->scal + 1, L->scal + 2, L->scal + 3);
-            pressure_shift_kernel<<<nblk(n, 256), 256, 0, s>>>(n, L->scal + 3, x);
+            CKE(dot(D, D->mass, pv, n, D->scal + 1, s));
+            mean_ratio_kernel<<<1, 1, 0, s>>>(D->scal + 1, D->scal + 2, D->scal + 3);
+            pressure_shift_kernel<<<nblk(n, 256), 256, 0, s>>>(n, D->scal + 3, x);
             CKE(cudaGetLastError());
         }
     }
-    L->has_jacobian = false;   // next solve starts with a fresh Jacobian
+    D->has_jacobian = false;   // next solve starts with a fresh Jacobian
     if (st) *st = stats;
     return cudaSuccess;
 }

@@ -97,14 +97,50 @@ class Mesh(dict):
         return int(self["cells"].shape[0])
 
 
-def cavity_mesh(n: int, jitter: float = 0.0, seed: int = 0, grouped: bool = True) -> Mesh:
+def first_level(idx: np.ndarray, n_fine: int, levels: int) -> np.ndarray:
+    """Level (0 = coarsest of levels + 1) at which grid line idx of a grid of
+    n_fine intervals refined `levels` times from n_fine / 2^levels appears."""
+    lev = np.full(idx.shape, levels, dtype=np.int64)
+    for s in range(levels - 1, -1, -1):
+        step = 1 << (levels - s)
+        lev = np.where(idx % step == 0, s, lev)
+    return lev
+
+
+def nested_order(i, j, k, flip, nbi, nbj, levels: int) -> np.ndarray:
+    """Order of cells (i, j, k) (indices at the finest level, `levels`
+    refinements of a base grid) such that every 8 consecutive cells are the
+    children of one parent, child (a, b, c) at offset a + 2 b + 4 c in the
+    parent's local frame, recursively: cells sorted by base cell, then by
+    child index at each level from the coarsest down.  flip marks cells whose
+    local xi axis runs against i.  nbi, nbj: base cells along i and j (the
+    base index is ib + nbi (jb + nbj kb))."""
+    i, j, k = (np.asarray(a, dtype=np.int64) for a in (i, j, k))
+    flip = np.asarray(flip, dtype=bool)
+    key = (i >> levels) + nbi * ((j >> levels) + nbj * (k >> levels))
+    for s in range(levels - 1, -1, -1):
+        a = (i >> s) & 1
+        a = np.where(flip, 1 - a, a)
+        key = key * 8 + a + 2 * ((j >> s) & 1) + 4 * ((k >> s) & 1)
+    return np.argsort(key, kind="stable")
+
+
+def cavity_mesh(n: int, jitter: float = 0.0, seed: int = 0, grouped: bool = True,
+                levels: int | None = None) -> Mesh:
     """Unit cube split into n^3 hexahedra (n even when ``grouped``).
 
     With ``grouped`` the cells are ordered parent by parent: the 8 children of
     parent (I, J, K) of the n/2 grid are consecutive, child (i, j, k) at
-    offset i + 2 j + 4 k.  ``jitter`` moves interior vertices by up to
-    jitter * h in each coordinate (seeded), which makes the cells non-affine.
+    offset i + 2 j + 4 k.  ``levels`` = k >= 1 nests this k times (n a
+    multiple of 2^k): see ``nested_order``; the mesh is then the k-th uniform
+    refinement of the (n / 2^k)^3 grid with its vertices numbered coarsest
+    level first.  ``jitter`` moves interior vertices by up to jitter * h in
+    each coordinate (seeded), which makes the cells non-affine.
     """
+    if levels is not None and levels >= 1:
+        if n % (1 << levels):
+            raise ValueError("nested cavity mesh needs n divisible by 2^levels")
+        grouped = True
     if grouped and n % 2:
         raise ValueError("grouped cavity mesh needs an even n")
     m = n + 1
@@ -120,12 +156,20 @@ def cavity_mesh(n: int, jitter: float = 0.0, seed: int = 0, grouped: bool = True
         di, dj, dk = c & 1, (c >> 1) & 1, (c >> 2) & 1
         corners.append((ii + di) + m * (jj + dj) + m * m * (kk + dk))
     cells = np.stack(corners, axis=1).astype(np.int32)
-    if grouped:
-        h = n // 2
-        parent = (ii // 2) + h * (jj // 2) + h * h * (kk // 2)
-        child = (ii % 2) + 2 * (jj % 2) + 4 * (kk % 2)
-        order = np.argsort(parent * 8 + child, kind="stable")
+    k_lev = levels if (levels is not None and levels >= 1) else (1 if grouped else 0)
+    if k_lev >= 1:
+        order = nested_order(ii, jj, kk, np.zeros_like(ii, dtype=bool), n >> k_lev, n >> k_lev, k_lev)
         cells = cells[order]
+    if levels is not None and levels >= 1:
+        vi = np.arange(m)
+        lev1 = first_level(vi, n, levels)
+        vl = np.maximum(np.maximum(lev1[:, None, None], lev1[None, :, None]), lev1[None, None, :])
+        vlev = vl.transpose(2, 1, 0).ravel()          # vertex id = i + m j + m^2 k
+        perm = np.argsort(vlev, kind="stable")        # new id -> old id
+        inv = np.empty_like(perm)
+        inv[perm] = np.arange(perm.size)
+        xyz = xyz[perm]
+        cells = inv[cells].astype(np.int32)
     on_b = np.any((xyz == 0.0) | (xyz == 1.0), axis=1)
     bc = np.where(on_b, 1, 0).astype(np.int32)
     bc[xyz[:, 2] == 1.0] = 2
@@ -136,7 +180,8 @@ def cavity_mesh(n: int, jitter: float = 0.0, seed: int = 0, grouped: bool = True
         xyz = xyz + d
     return Mesh(xyz=np.ascontiguousarray(xyz), cells=np.ascontiguousarray(cells),
                 vertex_bc=bc, patch_groups=bool(grouped),
-                meta=dict(kind="cavity", n=n, jitter=jitter, seed=seed))
+                meta=dict(kind="cavity", n=n, jitter=jitter, seed=seed,
+                          mg_levels=int(levels) if (levels is not None and levels >= 1) else 0))
 
 
 def channel_geometry(seed: int):
@@ -148,7 +193,7 @@ def channel_geometry(seed: int):
     return D, cx, cy
 
 
-def channel_mesh(nz: int, seed: int = 0, box_half: float = 0.15) -> Mesh:
+def channel_mesh(nz: int, seed: int = 0, box_half: float = 0.15, levels: int = 0) -> Mesh:
     """Hexahedral mesh of the channel with a cylindrical obstacle.
 
     The x-y cross-section is a 3 x 3 block layout: an O-grid of four blocks
@@ -156,17 +201,29 @@ def channel_mesh(nz: int, seed: int = 0, box_half: float = 0.15) -> Mesh:
     cylinder, and eight rectangular blocks filling the rest of the channel.
     The 2D mesh has cell size about H / nz and is extruded into nz layers in z.
     Cell counts: about 6.3 nz^3 (nz = 19 gives ~43k cells, nz = 37 ~318k).
+
+    ``levels`` = k >= 1 builds the k-th uniform refinement of the mesh with
+    nz / 2^k layers (nz a multiple of 2^k): every block keeps 2^k times the
+    base block's cells per direction, points on the circle stay on it, the
+    cells are ordered by ``nested_order`` (8 consecutive cells are the
+    children of one parent, recursively) and vertices are numbered by the
+    level on which they first appear, so the first vertices of the mesh are
+    those of each coarser level.  Base points are reproduced bit for bit.
     """
     H, Lx = CHANNEL_HEIGHT, CHANNEL_LENGTH
     D, cx, cy = channel_geometry(seed)
     R, b = 0.5 * D, box_half
-    h = H / nz
+    if levels < 0 or nz % (1 << levels):
+        raise ValueError("nz must be a multiple of 2^levels")
+    nzb = nz >> levels
+    h = H / nzb
     nx1 = max(1, round((cx - b) / h))
     nx3 = max(1, round((Lx - cx - b) / h))
     nth = max(2, round(2 * b / h))
     ny1 = max(1, round((cy - b) / h))
     ny3 = max(1, round((H - cy - b) / h))
     nr = max(2, round((b - R) / h))
+    f = 1 << levels
     xs = [0.0, cx - b, cx + b, Lx]
     ys = [0.0, cy - b, cy + b, H]
     ncx = [nx1, nth, nx3]
@@ -175,8 +232,16 @@ def channel_mesh(nz: int, seed: int = 0, box_half: float = 0.15) -> Mesh:
     pts: dict = {}
     plist: list = []
     flags: list = []
+    plev: list = []       # level on which a point first appears
 
-    def pid(x, y, on_circle=False):
+    def lev_of(i, j):
+        for s_ in range(levels + 1):
+            step = 1 << (levels - s_)
+            if i % step == 0 and j % step == 0:
+                return s_
+        return levels
+
+    def pid(x, y, lev, on_circle=False):
         key = (round(x * 1e9), round(y * 1e9))
         k = pts.get(key)
         if k is None:
@@ -184,27 +249,34 @@ def channel_mesh(nz: int, seed: int = 0, box_half: float = 0.15) -> Mesh:
             pts[key] = k
             plist.append((x, y))
             flags.append(on_circle)
-        elif on_circle:
-            flags[k] = True
+            plev.append(lev)
+        else:
+            if on_circle:
+                flags[k] = True
+            plev[k] = min(plev[k], lev)
         return k
 
     quads = []
+    qidx = []             # (block, i, j) of each quad at the finest level
 
-    def add_block(P):   # P: [nu+1][nv+1] point ids, structured
+    def add_block(P, blk):   # P: [nu+1][nv+1] point ids, structured
         nu, nv = len(P) - 1, len(P[0]) - 1
         for i in range(nu):
             for j in range(nv):
                 quads.append((P[i][j], P[i + 1][j], P[i][j + 1], P[i + 1][j + 1]))
+                qidx.append((blk, i, j))
 
+    blocks = []           # base cells of each block along i and j
     for bx in range(3):
         for by in range(3):
             if bx == 1 and by == 1:
                 continue
             x0, x1, y0, y1 = xs[bx], xs[bx + 1], ys[by], ys[by + 1]
-            nu, nv = ncx[bx], ncy[by]
-            P = [[pid(x0 + (x1 - x0) * i / nu, y0 + (y1 - y0) * j / nv) for j in range(nv + 1)]
+            nu, nv = ncx[bx] * f, ncy[by] * f
+            P = [[pid(x0 + (x1 - x0) * i / nu, y0 + (y1 - y0) * j / nv, lev_of(i, j)) for j in range(nv + 1)]
                  for i in range(nu + 1)]
-            add_block(P)
+            add_block(P, len(blocks))
+            blocks.append((ncx[bx], ncy[by]))
 
     # O-grid: side s of the square, parameter i along the side (nth cells),
     # radial index j from the circle (j = 0) to the square (j = nr).
@@ -214,21 +286,23 @@ def channel_mesh(nz: int, seed: int = 0, box_half: float = 0.15) -> Mesh:
         ((cx + b, cy + b), (cx - b, cy + b), 0.25 * math.pi, 0.75 * math.pi),   # top
         ((cx - b, cy + b), (cx - b, cy - b), 0.75 * math.pi, 1.25 * math.pi),   # left
     ]
+    nthf, nrf = nth * f, nr * f
     for (s0, s1, a0, a1) in sides:
         P = []
-        for i in range(nth + 1):
-            t = i / nth
+        for i in range(nthf + 1):
+            t = i / nthf
             sq = (s0[0] + (s1[0] - s0[0]) * t, s0[1] + (s1[1] - s0[1]) * t)
             a = a0 + (a1 - a0) * t
             ci = (cx + R * math.cos(a), cy + R * math.sin(a))
             col = []
-            for j in range(nr + 1):
-                w = j / nr
+            for j in range(nrf + 1):
+                w = j / nrf
                 x = (1 - w) * ci[0] + w * sq[0]
                 y = (1 - w) * ci[1] + w * sq[1]
-                col.append(pid(x, y, on_circle=(j == 0)))
+                col.append(pid(x, y, lev_of(i, j), on_circle=(j == 0)))
             P.append(col)
-        add_block(P)
+        add_block(P, len(blocks))
+        blocks.append((nth, nr))
 
     p2 = np.array(plist, dtype=np.float64)
     on_circle = np.array(flags, dtype=bool)
@@ -246,22 +320,51 @@ def channel_mesh(nz: int, seed: int = 0, box_half: float = 0.15) -> Mesh:
     for k in range(nz + 1):
         xyz[k * n2:(k + 1) * n2, 0:2] = p2
         xyz[k * n2:(k + 1) * n2, 2] = zs[k]
-    cells = np.empty((nz * q.shape[0], 8), dtype=np.int64)
+    nq = q.shape[0]
+    cells = np.empty((nz * nq, 8), dtype=np.int64)
     for k in range(nz):
-        sl = slice(k * q.shape[0], (k + 1) * q.shape[0])
+        sl = slice(k * nq, (k + 1) * nq)
         cells[sl, 0:4] = q + k * n2
         cells[sl, 4:8] = q + (k + 1) * n2
+    if levels >= 1:
+        qi = np.array(qidx, dtype=np.int64)
+        # one base grid per block: base cell index = block offset + (ib + nbi jb) + n_base2d * kb
+        off = np.cumsum([0] + [bi * bj for bi, bj in blocks])
+        nb2 = int(off[-1])
+        kk = np.repeat(np.arange(nz), nq)
+        ii = np.tile(qi[:, 1], nz)
+        jj = np.tile(qi[:, 2], nz)
+        blk = np.tile(qi[:, 0], nz)
+        fl = np.tile(flip, nz)
+        nbi = np.array([bi for bi, _ in blocks])[blk]
+        base = off[blk] + (ii >> levels) + nbi * (jj >> levels) + nb2 * (kk >> levels)
+        key = base
+        for s_ in range(levels - 1, -1, -1):
+            a_ = (ii >> s_) & 1
+            a_ = np.where(fl, 1 - a_, a_)
+            key = key * 8 + a_ + 2 * ((jj >> s_) & 1) + 4 * ((kk >> s_) & 1)
+        cells = cells[np.argsort(key, kind="stable")]
+        zlev = first_level(np.arange(nz + 1), nz, levels)
+        vlev = np.maximum(np.tile(np.array(plev, dtype=np.int64), nz + 1), np.repeat(zlev, n2))
+        perm = np.argsort(vlev, kind="stable")
+        inv = np.empty_like(perm)
+        inv[perm] = np.arange(perm.size)
+        xyz = xyz[perm]
+        on_circle = np.tile(on_circle, nz + 1)[perm]
+        cells = inv[cells]
+    else:
+        on_circle = np.tile(on_circle, nz + 1)
     eps = 1e-12
     x, y, z = xyz[:, 0], xyz[:, 1], xyz[:, 2]
     wall = (np.abs(y) < eps) | (np.abs(y - H) < eps) | (np.abs(z) < eps) | (np.abs(z - H) < eps)
-    wall |= np.tile(on_circle, nz + 1)
+    wall |= on_circle
     bc = np.zeros(xyz.shape[0], dtype=np.int32)
     bc[np.abs(x - Lx) < eps] = 3
     bc[wall] = 1
     bc[np.abs(x) < eps] = 2
-    return Mesh(xyz=xyz, cells=cells.astype(np.int32), vertex_bc=bc, patch_groups=False,
+    return Mesh(xyz=xyz, cells=cells.astype(np.int32), vertex_bc=bc, patch_groups=levels >= 1,
                 meta=dict(kind="channel", nz=nz, seed=seed, D=D, cx=cx, cy=cy,
-                          nu_re200=D / 200.0))
+                          nu_re200=D / 200.0, mg_levels=int(levels)))
 
 
 # --------------------------------------------------------------------------

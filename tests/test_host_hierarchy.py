@@ -69,3 +69,34 @@ def test_invalid_meshes_and_arguments_are_refused():
     twice["cells"][0, 1] = twice["cells"][0, 0]         # a repeated vertex
     with pytest.raises(capi.DnnmgError):
         capi.HostHierarchy(twice)
+
+
+def test_multigrid_levels_of_nested_meshes():
+    # the solver's coarsening (parents of the 27-node groups) recovers every
+    # level of a nested mesh; level L+1 coarsens to level L first
+    # (a coarser level needs 8 nodes of free velocity: the cavity stops at 4^3,
+    # as 2^3 has only its centre)
+    m = I.cavity_mesh(8, levels=3)
+    h = capi.HostHierarchy(m)
+    assert h.mg_nodes(0, 16) == [729, 125]
+    assert h.mg_nodes(0, 1) == [729, 125]
+    assert h.mg_nodes(0, 0) == [729]
+    assert h.mg_nodes(1, 16) == [17 ** 3, 729, 125]
+    assert h.mg_nodes(1, 0) == [17 ** 3]
+    h.close()
+    m = I.channel_mesh(8, seed=0, levels=2)
+    nv = [m.n_vertices]
+    cells = m["cells"]
+    for _ in range(2):
+        g = cells.reshape(-1, 8, 8)
+        cells = np.stack([g[:, K, K] for K in range(8)], axis=1)
+        nv.append(int(cells.max()) + 1)
+    h = capi.HostHierarchy(m)
+    assert h.mg_nodes(0, 16) == nv
+    h.close()
+    # a mesh that is not nested has no level below L (and L+1 only L)
+    m = I.channel_mesh(4, seed=1)
+    h = capi.HostHierarchy(m)
+    assert h.mg_nodes(0, 16) == [m.n_vertices]
+    assert h.mg_nodes(1, 16) == [h.sizes["n_fine_nodes"], m.n_vertices]
+    h.close()

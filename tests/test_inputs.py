@@ -66,3 +66,53 @@ def test_smooth_fields_take_the_papers_training_statistics():
     f = I.smooth_field(m["xyz"], seed=4)
     assert np.allclose(f.mean(axis=0), mean, rtol=0, atol=1e-9)
     assert np.allclose(f.std(axis=0), sigma, rtol=1e-12)
+
+
+def _coarsen(cells):
+    """Parents of consecutive 8-cell groups: corner K of parent g is vertex K
+    of child K; the 8 children must share the 27 nodes of a refined hex."""
+    g = np.asarray(cells).reshape(-1, 8, 8)
+    for t in range(8):
+        for k in range(8):
+            pos = ((t & 1) + (k & 1)) + 3 * (((t >> 1) & 1) + ((k >> 1) & 1)) + 9 * (((t >> 2) & 1) + ((k >> 2) & 1))
+            # any other (t', k') landing on the same node must name the same vertex
+            for t2 in range(t + 1, 8):
+                for k2 in range(8):
+                    pos2 = (((t2 & 1) + (k2 & 1)) + 3 * (((t2 >> 1) & 1) + ((k2 >> 1) & 1))
+                            + 9 * (((t2 >> 2) & 1) + ((k2 >> 2) & 1)))
+                    if pos2 == pos:
+                        assert np.array_equal(g[:, t, k], g[:, t2, k2])
+    return np.stack([g[:, K, K] for K in range(8)], axis=1)
+
+
+def test_nested_meshes_coarsen_to_their_base():
+    # a mesh with `levels` = k is the k-th refinement of its base: every 8
+    # consecutive cells are the children of one parent, recursively, and the
+    # parents' corners are the vertices 0 .. n - 1 of the coarser level
+    for m, base in [(I.cavity_mesh(8, levels=3, jitter=0.1, seed=2), I.cavity_mesh(1, grouped=False)),
+                    (I.channel_mesh(8, seed=1, levels=2), I.channel_mesh(2, seed=1))]:
+        k = m["meta"]["mg_levels"]
+        cells = m["cells"]
+        for _ in range(k):
+            cells = _coarsen(cells)
+            nv = cells.max() + 1
+            assert np.array_equal(np.unique(cells), np.arange(nv))
+        assert cells.shape[0] == base.n_cells and nv == base.n_vertices
+        if m["meta"]["kind"] == "channel":
+            # the base mesh's vertices, bit for bit, and its boundary kinds
+            key = lambda X: np.lexsort(X.T[::-1])   # noqa: E731
+            a, b = m["xyz"][:nv], base["xyz"]
+            assert np.array_equal(a[key(a)], b[key(b)])
+            assert np.array_equal(m["vertex_bc"][:nv][key(a)], base["vertex_bc"][key(b)])
+
+
+def test_nested_mesh_sizes():
+    # cavity n^3 refined from (n/8)^3: (n+1)^3 vertices; channel cells 8^k
+    # times the base's
+    m = I.cavity_mesh(8, levels=3)
+    assert m.n_cells == 512 and m.n_vertices == 729 and m["patch_groups"]
+    for nz, k in [(4, 1), (8, 2)]:
+        assert I.channel_mesh(nz, seed=0, levels=k).n_cells == 8 ** k * I.channel_mesh(nz >> k, seed=0).n_cells
+    # levels = 0 is the unrefined generator
+    a, b = I.channel_mesh(6, seed=3), I.channel_mesh(6, seed=3, levels=0)
+    assert all(np.array_equal(a[x], b[x]) for x in ("xyz", "cells", "vertex_bc"))
