@@ -124,14 +124,19 @@ def network_traffic(n_patches):
     return rec["bytes_per_patch"] * n_patches
 
 
-def stage_rooflines(stage_ms, n_patches, peaks, peak_src, clocks, affine_frac=0.0):
+def stage_rooflines(stage_ms, n_patches, peaks, peak_src, clocks, affine_frac=0.0, fp32_tflops=None):
     """Per-stage time and the fraction of the roof that binds it: FP32 ALU
-    (152 SMs x 128 lanes x 2 flop x the median SM clock under load) for the
-    element-integral stages (their work counted for the mesh's share of
-    parallelepiped cells), HBM (measured copy bandwidth) for the gathers,
-    BF16 tensor (measured sustained) for the network."""
-    sm_ghz = (clocks.get("sm_mhz") or 2070.0) / 1000.0
-    alu_tflops = 152 * FP32_LANES_PER_SM * 2 * sm_ghz / 1000.0
+    for the element-integral stages (their work counted for the mesh's share
+    of parallelepiped cells) against the FMA throughput measured by
+    dnnmg_probe_fma (else 152 SMs x 128 lanes x 2 flop x the median SM clock
+    under load), HBM (measured copy bandwidth) for the gathers, BF16 tensor
+    (measured sustained) for the network."""
+    if fp32_tflops:
+        alu_tflops, alu_src = fp32_tflops, "FP32 ALU measured by the FMA probe"
+    else:
+        sm_ghz = (clocks.get("sm_mhz") or 2070.0) / 1000.0
+        alu_tflops = 152 * FP32_LANES_PER_SM * 2 * sm_ghz / 1000.0
+        alu_src = "FP32 ALU from unit counts x median SM clock"
     out = {}
     for name in STAGES:
         ms = stage_ms[name]
@@ -151,7 +156,7 @@ def stage_rooflines(stage_ms, n_patches, peaks, peak_src, clocks, affine_frac=0.
                 e.update(bound="hbm", achieved=round(gbs, 1), peak=peaks["hbm_gbs"], unit="GB/s",
                          frac=round(gbs / peaks["hbm_gbs"], 3))
         out[name] = e
-    out["peak_source"] = f"{peak_src} (HBM copy, BF16 sustained); FP32 ALU from unit counts x median SM clock"
+    out["peak_source"] = f"{peak_src} (HBM copy, BF16 sustained); {alu_src}"
     out["parallelepiped_cells"] = round(affine_frac, 4)
     return out
 
@@ -406,9 +411,14 @@ def run_ours(args, rank, world, local_rank):
                            "patches_per_s": round(q.n_patches * 1000.0 / ms, 1), "timed_steps": 5}
             q.close()
 
+    # measured SIMT FMA peaks (the ALU roofs of the element-integral stages)
+    simt = {"fp32_tflops": round(capi.dnnmg_probe_fma(capi.FP32, iters=65536, blocks_per_sm=8), 2),
+            "fp64_tflops": round(capi.dnnmg_probe_fma(capi.FP64, iters=2048, blocks_per_sm=8), 3),
+            "how": "dnnmg_probe_fma: 8 x SMs blocks of 256 threads, 8 independent FMA chains each, "
+                   "best of 3 timed launches after a warm-up"}
     res = dict(elapsed_ms=elapsed_ms, net_ms=net_ms, stage_ms=stage_ms, launches=launches, clocks=clk.summary(),
                e2e_s=e2e_s, nc=nc, nf=nf, nv=nv, fp64=fp64, fp32=fp32, paper=paper,
-               affine_frac=parallelepiped_fraction(m))
+               affine_frac=parallelepiped_fraction(m), simt=simt)
     p.close()
     return res
 
@@ -486,29 +496,33 @@ def run_serving(args):
     print(json.dumps(line))
 
 
-def _fine_initial(p, m, x0):
-    """The prolongated initial coarse state with the fine Dirichlet data."""
+def _fine_initial(p, m):
+    """The fine-level initial state: at rest with the fine Dirichlet data (the
+    start of the training trajectories)."""
     import numpy as np
     import torch
     from paper_2307_14837_gb300 import capi, inputs as I
     kind = p.mesh_data(capi.FINE_KIND)
     dirf = (kind == 1) | (kind == 2)
-    xr = p.prolongate(torch.as_tensor(x0, device="cuda")).cpu().numpy()
+    xr = np.zeros((p.n_fine, 4))
     xr[dirf, 0:3] = I.dirichlet_values(m, p.mesh_data(capi.FINE_XYZ), kind)[dirf]
     return torch.as_tensor(xr, device="cuda")
 
 
-def equal_error(steps=20, train_steps=8, epochs=300):
+def equal_error(steps=20, train_steps=60, epochs=100, train_nus=(0.007, 0.0085, 0.0115, 0.013)):
     """Velocity error against the fine-mesh solution of the plain coarse
     scheme and of DNN-MG in the FP64 and BF16 forms, with a network trained
     on the project's own fine solves (the learned part, Sec. 6.4), on the
     cavity workload: 8^3 -> 16^3, Re 100 (nu = 0.01), backward Euler
     dt = 0.01, 20 steps, network 228-256-256-81.
 
-    Training: fine-level (L+1) trajectories at nu = 0.008 and 0.0125
-    (train_steps steps each) by the GPU Newton-GMRES-multigrid solver, BF16
-    training kernels, AdamW (lr 1e-3, weight decay 1e-5), `epochs` epochs of
-    batches of 1024.  Evaluation at the held-out nu = 0.01.
+    Training: fine-level (L+1) trajectories at nu = 0.007, 0.0085, 0.0115
+    and 0.013 (train_steps steps each, past the evaluation window: the
+    DNN-MG loop feeds its corrections back through the coarse right-hand
+    side, and states beyond the training horizon drift) by the GPU
+    Newton-GMRES-multigrid solver, BF16 training kernels, AdamW (lr 1e-3,
+    weight decay 1e-5), `epochs` epochs of batches of 1024.  Evaluation at
+    the held-out nu = 0.01.
 
     Errors (Sec. 6.5-6.6): e_v(n) = |v~_n + d_n - v_n| / |v_n| over the fine
     nodes' velocities (d = 0 for the plain scheme) and the time-integrated
@@ -528,7 +542,7 @@ def equal_error(steps=20, train_steps=8, epochs=300):
     widths = (228, 256, 256, 81)
     solver = lambda: capi.dnnmg_solver_defaults(mg_levels=3)   # noqa: E731
     Xs, Ts = [], []
-    for nu_t in (0.008, 0.0125):
+    for nu_t in train_nus:
         X, Tg, _ = T.make_samples(m, nu_t, dt, 1.0, train_steps, solver=solver())
         Xs.append(X)
         Ts.append(Tg)
@@ -564,7 +578,7 @@ def equal_error(steps=20, train_steps=8, epochs=300):
     vel, rate, stats = {}, {}, {}
     # fine reference: the plain scheme on level L+1
     p = PatchPath(m, nu, dt, 1.0, "fp64")
-    xr = _fine_initial(p, m, x0)
+    xr = _fine_initial(p, m)
     prm = solver()
 
     def fine_step():
@@ -602,7 +616,7 @@ def equal_error(steps=20, train_steps=8, epochs=300):
     ref = vel["fine"]
     out = {"workload": "cavity 8^3->16^3 (nested: multigrid 8^3, 4^3, 2^3), Re 100, BE dt 0.01, "
                        f"{steps} steps; network 228-256-256-81 trained on the GPU (BF16 kernels, AdamW) on "
-                       f"fine-level solves at nu 0.008 and 0.0125 ({train_steps} steps each, "
+                       f"fine-level solves at nu {', '.join(map(str, train_nus))} ({train_steps} steps each, "
                        f"{X.shape[0]} samples, {epochs} epochs), evaluated at nu 0.01",
            "reference": "plain scheme on level L+1 (GPU Newton-GMRES-multigrid, FP64)",
            "train_loss_first_last": [hist[0], hist[-1]], "train_seconds": round(t_train, 2)}
@@ -843,7 +857,9 @@ def result_line(res, args, world, el):
                      "network_ms_per_step": net_ms, "network_share": net_ms / ms},
         "e2e": {"value": world * K / res["e2e_s"] if res["e2e_s"] > 0 else None, "unit": UNIT,
                 "h2d_bytes_per_step": (nv + nf) * 16, "d2h_bytes_per_step": (nf + nv) * 16},
-        "stages": stage_rooflines(res["stage_ms"], nc, peaks, peak_src, res["clocks"], res["affine_frac"]),
+        "stages": stage_rooflines(res["stage_ms"], nc, peaks, peak_src, res["clocks"], res["affine_frac"],
+                                  (res.get("simt") or {}).get("fp32_tflops")),
+        "simt_peaks": res.get("simt"),
         "fp32_form": res["fp32"],
         "paper_forms": res["paper"],
         "gpu_launches": res["launches"],

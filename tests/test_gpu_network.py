@@ -66,3 +66,13 @@ def test_network_rows_against_oracle(mesh, precision, widths, M, bn):
     tol = 2e-2 if precision == "bf16" else 1e-5
     assert emax <= tol, (emax, ep99)
     p.close()
+
+
+def test_fma_probe_measures_a_plausible_simt_peak():
+    # the ALU roof of the element kernels is measured, not derived: FP32
+    # between 10 and 200 TFLOP/s on this part (152 SMs x 128 lanes x 2 flop
+    # x ~2 GHz = 80), FP64 far below FP32
+    f32 = capi.dnnmg_probe_fma(capi.FP32, iters=16384)
+    f64 = capi.dnnmg_probe_fma(capi.FP64, iters=512)
+    assert 10.0 < f32 < 200.0, f32
+    assert 0.0 < f64 < 0.5 * f32, (f32, f64)

@@ -89,6 +89,41 @@ def test_mixed_equals_alone(precision, workers):
             assert np.abs(xa[:, 0:3]).max() > 0.1
 
 
+def test_whole_steps_with_multigrid_mixed_equal_alone():
+    # whole DNN-MG steps (the coarse Newton-GMRES-multigrid solve on) for
+    # nested meshes of different sizes served together: every result is the
+    # one the simulation gets on its own, bit for bit
+    Ws, ss, ts = _net()
+    prm = capi.dnnmg_solver_defaults(mg_levels=3)
+    reqs = [Request("m8", I.cavity_mesh(8, levels=2), NU, DT, 1.0, 3),
+            Request("m8j", I.cavity_mesh(8, levels=2, jitter=0.1, seed=4), 2 * NU, DT, 1.0, 2),
+            Request("m16", I.cavity_mesh(16, levels=3), NU, DT, 1.0, 2)]
+    srv = Server(WIDTHS, Ws, ss, ts, memory_budget=1 << 33, max_rows=8192, precision="bf16", solver=prm)
+    for r in reqs:
+        srv.submit(r)
+    while srv.live or srv.queue:
+        srv.step()
+    srv.close()
+    for r in reqs:
+        p = PatchPath(r.mesh, r.nu, r.dt, r.theta, "bf16")
+        p.set_network(WIDTHS, Ws, ss, ts)
+        m = r.mesh
+        dirc = (np.asarray(m["vertex_bc"]) == 1) | (np.asarray(m["vertex_bc"]) == 2)
+        x0 = np.zeros((p.n_coarse, 4))
+        x0[dirc, 0:3] = I.dirichlet_values(m, m["xyz"], m["vertex_bc"])[dirc]
+        x = torch.as_tensor(x0, device="cuda")
+        F, bcf = p.rhs_restrict(x.to(p.dtype), torch.zeros((p.n_fine, 3), dtype=p.dtype, device="cuda"))
+        b = bcf.double().contiguous()
+        for _ in range(r.n_steps):
+            st = capi.dnnmg_time_step(p.ctx, 1, x, b, F, prm)
+            assert st["converged"] == 1
+        torch.cuda.synchronize()
+        assert capi.dnnmg_level_mg(p.ctx, capi.LEVEL_COARSE, prm)[-1] == 125   # down to 4^3
+        np.testing.assert_array_equal(srv.results[r.name]["x"], x.cpu().numpy(), err_msg=r.name)
+        np.testing.assert_array_equal(srv.results[r.name]["F"], F.double().cpu().numpy(), err_msg=r.name)
+        p.close()
+
+
 def test_served_fp64_matches_oracle():
     from oracle import dnnmg as odnnmg, fem, mesh as omesh
     Ws, ss, ts = _net()
