@@ -66,7 +66,7 @@
 extern "C" {
 #endif
 
-#define DNNMG_ABI_VERSION 4
+#define DNNMG_ABI_VERSION 5
 
 typedef struct dnnmg_ctx dnnmg_ctx;
 
@@ -115,7 +115,21 @@ typedef struct {
                            * level L+1 refined again by the same rules).
                            * J = 2: n_in = 1000 + features, X row stride
                            * 1024, n_out = 375 (Table 2) */
-    int32_t reserved;     /* must be 0 */
+    int32_t element;      /* 0 or 1 = Q1/Q1 on the refined mesh (27-node groups
+                           * of 8 children, two-level projection); 2 = Q2/Q2,
+                           * the paper's element (Sec. 3.2): triquadratic
+                           * velocity and pressure with the one-level
+                           * projection onto Q1 of each cell (Eq. (5)), 3 x 3
+                           * x 3 Gauss points.  With Q2 the coarse level's
+                           * unknowns sit at the nodes of the mesh refined
+                           * once (n_coarse_nodes of dnnmg_sizes: x_coarse and
+                           * b_coarse are [n_coarse_nodes][4]), the fine
+                           * level's at the nodes of the mesh refined twice,
+                           * and a patch is a coarse cell with those 125
+                           * nodes: patch_levels must be 0 or 2 (the J = 2
+                           * layout: n_in 1012 / 1024, n_out 375).  The fine
+                           * level's projection terms use alpha0 = 0.02,
+                           * delta0 = 0.1 (Eq. (8)). */
 } dnnmg_params;
 
 /* Patch network of Sec. 4 in inference form: layer i computes
@@ -137,6 +151,10 @@ typedef struct {
     int32_t n_in_padded;       /* row stride of X: 256 (J = 1), 1024 (J = 2) */
     int32_t n_out;             /* 3 x nodes per patch: 81 (J = 1), 375 (J = 2) */
     int32_t precision;
+    int64_t n_coarse_nodes;    /* rows of x_coarse / b_coarse: n_coarse_vertices (Q1) or
+                                * the nodes of the mesh refined once (Q2) */
+    int32_t element;           /* 1 (Q1) or 2 (Q2) */
+    int32_t reserved;
 } dnnmg_sizes;
 
 /* Mesh data a caller can read back (dnnmg_get_mesh_data). */
@@ -146,7 +164,10 @@ typedef enum {
     DNNMG_FINE_KIND = 2,    /* int32 [n_fine_nodes]: boundary kind 0..3 */
     DNNMG_FINE_XYZ = 3,     /* double [n_fine_nodes][3] */
     DNNMG_EDGE_LENGTHS = 4, /* double [n_patches][12] */
-    DNNMG_GEOMETRY = 5      /* double [n_patches][12 or 24]: the geometry features of the input row */
+    DNNMG_GEOMETRY = 5,     /* double [n_patches][12 or 24]: the geometry features of the input row */
+    DNNMG_COARSE_XYZ = 6,   /* double [n_coarse_nodes][3]: the nodes of x_coarse (the mesh's
+                             * vertices, or for Q2 the nodes of the mesh refined once) */
+    DNNMG_COARSE_KIND = 7   /* int32 [n_coarse_nodes]: their boundary kinds 0..3 */
 } dnnmg_mesh_item;
 
 /* Build the level-(L+1) hierarchy of a coarse mesh on the host, upload it to

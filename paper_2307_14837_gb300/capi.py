@@ -16,7 +16,7 @@ import numpy as np
 from . import build as _build
 
 FP64, FP32, BF16 = 0, 1, 2
-PATCH_MAP, VALENCE, FINE_KIND, FINE_XYZ, EDGE_LENGTHS, GEOMETRY = 0, 1, 2, 3, 4, 5
+PATCH_MAP, VALENCE, FINE_KIND, FINE_XYZ, EDGE_LENGTHS, GEOMETRY, COARSE_XYZ, COARSE_KIND = 0, 1, 2, 3, 4, 5, 6, 7
 BUF_R, BUF_X, BUF_Y, BUF_D = 0, 1, 2, 3
 N_IN, N_OUT = 228, 81
 
@@ -36,7 +36,7 @@ class MeshDesc(ctypes.Structure):
 class Params(ctypes.Structure):
     _fields_ = [("nu", ctypes.c_double), ("dt", ctypes.c_double), ("theta", ctypes.c_double),
                 ("precision", ctypes.c_int32), ("features", ctypes.c_int32),
-                ("patch_levels", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("patch_levels", ctypes.c_int32), ("element", ctypes.c_int32)]
 
 
 class NetDesc(ctypes.Structure):
@@ -48,7 +48,8 @@ class Sizes(ctypes.Structure):
     _fields_ = [("n_coarse_vertices", ctypes.c_int64), ("n_patches", ctypes.c_int64),
                 ("n_fine_nodes", ctypes.c_int64), ("n_coarse_edges", ctypes.c_int64),
                 ("n_coarse_faces", ctypes.c_int64), ("n_in", ctypes.c_int32),
-                ("n_in_padded", ctypes.c_int32), ("n_out", ctypes.c_int32), ("precision", ctypes.c_int32)]
+                ("n_in_padded", ctypes.c_int32), ("n_out", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("n_coarse_nodes", ctypes.c_int64), ("element", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 _VP = ctypes.c_void_p
@@ -151,7 +152,8 @@ def _mesh_item(sz, item):
     return {PATCH_MAP: ((sz["n_patches"], sz["n_out"] // 3), np.int32), VALENCE: ((sz["n_fine_nodes"],), np.int32),
             FINE_KIND: ((sz["n_fine_nodes"],), np.int32), FINE_XYZ: ((sz["n_fine_nodes"], 3), np.float64),
             EDGE_LENGTHS: ((sz["n_patches"], 12), np.float64),
-            GEOMETRY: ((sz["n_patches"], sz["n_in"] - 8 * (sz["n_out"] // 3)), np.float64)}[item]
+            GEOMETRY: ((sz["n_patches"], sz["n_in"] - 8 * (sz["n_out"] // 3)), np.float64),
+            COARSE_XYZ: ((sz["n_coarse_nodes"], 3), np.float64), COARSE_KIND: ((sz["n_coarse_nodes"],), np.int32)}[item]
 
 
 class HostHierarchy:
@@ -197,14 +199,15 @@ class HostHierarchy:
             pass
 
 
-def dnnmg_create(mesh, nu, dt, theta, precision, stream=None, features=12, patch_levels=1):
+def dnnmg_create(mesh, nu, dt, theta, precision, stream=None, features=12, patch_levels=1, element=1):
     """mesh: dict with xyz [nv,3] float64, cells [nc,8] int32, vertex_bc [nv] int32.
     stream: a torch.cuda.Stream, an int handle, or None (default stream).
     features: geometry features per patch, 12 (edge lengths) or 24.
-    patch_levels: J of the patches, 1 (27 nodes) or 2 (125 nodes)."""
+    patch_levels: J of the patches, 1 (27 nodes) or 2 (125 nodes).
+    element: 1 (Q1/Q1) or 2 (Q2/Q2, 125-node patches; patch_levels 0 or 2)."""
     lib = load()
     desc, keep = _mesh_desc(mesh)
-    prm = Params(float(nu), float(dt), float(theta), int(precision), int(features), int(patch_levels), 0)
+    prm = Params(float(nu), float(dt), float(theta), int(precision), int(features), int(patch_levels), int(element))
     handle = _VP()
     s = getattr(stream, "cuda_stream", stream)
     _check(None, lib.dnnmg_create(ctypes.byref(desc), ctypes.byref(prm), s, ctypes.byref(handle)))

@@ -114,7 +114,14 @@ void fill_sizes(const HostHierarchy& h, int32_t precision, dnnmg_sizes* out) {
     out->n_in_padded = n_in_pad(h);
     out->n_out = n_out(h);
     out->precision = precision;
+    out->n_coarse_nodes = h.element == 2 ? h.n_mid : h.nv;
+    out->element = h.element;
+    out->reserved = 0;
 }
+
+// rows of x_coarse / b_coarse: coarse vertices (Q1) or level L+1 nodes (Q2)
+int64_t coarse_nodes(const HostHierarchy& h) { return h.element == 2 ? h.n_mid : h.nv; }
+bool is_q2(const dnnmg_ctx* c) { return c->host.element == 2; }
 
 // one item of a host hierarchy into a caller buffer of `bytes` bytes
 dnnmg_status copy_mesh_item(const HostHierarchy& h, int32_t item, void* host_buf, size_t bytes) {
@@ -134,6 +141,14 @@ dnnmg_status copy_mesh_item(const HostHierarchy& h, int32_t item, void* host_buf
             return DNNMG_OK;
         }
         case DNNMG_GEOMETRY: src = h.geo.data(); n = h.geo.size() * 8; break;
+        case DNNMG_COARSE_XYZ:
+            src = h.element == 2 ? h.xyz_mid.data() : h.xyz_c.data();
+            n = (h.element == 2 ? h.xyz_mid.size() : h.xyz_c.size()) * 8;
+            break;
+        case DNNMG_COARSE_KIND:
+            src = h.element == 2 ? h.kind_mid.data() : h.bc_c.data();
+            n = (h.element == 2 ? h.kind_mid.size() : h.bc_c.size()) * 4;
+            break;
         default: return DNNMG_EINVAL;
     }
     if (bytes < n) return DNNMG_EINVAL;
@@ -183,8 +198,11 @@ dnnmg_status dnnmg_create(const dnnmg_mesh_desc* mesh, const dnnmg_params* param
     *out = nullptr;
     if (!mesh || !params) return DNNMG_EINVAL;
     if (params->features != 0 && params->features != 12 && params->features != 24) return DNNMG_EINVAL;
-    if (params->patch_levels < 0 || params->patch_levels > 2 || params->reserved != 0) return DNNMG_EINVAL;
-    const int J = params->patch_levels == 2 ? 2 : 1;
+    if (params->patch_levels < 0 || params->patch_levels > 2 || params->element < 0 || params->element > 2)
+        return DNNMG_EINVAL;
+    const bool q2 = params->element == 2;
+    if (q2 && params->patch_levels == 1) return DNNMG_EINVAL;   // Q2 patches have the J = 2 layout
+    const int J = (params->patch_levels == 2 || q2) ? 2 : 1;
     if (params->precision < DNNMG_FP64 || params->precision > DNNMG_BF16 ||
         !(params->dt > 0.0) || !(params->nu >= 0.0) || !(params->theta >= 0.0 && params->theta <= 1.0))
         return DNNMG_EINVAL;
@@ -196,6 +214,7 @@ dnnmg_status dnnmg_create(const dnnmg_mesh_desc* mesh, const dnnmg_params* param
         delete ctx;
         return st;
     }
+    ctx->host.element = q2 ? 2 : 1;
     ctx->precision = params->precision;
     ctx->op = OpParams{1.0 / params->dt, params->theta, params->nu};
     ctx->stream = static_cast<cudaStream_t>(cuda_stream);
@@ -254,9 +273,59 @@ dnnmg_status dnnmg_create(const dnnmg_mesh_desc* mesh, const dnnmg_params* param
         if ((st = upload(ctx, ef.data(), ef.size(), &pf)) != DNNMG_OK) return done(st);
         dm.geo_f = pf;
     }
+    if (q2) {
+        // coarse Q2 nodes (level L+1) and the fine Q2 level: the 8 cells of
+        // every patch (child (i, j, k) has patch nodes (2i + a, 2j + b, 2k + c))
+        dm.element = 2;
+        dm.n_mid = h.n_mid;
+        int32_t* q;
+        if ((st = upload(ctx, h.patch_map_mid.data(), h.patch_map_mid.size(), &q)) != DNNMG_OK) return done(st);
+        dm.patch_map_mid = q;
+        if ((st = upload(ctx, h.mid_ptr.data(), h.mid_ptr.size(), &q)) != DNNMG_OK) return done(st);
+        dm.mid_ptr = q;
+        if ((st = upload(ctx, h.mid_idx.data(), h.mid_idx.size(), &q)) != DNNMG_OK) return done(st);
+        dm.mid_idx = q;
+        std::vector<uint8_t> md(size_t(h.n_mid));
+        for (int64_t j = 0; j < h.n_mid; ++j) md[j] = (h.kind_mid[j] == 1 || h.kind_mid[j] == 2) ? 1 : 0;
+        if ((st = upload(ctx, md.data(), md.size(), &pu)) != DNNMG_OK) return done(st);
+        dm.mid_dir = pu;
+        const int64_t ncell = 8 * h.nc;
+        std::vector<int32_t> cells(size_t(27 * ncell));
+        for (int64_t P = 0; P < h.nc; ++P)
+            for (int t = 0; t < 8; ++t)
+                for (int a = 0; a < 27; ++a) {
+                    const int i = t & 1, j = (t >> 1) & 1, k = (t >> 2) & 1;
+                    const int iota = (2 * i + a % 3) + 5 * (2 * j + (a / 3) % 3) + 25 * (2 * k + a / 9);
+                    cells[size_t(27 * (8 * P + t) + a)] = h.patch_map[size_t(125 * P + iota)];
+                }
+        std::vector<int32_t> cptr(size_t(h.n_fine + 1), 0), cidx(cells.size());
+        for (int32_t v : cells) cptr[size_t(v) + 1]++;
+        for (int64_t j = 0; j < h.n_fine; ++j) cptr[j + 1] += cptr[j];
+        {
+            std::vector<int32_t> fill(cptr.begin(), cptr.end() - 1);
+            for (size_t e = 0; e < cells.size(); ++e) cidx[size_t(fill[size_t(cells[e])]++)] = int32_t(e);
+        }
+        Q2Level& L = dm.q2fine;
+        L.n = h.n_fine;
+        L.ncell = ncell;
+        if ((st = upload(ctx, cells.data(), cells.size(), &q)) != DNNMG_OK) return done(st);
+        L.cells = q;
+        if ((st = upload(ctx, cptr.data(), cptr.size(), &q)) != DNNMG_OK) return done(st);
+        L.node_ptr = q;
+        if ((st = upload(ctx, cidx.data(), cidx.size(), &q)) != DNNMG_OK) return done(st);
+        L.node_idx = q;
+        double* xd;
+        if ((st = upload(ctx, h.xyz_f.data(), h.xyz_f.size(), &xd)) != DNNMG_OK) return done(st);
+        L.xyz = xd;
+        L.dir = dm.fine_dir;
+    }
     const size_t fe = field_elem(ctx->precision);
     const size_t xe = ctx->precision == DNNMG_BF16 ? 2 : fe;
-    const size_t nc = size_t(h.nc), nf = size_t(h.n_fine), nv = size_t(h.nv);
+    const size_t nc = size_t(h.nc), nf = size_t(h.n_fine), nv = size_t(coarse_nodes(h));
+    if (q2) {
+        if ((st = alloc(ctx, nf * 4 * fe, &ctx->buf_xf)) != DNNMG_OK) return done(st);
+        if ((st = alloc(ctx, nc * 8 * 27 * 4 * fe, &ctx->q2_local)) != DNNMG_OK) return done(st);
+    }
     const size_t npn = size_t(h.npn);
     if ((st = alloc(ctx, nc * npn * 4 * fe, &ctx->partial)) != DNNMG_OK) return done(st);
     if ((st = alloc(ctx, nc * 8 * 4 * fe, &ctx->partial_c)) != DNNMG_OK) return done(st);
@@ -432,12 +501,72 @@ dnnmg_status dnnmg_set_network(dnnmg_ctx* ctx, const dnnmg_net_desc* net, const 
     return DNNMG_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// The Q2 stages (J = 2 layout): x~ = P x^L into the context's buffer, the
+// fine cells' rows, their gather; the rhs at x~ + d and its restriction.
+constexpr double kQ2Alpha0 = 0.02, kQ2Delta0 = 0.1;   // Eq. (8) parameters of the fine level
+
+template <typename T>
+cudaError_t q2_residual(dnnmg_ctx* ctx, const T* xc, const T* F, T* r, cudaEvent_t F_ready) {
+    const DeviceMesh& dm = ctx->dm;
+    cudaError_t e = q2_prolongate<T>(dm, xc, static_cast<T*>(ctx->buf_xf), ctx->stream);
+    if (e == cudaSuccess)
+        e = q2_level_local<T>(dm.q2fine, 0, static_cast<const T*>(ctx->buf_xf), nullptr, ctx->op, kQ2Alpha0,
+                              kQ2Delta0, 1, static_cast<T*>(ctx->q2_local), ctx->stream);
+    if (e == cudaSuccess && F_ready) e = cudaStreamWaitEvent(ctx->stream, F_ready, 0);
+    if (e == cudaSuccess) e = q2_gather<T>(dm.q2fine, 0, static_cast<const T*>(ctx->q2_local), F, r, ctx->stream);
+    ctx->launches += 3;
+    return e;
+}
+
+template <typename T>
+cudaError_t q2_rhs_restrict(dnnmg_ctx* ctx, const T* xc, const T* d, T* b_fine, T* b_coarse) {
+    const DeviceMesh& dm = ctx->dm;
+    T* xf = static_cast<T*>(ctx->buf_xf);
+    cudaError_t e = q2_prolongate<T>(dm, xc, xf, ctx->stream);
+    if (e == cudaSuccess)
+        e = q2_level_local<T>(dm.q2fine, 1, xf, d, ctx->op, kQ2Alpha0, kQ2Delta0, 0, static_cast<T*>(ctx->q2_local),
+                              ctx->stream);
+    // without b_fine the prolongated field's buffer (read above) holds it
+    T* bf = b_fine ? b_fine : xf;
+    if (e == cudaSuccess) e = q2_gather<T>(dm.q2fine, 1, static_cast<const T*>(ctx->q2_local), nullptr, bf, ctx->stream);
+    ctx->launches += 3;
+    if (e == cudaSuccess && b_coarse) {
+        e = q2_restrict<T>(dm, bf, static_cast<T*>(ctx->partial), b_coarse, ctx->stream);
+        ctx->launches += 2;
+    }
+    return e;
+}
+
+template <typename T, typename TX>
+cudaError_t q2_local_restrict_step(dnnmg_ctx* ctx, const T* xc, const T* r, TX* X) {
+    const DeviceMesh& dm = ctx->dm;
+    T* xf = static_cast<T*>(ctx->buf_xf);
+    cudaError_t e = q2_prolongate<T>(dm, xc, xf, ctx->stream);
+    const T* geo = sizeof(T) == 8 ? reinterpret_cast<const T*>(dm.geo_d) : reinterpret_cast<const T*>(dm.geo_f);
+    if (e == cudaSuccess) e = q2_local_restrict<T, TX>(dm, xf, r, geo, kNInPadJ2, X, ctx->stream);
+    ctx->launches += 2;
+    return e;
+}
+
+}  // namespace
+
+extern "C" {
+
 dnnmg_status dnnmg_prolongate(dnnmg_ctx* ctx, const void* x_coarse_dev, void* x_fine_dev) {
     Range nvtx_range("dnnmg_prolongate");
     if (!ctx || ctx->net_only || !x_coarse_dev || !x_fine_dev) return DNNMG_EINVAL;
     if (!node_fields_aligned(ctx, {x_coarse_dev, x_fine_dev})) return fail(ctx, DNNMG_EINVAL, "misaligned field");
-    cudaError_t e = is_fp64(ctx) ? launch_prolongate(ctx->dm, (const double*)x_coarse_dev, (double*)x_fine_dev, ctx->stream)
-                                 : launch_prolongate(ctx->dm, (const float*)x_coarse_dev, (float*)x_fine_dev, ctx->stream);
+    cudaError_t e;
+    if (is_q2(ctx))
+        e = is_fp64(ctx) ? q2_prolongate(ctx->dm, (const double*)x_coarse_dev, (double*)x_fine_dev, ctx->stream)
+                         : q2_prolongate(ctx->dm, (const float*)x_coarse_dev, (float*)x_fine_dev, ctx->stream);
+    else
+        e = is_fp64(ctx) ? launch_prolongate(ctx->dm, (const double*)x_coarse_dev, (double*)x_fine_dev, ctx->stream)
+                         : launch_prolongate(ctx->dm, (const float*)x_coarse_dev, (float*)x_fine_dev, ctx->stream);
     ctx->launches += 1;
     if (e != cudaSuccess) return cuda_fail(ctx, e, "prolongate");
     return DNNMG_OK;
@@ -446,6 +575,13 @@ dnnmg_status dnnmg_prolongate(dnnmg_ctx* ctx, const void* x_coarse_dev, void* x_
 // the residual; the gather reading F waits for F_ready when given
 static dnnmg_status residual_impl(dnnmg_ctx* ctx, const void* x_coarse_dev, const void* F_dev, void* r_dev,
                            cudaEvent_t F_ready) {
+    if (is_q2(ctx)) {
+        cudaError_t e = is_fp64(ctx) ? q2_residual(ctx, (const double*)x_coarse_dev, (const double*)F_dev,
+                                                   (double*)r_dev, F_ready)
+                                     : q2_residual(ctx, (const float*)x_coarse_dev, (const float*)F_dev,
+                                                   (float*)r_dev, F_ready);
+        return e == cudaSuccess ? DNNMG_OK : cuda_fail(ctx, e, "residual (Q2)");
+    }
     int launches = 0;
     cudaError_t e = is_fp64(ctx)
                         ? launch_residual(ctx->dm, ctx->op, (const double*)x_coarse_dev, (const double*)F_dev,
@@ -471,6 +607,15 @@ dnnmg_status dnnmg_local_restrict(dnnmg_ctx* ctx, const void* x_coarse_dev, cons
     if (!node_fields_aligned(ctx, {x_coarse_dev, r_dev}) || !aligned(X_dev, 16))
         return fail(ctx, DNNMG_EINVAL, "misaligned field");
     cudaError_t e;
+    if (is_q2(ctx)) {
+        if (ctx->precision == DNNMG_FP64)
+            e = q2_local_restrict_step(ctx, (const double*)x_coarse_dev, (const double*)r_dev, (double*)X_dev);
+        else if (ctx->precision == DNNMG_FP32)
+            e = q2_local_restrict_step(ctx, (const float*)x_coarse_dev, (const float*)r_dev, (float*)X_dev);
+        else
+            e = q2_local_restrict_step(ctx, (const float*)x_coarse_dev, (const float*)r_dev, (__nv_bfloat16*)X_dev);
+        return e == cudaSuccess ? DNNMG_OK : cuda_fail(ctx, e, "local_restrict (Q2)");
+    }
     if (ctx->precision == DNNMG_FP64)
         e = launch_local_restrict(ctx->dm, (const double*)x_coarse_dev, (const double*)r_dev, (double*)X_dev, ctx->stream);
     else if (ctx->precision == DNNMG_FP32)
@@ -560,6 +705,13 @@ dnnmg_status dnnmg_rhs_restrict(dnnmg_ctx* ctx, const void* x_coarse_dev, const 
     if (!ctx || ctx->net_only || !x_coarse_dev || !d_dev) return DNNMG_EINVAL;
     if (!node_fields_aligned(ctx, {x_coarse_dev, b_fine_dev, b_coarse_dev}) || !elem_aligned(ctx, {d_dev}))
         return fail(ctx, DNNMG_EINVAL, "misaligned field");
+    if (is_q2(ctx)) {
+        cudaError_t e = is_fp64(ctx) ? q2_rhs_restrict(ctx, (const double*)x_coarse_dev, (const double*)d_dev,
+                                                       (double*)b_fine_dev, (double*)b_coarse_dev)
+                                     : q2_rhs_restrict(ctx, (const float*)x_coarse_dev, (const float*)d_dev,
+                                                       (float*)b_fine_dev, (float*)b_coarse_dev);
+        return e == cudaSuccess ? DNNMG_OK : cuda_fail(ctx, e, "rhs_restrict (Q2)");
+    }
     int launches = 0;
     cudaError_t e =
         is_fp64(ctx)
@@ -578,6 +730,14 @@ dnnmg_status dnnmg_restrict(dnnmg_ctx* ctx, const void* b_fine_dev, void* b_coar
     Range nvtx_range("dnnmg_restrict");
     if (!ctx || ctx->net_only || !b_fine_dev || !b_coarse_dev) return DNNMG_EINVAL;
     if (!node_fields_aligned(ctx, {b_fine_dev, b_coarse_dev})) return fail(ctx, DNNMG_EINVAL, "misaligned field");
+    if (is_q2(ctx)) {
+        cudaError_t e = is_fp64(ctx) ? q2_restrict(ctx->dm, (const double*)b_fine_dev, (double*)ctx->partial,
+                                                   (double*)b_coarse_dev, ctx->stream)
+                                     : q2_restrict(ctx->dm, (const float*)b_fine_dev, (float*)ctx->partial,
+                                                   (float*)b_coarse_dev, ctx->stream);
+        ctx->launches += 2;
+        return e == cudaSuccess ? DNNMG_OK : cuda_fail(ctx, e, "restrict (Q2)");
+    }
     cudaError_t e = is_fp64(ctx) ? launch_restrict(ctx->dm, (const double*)b_fine_dev, (double*)b_coarse_dev,
                                                    (double*)ctx->partial_c, ctx->stream)
                                  : launch_restrict(ctx->dm, (const float*)b_fine_dev, (float*)b_coarse_dev,
@@ -606,7 +766,7 @@ dnnmg_status dnnmg_patch_step_host(dnnmg_ctx* ctx, const void* x_coarse_host, co
     if (!ctx || ctx->net_only || !x_coarse_host || !F_host) return DNNMG_EINVAL;
     if (!ctx->has_net) return fail(ctx, DNNMG_ESTATE, "dnnmg_patch_step_host before dnnmg_set_network");
     const size_t fe = field_elem(ctx->precision);
-    const size_t nv = size_t(ctx->host.nv), nf = size_t(ctx->host.n_fine);
+    const size_t nv = size_t(coarse_nodes(ctx->host)), nf = size_t(ctx->host.n_fine);
     if (!ctx->copy_stream) {
         CK(ctx, cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
         CK(ctx, cudaEventCreateWithFlags(&ctx->ev_ready, cudaEventDisableTiming));
@@ -717,8 +877,8 @@ namespace {
 
 dnnmg_status get_level(dnnmg_ctx* ctx, int32_t level, const dnnmg_solver_params* prm, DeviceLevel** out) {
     if (level != DNNMG_LEVEL_COARSE && level != DNNMG_LEVEL_FINE) return DNNMG_EINVAL;
-    if (level == DNNMG_LEVEL_FINE && ctx->host.J != 1)
-        return fail(ctx, DNNMG_EUNSUPPORTED, "the fine-level solver is built for J = 1 patches only");
+    if (level == DNNMG_LEVEL_FINE && ctx->host.J != 1 && ctx->host.element != 2)
+        return fail(ctx, DNNMG_EUNSUPPORTED, "the fine-level solver is built for J = 1 patches (and Q2) only");
     if (!ctx->level[level]) {
         const int krylov = prm && prm->gmres_restart > 0 ? prm->gmres_restart : 40;
         if (krylov > 200) return fail(ctx, DNNMG_EINVAL, "gmres_restart > 200");
@@ -833,7 +993,7 @@ dnnmg_status dnnmg_time_step(dnnmg_ctx* ctx, int32_t n_steps, const dnnmg_solver
     Range nvtx_range("dnnmg_time_step");
     if (!ctx || ctx->net_only || !x_coarse_dev || !b_coarse_dev || !F_dev || n_steps < 0) return DNNMG_EINVAL;
     if (!ctx->has_net) return fail(ctx, DNNMG_ESTATE, "dnnmg_time_step before dnnmg_set_network");
-    const int64_t nv = ctx->host.nv;
+    const int64_t nv = coarse_nodes(ctx->host);
     dnnmg_status st;
     if (!is_fp64(ctx) && !ctx->xc_field) {
         if ((st = alloc(ctx, size_t(nv) * 4 * 4, &ctx->xc_field)) != DNNMG_OK) return st;
@@ -855,7 +1015,7 @@ dnnmg_status dnnmg_step_begin(dnnmg_ctx* ctx, const dnnmg_solver_params* prm, in
                               const double* b_coarse_dev, const void* F_dev, void* X_dev, dnnmg_solve_stats* stats) {
     Range nvtx_range("dnnmg_step_begin");
     if (!ctx || ctx->net_only || !x_coarse_dev || !F_dev || !X_dev || (solve && !b_coarse_dev)) return DNNMG_EINVAL;
-    const int64_t nv = ctx->host.nv;
+    const int64_t nv = coarse_nodes(ctx->host);
     dnnmg_status st = DNNMG_OK, solve_st = DNNMG_OK;
     if (!is_fp64(ctx) && !ctx->xc_field) {
         if ((st = alloc(ctx, size_t(nv) * 4 * 4, &ctx->xc_field)) != DNNMG_OK) return st;
@@ -883,7 +1043,7 @@ dnnmg_status dnnmg_step_end(dnnmg_ctx* ctx, const void* Y_dev, void* F_dev, doub
     Range nvtx_range("dnnmg_step_end");
     if (!ctx || ctx->net_only || !Y_dev || !F_dev || !b_coarse_dev) return DNNMG_EINVAL;
     if (!ctx->last_xc) return fail(ctx, DNNMG_ESTATE, "dnnmg_step_end before dnnmg_step_begin");
-    const int64_t nv = ctx->host.nv;
+    const int64_t nv = coarse_nodes(ctx->host);
     dnnmg_status st;
     if ((st = dnnmg_extend(ctx, Y_dev, ctx->buf_d)) != DNNMG_OK) return st;
     // the coarse state of the last dnnmg_step_begin (caller's array in FP64, else its float copy)

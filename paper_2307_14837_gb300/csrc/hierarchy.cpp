@@ -362,7 +362,16 @@ dnnmg_status build_hierarchy(const dnnmg_mesh_desc* mesh, int n_geo, int J, Host
     if ((st = build_one(&m1, 12, &h2, err)) != DNNMG_OK) return st;
     // the patch of coarse cell P: node (a, b, c) in {0..4}^3 is node
     // (a - 2 ci, b - 2 cj, c - 2 ck) of child (ci, cj, ck), ci = min(a / 2, 1)
+    std::vector<int32_t> pm_mid = h1.patch_map, kind_mid = h1.kind_f, mid_ptr = h1.node_ptr, mid_idx = h1.node_idx;
+    std::vector<double> xyz_mid = h1.xyz_f;
+    const int64_t n_mid = h1.n_fine;
     *h = std::move(h1);
+    h->n_mid = n_mid;
+    h->patch_map_mid = std::move(pm_mid);
+    h->kind_mid = std::move(kind_mid);
+    h->xyz_mid = std::move(xyz_mid);
+    h->mid_ptr = std::move(mid_ptr);
+    h->mid_idx = std::move(mid_idx);
     h->J = 2;
     h->npn = 125;
     h->n_fine = h2.n_fine;
@@ -540,6 +549,40 @@ double corner_weight(int iota, int K) {
 }  // namespace
 
 void build_level(const HostHierarchy& h, bool fine, HostLevel* lv) {
+    if (h.element == 2) {
+        // Q2 levels: the coarse level's cells are the coarse cells with their
+        // 27 level-(L+1) nodes, the fine level's the 8 children of every
+        // patch with their 27 level-(L+2) nodes
+        const std::vector<int32_t>& kind = fine ? h.kind_f : h.kind_mid;
+        lv->q2 = true;
+        lv->npg = 27;
+        lv->lps = true;
+        lv->n = fine ? h.n_fine : h.n_mid;
+        lv->xyz = fine ? h.xyz_f : h.xyz_mid;
+        lv->dir.resize(size_t(lv->n));
+        bool outflow = false;
+        for (int64_t j = 0; j < lv->n; ++j) {
+            lv->dir[j] = (kind[j] == 1 || kind[j] == 2) ? 1 : 0;
+            outflow |= kind[j] == 3;
+        }
+        lv->mean_zero_pressure = !outflow;
+        if (fine) {
+            lv->ng = 8 * h.nc;
+            lv->groups.resize(size_t(27 * lv->ng));
+            for (int64_t P = 0; P < h.nc; ++P)
+                for (int t = 0; t < 8; ++t)
+                    for (int a = 0; a < 27; ++a) {
+                        const int i = t & 1, j = (t >> 1) & 1, k = (t >> 2) & 1;
+                        const int iota = (2 * i + a % 3) + 5 * (2 * j + (a / 3) % 3) + 25 * (2 * k + a / 9);
+                        lv->groups[size_t(27 * (8 * P + t) + a)] = h.patch_map[size_t(125 * P + iota)];
+                    }
+        } else {
+            lv->ng = h.nc;
+            lv->groups = h.patch_map_mid;
+        }
+        finish_level(lv);
+        return;
+    }
     if (fine) {
         lv->n = h.n_fine;
         lv->ng = h.nc;
@@ -567,7 +610,7 @@ void build_level(const HostHierarchy& h, bool fine, HostLevel* lv) {
 }
 
 bool coarsen_level(const HostLevel& f, HostLevel* c, MgTransfer* t) {
-    if (f.npg != 27 || f.ng == 0) return false;
+    if (f.npg != 27 || f.ng == 0 || f.q2) return false;   // Q2 transfer is not the trilinear one
     const int64_t ng = f.ng;
     // parent cells: the 8 corners of each group; they must be the nodes
     // 0 .. nc - 1 of the level (numbered coarsest level first)

@@ -33,9 +33,17 @@ struct HostHierarchy {
     int J = 1;                       // refinement levels per patch (1 or 2)
     int npn = 27;                    // nodes per patch (27, 125)
     int n_geo = 12;                  // geometry features per patch: 12 or 24
+    int element = 1;                 // 1 (Q1) or 2 (Q2: J = 2 layout, coarse unknowns at level L+1)
     std::vector<double> geo;         // [nc][n_geo]: 12 edge lengths (+ 4 diagonals, 8 mean dihedral angles)
     std::vector<int32_t> node_ptr, node_idx;   // fine node -> P*27+iota, patch order
     std::vector<int32_t> vert_ptr, vert_idx;   // coarse vertex -> P*8+k, patch order
+    // J = 2: level L+1 kept beside level L+2 (the coarse Q2 level's nodes are
+    // level L+1's, a coarse cell's 27 of them in patch_map_mid)
+    int64_t n_mid = 0;
+    std::vector<int32_t> patch_map_mid;        // [nc][27]
+    std::vector<int32_t> kind_mid;             // [n_mid]
+    std::vector<double> xyz_mid;               // [n_mid][3]
+    std::vector<int32_t> mid_ptr, mid_idx;     // level L+1 node -> P*27+iota, patch order
 };
 
 // Level L+J (J = 1 or 2) of a coarse mesh and its patches; level L+2 is
@@ -62,6 +70,7 @@ struct HostLevel {
     std::vector<int32_t> blk_ptr, blk_src;     // block -> local entries g*npg*npg + i*npg + j
     std::vector<int32_t> grp_blk;              // [ng][npg][npg] block index
     std::vector<int32_t> color_ptr, color_groups;  // groups by colour: no two of a colour share a node
+    bool q2 = false;                 // groups are Q2 cells (27 nodes, one element) instead of 8 Q1 children
 };
 
 // Level L from the coarse mesh (grouped if its cells come in consistent
@@ -107,6 +116,18 @@ cudaError_t level_dense_jacobian(DeviceLevel* L, const OpParams& op, const dnnmg
 cudaError_t level_solve(DeviceLevel* L, const OpParams& op, const dnnmg_solver_params* sp, const double* b, double* x,
                         cudaStream_t s, dnnmg_solve_stats* st);
 
+// Device view of a Q2 level (q2.cu): cells of 27 nodes (local node
+// a + 3 b + 9 c), the node -> (cell, local) CSR in cell order, node
+// coordinates (double) and Dirichlet velocity flags.
+struct Q2Level {
+    int64_t n = 0, ncell = 0;
+    const int32_t* cells = nullptr;      // [ncell][27]
+    const int32_t* node_ptr = nullptr;   // [n+1]
+    const int32_t* node_idx = nullptr;   // [27 ncell]: cell * 27 + local
+    const double* xyz = nullptr;         // [n][3]
+    const uint8_t* dir = nullptr;        // [n]
+};
+
 // Device copy of the mesh data the kernels read.
 struct DeviceMesh {
     int64_t nv = 0, nc = 0, n_fine = 0;
@@ -124,13 +145,36 @@ struct DeviceMesh {
     int n_geo = 12;                      // geometry features per patch
     const double* geo_d = nullptr;       // [nc][n_geo]
     const float* geo_f = nullptr;        // [nc][n_geo]
+    // Q2 elements (J = 2 layout): coarse Q2 nodes = level L+1 nodes
+    int element = 1;                     // 1 (Q1) or 2 (Q2)
+    int64_t n_mid = 0;
+    const int32_t* patch_map_mid = nullptr;   // [nc][27] level L+1 nodes of each coarse cell
+    const int32_t* mid_ptr = nullptr;         // [n_mid+1]
+    const int32_t* mid_idx = nullptr;         // [27 nc] P*27+m, patch order
+    const uint8_t* mid_dir = nullptr;         // [n_mid]
+    Q2Level q2fine;                           // the fine Q2 level (level L+2 nodes, 8 cells per patch)
 };
+
+// ---- Q2 kernels (q2.cu); T = double or float; mode 0 operator, 1 rhs, 2 mass
+template <typename T>
+cudaError_t q2_level_local(const Q2Level& L, int mode, const T* x, const T* d, OpParams op, double a0, double d0,
+                           int lps, T* local, cudaStream_t s);
+template <typename T>
+cudaError_t q2_gather(const Q2Level& L, int mode, const T* local, const T* F, T* out, cudaStream_t s);
+template <typename T>
+cudaError_t q2_prolongate(const DeviceMesh& dm, const T* xc, T* xf, cudaStream_t s);
+template <typename T>
+cudaError_t q2_restrict(const DeviceMesh& dm, const T* b_fine, T* part, T* b_coarse, cudaStream_t s);
+template <typename T, typename TX>
+cudaError_t q2_local_restrict(const DeviceMesh& dm, const T* xf, const T* r, const T* geo, int ld, TX* X,
+                              cudaStream_t s);
 
 struct OpParams {
     double m;      // 1 / dt
     double theta;
     double nu;
 };
+
 
 // ---- patch kernels (kernels.cu); T = double or float -------------------
 template <typename T>
@@ -211,6 +255,8 @@ struct dnnmg_ctx {
     void* xc_field = nullptr;   // [nv][4] x^L in the field type (time stepping)
     void* bc_field = nullptr;   // [nv][4] b^L in the field type
     void* plain_b[2] = {nullptr, nullptr};   // [n][4] double rhs of dnnmg_plain_step per level
+    void* buf_xf = nullptr;      // Q2: [n_fine][4] prolongated field
+    void* q2_local = nullptr;    // Q2: [8 nc][27][4] rows of the fine cells
 };
 
 namespace dnnmg {

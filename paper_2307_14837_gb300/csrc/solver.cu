@@ -602,6 +602,222 @@ __global__ void __launch_bounds__(128) jacobian_kernel(int64_t ng, const int32_t
     for (int e = threadIdx.x; e < NL * NL; e += blockDim.x) out[e] = M[e];
 }
 
+// The Jacobian of a Q2 cell (27 nodes, one element, 3 x 3 x 3 Gauss points)
+// with the same closed-form column formulas as jacobian_kernel: the child
+// basis is the cell's Q2 basis, and Pi_K the cell's own trilinear vertex
+// functions (the range of the one-level projection pi_h: Q2 -> Q1).
+template <typename T>
+struct QPointQ2 {
+    T w, N[27], G[27][3];    // weight x det J, Q2 basis values, physical gradients
+    T Pi[8], dPi[8][3];      // trilinear vertex functions
+    T v[3], Dv[3][3];
+    T pv[3], Dpv[3][3];      // pi v and its gradient
+    T gv[3];                 // v.grad v - pi v.grad pi v
+};
+
+template <typename T>
+constexpr size_t jac_q2_smem_bytes() {
+    return 27 * sizeof(QPointQ2<T>) + size_t(108) * 108 * sizeof(T);
+}
+
+__device__ __forceinline__ double g3pt_s(int i) { return i == 0 ? 0.5 - 0.38729833462074168851792653997824 : (i == 1 ? 0.5 : 0.5 + 0.38729833462074168851792653997824); }
+__device__ __forceinline__ double g3wt_s(int i) { return i == 1 ? 8.0 / 18.0 : 5.0 / 18.0; }
+__device__ __forceinline__ void lag2_s(double x, double (&v)[3], double (&d)[3]) {
+    v[0] = 2.0 * (x - 0.5) * (x - 1.0);
+    v[1] = -4.0 * x * (x - 1.0);
+    v[2] = 2.0 * x * (x - 0.5);
+    d[0] = 4.0 * x - 3.0;
+    d[1] = 4.0 - 8.0 * x;
+    d[2] = 4.0 * x - 1.0;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) jacobian_q2_kernel(int64_t ng, const int32_t* __restrict__ groups,
+                                                          const double* __restrict__ xyz,
+                                                          const double* __restrict__ x, LvPrm p, int stab,
+                                                          T* __restrict__ Jloc) {
+    constexpr int NL = 108;
+    extern __shared__ __align__(16) unsigned char jq_smem[];
+    QPointQ2<T>* P = reinterpret_cast<QPointQ2<T>*>(jq_smem);
+    T* M = reinterpret_cast<T*>(jq_smem + 27 * sizeof(QPointQ2<T>));
+    __shared__ double Xs[27][3];
+    __shared__ T Us[27][4];
+    __shared__ T prm_s[2];
+    const int64_t g = blockIdx.x;
+    for (int i = threadIdx.x; i < 27; i += blockDim.x) {
+        const int64_t n = groups[g * 27 + i];
+        for (int d = 0; d < 3; ++d) Xs[i][d] = xyz[3 * n + d];
+        for (int c = 0; c < 4; ++c) Us[i][c] = T(x[4 * n + c]);
+    }
+    for (int e = threadIdx.x; e < NL * NL; e += blockDim.x) M[e] = T(0);
+    __syncthreads();
+    if (threadIdx.x < 27) {
+        const int q = threadIdx.x;
+        QPointQ2<T>& Q = P[q];
+        const double xi[3] = {g3pt_s(q % 3), g3pt_s((q / 3) % 3), g3pt_s(q / 9)};
+        T J[3][3], N1[8], dN1[8][3];
+        for (int d = 0; d < 3; ++d)
+            for (int e = 0; e < 3; ++e) J[d][e] = T(0);
+        for (int k = 0; k < 8; ++k) {
+            double f[3], df[3];
+            for (int d = 0; d < 3; ++d) {
+                f[d] = ((k >> d) & 1) ? xi[d] : 1.0 - xi[d];
+                df[d] = ((k >> d) & 1) ? 1.0 : -1.0;
+            }
+            N1[k] = T(f[0] * f[1] * f[2]);
+            dN1[k][0] = T(df[0] * f[1] * f[2]);
+            dN1[k][1] = T(f[0] * df[1] * f[2]);
+            dN1[k][2] = T(f[0] * f[1] * df[2]);
+            const int nk = corner_node(k);
+            for (int d = 0; d < 3; ++d)
+                for (int e = 0; e < 3; ++e) J[d][e] += T(Xs[nk][d] - Xs[0][d]) * dN1[k][e];
+        }
+        const T c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+        const T c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+        const T c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+        const T det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+        const T idet = T(1) / det;
+        T Ji[3][3];
+        Ji[0][0] = c00 * idet;
+        Ji[1][0] = c01 * idet;
+        Ji[2][0] = c02 * idet;
+        Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) * idet;
+        Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) * idet;
+        Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) * idet;
+        Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) * idet;
+        Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) * idet;
+        Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) * idet;
+        Q.w = T(g3wt_s(q % 3) * g3wt_s((q / 3) % 3) * g3wt_s(q / 9)) * det;
+        double vx[3], dx[3], vy[3], dy[3], vz[3], dz[3];
+        lag2_s(xi[0], vx, dx);
+        lag2_s(xi[1], vy, dy);
+        lag2_s(xi[2], vz, dz);
+        for (int i = 0; i < 27; ++i) {
+            const int a = i % 3, b = (i / 3) % 3, c = i / 9;
+            Q.N[i] = T(vx[a] * vy[b] * vz[c]);
+            const T gr[3] = {T(dx[a] * vy[b] * vz[c]), T(vx[a] * dy[b] * vz[c]), T(vx[a] * vy[b] * dz[c])};
+            for (int d = 0; d < 3; ++d) Q.G[i][d] = gr[0] * Ji[0][d] + gr[1] * Ji[1][d] + gr[2] * Ji[2][d];
+        }
+        for (int K = 0; K < 8; ++K) {
+            Q.Pi[K] = stab ? N1[K] : T(0);
+            for (int d = 0; d < 3; ++d)
+                Q.dPi[K][d] = stab ? dN1[K][0] * Ji[0][d] + dN1[K][1] * Ji[1][d] + dN1[K][2] * Ji[2][d] : T(0);
+        }
+        for (int c = 0; c < 3; ++c) {
+            T v = T(0), pv = T(0), Dv[3] = {T(0), T(0), T(0)}, Dp[3] = {T(0), T(0), T(0)};
+            for (int i = 0; i < 27; ++i) {
+                v += Q.N[i] * Us[i][c];
+                for (int d = 0; d < 3; ++d) Dv[d] += Q.G[i][d] * Us[i][c];
+            }
+            for (int K = 0; K < 8; ++K) {
+                const T u = Us[corner_node(K)][c];
+                pv += Q.Pi[K] * u;
+                for (int d = 0; d < 3; ++d) Dp[d] += Q.dPi[K][d] * u;
+            }
+            Q.v[c] = v;
+            Q.pv[c] = pv;
+            for (int d = 0; d < 3; ++d) {
+                Q.Dv[c][d] = Dv[d];
+                Q.Dpv[c][d] = Dp[d];
+            }
+        }
+        for (int c = 0; c < 3; ++c)
+            Q.gv[c] = Q.v[0] * Q.Dv[c][0] + Q.v[1] * Q.Dv[c][1] + Q.v[2] * Q.Dv[c][2] -
+                      (Q.pv[0] * Q.Dpv[c][0] + Q.pv[1] * Q.Dpv[c][1] + Q.pv[2] * Q.Dpv[c][2]);
+    }
+    if (threadIdx.x == 0) {
+        // frozen alpha_T, delta_T (Eq. (8)): h_T the largest vertex distance,
+        // |v|_inf over the cell's 27 nodes
+        double h = 0.0, vmax = 0.0;
+        for (int a = 0; a < 8; ++a)
+            for (int b = a + 1; b < 8; ++b) {
+                double s2 = 0.0;
+                for (int d = 0; d < 3; ++d) {
+                    const double t0 = Xs[corner_node(a)][d] - Xs[corner_node(b)][d];
+                    s2 += t0 * t0;
+                }
+                h = fmax(h, sqrt(s2));
+            }
+        for (int i = 0; i < 27; ++i) {
+            double s2 = 0.0;
+            for (int d = 0; d < 3; ++d) s2 += double(Us[i][d]) * double(Us[i][d]);
+            vmax = fmax(vmax, sqrt(s2));
+        }
+        const double den = p.nu / (h * h) + vmax / h + p.m;
+        prm_s[0] = T(stab ? p.a0 / den : 0.0);
+        prm_s[1] = T(stab ? p.d0 / den : 0.0);
+    }
+    __syncthreads();
+    const int j = threadIdx.x;
+    if (j < NL) {
+        const int b = j >> 2, e = j & 3;
+        int Kb = -1;
+        if (stab)
+            for (int K = 0; K < 8; ++K)
+                if (corner_node(K) == b) Kb = K;
+        const T m = T(p.m), th = T(p.th), nu = T(p.nu);
+        const T aT = prm_s[0], dT = prm_s[1];
+        for (int q = 0; q < 27; ++q) {
+            const QPointQ2<T>& Q = P[q];
+            const T w = Q.w;
+            const T phib = Q.N[b];
+            const T gb[3] = {Q.G[b][0], Q.G[b][1], Q.G[b][2]};
+            T gP[3];
+            for (int d = 0; d < 3; ++d) gP[d] = Kb >= 0 ? Q.dPi[Kb][d] : T(0);
+            const T Pib = Kb >= 0 ? Q.Pi[Kb] : T(0);
+            if (e < 3) {
+                const T vgb = Q.v[0] * gb[0] + Q.v[1] * gb[1] + Q.v[2] * gb[2];
+                for (int a = 0; a < 27; ++a) {
+                    const T Na = Q.N[a];
+                    const T ggb = Q.G[a][0] * gb[0] + Q.G[a][1] * gb[1] + Q.G[a][2] * gb[2];
+                    T* row = M + (4 * a) * NL + j;
+                    for (int c = 0; c < 3; ++c) {
+                        T val = th * Na * phib * Q.Dv[c][e];
+                        if (c == e) val += m * Na * phib + th * Na * vgb + th * nu * ggb;
+                        row[c * NL] += w * val;
+                    }
+                    row[3 * NL] += w * Na * gb[e];
+                }
+                if (stab) {
+                    const T pvgP = Q.pv[0] * gP[0] + Q.pv[1] * gP[1] + Q.pv[2] * gP[2];
+                    T gvp[3];
+                    for (int c = 0; c < 3; ++c) {
+                        gvp[c] = phib * Q.Dv[c][e] - Pib * Q.Dpv[c][e];
+                        if (c == e) gvp[c] += vgb - pvgP;
+                    }
+                    for (int a = 0; a < 27; ++a) {
+                        const T vGa = Q.v[0] * Q.G[a][0] + Q.v[1] * Q.G[a][1] + Q.v[2] * Q.G[a][2];
+                        T* row = M + (4 * a) * NL + j;
+                        for (int c = 0; c < 3; ++c) row[c * NL] += dT * w * (gvp[c] * vGa + Q.gv[c] * phib * Q.G[a][e]);
+                    }
+                    for (int K = 0; K < 8; ++K) {
+                        const T pvdP = Q.pv[0] * Q.dPi[K][0] + Q.pv[1] * Q.dPi[K][1] + Q.pv[2] * Q.dPi[K][2];
+                        T* row = M + (4 * corner_node(K)) * NL + j;
+                        for (int c = 0; c < 3; ++c)
+                            row[c * NL] -= dT * w * (gvp[c] * pvdP + Q.gv[c] * Pib * Q.dPi[K][e]);
+                    }
+                }
+            } else {
+                for (int a = 0; a < 27; ++a) {
+                    T* row = M + (4 * a) * NL + j;
+                    for (int c = 0; c < 3; ++c) row[c * NL] -= w * Q.G[a][c] * phib;
+                }
+                if (stab) {
+                    const T gq[3] = {gb[0] - gP[0], gb[1] - gP[1], gb[2] - gP[2]};
+                    for (int a = 0; a < 27; ++a)
+                        M[(4 * a + 3) * NL + j] += aT * w * (gq[0] * Q.G[a][0] + gq[1] * Q.G[a][1] + gq[2] * Q.G[a][2]);
+                    for (int K = 0; K < 8; ++K)
+                        M[(4 * corner_node(K) + 3) * NL + j] -=
+                            aT * w * (gq[0] * Q.dPi[K][0] + gq[1] * Q.dPi[K][1] + gq[2] * Q.dPi[K][2]);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    T* out = Jloc + g * NL * NL;
+    for (int e = threadIdx.x; e < NL * NL; e += blockDim.x) out[e] = M[e];
+}
+
 // BSR block b = sum of its local entries in group order; 16 threads per block
 template <typename T, int NPG>
 __global__ void bsr_assemble_kernel(int64_t nnzb, const int32_t* __restrict__ bptr, const int32_t* __restrict__ bsrc,
@@ -1438,7 +1654,19 @@ cudaError_t local_terms(DeviceLevel* D, const double* x, LvPrm p, cudaStream_t s
     const LevelData& L = D->top;
     const HostLevel& h = L.h;
     p.lps = h.lps ? p.lps : 0;
-    if (h.npg == 27) {
+    if (h.q2) {
+        Q2Level q;
+        q.n = h.n;
+        q.ncell = h.ng;
+        q.cells = L.groups;
+        q.node_ptr = L.node_ptr;
+        q.node_idx = L.node_idx;
+        q.xyz = L.xyz;
+        q.dir = L.dir;
+        const int mode = MODE == LV_OPERATOR ? 0 : (MODE == LV_RHS ? 1 : 2);
+        OpParams op{p.m, p.th, p.nu};
+        CKE(q2_level_local<double>(q, mode, x, nullptr, op, p.a0, p.d0, p.lps, D->local, s));
+    } else if (h.npg == 27) {
         static bool attr = false;
         if (!attr) {
             CKE(cudaFuncSetAttribute(level_local_child_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1509,10 +1737,20 @@ cudaError_t launch_jacobian(const LevelData& L, const double* x, const LvPrm& p,
 template <typename T>
 cudaError_t assemble(const LevelData& L, const double* x, const LvPrm& p, T* Jloc, T* A, cudaStream_t s) {
     const HostLevel& h = L.h;
-    if (h.npg == 27)
+    if (h.q2) {
+        constexpr size_t smem = jac_q2_smem_bytes<T>();
+        static bool attr = false;
+        if (!attr) {
+            CKE(cudaFuncSetAttribute(jacobian_q2_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+            attr = true;
+        }
+        jacobian_q2_kernel<T><<<unsigned(h.ng), 128, smem, s>>>(h.ng, L.groups, L.xyz, x, p, L.stab, Jloc);
+        CKE(cudaGetLastError());
+    } else if (h.npg == 27) {
         CKE((launch_jacobian<T, 27>(L, x, p, Jloc, s)));
-    else
+    } else {
         CKE((launch_jacobian<T, 8>(L, x, p, Jloc, s)));
+    }
     const int64_t nnzb = int64_t(h.col_idx.size());
     if (h.npg == 27)
         bsr_assemble_kernel<T, 27><<<nblk(nnzb * 16, 256), 256, 0, s>>>(nnzb, L.blk_ptr, L.blk_src, Jloc, A);

@@ -17,7 +17,8 @@ PRECISIONS = {"fp64": capi.FP64, "fp32": capi.FP32, "bf16": capi.BF16}
 
 
 class PatchPath:
-    def __init__(self, mesh, nu, dt, theta, precision, device="cuda", stream=None, features=12, patch_levels=1):
+    def __init__(self, mesh, nu, dt, theta, precision, device="cuda", stream=None, features=12, patch_levels=1,
+                 element=1):
         if isinstance(precision, str):
             precision = PRECISIONS[precision]
         self.device = torch.device(device)
@@ -27,7 +28,7 @@ class PatchPath:
         self.precision = precision
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         self.ctx = capi.dnnmg_create(mesh, nu, dt, theta, precision, self.stream, features=features,
-                                     patch_levels=patch_levels)
+                                     patch_levels=patch_levels, element=element)
         self.sizes = capi.dnnmg_get_sizes(self.ctx)
         self.dtype = _FIELD_DTYPE[precision]
         self.x_dtype = _X_DTYPE[precision]
@@ -36,7 +37,9 @@ class PatchPath:
     # -- allocation helpers ---------------------------------------------------
     @property
     def n_coarse(self):
-        return self.sizes["n_coarse_vertices"]
+        """Rows of the coarse fields: coarse vertices (Q1) or the nodes of the
+        mesh refined once (Q2)."""
+        return self.sizes["n_coarse_nodes"]
 
     @property
     def n_fine(self):
