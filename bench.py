@@ -773,6 +773,8 @@ def main():
     ap.add_argument("--serving-sims", type=int, default=SERVING_SIMS)
     ap.add_argument("--serving-budget-gb", type=float, default=96.0)
     ap.add_argument("--serving-rows", type=int, default=6_000_000)
+    ap.add_argument("--whole-steps-only", type=int, default=0, metavar="K",
+                    help="print only the whole-time-step measurement (K timed steps) as one JSON line")
     ap.add_argument("--nz", type=int, default=NZ,
                     help="channel resolution (cells across the height); the measured workload is nz=37")
     args = ap.parse_args()
@@ -807,6 +809,13 @@ def main():
     if args.serving:
         if rank == 0:
             run_serving(args)
+        return
+
+    if args.whole_steps_only:
+        if rank == 0:
+            import torch
+            torch.cuda.set_device(0)
+            print(json.dumps({"whole_time_steps": whole_steps(steps=args.whole_steps_only)}))
         return
 
     import torch
