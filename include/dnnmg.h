@@ -236,6 +236,22 @@ dnnmg_status dnnmg_set_network(dnnmg_ctx* ctx, const dnnmg_net_desc* net,
  * x_coarse_dev [n_coarse_vertices][4] -> x_fine_dev [n_fine_nodes][4]. */
 dnnmg_status dnnmg_prolongate(dnnmg_ctx* ctx, const void* x_coarse_dev, void* x_fine_dev);
 
+/* Training targets of Sec. 5.2 (the correction the network learns, used
+ * with the loss of Sec. 6.4): for every patch P and patch node iota,
+ *   T_dev[P * ldt + 3 iota + c] = v_fine[j][c] - (P x_coarse)[j][c],
+ *   j = the fine node of (P, iota), c = 0..2 (velocity),
+ * written in fp32.  x_coarse_dev [n_coarse_nodes][4] and v_fine_dev
+ * [n_fine_nodes][4] are fields of the context's type (double for FP64,
+ * float otherwise), aligned as for dnnmg_prolongate; P is the prolongation
+ * of dnnmg_prolongate (the context's element); iota runs over the patch's
+ * nodes (27 for J = 1, 125 for J = 2), so a row holds n_out values and
+ * ldt >= n_out.  The first call allocates a fine-level scratch field
+ * (ENOMEM if that fails).  EINVAL for NULL pointers, a network-only
+ * context, ldt < n_out or a misaligned field; asynchronous on the
+ * context's stream. */
+dnnmg_status dnnmg_patch_targets(dnnmg_ctx* ctx, const void* x_coarse_dev, const void* v_fine_dev, float* T_dev,
+                                 int64_t ldt);
+
 /* Fine residual r = F - A_{L+1}(P x^L) of Eq. (9), the Q1/Q1 Galerkin form
  * of Eq. (6) with 2x2x2 Gauss quadrature on every fine cell (fused with the
  * prolongation; the local projection terms vanish on prolongated fields and
@@ -337,8 +353,13 @@ int64_t dnnmg_launch_count(const dnnmg_ctx* ctx);
  *
  * Levels: DNNMG_LEVEL_COARSE is level L (the context's mesh), solved with the
  * two-level local projection when its cells come in consecutive groups of 8
- * children of a parent (else without it); DNNMG_LEVEL_FINE is level L+1 (the
- * patches are its groups), used as the fine-mesh reference.  Level fields are
+ * children of a parent (else without it); DNNMG_LEVEL_FINE is the patches'
+ * fine level, used as the fine-mesh reference: level L+1 for J = 1 (the
+ * patches are its groups), level L+2 for J = 2 (one group per level-(L+1)
+ * cell, 8 per patch, with its 27 level-(L+2) nodes; its multigrid passes
+ * through levels L+1 and L, whose nodes are the first nodes of level L+2 in
+ * the numbering of a J = 1 context on the same mesh, so the injection of a
+ * level-(L+2) field onto level L+1 is its first n_fine(J = 1) rows).  Level fields are
  * double [n_nodes][4] (u, v, w, p) device arrays in every precision form.
  *
  * The solver: Newton with the exact Jacobian of A_h (stabilisation
@@ -515,6 +536,37 @@ dnnmg_status dnnmg_mse_loss(int64_t batch, const float* Y_dev, const float* T_de
  * are formed in double and rounded once to fp32 for the update. */
 dnnmg_status dnnmg_adamw(int64_t n, float* w_dev, const float* g_dev, float* m_dev, float* v_dev, double lr,
                          double beta1, double beta2, double eps, double weight_decay, int32_t step, void* cuda_stream);
+
+/* Training data (Sec. 6.4: inputs standardised per feature, batches drawn
+ * at random from the sample set).  Matrices are row-major device arrays,
+ * row stride ld elements (ld >= cols); dtype is DNNMG_FP64 (double),
+ * DNNMG_FP32 (float) or DNNMG_BF16 (bf16 storage).  All three calls are
+ * asynchronous on cuda_stream (NULL: the legacy default stream) and return
+ * EINVAL for NULL pointers, bad sizes or an unknown dtype, ECUDA if a
+ * launch fails.
+ *
+ * dnnmg_column_stats: mean_dev[j] = (1/rows) sum_i A[i][j] and sd_dev[j] =
+ * sqrt(sum_i (A[i][j] - mean_j)^2 / (rows - 1)) for j < cols (double device
+ * arrays), accumulated in FP64 over a fixed partition of the rows (mean
+ * first, then the deviations), so equal inputs give equal bits.  rows >= 2.
+ * Uses stream-ordered scratch of 512 x cols doubles (ENOMEM if it fails). */
+dnnmg_status dnnmg_column_stats(const void* A_dev, int32_t dtype, int64_t rows, int32_t cols, int64_t ld,
+                                double* mean_dev, double* sd_dev, void* cuda_stream);
+
+/* dnnmg_standardize: B[i][j] = (A[i][j] - shift[j]) / scale[j] for j < cols
+ * (shift, scale: double device arrays [cols]), computed in float for float
+ * and bf16 data and in double for double data, rounded once to the dtype;
+ * B has A's dtype and stride and may be A itself.  Columns >= cols of B are
+ * not written. */
+dnnmg_status dnnmg_standardize(const void* A_dev, int32_t dtype, int64_t rows, int32_t cols, int64_t ld,
+                               const double* shift_dev, const double* scale_dev, void* B_dev, void* cuda_stream);
+
+/* dnnmg_gather_rows: row i of dst = row idx[i] of src for i < n, rows of
+ * row_bytes bytes, packed in both (idx: int64 device array).  An index
+ * outside [0, n_src) gives a zero row instead of a read.  src and dst must
+ * not overlap. */
+dnnmg_status dnnmg_gather_rows(const void* src_dev, int64_t n_src, int64_t row_bytes, const int64_t* idx_dev,
+                               int64_t n, void* dst_dev, void* cuda_stream);
 
 /* Measured peak of the SIMT fused multiply-add pipe on the current device
  * (the paper has no counterpart: a roofline denominator for the kernels

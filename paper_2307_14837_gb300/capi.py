@@ -69,6 +69,7 @@ _SIGS = {
     "dnnmg_set_network": ([_VP, ctypes.POINTER(NetDesc), ctypes.POINTER(_VP), ctypes.POINTER(_VP),
                            ctypes.POINTER(_VP)], ctypes.c_int),
     "dnnmg_prolongate": ([_VP, _VP, _VP], ctypes.c_int),
+    "dnnmg_patch_targets": ([_VP, _VP, _VP, _VP, ctypes.c_int64], ctypes.c_int),
     "dnnmg_residual": ([_VP, _VP, _VP, _VP], ctypes.c_int),
     "dnnmg_local_restrict": ([_VP, _VP, _VP, _VP], ctypes.c_int),
     "dnnmg_network": ([_VP, _VP, _VP, ctypes.c_int64], ctypes.c_int),
@@ -249,6 +250,12 @@ def dnnmg_set_network(ctx, widths, Ws, scales=None, shifts=None, skip=True):
 
 def dnnmg_prolongate(ctx, x_coarse, x_fine):
     _check(ctx, load().dnnmg_prolongate(ctx, _ptr(x_coarse), _ptr(x_fine)))
+
+
+def dnnmg_patch_targets(ctx, x_coarse, v_fine, T, ldt=None):
+    """T[P][3 iota + c] = (v_fine - P x_coarse)[node(P, iota)][c] in fp32."""
+    _check(ctx, load().dnnmg_patch_targets(ctx, _ptr(x_coarse), _ptr(v_fine), _ptr(T),
+                                           int(ldt if ldt is not None else T.shape[1])))
 
 
 def dnnmg_residual(ctx, x_coarse, F, r):
@@ -438,6 +445,11 @@ _SIGS.update({
     "dnnmg_trainer_forward": ([_VP, _VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _VP, ctypes.c_int64], ctypes.c_int),
     "dnnmg_trainer_backward": ([_VP, _VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP)], ctypes.c_int),
     "dnnmg_mse_loss": ([ctypes.c_int64, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
+    "dnnmg_column_stats": ([_VP, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64, _VP, _VP, _VP],
+                           ctypes.c_int),
+    "dnnmg_standardize": ([_VP, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64, _VP, _VP, _VP, _VP],
+                          ctypes.c_int),
+    "dnnmg_gather_rows": ([_VP, ctypes.c_int64, ctypes.c_int64, _VP, ctypes.c_int64, _VP, _VP], ctypes.c_int),
     "dnnmg_adamw": ([ctypes.c_int64, _VP, _VP, _VP, _VP, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                      ctypes.c_double, ctypes.c_double, ctypes.c_int32, _VP], ctypes.c_int),
 })
@@ -509,6 +521,36 @@ def dnnmg_trainer_backward(tr, dY, dWs, dbs):
 def dnnmg_mse_loss(batch, Y, T, loss, dY=None, stream=None):
     _check(None, load().dnnmg_mse_loss(int(batch), _ptr(Y), _ptr(T), _ptr(loss), _ptr(dY),
                                        getattr(stream, "cuda_stream", stream)))
+
+
+def _dtype_code(t):
+    import torch
+    return {torch.float64: FP64, torch.float32: FP32, torch.bfloat16: BF16}[t.dtype]
+
+
+def dnnmg_column_stats(A, mean, sd, cols=None, stream=None):
+    """Per-column mean and sample deviation (double device tensors [cols]) of
+    the rows of the 2-D tensor A (row stride A.stride(0))."""
+    cols = int(cols if cols is not None else A.shape[1])
+    _check(None, load().dnnmg_column_stats(_ptr(A), _dtype_code(A), int(A.shape[0]), cols, int(A.stride(0)),
+                                           _ptr(mean), _ptr(sd), getattr(stream, "cuda_stream", stream)))
+
+
+def dnnmg_standardize(A, shift, scale, B, cols=None, stream=None):
+    """B[:, :cols] = (A[:, :cols] - shift) / scale (double device tensors)."""
+    cols = int(cols if cols is not None else A.shape[1])
+    assert B.dtype == A.dtype and B.stride(0) == A.stride(0) and B.shape[0] == A.shape[0]
+    _check(None, load().dnnmg_standardize(_ptr(A), _dtype_code(A), int(A.shape[0]), cols, int(A.stride(0)),
+                                          _ptr(shift), _ptr(scale), _ptr(B), getattr(stream, "cuda_stream", stream)))
+
+
+def dnnmg_gather_rows(src, idx, dst, stream=None):
+    """dst[i] = src[idx[i]] for contiguous 2-D tensors, idx int64 on the device."""
+    assert src.is_contiguous() and dst.is_contiguous() and src.dtype == dst.dtype
+    row_bytes = src.stride(0) * src.element_size()
+    assert dst.stride(0) * dst.element_size() == row_bytes and dst.shape[0] >= idx.shape[0]
+    _check(None, load().dnnmg_gather_rows(_ptr(src), int(src.shape[0]), int(row_bytes), _ptr(idx), int(idx.shape[0]),
+                                          _ptr(dst), getattr(stream, "cuda_stream", stream)))
 
 
 def dnnmg_adamw(w, g, m, v, lr, beta1, beta2, eps, weight_decay, step, stream=None):

@@ -572,6 +572,37 @@ dnnmg_status dnnmg_prolongate(dnnmg_ctx* ctx, const void* x_coarse_dev, void* x_
     return DNNMG_OK;
 }
 
+dnnmg_status dnnmg_patch_targets(dnnmg_ctx* ctx, const void* x_coarse_dev, const void* v_fine_dev, float* T_dev,
+                                 int64_t ldt) {
+    Range nvtx_range("dnnmg_patch_targets");
+    if (!ctx || ctx->net_only || !x_coarse_dev || !v_fine_dev || !T_dev) return DNNMG_EINVAL;
+    if (ldt < n_out(ctx)) return fail(ctx, DNNMG_EINVAL, "ldt < n_out");
+    if (!node_fields_aligned(ctx, {x_coarse_dev, v_fine_dev})) return fail(ctx, DNNMG_EINVAL, "misaligned field");
+    if (!ctx->buf_xf) {
+        const size_t bytes = size_t(ctx->host.n_fine) * 4 * field_elem(ctx->precision);
+        const dnnmg_status st = alloc(ctx, bytes, &ctx->buf_xf);
+        if (st != DNNMG_OK) return st;
+    }
+    const int npn = ctx->host.npn;
+    cudaError_t e;
+    if (is_fp64(ctx)) {
+        const double* xc = static_cast<const double*>(x_coarse_dev);
+        double* xt = static_cast<double*>(ctx->buf_xf);
+        e = is_q2(ctx) ? q2_prolongate(ctx->dm, xc, xt, ctx->stream) : launch_prolongate(ctx->dm, xc, xt, ctx->stream);
+        if (e == cudaSuccess)
+            e = launch_targets(ctx->dm, npn, static_cast<const double*>(v_fine_dev), xt, T_dev, ldt, ctx->stream);
+    } else {
+        const float* xc = static_cast<const float*>(x_coarse_dev);
+        float* xt = static_cast<float*>(ctx->buf_xf);
+        e = is_q2(ctx) ? q2_prolongate(ctx->dm, xc, xt, ctx->stream) : launch_prolongate(ctx->dm, xc, xt, ctx->stream);
+        if (e == cudaSuccess)
+            e = launch_targets(ctx->dm, npn, static_cast<const float*>(v_fine_dev), xt, T_dev, ldt, ctx->stream);
+    }
+    ctx->launches += 2;
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "patch targets");
+    return DNNMG_OK;
+}
+
 // the residual; the gather reading F waits for F_ready when given
 static dnnmg_status residual_impl(dnnmg_ctx* ctx, const void* x_coarse_dev, const void* F_dev, void* r_dev,
                            cudaEvent_t F_ready) {
@@ -857,7 +888,6 @@ dnnmg_status dnnmg_hierarchy_mg(const dnnmg_hierarchy* h, int32_t level, int32_t
     if (!h || !n_levels || (level != DNNMG_LEVEL_COARSE && level != DNNMG_LEVEL_FINE) || mg_levels < 0 ||
         max_levels < 0 || (max_levels > 0 && !nodes))
         return DNNMG_EINVAL;
-    if (level == DNNMG_LEVEL_FINE && h->host.J != 1) return DNNMG_EUNSUPPORTED;
     std::vector<HostLevel> lv(1);
     build_level(h->host, level == DNNMG_LEVEL_FINE, &lv[0]);
     for (int k = 0; k < mg_levels; ++k) {
@@ -877,8 +907,6 @@ namespace {
 
 dnnmg_status get_level(dnnmg_ctx* ctx, int32_t level, const dnnmg_solver_params* prm, DeviceLevel** out) {
     if (level != DNNMG_LEVEL_COARSE && level != DNNMG_LEVEL_FINE) return DNNMG_EINVAL;
-    if (level == DNNMG_LEVEL_FINE && ctx->host.J != 1 && ctx->host.element != 2)
-        return fail(ctx, DNNMG_EUNSUPPORTED, "the fine-level solver is built for J = 1 patches (and Q2) only");
     if (!ctx->level[level]) {
         const int krylov = prm && prm->gmres_restart > 0 ? prm->gmres_restart : 40;
         if (krylov > 200) return fail(ctx, DNNMG_EINVAL, "gmres_restart > 200");

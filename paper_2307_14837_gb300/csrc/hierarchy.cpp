@@ -585,10 +585,24 @@ void build_level(const HostHierarchy& h, bool fine, HostLevel* lv) {
     }
     if (fine) {
         lv->n = h.n_fine;
-        lv->ng = h.nc;
         lv->npg = 27;
         lv->lps = true;
-        lv->groups = h.patch_map;
+        if (h.J == 2) {
+            // level L+2: one group per level-(L+1) cell (8 per patch), its 27
+            // level-(L+2) nodes taken from the 125-node patch
+            lv->ng = 8 * h.nc;
+            lv->groups.resize(size_t(27 * lv->ng));
+            for (int64_t P = 0; P < h.nc; ++P)
+                for (int t = 0; t < 8; ++t)
+                    for (int a = 0; a < 27; ++a) {
+                        const int i = t & 1, j = (t >> 1) & 1, k = (t >> 2) & 1;
+                        const int iota = (2 * i + a % 3) + 5 * (2 * j + (a / 3) % 3) + 25 * (2 * k + a / 9);
+                        lv->groups[size_t(27 * (8 * P + t) + a)] = h.patch_map[size_t(125 * P + iota)];
+                    }
+        } else {
+            lv->ng = h.nc;
+            lv->groups = h.patch_map;
+        }
         lv->xyz = h.xyz_f;
         lv->dir.resize(size_t(h.n_fine));
         bool outflow = false;

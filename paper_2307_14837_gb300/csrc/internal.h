@@ -179,6 +179,9 @@ struct OpParams {
 // ---- patch kernels (kernels.cu); T = double or float -------------------
 template <typename T>
 cudaError_t launch_prolongate(const DeviceMesh& dm, const T* xc, T* xf, cudaStream_t s);
+template <typename T>
+cudaError_t launch_targets(const DeviceMesh& dm, int npn, const T* v, const T* xt, float* out, int64_t ldt,
+                           cudaStream_t s);
 // F_ready (may be null): an event the gather waits for before reading F,
 // so that F can still be arriving while the element kernel runs
 template <typename T>

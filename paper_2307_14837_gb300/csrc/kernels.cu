@@ -854,6 +854,35 @@ cudaError_t launch_prolongate(const DeviceMesh& dm, const T* xc, T* xf, cudaStre
     return cudaGetLastError();
 }
 
+// training targets: out[P ldt + 3 iota + c] = v[j][c] - xt[j][c] for the
+// patch's node j = patch_map[P][iota], velocity components, in fp32
+template <typename T>
+__global__ void __launch_bounds__(256) targets_kernel(int64_t nc, int npn, const int32_t* __restrict__ pm,
+                                                      const T* __restrict__ v, const T* __restrict__ xt,
+                                                      float* __restrict__ out, int64_t ldt) {
+    const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (e >= nc * npn) return;
+    const int64_t P = e / npn;
+    const int iota = int(e - P * npn);
+    const int64_t j = pm[e];
+    const V4<T> a = ld4(v + 4 * j), b = ld4(xt + 4 * j);
+    float* o = out + P * ldt + 3 * iota;
+    o[0] = float(a.x - b.x);
+    o[1] = float(a.y - b.y);
+    o[2] = float(a.z - b.z);
+}
+
+template <typename T>
+cudaError_t launch_targets(const DeviceMesh& dm, int npn, const T* v, const T* xt, float* out, int64_t ldt,
+                           cudaStream_t s) {
+    targets_kernel<T><<<blocks_for(dm.nc * npn, 256), 256, 0, s>>>(dm.nc, npn, dm.patch_map, v, xt, out, ldt);
+    return cudaGetLastError();
+}
+template cudaError_t launch_targets<double>(const DeviceMesh&, int, const double*, const double*, float*, int64_t,
+                                            cudaStream_t);
+template cudaError_t launch_targets<float>(const DeviceMesh&, int, const float*, const float*, float*, int64_t,
+                                           cudaStream_t);
+
 // patch operator launch for J = 1 or 2 (64-thread blocks of 8 or 1 patches)
 template <typename T, int MODE>
 void launch_patch_operator(const DeviceMesh& dm, OpParams p, const T* xc, const T* dfine, T* partial, T* partial_c,

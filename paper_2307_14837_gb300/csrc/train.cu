@@ -13,6 +13,7 @@
 // Reductions (bias gradients, loss) are two-pass and deterministic.
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 #include "internal.h"
@@ -150,6 +151,104 @@ __global__ void adamw_kernel(int64_t n, float* __restrict__ w, const float* __re
     v[i] = vi;
     const float mh = mi / c1, vh = vi / c2;
     w[i] -= lr * (mh / (sqrtf(vh) + eps) + wd * w[i]);
+}
+
+
+// ---- training data: column statistics, standardisation, row gather ---------
+
+template <typename T>
+__device__ __forceinline__ double tod(T v) { return double(tof(v)); }
+template <>
+__device__ __forceinline__ double tod<double>(double v) { return v; }
+
+// Column sums over one fixed row range per block (FP64): PASS 0 sums a,
+// PASS 1 sums (a - mean)^2.  The grid size is fixed, so the partials and
+// their order do not depend on the device.
+constexpr int kStatBlocks = 512;
+template <typename T, int PASS>
+__global__ void __launch_bounds__(256) colstat_partial_kernel(int64_t rows, int cols, int64_t ld,
+                                                              const T* __restrict__ A,
+                                                              const double* __restrict__ mean,
+                                                              double* __restrict__ part) {
+    const int64_t chunk = (rows + kStatBlocks - 1) / kStatBlocks;
+    const int64_t r0 = int64_t(blockIdx.x) * chunk;
+    const int64_t r1 = r0 + chunk < rows ? r0 + chunk : rows;
+    for (int j = threadIdx.x; j < cols; j += blockDim.x) {
+        const double mu = PASS ? mean[j] : 0.0;
+        double acc = 0.0;
+        for (int64_t i = r0; i < r1; ++i) {
+            const double a = tod(A[i * ld + j]);
+            acc += PASS ? (a - mu) * (a - mu) : a;
+        }
+        part[int64_t(blockIdx.x) * cols + j] = acc;
+    }
+}
+
+// out[j] = sum_b part[b][j] / rows (PASS 0: the mean) or
+// sqrt(sum_b part[b][j] / (rows - 1)) (PASS 1: the sample deviation)
+template <int PASS>
+__global__ void colstat_final_kernel(int64_t rows, int cols, const double* __restrict__ part,
+                                     double* __restrict__ out) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= cols) return;
+    double acc = 0.0;
+    for (int b = 0; b < kStatBlocks; ++b) acc += part[int64_t(b) * cols + j];
+    out[j] = PASS ? sqrt(acc / double(rows - 1)) : acc / double(rows);
+}
+
+template <typename T>
+struct StdAcc {
+    using type = float;
+};
+template <>
+struct StdAcc<double> {
+    using type = double;
+};
+
+// B[i][j] = (A[i][j] - shift[j]) / scale[j], j < cols, in float (double for
+// double data), rounded once to A's type
+template <typename T>
+__global__ void __launch_bounds__(256) standardize_kernel(int64_t rows, int cols, int64_t ld, const T* A,
+                                                          const double* __restrict__ shift,
+                                                          const double* __restrict__ scale, T* B) {
+    using Acc = typename StdAcc<T>::type;
+    const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (e >= rows * cols) return;
+    const int64_t i = e / cols;
+    const int j = int(e - i * cols);
+    const Acc a = Acc(tod(A[i * ld + j]));
+    const Acc v = (a - Acc(shift[j])) / Acc(scale[j]);
+    if constexpr (std::is_same<T, double>::value)
+        B[i * ld + j] = v;
+    else
+        B[i * ld + j] = fromf<T>(float(v));
+}
+
+// dst row i = src row idx[i] in words of W; an index outside [0, n_src)
+// gives a zero row
+template <typename W>
+__global__ void __launch_bounds__(256) gather_rows_kernel(int64_t n, int64_t n_src, int64_t q,
+                                                          const int64_t* __restrict__ idx, const W* __restrict__ src,
+                                                          W* __restrict__ dst) {
+    const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (e >= n * q) return;
+    const int64_t i = e / q, w = e - i * q;
+    const int64_t r = idx[i];
+    dst[e] = (r >= 0 && r < n_src) ? src[r * q + w] : W{};
+}
+
+template <typename T>
+dnnmg_status column_stats_t(const T* A, int64_t rows, int cols, int64_t ld, double* mean, double* sd,
+                            cudaStream_t s) {
+    double* part = nullptr;
+    if (cudaMallocAsync(&part, sizeof(double) * kStatBlocks * cols, s) != cudaSuccess) return DNNMG_ENOMEM;
+    colstat_partial_kernel<T, 0><<<kStatBlocks, 256, 0, s>>>(rows, cols, ld, A, nullptr, part);
+    colstat_final_kernel<0><<<nb(cols, 256), 256, 0, s>>>(rows, cols, part, mean);
+    colstat_partial_kernel<T, 1><<<kStatBlocks, 256, 0, s>>>(rows, cols, ld, A, mean, part);
+    colstat_final_kernel<1><<<nb(cols, 256), 256, 0, s>>>(rows, cols, part, sd);
+    const cudaError_t e = cudaGetLastError();
+    cudaFreeAsync(part, s);
+    return e == cudaSuccess ? DNNMG_OK : DNNMG_ECUDA;
 }
 
 }  // namespace
@@ -393,6 +492,64 @@ dnnmg_status dnnmg_adamw(int64_t n, float* w_dev, const float* g_dev, float* m_d
     adamw_kernel<<<nb(n, 256), 256, 0, static_cast<cudaStream_t>(cuda_stream)>>>(
         n, w_dev, g_dev, m_dev, v_dev, float(lr), float(beta1), float(1.0 - beta1), float(beta2), float(1.0 - beta2),
         float(eps), float(weight_decay), float(c1), float(c2));
+    return cudaGetLastError() == cudaSuccess ? DNNMG_OK : DNNMG_ECUDA;
+}
+
+dnnmg_status dnnmg_column_stats(const void* A_dev, int32_t dtype, int64_t rows, int32_t cols, int64_t ld,
+                                double* mean_dev, double* sd_dev, void* cuda_stream) {
+    if (!A_dev || !mean_dev || !sd_dev || rows < 2 || cols <= 0 || ld < cols) return DNNMG_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    switch (dtype) {
+        case DNNMG_FP64: return column_stats_t(static_cast<const double*>(A_dev), rows, cols, ld, mean_dev, sd_dev, s);
+        case DNNMG_FP32: return column_stats_t(static_cast<const float*>(A_dev), rows, cols, ld, mean_dev, sd_dev, s);
+        case DNNMG_BF16:
+            return column_stats_t(static_cast<const __nv_bfloat16*>(A_dev), rows, cols, ld, mean_dev, sd_dev, s);
+        default: return DNNMG_EINVAL;
+    }
+}
+
+dnnmg_status dnnmg_standardize(const void* A_dev, int32_t dtype, int64_t rows, int32_t cols, int64_t ld,
+                               const double* shift_dev, const double* scale_dev, void* B_dev, void* cuda_stream) {
+    if (!A_dev || !shift_dev || !scale_dev || !B_dev || rows < 0 || cols <= 0 || ld < cols) return DNNMG_EINVAL;
+    if (rows == 0) return DNNMG_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    const unsigned g = nb(rows * cols, 256);
+    switch (dtype) {
+        case DNNMG_FP64:
+            standardize_kernel<<<g, 256, 0, s>>>(rows, cols, ld, static_cast<const double*>(A_dev), shift_dev,
+                                                 scale_dev, static_cast<double*>(B_dev));
+            break;
+        case DNNMG_FP32:
+            standardize_kernel<<<g, 256, 0, s>>>(rows, cols, ld, static_cast<const float*>(A_dev), shift_dev,
+                                                 scale_dev, static_cast<float*>(B_dev));
+            break;
+        case DNNMG_BF16:
+            standardize_kernel<<<g, 256, 0, s>>>(rows, cols, ld, static_cast<const __nv_bfloat16*>(A_dev), shift_dev,
+                                                 scale_dev, static_cast<__nv_bfloat16*>(B_dev));
+            break;
+        default: return DNNMG_EINVAL;
+    }
+    return cudaGetLastError() == cudaSuccess ? DNNMG_OK : DNNMG_ECUDA;
+}
+
+dnnmg_status dnnmg_gather_rows(const void* src_dev, int64_t n_src, int64_t row_bytes, const int64_t* idx_dev,
+                               int64_t n, void* dst_dev, void* cuda_stream) {
+    if (!src_dev || !idx_dev || !dst_dev || n_src < 0 || n < 0 || row_bytes <= 0) return DNNMG_EINVAL;
+    if (n == 0) return DNNMG_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    const uintptr_t a = reinterpret_cast<uintptr_t>(src_dev) | reinterpret_cast<uintptr_t>(dst_dev);
+    if (row_bytes % 16 == 0 && a % 16 == 0) {
+        const int64_t q = row_bytes / 16;
+        gather_rows_kernel<uint4><<<nb(n * q, 256), 256, 0, s>>>(n, n_src, q, idx_dev, static_cast<const uint4*>(src_dev),
+                                                                static_cast<uint4*>(dst_dev));
+    } else if (row_bytes % 4 == 0 && a % 4 == 0) {
+        const int64_t q = row_bytes / 4;
+        gather_rows_kernel<uint32_t><<<nb(n * q, 256), 256, 0, s>>>(
+            n, n_src, q, idx_dev, static_cast<const uint32_t*>(src_dev), static_cast<uint32_t*>(dst_dev));
+    } else {
+        gather_rows_kernel<uint8_t><<<nb(n * row_bytes, 256), 256, 0, s>>>(
+            n, n_src, row_bytes, idx_dev, static_cast<const uint8_t*>(src_dev), static_cast<uint8_t*>(dst_dev));
+    }
     return cudaGetLastError() == cudaSuccess ? DNNMG_OK : DNNMG_ECUDA;
 }
 

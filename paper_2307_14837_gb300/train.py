@@ -5,12 +5,16 @@
   parameters are fp32 torch tensors owned by ``PatchNet``.
 * ``AdamW``: the optimiser of Sec. 6.4 through libdnnmg's AdamW kernel
   (weight decay 1e-5 stands for the paper's Tikhonov term).
-* ``make_samples``: training pairs from a fine-level simulation (Sec. 5.2):
-  for each time step n the fine solution v_n (level L+1) and its right-hand
-  side F_n = Rhs(v_{n-1}); the coarse state x^L_n solves the coarse system
+* ``make_samples``: training pairs from a fine simulation (Sec. 5.2): for
+  each time step n the reference velocity v_n (the solve on level L+1, or on
+  level L+2 injected onto level L+1) and the fine right-hand side
+  F_n = Rhs_{L+1}(v_{n-1}); the coarse state x^L_n solves the coarse system
   with the restricted rhs R F_n (what the DNN-MG coarse solve computes after
   exact corrections); the network input is the row X of x^L_n and of the
   residual F_n - A(P x^L_n), the target T = Q(v_n - P x^L_n), velocity only.
+* Standardisation, batch assembly and targets run in libdnnmg
+  (dnnmg_column_stats, dnnmg_standardize, dnnmg_gather_rows,
+  dnnmg_patch_targets); PyTorch holds the memory and the autograd wrapper.
 """
 from __future__ import annotations
 
@@ -144,133 +148,232 @@ class _MSE(torch.autograd.Function):
         return dY * g, None
 
 
-def make_samples(mesh, nu, dt, theta, n_steps, x_dtype=torch.bfloat16, solver=None, features=12):
-    """(X, T) training pairs from a fine-level simulation started at rest
-    with the mesh's Dirichlet data.  X [n_steps * N_c][256] in x_dtype (216 +
-    features used columns), T [n_steps * N_c][81] fp32.  Also returns the
-    per-step arrays for evaluation."""
+def _rest_state(p, mesh, fine):
+    """Field at rest with the Dirichlet data of the fine (or coarse) nodes."""
+    if fine:
+        kind, xyz = p.mesh_data(capi.FINE_KIND), p.mesh_data(capi.FINE_XYZ)
+    else:
+        kind, xyz = mesh["vertex_bc"], mesh["xyz"]
+    d = (kind == 1) | (kind == 2)
+    x = np.zeros((xyz.shape[0], 4))
+    x[d, 0:3] = I.dirichlet_values(mesh, xyz, kind)[d]
+    return torch.as_tensor(x, device=p.device)
+
+
+def make_samples(mesh, nu, dt, theta, n_steps, x_dtype=torch.bfloat16, solver=None, features=12, ref_levels=1,
+                 ref_solver=None, keep_steps=True):
+    """(X, T) training pairs from a fine simulation started at rest with the
+    mesh's Dirichlet data.  X [n_steps * N_c][256] in x_dtype (216 +
+    features used columns), T [n_steps * N_c][81] fp32, both written by
+    libdnnmg (dnnmg_local_restrict, dnnmg_patch_targets).  Also returns the
+    per-step states (x^L_n, the reference velocity on level L+1, F_n) when
+    keep_steps.
+
+    ref_levels = 1: the reference v_n is the solve on level L+1 with
+    F_n = Rhs_{L+1}(v_{n-1}).  ref_levels = 2 (the twofold refinement of
+    Sec. 6.4): v_n is the solve on level L+2 (the fine level of a J = 2
+    context, its own right-hand side from its previous state), injected
+    onto level L+1 (its first n_fine(L+1) nodes), and F_n =
+    Rhs_{L+1}(injected v_{n-1})."""
+    if ref_levels not in (1, 2):
+        raise ValueError("ref_levels must be 1 or 2")
     prec = "bf16" if x_dtype == torch.bfloat16 else "fp32"
-    f64 = PatchPath(mesh, nu, dt, theta, "fp64")          # fine solves, restriction
+    f64 = PatchPath(mesh, nu, dt, theta, "fp64")          # level L+1 rhs, restriction, coarse solve, targets
     low = PatchPath(mesh, nu, dt, theta, prec, features=features)   # network inputs as at inference
+    ref = f64 if ref_levels == 1 else PatchPath(mesh, nu, dt, theta, "fp64", patch_levels=2)
     dev = f64.device
     nv, nf, nc = f64.n_coarse, f64.n_fine, f64.n_patches
-    kind = f64.mesh_data(capi.FINE_KIND)
-    fxyz = f64.mesh_data(capi.FINE_XYZ)
-    dirf = (kind == 1) | (kind == 2)
-    pm = torch.as_tensor(f64.mesh_data(capi.PATCH_MAP).astype(np.int64), device=dev)
-    dirc = (mesh["vertex_bc"] == 1) | (mesh["vertex_bc"] == 2)
-    xc = np.zeros((nv, 4))
-    xc[dirc, 0:3] = I.dirichlet_values(mesh, mesh["xyz"], mesh["vertex_bc"])[dirc]
-    vf = np.zeros((nf, 4))
-    vf[dirf, 0:3] = I.dirichlet_values(mesh, fxyz, kind)[dirf]
-    xc, vf = torch.as_tensor(xc, device=dev), torch.as_tensor(vf, device=dev)
+    xc = _rest_state(f64, mesh, fine=False)
+    vr = _rest_state(ref, mesh, fine=True)                # reference state on its own level
     F = torch.empty((nf, 4), dtype=torch.float64, device=dev)
+    Fr = F if ref_levels == 1 else torch.empty((ref.n_fine, 4), dtype=torch.float64, device=dev)
     bL = torch.empty((nv, 4), dtype=torch.float64, device=dev)
-    Xs, Ts, steps = [], [], []
+    X = torch.empty((n_steps * nc, low.sizes["n_in_padded"]), dtype=low.x_dtype, device=dev)
+    T = torch.empty((n_steps * nc, 81), dtype=torch.float32, device=dev)
+    steps = []
     for n in range(n_steps):
-        capi.dnnmg_level_rhs(f64.ctx, capi.LEVEL_FINE, vf, F)            # F_n = Rhs(v_{n-1})
-        capi.dnnmg_solve(f64.ctx, capi.LEVEL_FINE, F, vf, solver)        # v_n
-        capi.dnnmg_restrict(f64.ctx, F, bL)                              # R F_n
-        capi.dnnmg_solve(f64.ctx, capi.LEVEL_COARSE, bL, xc, solver)     # x^L_n
-        xt = f64.prolongate(xc)
+        if ref_levels == 2:
+            capi.dnnmg_level_rhs(f64.ctx, capi.LEVEL_FINE, vr[:nf], F)     # F_n = Rhs_{L+1}(inj v_{n-1})
+        capi.dnnmg_level_rhs(ref.ctx, capi.LEVEL_FINE, vr, Fr)             # the reference level's rhs
+        capi.dnnmg_solve(ref.ctx, capi.LEVEL_FINE, Fr, vr, ref_solver if ref_levels == 2 else solver)
+        capi.dnnmg_restrict(f64.ctx, F, bL)                                # R F_n
+        capi.dnnmg_solve(f64.ctx, capi.LEVEL_COARSE, bL, xc, solver)       # x^L_n
+        v = vr[:nf]                                                        # v_n on level L+1
         xcl, Fl = xc.to(low.dtype), F.to(low.dtype)
         r = low.residual(xcl, Fl)
-        X = low.local_restrict(xcl, r)
-        D = (vf - xt)[:, 0:3].float()
-        T = D[pm].reshape(nc, 81)
-        Xs.append(X.clone())
-        Ts.append(T)
-        steps.append(dict(x_coarse=xc.clone(), v_fine=vf.clone(), F=F.clone()))
+        capi.dnnmg_local_restrict(low.ctx, xcl, r, X[n * nc:(n + 1) * nc])
+        capi.dnnmg_patch_targets(f64.ctx, xc, v, T[n * nc:(n + 1) * nc])
+        if keep_steps:
+            steps.append(dict(x_coarse=xc.clone(), v_fine=v.clone(), F=F.clone()))
+    if ref is not f64:
+        ref.close()
     f64.close()
     low.close()
-    return torch.cat(Xs), torch.cat(Ts), steps
+    return X, T, steps
 
 
-def trajectory_errors(mesh, nu, dt, theta, steps, network=None, solver=None):
-    """l2 velocity error against a fine trajectory (``steps`` from
-    make_samples) of DNN-MG with ``network`` = (widths, Ws, scales, shifts)
-    on the FP64 path, or of the plain coarse scheme when network is None;
-    one value per time step (the corrected fine velocity P x^L + d for
-    DNN-MG, P x^L for the plain scheme)."""
-    p = PatchPath(mesh, nu, dt, theta, "fp64")
-    dirc = (mesh["vertex_bc"] == 1) | (mesh["vertex_bc"] == 2)
-    x0 = np.zeros((p.n_coarse, 4))
-    x0[dirc, 0:3] = I.dirichlet_values(mesh, mesh["xyz"], mesh["vertex_bc"])[dirc]
-    x = torch.as_tensor(x0, device=p.device)
+def velocity_errors(vel, ref):
+    """The error measures of Sec. 6.5-6.6 of velocity snapshots ``vel``
+    against ``ref`` (lists of [n][3] arrays, one per time step):
+    e_v(n) = |v_n - v_ref,n| / |v_ref,n| and the time-integrated
+    E_v = (sum_n |v_n - v_ref,n|^2 / sum_n |v_ref,n|^2)^(1/2) (equal steps)."""
+    err = [float(np.linalg.norm(v - r)) for v, r in zip(vel, ref)]
+    nrm = [float(np.linalg.norm(r)) for r in ref]
+    return {"e_v": [e / n for e, n in zip(err, nrm)],
+            "E_v": (sum(e * e for e in err) / sum(n * n for n in nrm)) ** 0.5}
+
+
+def trajectory_errors(mesh, nu, dt, theta, steps, network=None, solver=None, precision="fp64", velocities=None):
+    """l2 velocity errors |v_n - v_ref,n| per time step against the
+    reference velocities of ``steps`` (from make_samples), for DNN-MG with
+    ``network`` = (widths, Ws, scales, shifts) in the given precision form
+    (the corrected fine velocity P x^L + d) or for the plain coarse scheme
+    when network is None (P x^L).  The coarse state and the coarse
+    right-hand side stay FP64 in every form.  With a list ``velocities``,
+    the corrected velocities are appended to it (numpy [n][3])."""
+    p = PatchPath(mesh, nu, dt, theta, precision if network is not None else "fp64")
+    x = _rest_state(p, mesh, fine=False)
     errs = []
-    if network is not None:
-        widths, Ws, ss, ts = network
-        p.set_network(widths, Ws, ss, ts)
-        bf, bc = p.rhs_restrict(x, torch.zeros((p.n_fine, 3), dtype=torch.float64, device=p.device))
-    for s in steps:
+    try:
         if network is not None:
-            capi.dnnmg_time_step(p.ctx, 1, x, bc, bf, solver)
-            d = torch.empty((p.n_fine, 3), dtype=torch.float64, device=p.device)
-            capi.dnnmg_extend(p.ctx, capi.dnnmg_get_buffer(p.ctx, capi.BUF_Y), d)
-            v = p.prolongate(x)[:, 0:3] + d
-        else:
-            capi.dnnmg_plain_step(p.ctx, capi.LEVEL_COARSE, 1, x, solver)
-            v = p.prolongate(x)[:, 0:3]
-        errs.append(float(torch.linalg.norm(v - s["v_fine"][:, 0:3])))
-    p.close()
+            widths, Ws, ss, ts = network
+            p.set_network(widths, Ws, ss, ts)
+            bf, bcf = p.rhs_restrict(x.to(p.dtype), torch.zeros((p.n_fine, 3), dtype=p.dtype, device=p.device))
+            bc = bcf.double().contiguous()
+        for s in steps:
+            if network is not None:
+                capi.dnnmg_time_step(p.ctx, 1, x, bc, bf, solver)
+                d = torch.empty((p.n_fine, 3), dtype=p.dtype, device=p.device)
+                capi.dnnmg_extend(p.ctx, capi.dnnmg_get_buffer(p.ctx, capi.BUF_Y), d)
+                v = (p.prolongate(x.to(p.dtype))[:, 0:3] + d).double()
+            else:
+                capi.dnnmg_plain_step(p.ctx, capi.LEVEL_COARSE, 1, x, solver)
+                v = p.prolongate(x)[:, 0:3]
+            errs.append(float(torch.linalg.norm(v - s["v_fine"][:, 0:3])))
+            if velocities is not None:
+                velocities.append(v.cpu().numpy())
+    finally:
+        p.close()
     return errs
 
 
-def fit_normalization(X, T, n_in=228):
-    """Per-column mean and standard deviation of the input rows (padding
-    columns and constant columns get mean 0 / sigma 1) and one scale for the
-    targets (their root mean square).  n_in = 228 (edge lengths) or 240
-    (edge lengths, diagonals, angles)."""
-    Xf = X.float()
-    mu = Xf.mean(dim=0)
-    sig = Xf.std(dim=0)
-    # a column whose spread is far below that of its kind (the same unknown
-    # of x~ or of r at the other patch nodes, or the edge lengths) would be
-    # amplified without bound: floor sigma at 5% of the kind's median
+def column_groups(n_in=228):
+    """Input columns by kind: each unknown of x~ and of r over the patch
+    nodes, the edge lengths, and (n_in = 240) the diagonals and the angles."""
     groups = [list(range(c, 108, 4)) for c in range(4)] + [list(range(108 + c, 216, 4)) for c in range(4)]
     groups.append(list(range(216, 228)))
     if n_in > 228:
-        groups += [list(range(228, 232)), list(range(232, n_in))]   # diagonals, angles
-    for g in groups:
-        floor = 0.05 * float(sig[g].median())
+        groups += [list(range(228, 232)), list(range(232, n_in))]
+    return groups
+
+
+def normalization_from_stats(x_mean, x_sd, t_mean, t_sd, n_rows, n_in=228):
+    """The standardisation from column statistics (numpy float64 arrays):
+    input shift = column mean and scale = column deviation, the deviation
+    floored at 5% of the lower median deviation of the columns of the same
+    kind (a column whose spread is far below its kind's would be amplified
+    without bound), shift 0 / scale 1 on the padding columns; one target
+    scale, the root mean square of all target entries, from the target
+    columns' means and sample deviations over n_rows rows.  Returns
+    (mu, sigma, t_scale)."""
+    mu = np.array(x_mean, dtype=np.float64)
+    sig = np.array(x_sd, dtype=np.float64)
+    for g in column_groups(n_in):
+        floor = 0.05 * float(np.sort(sig[g])[(len(g) - 1) // 2])
         if floor <= 0.0:
             floor = 1.0
-        sig[g] = torch.clamp(sig[g], min=floor)
+        sig[g] = np.maximum(sig[g], floor)
     mu[n_in:] = 0.0
     sig[n_in:] = 1.0
-    ts = float(torch.sqrt((T.float() ** 2).mean()))
+    tm, tsd = np.asarray(t_mean, dtype=np.float64), np.asarray(t_sd, dtype=np.float64)
+    ms = float(np.mean(tsd ** 2 * (n_rows - 1) / n_rows + tm ** 2))
+    ts = ms ** 0.5
     return mu, sig, (ts if ts > 0 else 1.0)
 
 
+def fit_normalization(X, T, n_in=228):
+    """Per-column mean and deviation of the input rows and the target scale
+    (normalization_from_stats), the statistics computed by libdnnmg
+    (dnnmg_column_stats) on the device tensors X and T."""
+    def stats(A):
+        mean = torch.empty(A.shape[1], dtype=torch.float64, device=A.device)
+        sd = torch.empty_like(mean)
+        capi.dnnmg_column_stats(A, mean, sd, stream=torch.cuda.current_stream(A.device))
+        return mean.cpu().numpy(), sd.cpu().numpy()
+    xm, xs = stats(X)
+    tm, tsd = stats(T)
+    return normalization_from_stats(xm, xs, tm, tsd, X.shape[0], n_in=n_in)
+
+
 def normalize(X, norm, T=None):
-    """Standardised input rows in X's dtype (and targets divided by the scale)."""
+    """Standardised input rows in X's dtype (and targets divided by the
+    scale), written by libdnnmg (dnnmg_standardize) into new tensors."""
     mu, sig, ts = norm
-    Xn = ((X.float() - mu[None, :]) / sig[None, :]).to(X.dtype)
-    return (Xn, T / ts) if T is not None else Xn
+    dev = X.device
+    st = torch.cuda.current_stream(dev)
+    Xn = torch.empty_like(X)
+    capi.dnnmg_standardize(X, torch.as_tensor(mu, dtype=torch.float64, device=dev),
+                           torch.as_tensor(sig, dtype=torch.float64, device=dev), Xn, stream=st)
+    if T is None:
+        return Xn
+    Tn = torch.empty_like(T)
+    capi.dnnmg_standardize(T, torch.zeros(T.shape[1], dtype=torch.float64, device=dev),
+                           torch.full((T.shape[1],), float(ts), dtype=torch.float64, device=dev), Tn, stream=st)
+    return Xn, Tn
 
 
-def train(net, X, T, epochs=100, batch=4096, lr=1e-3, weight_decay=1e-5, seed=0, log=None):
+def train(net, X, T, epochs=100, batch=4096, lr=1e-3, weight_decay=1e-5, seed=0, log=None, val=None,
+          val_hist=None):
     """AdamW on the l2 loss; batches are multiples of 64 (the tail of an epoch
-    is dropped).  Returns the loss history (one value per epoch, mean over
-    its batches)."""
+    is dropped), gathered from X and T by libdnnmg (dnnmg_gather_rows) in a
+    seeded random order.  Returns the loss history (one value per epoch,
+    mean over its batches).  With ``val`` = (Xv, Tv) the validation loss is
+    taken after every epoch (appended to ``val_hist`` when given) and the
+    parameters of the epoch with the lowest one are kept (Sec. 6.4)."""
     opt = AdamW(net.params(), lr=lr, weight_decay=weight_decay)
     n = X.shape[0]
     batch = min(batch, n) // 64 * 64
+    st = torch.cuda.current_stream(X.device)
+    Xb = torch.empty((batch, X.shape[1]), dtype=X.dtype, device=X.device)
+    Tb = torch.empty((batch, T.shape[1]), dtype=T.dtype, device=T.device)
     g = torch.Generator(device="cpu").manual_seed(seed)
     hist = []
+    best, best_params = None, None
     for ep in range(epochs):
         perm = torch.randperm(n, generator=g).to(X.device)
         tot, cnt = 0.0, 0
         for i in range(0, n - batch + 1, batch):
             idx = perm[i:i + batch]
-            Y = net(X[idx].contiguous())
-            loss = mse_loss(Y, T[idx].contiguous())
+            capi.dnnmg_gather_rows(X, idx, Xb, stream=st)
+            capi.dnnmg_gather_rows(T, idx, Tb, stream=st)
+            Y = net(Xb)
+            loss = mse_loss(Y, Tb)
             opt.zero_grad()
             loss.backward()
             opt.step()
             tot += float(loss.detach())
             cnt += 1
         hist.append(tot / max(cnt, 1))
+        if val is not None:
+            vl = validation_loss(net, *val)
+            if val_hist is not None:
+                val_hist.append(vl)
+            if best is None or vl < best:
+                best = vl
+                best_params = [p.detach().clone() for p in net.params()]
         if log:
             log(ep, hist[-1])
+    if best_params is not None:
+        with torch.no_grad():
+            for p, q in zip(net.params(), best_params):
+                p.copy_(q)
     return hist
+
+
+@torch.no_grad()
+def validation_loss(net, Xv, Tv):
+    """(1/rows) sum_P |N(X_P) - T_P|^2 over all validation rows."""
+    Y = net.predict(Xv)
+    loss = torch.empty(1, dtype=torch.float32, device=Y.device)
+    capi.dnnmg_mse_loss(Y.shape[0], Y, Tv.contiguous(), loss, stream=torch.cuda.current_stream(Y.device))
+    return float(loss)

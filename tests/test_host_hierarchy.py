@@ -100,3 +100,27 @@ def test_multigrid_levels_of_nested_meshes():
     assert h.mg_nodes(0, 16) == [m.n_vertices]
     assert h.mg_nodes(1, 16) == [h.sizes["n_fine_nodes"], m.n_vertices]
     h.close()
+
+
+def test_two_level_fine_level_multigrid_and_injection():
+    # level L+2 of a J = 2 context over L = 4^3 (nested over 2^3): the solver
+    # coarsens it through L+1 (9^3 nodes) and L (5^3); 3^3 has one free
+    # velocity node and stops the hierarchy
+    m = I.cavity_mesh(4, levels=1)
+    j2 = capi.HostHierarchy(m, patch_levels=2)
+    j1 = capi.HostHierarchy(m, patch_levels=1)
+    assert j2.mg_nodes(level=capi.LEVEL_FINE) == [17 ** 3, 9 ** 3, 5 ** 3]
+    # the first nodes of level L+2 are level L+1's, in the J = 1 numbering:
+    # injection onto level L+1 is a prefix of the rows
+    n1 = j1.sizes["n_fine_nodes"]
+    assert np.array_equal(j2.data(capi.FINE_XYZ)[:n1], j1.data(capi.FINE_XYZ))
+    assert np.array_equal(j2.data(capi.FINE_KIND)[:n1], j1.data(capi.FINE_KIND))
+    # and on the nested channel: L+2 -> L+1 -> L -> L-1
+    c = I.channel_mesh(4, seed=2, levels=1)
+    c2 = capi.HostHierarchy(c, patch_levels=2)
+    c1 = capi.HostHierarchy(c, patch_levels=1)
+    nodes = c2.mg_nodes(level=capi.LEVEL_FINE)
+    assert nodes[1] == c1.sizes["n_fine_nodes"] and nodes[2] == c["xyz"].shape[0] and len(nodes) == 4
+    assert np.array_equal(c2.data(capi.FINE_XYZ)[:nodes[1]], c1.data(capi.FINE_XYZ))
+    for h in (j2, j1, c2, c1):
+        h.close()
