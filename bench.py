@@ -471,18 +471,67 @@ def serving_requests(n=SERVING_SIMS, seed=5, rate=12.0, steps=(50, 500), cells=(
     return poisson_requests(n, rate, seed, make)
 
 
+# nested meshes for whole-step serving (multigrid coarse solve): (nz, levels)
+# of the channel and (n, levels) of the cavity, 4k-135k coarse hex
+NESTED_CHANNELS = ((8, 2), (12, 2), (16, 3), (24, 3))
+NESTED_CAVITIES = ((16, 2), (24, 3), (32, 4), (40, 3))
+
+
+def serving_requests_solve(n=16, seed=7, rate=4.0, steps=(10, 40), cells=(4000, 65536)):
+    """The whole-step serving stream: n simulations arriving as a Poisson
+    process, each a nested channel or cavity (even odds) whose coarse size
+    is the nested mesh nearest to a log-uniform draw in `cells`, with a step
+    count uniform in `steps`, started from rest with its Dirichlet data;
+    every step runs the coarse Newton-GMRES-multigrid solve.  Draws are
+    SplitMix64."""
+    from paper_2307_14837_gb300 import inputs as I
+    from paper_2307_14837_gb300.serve import Request, poisson_requests
+    u = I.splitmix_uniform(seed * 104729 + 11, 3 * n).reshape(n, 3)
+    sizes = {}
+
+    def nearest(options, build, target):
+        best = None
+        for o in options:
+            if o not in sizes:
+                sizes[o] = len(build(o)["cells"])
+            if best is None or abs(math.log(sizes[o] / target)) < abs(math.log(sizes[best] / target)):
+                best = o
+        return best
+
+    def make(i, _):
+        target = cells[0] * (cells[1] / cells[0]) ** u[i, 0]
+        n_steps = int(steps[0] + (steps[1] - steps[0]) * u[i, 1])
+        if u[i, 2] < 0.5:
+            nz, lv = nearest(NESTED_CHANNELS, lambda o: I.channel_mesh(o[0], seed=0, levels=o[1]), target)
+            m = I.channel_mesh(nz, seed=i, levels=lv)
+            nu, dt, theta = m["meta"]["D"] / 200.0, DT, THETA
+        else:
+            k, lv = nearest(NESTED_CAVITIES, lambda o: I.cavity_mesh(o[0], levels=o[1]), target)
+            m = I.cavity_mesh(k, levels=lv)
+            nu, dt, theta = 0.01, 0.01, 1.0
+        return Request(f"sim{i}", m, nu, dt, theta, n_steps, solve=True)
+
+    return poisson_requests(n, rate, seed, make)
+
+
 def run_serving(args):
     """Serve the stream with one BF16 network launch per server step over all
-    live patches; each simulation's coarse state is held fixed (the patch
-    correction alone, as in the step benchmark)."""
+    live patches.  Default: each simulation's coarse state is held fixed
+    (the patch correction alone, as in the step benchmark).  With
+    --serving-solve: whole DNN-MG time steps (the coarse multigrid solve,
+    then the patch correction) on nested meshes."""
     import torch
-    from paper_2307_14837_gb300 import inputs as I
+    from paper_2307_14837_gb300 import capi, inputs as I
     from paper_2307_14837_gb300.serve import Server
     torch.cuda.set_device(0)
-    reqs = serving_requests(n=args.serving_sims)
+    solve = bool(args.serving_solve)
+    reqs = serving_requests_solve() if solve else serving_requests(n=args.serving_sims)
     Ws, ss, ts = I.network_weights(WIDTHS, seed=0)
     budget = int(args.serving_budget_gb * (1 << 30))
-    srv = Server(WIDTHS, Ws, ss, ts, memory_budget=budget, max_rows=args.serving_rows, precision="bf16")
+    prm = capi.dnnmg_solver_defaults(mg_levels=16, mg_pre=4, mg_post=4, mg_omega=0.8, newton_rtol=1e-9,
+                                     newton_atol=1e-10, gmres_rtol=GMRES_FORCING) if solve else None
+    srv = Server(WIDTHS, Ws, ss, ts, memory_budget=budget, max_rows=args.serving_rows, precision="bf16",
+                 solver=prm)
     with Clocks(0) as clk:
         stats = srv.run(reqs, timeout=1800.0)
     srv.close()
@@ -492,11 +541,17 @@ def run_serving(args):
             "n_gpus": 1, "higher_is_better": True, "dtype": "bf16", "data": "synthetic",
             "p50_step_latency_ms": stats["p50_step_latency_ms"], "p99_step_latency_ms": stats["p99_step_latency_ms"],
             "server_steps": stats["server_steps"], "network_launches": stats["network_launches"],
-            "wall_s": stats["wall_s"], "simulations": stats["simulations"],
-            "config": {"workload": f"{len(reqs)} simulations, channel/cavity mix, coarse meshes "
-                                   f"{min(cells)}-{max(cells)} hex (log-uniform 4k-300k), 50-500 steps each, "
-                                   f"Poisson arrivals 12/s; network {'-'.join(map(str, WIDTHS))}; "
-                                   "patch correction only (coarse state held)",
+            "wall_s": stats["wall_s"], "simulations": stats["simulations"], "failed": len(srv.failures),
+            "failures": {k: v[:160] for k, v in srv.failures.items()},
+            "config": {"workload": (f"{len(reqs)} simulations, nested channel/cavity mix, coarse meshes "
+                                    f"{min(cells)}-{max(cells)} hex (nearest to log-uniform 4k-65k), 10-40 "
+                                    f"steps each, Poisson arrivals 4/s; network {'-'.join(map(str, WIDTHS))}; "
+                                    "whole DNN-MG time steps (coarse Newton-GMRES-multigrid solve + patch "
+                                    "correction), from rest") if solve else
+                                   (f"{len(reqs)} simulations, channel/cavity mix, coarse meshes "
+                                    f"{min(cells)}-{max(cells)} hex (log-uniform 4k-300k), 50-500 steps each, "
+                                    f"Poisson arrivals 12/s; network {'-'.join(map(str, WIDTHS))}; "
+                                    "patch correction only (coarse state held)"),
                        "memory_budget_gb": args.serving_budget_gb, "max_rows": args.serving_rows,
                        "total_patch_steps": int(sum(c * r.n_steps for c, r in zip(cells, reqs)))},
             "clocks": clk.summary()}
@@ -547,7 +602,7 @@ def equal_error(steps=20, train_steps=60, epochs=100, train_nus=(0.007, 0.0085, 
     m = I.cavity_mesh(8, levels=2)
     dt, nu = 0.01, 0.01
     widths = (228, 256, 256, 81)
-    solver = lambda: capi.dnnmg_solver_defaults(mg_levels=3)   # noqa: E731
+    solver = lambda: capi.dnnmg_solver_defaults(mg_levels=3, gmres_rtol=GMRES_FORCING)   # noqa: E731
     Xs, Ts = [], []
     for nu_t in train_nus:
         X, Tg, _ = T.make_samples(m, nu_t, dt, 1.0, train_steps, solver=solver())
@@ -644,6 +699,10 @@ def equal_error(steps=20, train_steps=60, epochs=100, train_nus=(0.007, 0.0085, 
 
 
 WHOLE_NZ, WHOLE_LEVELS = 16, 3
+# GMRES stops each Newton step at this relative residual (inexact Newton):
+# Newton's own tolerance decides convergence, and on the 65,536-cell channel
+# a whole step takes 119 ms at 1e-2 against 306 ms at 1e-8
+GMRES_FORCING = 1e-2
 
 
 def whole_steps(steps=10, nz=WHOLE_NZ, levels=WHOLE_LEVELS):
@@ -676,7 +735,7 @@ def whole_steps(steps=10, nz=WHOLE_NZ, levels=WHOLE_LEVELS):
         return x0
 
     prm = lambda: capi.dnnmg_solver_defaults(mg_levels=levels, mg_pre=4, mg_post=4, mg_omega=0.8,  # noqa: E731
-                                             newton_rtol=1e-9, newton_atol=1e-10, gmres_rtol=1e-8)
+                                             newton_rtol=1e-9, newton_atol=1e-10, gmres_rtol=GMRES_FORCING)
     out = {"workload": f"channel nz={nz} nested ({levels} refinements of nz={nz >> levels}): "
                        f"{m.n_cells} coarse hex, {8 * m.n_cells} fine hex; Re 200, CN dt={DT}; "
                        f"{steps} timed whole time steps after 1 untimed",
@@ -760,6 +819,146 @@ class OracleSample:
         return n
 
 
+TRAIN_NZ, TRAIN_LEVELS = 4, 1
+
+
+def train_at_scale(n_geometries=8, steps=128, eval_steps=64, epochs=150, batch=65536, nz=TRAIN_NZ,
+                   levels=TRAIN_LEVELS, dt=0.01, theta=1.0, widths=(228, 1024, 1024, 1024, 1024, 81),
+                   val_fraction=0.05, seed0=100, ref_gmres_rtol=None, save_net=None):
+    """The learned part at scale (Sec. 6.4): training data from the
+    project's own solver on n_geometries seeded channel obstacles (cylinder
+    diameter and centre from the seed) at Re ~ U[100, 300] (nu = D / Re,
+    mean inflow 1), a coarse mesh of nz layers nested `levels` times
+    (nz = 4: 1,024 coarse hex, level L+1 8,192, level L+2 65,536), the
+    reference two refinements up (level L+2, Newton-GMRES-multigrid over
+    L+2, L+1, L and L-1) injected onto level L+1, backward Euler dt = 0.01
+    from rest with the full inflow, `steps` steps per geometry; then BF16
+    training (AdamW lr 1e-3, weight decay 1e-5, batch 65,536), the
+    parameters of the epoch with the lowest loss on a held-back random
+    val_fraction of the samples kept; then, on an unseen geometry (seed
+    seed0 + n_geometries, its own Re draw): the network's relative error on
+    that geometry's samples (no feedback), and e_v and E_v of the plain
+    coarse scheme and of DNN-MG (BF16 and FP64 forms) against the
+    level-(L+2) reference over eval_steps steps; a form whose solve fails
+    reports the step.  save_net: a path for the exported network (.npz)."""
+    import numpy as np
+    import torch
+
+    from paper_2307_14837_gb300 import capi, inputs as I
+    from paper_2307_14837_gb300 import train as T
+
+    t0 = time.perf_counter()
+    ref_solver = lambda: capi.dnnmg_solver_defaults(  # noqa: E731
+        mg_levels=levels + 2, mg_pre=4, mg_post=4, mg_omega=0.8, newton_rtol=1e-9, newton_atol=1e-10,
+        gmres_rtol=ref_gmres_rtol or GMRES_FORCING)
+    coarse_solver = lambda: capi.dnnmg_solver_defaults(  # noqa: E731
+        mg_levels=levels, newton_rtol=1e-9, newton_atol=1e-10, gmres_rtol=GMRES_FORCING)
+    re = 100.0 + 200.0 * I.splitmix_uniform(9000 + seed0, n_geometries + 1)
+    geos = []
+    Xs, Ts = [], []
+    for k in range(n_geometries):
+        seed = seed0 + k
+        m = I.channel_mesh(nz, seed=seed, levels=levels)
+        D = I.channel_geometry(seed)[0]
+        nu = D / re[k]
+        X, Tg, _ = T.make_samples(m, nu, dt, theta, steps, solver=coarse_solver(), ref_levels=2,
+                                  ref_solver=ref_solver(), keep_steps=False)
+        Xs.append(X)
+        Ts.append(Tg)
+        geos.append({"seed": seed, "D": round(float(D), 5), "Re": round(float(re[k]), 2), "nu": float(nu),
+                     "patches": int(m["cells"].shape[0])})
+        print(f"[train-scale] geometry {k}: Re {re[k]:.1f}, {X.shape[0]} samples, "
+              f"{time.perf_counter() - t0:.1f} s", file=sys.stderr, flush=True)
+    X, Tg = torch.cat(Xs), torch.cat(Ts)
+    del Xs, Ts
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    # validation rows: a seeded random subset
+    n = X.shape[0]
+    perm = torch.randperm(n, generator=torch.Generator(device="cpu").manual_seed(seed0)).to(X.device)
+    n_val = int(val_fraction * n)
+    vi, ti = perm[:n_val], perm[n_val:]
+    Xv = torch.empty((n_val, X.shape[1]), dtype=X.dtype, device=X.device)
+    Tv = torch.empty((n_val, 81), dtype=Tg.dtype, device=X.device)
+    Xt = torch.empty((n - n_val, X.shape[1]), dtype=X.dtype, device=X.device)
+    Tt = torch.empty((n - n_val, 81), dtype=Tg.dtype, device=X.device)
+    for src, idx, dst in ((X, vi, Xv), (Tg, vi, Tv), (X, ti, Xt), (Tg, ti, Tt)):
+        capi.dnnmg_gather_rows(src, idx, dst, stream=torch.cuda.current_stream())
+    del X, Tg
+    norm = T.fit_normalization(Xt, Tt)
+    Xn, Tn = T.normalize(Xt, norm, Tt)
+    Xvn, Tvn = T.normalize(Xv, norm, Tv)
+    del Xt, Tt, Xv, Tv
+    net = T.PatchNet(widths, precision="bf16", max_batch=batch, seed=0)
+    vh = []
+    t1 = time.perf_counter()
+
+    def log(ep, loss):
+        if ep % 10 == 0 or ep == epochs - 1:
+            print(f"[train-scale] epoch {ep}: loss {loss:.4g}, validation {vh[-1]:.4g}, "
+                  f"{time.perf_counter() - t1:.1f} s", file=sys.stderr, flush=True)
+
+    hist = T.train(net, Xn, Tn, epochs=epochs, batch=batch, lr=1e-3, weight_decay=1e-5, val=(Xvn, Tvn),
+                   val_hist=vh, log=log)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t1
+    network = (widths, *net.export(norm))
+    n_train = Xn.shape[0]
+    del Xn, Tn, Xvn, Tvn
+    if save_net:
+        np.savez(save_net, widths=np.array(widths), norm_mu=norm[0], norm_sigma=norm[1], t_scale=norm[2],
+                 **{f"W{i}": w.astype(np.float32) for i, w in enumerate(network[1])},
+                 **{f"shift{i}": b for i, b in enumerate(network[3])})
+
+    # the unseen geometry
+    seed = seed0 + n_geometries
+    m = I.channel_mesh(nz, seed=seed, levels=levels)
+    D = I.channel_geometry(seed)[0]
+    nu = D / re[n_geometries]
+    t2 = time.perf_counter()
+    Xh, Th, held = T.make_samples(m, nu, dt, theta, eval_steps, solver=coarse_solver(), ref_levels=2,
+                                  ref_solver=ref_solver())
+    # the network alone on the unseen geometry's samples (exact inputs)
+    Yh = net.predict(T.normalize(Xh, norm)) * norm[2]
+    net.close()
+    prior = float(torch.linalg.norm(Yh - Th) / torch.linalg.norm(Th))
+    del Xh, Th, Yh
+    ref = [s_["v_fine"][:, 0:3].cpu().numpy() for s_ in held]
+    out_eval = {"seed": seed, "D": round(float(D), 5), "Re": round(float(re[n_geometries]), 2),
+                "steps": eval_steps, "network_relative_error_exact_inputs": prior}
+    for name, netw, prec in (("plain_coarse", None, "fp64"), ("dnnmg_bf16", network, "bf16"),
+                             ("dnnmg_fp64", network, "fp64")):
+        vel = []
+        try:
+            T.trajectory_errors(m, nu, dt, theta, held, network=netw, solver=coarse_solver(), precision=prec,
+                                velocities=vel)
+            failed = None
+        except capi.DnnmgError as e:
+            failed = {"step": len(vel) + 1, "status": e.status}
+        e = T.velocity_errors(vel, ref[:len(vel)]) if vel else {"e_v": [], "E_v": None}
+        out_eval[name] = {"E_v": e["E_v"], "e_v_last": e["e_v"][-1] if vel else None,
+                          "e_v": [round(v, 6) for v in e["e_v"]], "failed": failed}
+        print(f"[train-scale] held-out {name}: E_v {e['E_v']}, failed {failed}", file=sys.stderr, flush=True)
+    epl = out_eval["plain_coarse"]["E_v"]
+    out_eval["E_v_dnnmg_over_plain_coarse"] = {
+        k: (out_eval[f"dnnmg_{k}"]["E_v"] / epl if out_eval[f"dnnmg_{k}"]["failed"] is None else None)
+        for k in ("bf16", "fp64")}
+    t_eval = time.perf_counter() - t2
+    lay = "-".join(str(w) for w in widths)
+    scheme = "backward Euler" if theta == 1.0 else ("Crank-Nicolson" if theta == 0.5 else f"theta={theta}")
+    return {"workload": f"channel nz={nz} nested ({levels} refinement of nz={nz >> levels}) with a seeded "
+                        f"cylinder: {geos[0]['patches']} coarse hex, targets from level L+2 "
+                        f"({64 * geos[0]['patches']} hex) injected onto L+1; {scheme} dt={dt}, {steps} steps "
+                        f"per geometry from rest; BF16 network {lay}",
+            "geometries": geos, "samples": n, "train_samples": n_train, "validation_samples": n_val,
+            "batch": batch, "epochs": epochs, "optimizer": "AdamW lr 1e-3, weight decay 1e-5",
+            "train_loss_first_last": [hist[0], hist[-1]], "validation_loss_best": min(vh),
+            "validation_best_epoch": int(np.argmin(vh)),
+            "seconds": {"data": round(t_data, 1), "train": round(t_train, 1), "held_out": round(t_eval, 1),
+                        "total": round(time.perf_counter() - t0, 1)},
+            "held_out": out_eval}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -773,11 +972,26 @@ def main():
     ap.add_argument("--serving-sims", type=int, default=SERVING_SIMS)
     ap.add_argument("--serving-budget-gb", type=float, default=96.0)
     ap.add_argument("--serving-rows", type=int, default=6_000_000)
+    ap.add_argument("--gmres-forcing", type=float, default=None,
+                    help="GMRES tolerance per Newton step in the whole-step legs (default 1e-2)")
+    ap.add_argument("--serving-solve", action="store_true",
+                    help="serve whole time steps (coarse multigrid solve on) on a stream of nested meshes")
+    ap.add_argument("--train-scale", action="store_true",
+                    help="run only the learned part at scale (8 seeded channel obstacles, level L+2 targets, "
+                         "held-out geometry) and print its JSON line")
+    ap.add_argument("--train-steps", type=int, default=128, help="time steps per training geometry")
+    ap.add_argument("--train-epochs", type=int, default=150)
+    ap.add_argument("--train-ref-gmres-rtol", type=float, default=None,
+                    help="GMRES tolerance per Newton step of the level-(L+2) reference solves")
+    ap.add_argument("--save-net", default=None, help="write the trained network (.npz) to this path")
     ap.add_argument("--whole-steps-only", type=int, default=0, metavar="K",
                     help="print only the whole-time-step measurement (K timed steps) as one JSON line")
     ap.add_argument("--nz", type=int, default=NZ,
                     help="channel resolution (cells across the height); the measured workload is nz=37")
     args = ap.parse_args()
+    if args.gmres_forcing is not None:
+        global GMRES_FORCING
+        GMRES_FORCING = args.gmres_forcing
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
@@ -809,6 +1023,15 @@ def main():
     if args.serving:
         if rank == 0:
             run_serving(args)
+        return
+
+    if args.train_scale:
+        if rank == 0:
+            import torch
+            torch.cuda.set_device(0)
+            print(json.dumps({"train_at_scale": train_at_scale(steps=args.train_steps, epochs=args.train_epochs,
+                                                               ref_gmres_rtol=args.train_ref_gmres_rtol,
+                                                               save_net=args.save_net)}))
         return
 
     if args.whole_steps_only:

@@ -221,13 +221,26 @@ class Server:
         yb = self.Y.element_size() * capi.N_OUT
         off = 0
         offsets = []
-        for s in self.live:
+        for s in list(self.live):
+            try:
+                with torch.cuda.stream(s.stream):
+                    capi.dnnmg_step_begin(s.path.ctx, s.x, s.b, s.F, self.X.data_ptr() + off * xb,
+                                          solve=s.req.solve, prm=self.solver)
+                    s.ev_begin.record(s.stream)
+            except capi.DnnmgError as e:
+                # this simulation's solve failed (no convergence, a non-finite
+                # rhs): it leaves the batch before the network launch
+                s.stream.synchronize()
+                self.live.remove(s)
+                self.used -= s.mem
+                s.path.close()
+                self.log.append(("failed", s.req.name, now))
+                self.failures[s.req.name] = str(e)
+                continue
             offsets.append(off)
-            with torch.cuda.stream(s.stream):
-                capi.dnnmg_step_begin(s.path.ctx, s.x, s.b, s.F, self.X.data_ptr() + off * xb, solve=s.req.solve,
-                                      prm=self.solver)
-                s.ev_begin.record(s.stream)
             off += s.path.n_patches
+        if not self.live:
+            return 0
         for s in self.live:
             self.stream.wait_event(s.ev_begin)
         capi.dnnmg_network(self.net, self.X, self.Y, off)

@@ -93,3 +93,57 @@ def test_injected_allocation_failure_fails_one_request(workers):
     assert s.reserved == 0 and s.rows_reserved == 0 and not s.preparing
     if s.pool:
         s.pool.shutdown()
+
+
+def test_a_failed_coarse_solve_fails_its_simulation_alone(monkeypatch):
+    # one server step with the device calls faked: the solve of "bad" fails
+    # (no convergence); it leaves before the network launch, its memory
+    # comes back, and the others are batched and finished as usual
+    import contextlib
+    s = _server(budget=100, max_rows=100, workers=0)
+    closed, calls = [], {}
+
+    class Ev:
+        def record(self, stream=None):
+            pass
+
+        def synchronize(self):
+            pass
+
+    class St:
+        def synchronize(self):
+            pass
+
+        def wait_event(self, e):
+            pass
+
+    def sim(name):
+        return SimpleNamespace(req=SimpleNamespace(name=name, solve=True, n_steps=5),
+                               path=SimpleNamespace(ctx=name, n_patches=4, close=lambda: closed.append(name)),
+                               stream=St(), x=None, b=None, F=None, mem=1, ev_begin=Ev(), ev_end=Ev(),
+                               steps_done=0, latencies=[])
+
+    s.live = [sim("a"), sim("bad"), sim("c")]
+    s.used = 3
+    s.X = SimpleNamespace(element_size=lambda: 2, data_ptr=lambda: 0)
+    s.Y = SimpleNamespace(element_size=lambda: 4, data_ptr=lambda: 0)
+    s.stream, s.ev_net, s.net, s.solver = St(), Ev(), "net", None
+    s.patches, s.step_latencies = 0, []
+    s._admit = lambda now: None
+
+    def begin(ctx, x, b, F, X, solve, prm):
+        if ctx == "bad":
+            raise capi.DnnmgError(-4, "Newton did not converge (injected)")
+        calls.setdefault("begin", []).append((ctx, X))
+
+    monkeypatch.setattr(serve.torch.cuda, "stream", lambda st: contextlib.nullcontext())
+    monkeypatch.setattr(capi, "dnnmg_step_begin", begin)
+    monkeypatch.setattr(capi, "dnnmg_network", lambda net, X, Y, rows: calls.setdefault("rows", []).append(rows))
+    monkeypatch.setattr(capi, "dnnmg_step_end", lambda ctx, Y, F, b: calls.setdefault("end", []).append((ctx, Y)))
+    monkeypatch.setattr(capi, "dnnmg_sync", lambda net: None)
+    s.step(0.0)
+    assert list(s.failures) == ["bad"] and closed == ["bad"] and s.used == 2
+    assert [x.req.name for x in s.live] == ["a", "c"]
+    assert calls["begin"] == [("a", 0), ("c", 4 * 256 * 2)]      # rows packed without the failed one
+    assert calls["rows"] == [8] and calls["end"] == [("a", 0), ("c", 4 * 81 * 4)]
+    assert [x.steps_done for x in s.live] == [1, 1]
