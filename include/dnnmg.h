@@ -400,7 +400,11 @@ typedef struct {
                               * groups sharing a node); 1 multiplicative: groups in colours
                               * sharing no node, updated colour after colour (forward before,
                               * backward after the coarse-grid correction) */
-    int32_t reserved;        /* must be 0 */
+    int32_t mg_bf16;         /* 1: the additive smoother reads bf16 copies of the level
+                              * matrices and of the group inverses (half the bytes of its
+                              * products; the Krylov products keep the FP32 matrix and
+                              * Newton's residual stays FP64); 0: FP32.  The
+                              * multiplicative smoother always uses FP32. */
 } dnnmg_solver_params;
 
 typedef struct {

@@ -337,7 +337,7 @@ class SolverParams(ctypes.Structure):
                 ("newton_rtol", ctypes.c_double), ("newton_max", ctypes.c_int32), ("gmres_restart", ctypes.c_int32),
                 ("gmres_max", ctypes.c_int32), ("mg_levels", ctypes.c_int32), ("gmres_rtol", ctypes.c_double),
                 ("rho_max", ctypes.c_double), ("mg_pre", ctypes.c_int32), ("mg_post", ctypes.c_int32),
-                ("mg_omega", ctypes.c_double), ("mg_smoother", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("mg_omega", ctypes.c_double), ("mg_smoother", ctypes.c_int32), ("mg_bf16", ctypes.c_int32)]
 
 
 class SolveStats(ctypes.Structure):

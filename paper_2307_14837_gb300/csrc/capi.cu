@@ -880,7 +880,7 @@ void dnnmg_solver_defaults(dnnmg_solver_params* p) {
     p->mg_post = 2;
     p->mg_omega = 0.7;
     p->mg_smoother = 0;
-    p->reserved = 0;
+    p->mg_bf16 = 0;
 }
 
 dnnmg_status dnnmg_hierarchy_mg(const dnnmg_hierarchy* h, int32_t level, int32_t mg_levels, int32_t max_levels,
@@ -1000,7 +1000,7 @@ dnnmg_status dnnmg_solve(dnnmg_ctx* ctx, int32_t level, const dnnmg_solver_param
     dnnmg_solver_params d;
     dnnmg_solver_defaults(&d);
     if (!prm) prm = &d;
-    if (prm->reserved != 0 || prm->mg_smoother < 0 || prm->mg_smoother > 1 || prm->newton_max < 0 || prm->gmres_max < 1 ||
+    if (prm->mg_bf16 < 0 || prm->mg_bf16 > 1 || prm->mg_smoother < 0 || prm->mg_smoother > 1 || prm->newton_max < 0 || prm->gmres_max < 1 ||
         prm->mg_pre < 0 || prm->mg_post < 0 || prm->mg_pre + prm->mg_post > 64 || !(prm->mg_omega > 0.0) ||
         prm->mg_omega > 2.0)
         return DNNMG_EINVAL;

@@ -885,33 +885,64 @@ __global__ void __launch_bounds__(256) bsr_spmv_kernel(int64_t n, const int32_t*
     if (lane < 4) y[4 * i + rr] = r ? r[4 * i + rr] - acc : acc;
 }
 
-// Group block of the global matrix: LU with partial pivoting in shared
-// memory, then its inverse (one column per thread: the pivots, a forward and
-// a back substitution of a unit vector), stored column-major in Ainv so that
-// applying it is a coalesced dense product.  A zero pivot gives a zero
-// component, as a triangular solve with that convention would.
-template <typename T, int NPG>
-__global__ void vanka_factor_kernel(int64_t ng, const int32_t* __restrict__ grp_blk, const T* __restrict__ A,
-                                    T* __restrict__ Ainv) {
+// The same product with the blocks stored in bf16 (the smoother's copy of
+// the matrix): lane rr of a quad reads row rr of a block as 4 bf16 (8 bytes).
+__global__ void __launch_bounds__(256) bsr_spmv_bf16_kernel(int64_t n, const int32_t* __restrict__ rp,
+                                                            const int32_t* __restrict__ ci,
+                                                            const __nv_bfloat16* __restrict__ A,
+                                                            const float* __restrict__ x, const float* __restrict__ r,
+                                                            float* __restrict__ y) {
+    const int64_t i = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (i >= n) return;
+    const int rr = lane & 3;
+    const uint2* A2 = reinterpret_cast<const uint2*>(A);
+    const float4* x4 = reinterpret_cast<const float4*>(x);
+    float acc = 0.f;
+    for (int32_t b = rp[i] + (lane >> 2); b < rp[i + 1]; b += 8) {
+        const uint2 raw = A2[4 * int64_t(b) + rr];
+        const float2 a01 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&raw.x));
+        const float2 a23 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&raw.y));
+        const float4 v = x4[ci[b]];
+        acc += a01.x * v.x + a01.y * v.y + a23.x * v.z + a23.y * v.w;
+    }
+    acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 8);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 16);
+    if (lane < 4) y[4 * i + rr] = r ? r[4 * i + rr] - acc : acc;
+}
+
+// Group block of the global matrix inverted in place in shared memory by
+// Gauss-Jordan elimination with partial pivoting (rows swapped, the column
+// order restored at the end), stored column-major in Ainv so that applying
+// it is a coalesced dense product.  Thread (ty, tx) of a 16 x 16 layout
+// updates rows ty + 16 a and columns tx + 16 b at every step.  A zero pivot
+// leaves its row at zero (the inverse then has a zero component there, as a
+// triangular solve with that convention would).
+template <typename T, int NPG, typename TO>
+__global__ void __launch_bounds__(256) vanka_factor_kernel(int64_t ng, const int32_t* __restrict__ grp_blk,
+                                                           const T* __restrict__ A, TO* __restrict__ Ainv) {
     constexpr int NL = 4 * NPG;
+    constexpr int RB = (NL + 15) / 16;   // rows (and columns) per thread
     extern __shared__ __align__(16) unsigned char vf_smem[];
-    T* M = reinterpret_cast<T*>(vf_smem);   // NL x NL
-    T* X = M + NL * NL;                     // NL x NL: X[i * NL + c] = (A^{-1})_{ic}
-    __shared__ int s_p;
+    T* M = reinterpret_cast<T*>(vf_smem);   // NL x NL, row-major
+    __shared__ T s_f[NL];
     __shared__ int s_piv[NL];
+    __shared__ int s_col[NL];
     const int64_t g = blockIdx.x;
-    for (int e = threadIdx.x; e < NL * NL; e += blockDim.x) {
+    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+    for (int e = tid; e < NL * NL; e += blockDim.x) {
         const int i = e / NL, j = e % NL;
         const int32_t b = grp_blk[(g * NPG + i / 4) * NPG + j / 4];
         M[e] = A[16 * int64_t(b) + 4 * (i % 4) + (j % 4)];
     }
     __syncthreads();
     for (int k = 0; k < NL; ++k) {
-        if (threadIdx.x < 32) {
+        if (tid < 32) {
             // pivot: largest |M[i][k]|, i >= k, smallest i on ties (warp argmax)
             T bv = T(-1);
             int bi = k;
-            for (int i = k + threadIdx.x; i < NL; i += 32) {
+            for (int i = k + tid; i < NL; i += 32) {
                 const T a = fabs(M[i * NL + k]);
                 if (a > bv) {
                     bv = a;
@@ -926,59 +957,55 @@ __global__ void vanka_factor_kernel(int64_t ng, const int32_t* __restrict__ grp_
                     bi = oi;
                 }
             }
-            if (threadIdx.x == 0) {
-                s_p = bi;
-                s_piv[k] = bi;
-            }
+            if (tid == 0) s_piv[k] = bi;
         }
         __syncthreads();
-        const int pr = s_p;
+        const int pr = s_piv[k];
         if (pr != k)
-            for (int j = threadIdx.x; j < NL; j += blockDim.x) {
+            for (int j = tid; j < NL; j += blockDim.x) {
                 const T t = M[k * NL + j];
                 M[k * NL + j] = M[pr * NL + j];
                 M[pr * NL + j] = t;
             }
         __syncthreads();
+        // row k / pivot (the pivot's own slot becomes 1 / pivot); column k kept
         const T d = M[k * NL + k];
         const T inv = d != T(0) ? T(1) / d : T(0);
-        for (int i = k + 1 + threadIdx.x; i < NL; i += blockDim.x) M[i * NL + k] *= inv;
+        for (int i = tid; i < NL; i += blockDim.x) s_f[i] = i == k ? T(0) : M[i * NL + k];
         __syncthreads();
-        const int rem = NL - k - 1;
-        for (int e = threadIdx.x; e < rem * rem; e += blockDim.x) {
-            const int i = k + 1 + e / rem, j = k + 1 + e % rem;
-            M[i * NL + j] -= M[i * NL + k] * M[k * NL + j];
+        for (int j = tid; j < NL; j += blockDim.x) M[k * NL + j] = (j == k ? T(1) : M[k * NL + j]) * inv;
+        __syncthreads();
+        // every other row: row_i -= f_i row_k, with column k starting from 0
+#pragma unroll
+        for (int a = 0; a < RB; ++a) {
+            const int i = ty + 16 * a;
+            if (i >= NL || i == k) continue;
+            const T f = s_f[i];
+#pragma unroll
+            for (int b = 0; b < RB; ++b) {
+                const int j = tx + 16 * b;
+                if (j >= NL) continue;
+                const T m = j == k ? T(0) : M[i * NL + j];
+                M[i * NL + j] = m - f * M[k * NL + j];
+            }
         }
         __syncthreads();
     }
-    const int c = threadIdx.x;
-    if (c < NL) {
-        for (int i = 0; i < NL; ++i) X[i * NL + c] = i == c ? T(1) : T(0);
-        for (int k = 0; k < NL; ++k) {
-            const int pr = s_piv[k];
-            if (pr != k) {
-                const T t = X[k * NL + c];
-                X[k * NL + c] = X[pr * NL + c];
-                X[pr * NL + c] = t;
-            }
-        }
-        for (int i = 1; i < NL; ++i) {
-            T acc = X[i * NL + c];
-            for (int j = 0; j < i; ++j) acc -= M[i * NL + j] * X[j * NL + c];
-            X[i * NL + c] = acc;
-        }
-        for (int i = NL - 1; i >= 0; --i) {
-            T acc = X[i * NL + c];
-            for (int j = i + 1; j < NL; ++j) acc -= M[i * NL + j] * X[j * NL + c];
-            const T d = M[i * NL + i];
-            X[i * NL + c] = d != T(0) ? acc / d : T(0);
+    // the row swaps of the elimination become column swaps of the inverse,
+    // undone in reverse order: column c of the inverse is column s_col[c]
+    if (tid == 0) {
+        for (int c = 0; c < NL; ++c) s_col[c] = c;
+        for (int k = NL - 1; k >= 0; --k) {
+            const int t = s_col[k];
+            s_col[k] = s_col[s_piv[k]];
+            s_col[s_piv[k]] = t;
         }
     }
     __syncthreads();
-    // column-major: Ainv[g][j * NL + i] = (A^{-1})_{ij}
-    for (int e = threadIdx.x; e < NL * NL; e += blockDim.x) {
+    // column-major: Ainv[g][j * NL + i] = (A^{-1})_{ij} (rounded once to TO)
+    for (int e = tid; e < NL * NL; e += blockDim.x) {
         const int j = e / NL, i = e % NL;
-        Ainv[g * NL * NL + e] = X[i * NL + j];
+        Ainv[g * NL * NL + e] = TO(M[i * NL + s_col[j]]);
     }
 }
 
@@ -999,6 +1026,32 @@ __global__ void __launch_bounds__(128) vanka_apply_kernel(int64_t ng, const int3
         for (int j = 0; j < NL; ++j) acc += Ag[j * NL + i] * s_r[j];
         zloc[g * NL + i] = acc;
     }
+}
+
+// The same with bf16 inverses: thread t computes rows 2t and 2t + 1 from
+// one bf16 pair per column (column-major, so a warp's pairs are contiguous).
+template <int NPG>
+__global__ void __launch_bounds__(64) vanka_apply_bf16_kernel(int64_t ng, const int32_t* __restrict__ groups,
+                                                              const __nv_bfloat16* __restrict__ Ainv,
+                                                              const float* __restrict__ r,
+                                                              float* __restrict__ zloc) {
+    constexpr int NL = 4 * NPG, NH = NL / 2;
+    __shared__ float s_r[NL];
+    const int64_t g = blockIdx.x;
+    for (int e = threadIdx.x; e < NL; e += blockDim.x) s_r[e] = r[4 * int64_t(groups[g * NPG + e / 4]) + e % 4];
+    __syncthreads();
+    const int t = threadIdx.x;
+    if (t >= NH) return;
+    const __nv_bfloat162* Ag = reinterpret_cast<const __nv_bfloat162*>(Ainv + g * NL * NL) + t;
+    float a0 = 0.f, a1 = 0.f;
+#pragma unroll 6
+    for (int j = 0; j < NL; ++j) {
+        const float2 w = __bfloat1622float2(Ag[j * NH]);
+        a0 = fmaf(w.x, s_r[j], a0);
+        a1 = fmaf(w.y, s_r[j], a1);
+    }
+    zloc[g * NL + 2 * t] = a0;
+    zloc[g * NL + 2 * t + 1] = a1;
 }
 
 // e_j = (first ? 0 : e_j) + omega / valence_j * (sum of the groups' local
@@ -1423,7 +1476,10 @@ struct LevelData {
     double* xyz = nullptr;
     uint8_t* dir = nullptr;
     float* A = nullptr;       // BSR values [nnzb][4][4]
-    float* G = nullptr;       // [ng][nl][nl]: local Jacobians, then the group inverses (column-major)
+    float* G = nullptr;       // [ng][nl][nl]: local Jacobians, then the group inverses (column-major;
+                              // in bf16, packed at the start of the same storage, when g_bf16)
+    __nv_bfloat16* Ab = nullptr;   // BSR values in bf16 for the smoother's products (when g_bf16)
+    bool g_bf16 = false;
     float* zloc = nullptr;    // [ng][nl]
     float *r = nullptr, *e = nullptr, *d = nullptr;   // [n][4]
     float *r2 = nullptr, *e2 = nullptr, *d2 = nullptr;  // [n][4] operands of the Krylov products (solve level)
@@ -1444,6 +1500,7 @@ struct DeviceLevel {
     std::vector<LevelData*> mg;      // coarser levels, mg[0] the next coarser
     int mg_pre = 2, mg_post = 2;
     int mg_smoother = 0;        // 0 additive, 1 multiplicative (coloured) group-Vanka
+    int mg_bf16 = 0;            // additive smoother on bf16 copies of the matrix and the inverses
     float omega = 0.7f;
     double* local = nullptr;    // [ng][npg][4] FP64 local residuals
     double* mass = nullptr;     // [n] lumped mass
@@ -1764,20 +1821,36 @@ cudaError_t assemble(const LevelData& L, const double* x, const LvPrm& p, T* Jlo
 template <int NPG>
 cudaError_t launch_vanka_factor(const LevelData& L, cudaStream_t s) {
     constexpr int NL = 4 * NPG;
-    constexpr size_t smem = 2 * size_t(NL) * NL * sizeof(float);
+    constexpr size_t smem = size_t(NL) * NL * sizeof(float);
     static bool attr = false;
     if (!attr) {
-        CKE(cudaFuncSetAttribute(vanka_factor_kernel<float, NPG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 int(smem)));
+        CKE(cudaFuncSetAttribute(vanka_factor_kernel<float, NPG, float>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+        CKE(cudaFuncSetAttribute(vanka_factor_kernel<float, NPG, __nv_bfloat16>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
         attr = true;
     }
-    vanka_factor_kernel<float, NPG><<<unsigned(L.h.ng), 256, smem, s>>>(L.h.ng, L.grp_blk, L.A, L.G);
+    // the kernel reads the assembled matrix, not G, so the bf16 inverses may
+    // overwrite G's local Jacobians in place
+    if (L.g_bf16)
+        vanka_factor_kernel<float, NPG, __nv_bfloat16><<<unsigned(L.h.ng), 256, smem, s>>>(
+            L.h.ng, L.grp_blk, L.A, reinterpret_cast<__nv_bfloat16*>(L.G));
+    else
+        vanka_factor_kernel<float, NPG, float><<<unsigned(L.h.ng), 256, smem, s>>>(L.h.ng, L.grp_blk, L.A, L.G);
     return cudaGetLastError();
 }
 
-// FP32 matrix and group inverses of a smoothing level
-cudaError_t setup_smoother(LevelData& L, const double* x, const LvPrm& p, cudaStream_t s) {
+// FP32 matrix and group inverses of a smoothing level; with bf16 also the
+// bf16 copy of the matrix for the smoother's products
+cudaError_t setup_smoother(LevelData& L, const double* x, const LvPrm& p, bool bf16, cudaStream_t s) {
     CKE(assemble<float>(L, x, p, L.G, L.A, s));
+    L.g_bf16 = bf16;
+    if (bf16) {
+        const int64_t nv = int64_t(L.h.col_idx.size()) * 16;
+        if (!L.Ab) CKE(dalloc(L.allocs, size_t(nv), &L.Ab));
+        convert_kernel<float, __nv_bfloat16><<<nblk(nv, 256), 256, 0, s>>>(nv, L.A, L.Ab);
+        CKE(cudaGetLastError());
+    }
     return L.h.npg == 27 ? launch_vanka_factor<27>(L, s) : launch_vanka_factor<8>(L, s);
 }
 
@@ -1841,8 +1914,9 @@ cudaError_t level_rhs(DeviceLevel* D, const OpParams& op, const double* x_old, d
 cudaError_t level_jacobian(DeviceLevel* D, const OpParams& op, const dnnmg_solver_params* sp, const double* x,
                            cudaStream_t s) {
     const LvPrm p = make_prm(op, sp);
-    CKE(setup_smoother(D->top, x, p, s));
-    for (LevelData* L : D->mg) CKE(L->coarsest ? setup_coarsest(*L, x, p, s) : setup_smoother(*L, x, p, s));
+    const bool bf16 = D->mg_bf16 != 0 && D->mg_smoother == 0;
+    CKE(setup_smoother(D->top, x, p, bf16, s));
+    for (LevelData* L : D->mg) CKE(L->coarsest ? setup_coarsest(*L, x, p, s) : setup_smoother(*L, x, p, bf16, s));
     D->has_jacobian = true;
     return cudaSuccess;
 }
@@ -1896,6 +1970,17 @@ cudaError_t smooth_mult(LevelData& L, int sweeps, bool e_zero, float omega, bool
     return cudaGetLastError();
 }
 
+// d = r - A e on a smoothing level (the bf16 copy of A when the smoother
+// runs in bf16)
+cudaError_t smoother_residual(LevelData& L, cudaStream_t s) {
+    const int64_t n = L.h.n;
+    if (L.g_bf16)
+        bsr_spmv_bf16_kernel<<<nblk(32 * n, 256), 256, 0, s>>>(n, L.row_ptr, L.col_idx, L.Ab, L.e, L.r, L.d);
+    else
+        bsr_spmv_kernel<float><<<nblk(32 * n, 256), 256, 0, s>>>(n, L.row_ptr, L.col_idx, L.A, L.e, L.r, L.d);
+    return cudaGetLastError();
+}
+
 // `sweeps` damped additive group-Vanka sweeps on L: e += omega V(r - A e)
 // (e = omega V(r) first when e_zero)
 cudaError_t smooth(LevelData& L, int sweeps, bool e_zero, float omega, cudaStream_t s) {
@@ -1904,14 +1989,21 @@ cudaError_t smooth(LevelData& L, int sweeps, bool e_zero, float omega, cudaStrea
         const bool first = it == 0 && e_zero;
         const float* d = L.r;
         if (!first) {
-            bsr_spmv_kernel<float><<<nblk(32 * h.n, 256), 256, 0, s>>>(h.n, L.row_ptr, L.col_idx, L.A, L.e,
-                                                                              L.r, L.d);
+            CKE(smoother_residual(L, s));
             d = L.d;
         }
-        if (h.npg == 27)
-            vanka_apply_kernel<float, 27><<<unsigned(h.ng), 128, 0, s>>>(h.ng, L.groups, L.G, d, L.zloc);
-        else
-            vanka_apply_kernel<float, 8><<<unsigned(h.ng), 32, 0, s>>>(h.ng, L.groups, L.G, d, L.zloc);
+        const __nv_bfloat16* Gb = reinterpret_cast<const __nv_bfloat16*>(L.G);
+        if (h.npg == 27) {
+            if (L.g_bf16)
+                vanka_apply_bf16_kernel<27><<<unsigned(h.ng), 64, 0, s>>>(h.ng, L.groups, Gb, d, L.zloc);
+            else
+                vanka_apply_kernel<float, 27><<<unsigned(h.ng), 128, 0, s>>>(h.ng, L.groups, L.G, d, L.zloc);
+        } else {
+            if (L.g_bf16)
+                vanka_apply_bf16_kernel<8><<<unsigned(h.ng), 32, 0, s>>>(h.ng, L.groups, Gb, d, L.zloc);
+            else
+                vanka_apply_kernel<float, 8><<<unsigned(h.ng), 32, 0, s>>>(h.ng, L.groups, L.G, d, L.zloc);
+        }
         vanka_update_kernel<float><<<nblk(h.n, 256), 256, 0, s>>>(h.n, L.node_ptr, L.node_idx, L.zloc, omega,
                                                                    first ? 1 : 0, L.e);
     }
@@ -1936,7 +2028,7 @@ cudaError_t vcycle(DeviceLevel* D, int k, cudaStream_t s) {
         e_zero = false;
     }
     if (e_zero) CKE(cudaMemsetAsync(L.e, 0, size_t(4 * h.n) * 4, s));
-    bsr_spmv_kernel<float><<<nblk(32 * h.n, 256), 256, 0, s>>>(h.n, L.row_ptr, L.col_idx, L.A, L.e, L.r, L.d);
+    CKE(smoother_residual(L, s));
     LevelData& C = *D->mg[size_t(k)];
     mg_restrict_kernel<float><<<nblk(C.h.n, 256), 256, 0, s>>>(C.h.n, L.R_ptr, L.R_idx, L.R_w, L.d, C.dir, C.h.pin,
                                                                 C.r);
@@ -2057,6 +2149,7 @@ cudaError_t level_solve(DeviceLevel* D, const OpParams& op, const dnnmg_solver_p
     D->mg_pre = sp->mg_pre;
     D->mg_post = sp->mg_post;
     D->mg_smoother = sp->mg_smoother;
+    D->mg_bf16 = sp->mg_bf16;
     D->omega = float(sp->mg_omega);
     if (D->top.h.mean_zero_pressure) CKE(compute_mass(D, op, s));
     double r0 = -1.0, rprev = -1.0;

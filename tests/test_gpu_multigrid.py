@@ -109,3 +109,33 @@ def test_gmres_iterations_stay_flat_under_refinement():
     assert max(its) <= 1.2 * mean and min(its) >= 0.8 * mean, its
     one = _gmres_per_newton(I.cavity_mesh(16, levels=3), 0)
     assert its[1] < 0.5 * one, (its, one)
+
+
+@pytest.mark.parametrize("theta", [1.0, 0.5])
+def test_bf16_smoother_newton_matches_oracle(theta):
+    # the additive smoother on bf16 copies of the matrices and inverses: a
+    # cheaper preconditioner, the same Newton solution (FP64 residual)
+    m = I.cavity_mesh(8, levels=2, jitter=0.1, seed=1)
+    lev = fem.Level(m["xyz"], m["cells"], m["vertex_bc"], True)
+    prm = dict(PRM, theta=theta)
+    x_old = _start(m, m["xyz"], m["vertex_bc"])
+    b = lev.rhs(x_old[:, 0:3], prm)
+    ref, _ = osolve.newton(lev, x_old, b, prm, tol=1e-14, rtol=1e-15)
+    its = {}
+    for bf16 in (0, 1):
+        p = PatchPath(m, NU, DT, theta, "fp64")
+        sp = capi.dnnmg_solver_defaults(mg_levels=2, newton_atol=1e-13, newton_rtol=1e-13, gmres_rtol=1e-10,
+                                        mg_bf16=bf16)
+        x = _dev(x_old)
+        st = capi.dnnmg_solve(p.ctx, capi.LEVEL_COARSE, _dev(b), x, sp)
+        assert st["converged"] == 1
+        assert np.abs(x.cpu().numpy() - ref).max() <= 1e-9 * np.abs(ref).max()
+        its[bf16] = st["gmres_iterations"] / max(1, st["newton_iterations"])
+        p.close()
+    assert its[1] <= 1.3 * its[0] + 1
+    p = PatchPath(m, NU, DT, theta, "fp64")
+    try:
+        with pytest.raises(capi.DnnmgError):
+            capi.dnnmg_solve(p.ctx, capi.LEVEL_COARSE, _dev(b), _dev(x_old), capi.dnnmg_solver_defaults(mg_bf16=2))
+    finally:
+        p.close()
