@@ -204,6 +204,11 @@ class Server:
             # first right-hand sides: the fine Rhs of the prolongated state, restricted
             F, bcf = p.rhs_restrict(x.to(p.dtype), torch.zeros((p.n_fine, 3), dtype=p.dtype, device=self.device))
             b = bcf.double().contiguous() if p.dtype != torch.float64 else bcf
+            if req.solve:
+                # the solver's level (multigrid hierarchy, matrix and factor
+                # storage) is built here, on the preparing thread, rather
+                # than inside the simulation's first server step
+                capi.dnnmg_level_mg(p.ctx, capi.LEVEL_COARSE, self.solver)
         sim = Simulation(req=req, path=p, stream=stream, x=x, b=b, F=F, mem=mem, admitted=now)
         sim.ev_begin = torch.cuda.Event()
         sim.ev_end = torch.cuda.Event()
