@@ -414,7 +414,8 @@ typedef struct {
 
 /* Defaults: alpha0 0.02, delta0 0.1, atol 1e-11, rtol 1e-12, 25 Newton steps,
  * restart 40, 400 GMRES iterations, gmres_rtol 1e-10, rho_max 0.1,
- * mg_levels 0, 2 + 2 additive Vanka sweeps, damping 0.7. */
+ * mg_levels 0, 2 + 2 additive Vanka sweeps, damping 0.7, FP32 smoother
+ * storage (mg_bf16 0). */
 void dnnmg_solver_defaults(dnnmg_solver_params* p);
 
 /* Number of nodes of a level and whether it uses the local projection. */
