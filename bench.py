@@ -829,27 +829,35 @@ class OracleSample:
 
 
 TRAIN_NZ, TRAIN_LEVELS = 4, 1
+BIG = (228, 1024, 1024, 1024, 1024, 81)
+# (name, widths, deviation of the training noise on the residual columns
+# Q(r) in standardised units); the first noisy one is the method, the others
+# are reported beside it
+TRAIN_VARIANTS = (("w1024x4_noise0.1", BIG, 0.1), ("w1024x4", BIG, 0.0), ("w1024x4_noise0.3", BIG, 0.3),
+                  ("w512x3_noise0.1", (228, 512, 512, 512, 81), 0.1))
 
 
 def train_at_scale(n_geometries=8, steps=128, eval_steps=64, epochs=150, batch=65536, nz=TRAIN_NZ,
-                   levels=TRAIN_LEVELS, dt=0.01, theta=1.0, widths=(228, 1024, 1024, 1024, 1024, 81),
-                   val_fraction=0.05, seed0=100, ref_gmres_rtol=None, save_net=None):
+                   levels=TRAIN_LEVELS, dt=0.01, theta=1.0, variants=TRAIN_VARIANTS, val_fraction=0.05, seed0=100,
+                   ref_gmres_rtol=None, save_net=None):
     """The learned part at scale (Sec. 6.4): training data from the
     project's own solver on n_geometries seeded channel obstacles (cylinder
     diameter and centre from the seed) at Re ~ U[100, 300] (nu = D / Re,
     mean inflow 1), a coarse mesh of nz layers nested `levels` times
     (nz = 4: 1,024 coarse hex, level L+1 8,192, level L+2 65,536), the
     reference two refinements up (level L+2, Newton-GMRES-multigrid over
-    L+2, L+1, L and L-1) injected onto level L+1, backward Euler dt = 0.01
-    from rest with the full inflow, `steps` steps per geometry; then BF16
-    training (AdamW lr 1e-3, weight decay 1e-5, batch 65,536), the
-    parameters of the epoch with the lowest loss on a held-back random
-    val_fraction of the samples kept; then, on an unseen geometry (seed
-    seed0 + n_geometries, its own Re draw): the network's relative error on
-    that geometry's samples (no feedback), and e_v and E_v of the plain
-    coarse scheme and of DNN-MG (BF16 and FP64 forms) against the
-    level-(L+2) reference over eval_steps steps; a form whose solve fails
-    reports the step.  save_net: a path for the exported network (.npz)."""
+    L+2, L+1, L and L-1, its Dirichlet values the prolongated coarse data)
+    injected onto level L+1, backward Euler dt = 0.01 from rest with the
+    full inflow, `steps` steps per geometry.  Then, per variant (widths,
+    training noise on the residual columns), BF16 training (AdamW lr 1e-3,
+    weight decay 1e-5, batch 65,536, `epochs` epochs), the parameters of
+    the epoch with the lowest loss on a held-back random val_fraction of
+    the samples kept.  On an unseen geometry (seed seed0 + n_geometries,
+    its own Re draw): each network's relative error on that geometry's
+    samples (no feedback), and e_v and E_v of the plain coarse scheme and of
+    DNN-MG (BF16; FP64 too for the first variant) against the level-(L+2)
+    reference over eval_steps steps; a run whose solve fails reports the
+    step.  save_net: a path for the first variant's network (.npz)."""
     import numpy as np
     import torch
 
@@ -863,6 +871,8 @@ def train_at_scale(n_geometries=8, steps=128, eval_steps=64, epochs=150, batch=6
     coarse_solver = lambda: capi.dnnmg_solver_defaults(  # noqa: E731
         mg_levels=levels, newton_rtol=1e-9, newton_atol=1e-10, gmres_rtol=GMRES_FORCING)
     re = 100.0 + 200.0 * I.splitmix_uniform(9000 + seed0, n_geometries + 1)
+    log = lambda msg: print(f"[train-scale] {msg}, {time.perf_counter() - t0:.1f} s",  # noqa: E731
+                            file=sys.stderr, flush=True)
     geos = []
     Xs, Ts = [], []
     for k in range(n_geometries):
@@ -871,13 +881,12 @@ def train_at_scale(n_geometries=8, steps=128, eval_steps=64, epochs=150, batch=6
         D = I.channel_geometry(seed)[0]
         nu = D / re[k]
         X, Tg, _ = T.make_samples(m, nu, dt, theta, steps, solver=coarse_solver(), ref_levels=2,
-                                  ref_solver=ref_solver(), keep_steps=False)
+                                  ref_solver=ref_solver(), keep_steps=False, fine_boundary="prolongated")
         Xs.append(X)
         Ts.append(Tg)
         geos.append({"seed": seed, "D": round(float(D), 5), "Re": round(float(re[k]), 2), "nu": float(nu),
                      "patches": int(m["cells"].shape[0])})
-        print(f"[train-scale] geometry {k}: Re {re[k]:.1f}, {X.shape[0]} samples, "
-              f"{time.perf_counter() - t0:.1f} s", file=sys.stderr, flush=True)
+        log(f"geometry {k}: Re {re[k]:.1f}, {X.shape[0]} samples")
     X, Tg = torch.cat(Xs), torch.cat(Ts)
     del Xs, Ts
     torch.cuda.synchronize()
@@ -897,46 +906,21 @@ def train_at_scale(n_geometries=8, steps=128, eval_steps=64, epochs=150, batch=6
     norm = T.fit_normalization(Xt, Tt)
     Xn, Tn = T.normalize(Xt, norm, Tt)
     Xvn, Tvn = T.normalize(Xv, norm, Tv)
-    del Xt, Tt, Xv, Tv
-    net = T.PatchNet(widths, precision="bf16", max_batch=batch, seed=0)
-    vh = []
-    t1 = time.perf_counter()
-
-    def log(ep, loss):
-        if ep % 10 == 0 or ep == epochs - 1:
-            print(f"[train-scale] epoch {ep}: loss {loss:.4g}, validation {vh[-1]:.4g}, "
-                  f"{time.perf_counter() - t1:.1f} s", file=sys.stderr, flush=True)
-
-    hist = T.train(net, Xn, Tn, epochs=epochs, batch=batch, lr=1e-3, weight_decay=1e-5, val=(Xvn, Tvn),
-                   val_hist=vh, log=log)
-    torch.cuda.synchronize()
-    t_train = time.perf_counter() - t1
-    network = (widths, *net.export(norm))
     n_train = Xn.shape[0]
-    del Xn, Tn, Xvn, Tvn
-    if save_net:
-        np.savez(save_net, widths=np.array(widths), norm_mu=norm[0], norm_sigma=norm[1], t_scale=norm[2],
-                 **{f"W{i}": w.astype(np.float32) for i, w in enumerate(network[1])},
-                 **{f"shift{i}": b for i, b in enumerate(network[3])})
+    del Xt, Tt, Xv, Tv
 
-    # the unseen geometry
+    # the unseen geometry: its reference trajectory and samples
     seed = seed0 + n_geometries
     m = I.channel_mesh(nz, seed=seed, levels=levels)
     D = I.channel_geometry(seed)[0]
     nu = D / re[n_geometries]
-    t2 = time.perf_counter()
     Xh, Th, held = T.make_samples(m, nu, dt, theta, eval_steps, solver=coarse_solver(), ref_levels=2,
-                                  ref_solver=ref_solver())
-    # the network alone on the unseen geometry's samples (exact inputs)
-    Yh = net.predict(T.normalize(Xh, norm)) * norm[2]
-    net.close()
-    prior = float(torch.linalg.norm(Yh - Th) / torch.linalg.norm(Th))
-    del Xh, Th, Yh
+                                  ref_solver=ref_solver(), fine_boundary="prolongated")
+    Xhn = T.normalize(Xh, norm)
     ref = [s_["v_fine"][:, 0:3].cpu().numpy() for s_ in held]
-    out_eval = {"seed": seed, "D": round(float(D), 5), "Re": round(float(re[n_geometries]), 2),
-                "steps": eval_steps, "network_relative_error_exact_inputs": prior}
-    for name, netw, prec in (("plain_coarse", None, "fp64"), ("dnnmg_bf16", network, "bf16"),
-                             ("dnnmg_fp64", network, "fp64")):
+    log("held-out reference")
+
+    def run_loop(netw, prec):
         vel = []
         try:
             T.trajectory_errors(m, nu, dt, theta, held, network=netw, solver=coarse_solver(), precision=prec,
@@ -945,27 +929,53 @@ def train_at_scale(n_geometries=8, steps=128, eval_steps=64, epochs=150, batch=6
         except capi.DnnmgError as e:
             failed = {"step": len(vel) + 1, "status": e.status}
         e = T.velocity_errors(vel, ref[:len(vel)]) if vel else {"e_v": [], "E_v": None}
-        out_eval[name] = {"E_v": e["E_v"], "e_v_last": e["e_v"][-1] if vel else None,
-                          "e_v": [round(v, 6) for v in e["e_v"]], "failed": failed}
-        print(f"[train-scale] held-out {name}: E_v {e['E_v']}, failed {failed}", file=sys.stderr, flush=True)
-    epl = out_eval["plain_coarse"]["E_v"]
-    out_eval["E_v_dnnmg_over_plain_coarse"] = {
-        k: (out_eval[f"dnnmg_{k}"]["E_v"] / epl if out_eval[f"dnnmg_{k}"]["failed"] is None else None)
-        for k in ("bf16", "fp64")}
-    t_eval = time.perf_counter() - t2
-    lay = "-".join(str(w) for w in widths)
-    scheme = "backward Euler" if theta == 1.0 else ("Crank-Nicolson" if theta == 0.5 else f"theta={theta}")
+        return {"E_v": e["E_v"], "e_v_last": e["e_v"][-1] if vel else None,
+                "e_v": [round(v, 6) for v in e["e_v"]], "failed": failed}
+
+    plain = run_loop(None, "fp64")
+    log(f"plain coarse E_v {plain['E_v']}")
+    out_var = {}
+    t_train = 0.0
+    for vi_, (name, widths, sigma) in enumerate(variants):
+        net = T.PatchNet(widths, precision="bf16", max_batch=batch, seed=0)
+        vh = []
+        t1 = time.perf_counter()
+        hist = T.train(net, Xn, Tn, epochs=epochs, batch=batch, lr=1e-3, weight_decay=1e-5, val=(Xvn, Tvn),
+                       val_hist=vh, noise=(108, 216, sigma) if sigma > 0 else None)
+        torch.cuda.synchronize()
+        t_train += time.perf_counter() - t1
+        network = (widths, *net.export(norm))
+        Yh = net.predict(Xhn) * norm[2]
+        net.close()
+        prior = float(torch.linalg.norm(Yh - Th) / torch.linalg.norm(Th))
+        del Yh
+        if vi_ == 0 and save_net:
+            np.savez(save_net, widths=np.array(widths), norm_mu=norm[0], norm_sigma=norm[1], t_scale=norm[2],
+                     **{f"W{i}": w.astype(np.float32) for i, w in enumerate(network[1])},
+                     **{f"shift{i}": b for i, b in enumerate(network[3])})
+        res = {"widths": "-".join(map(str, widths)), "noise_sigma": sigma,
+               "train_loss_first_last": [hist[0], hist[-1]], "validation_loss_best": min(vh),
+               "validation_best_epoch": int(np.argmin(vh)), "network_relative_error_exact_inputs": prior,
+               "dnnmg_bf16": run_loop(network, "bf16")}
+        if vi_ == 0:
+            res["dnnmg_fp64"] = run_loop(network, "fp64")
+        for k in ("dnnmg_bf16", "dnnmg_fp64"):
+            if k in res and res[k]["failed"] is None:
+                res[k]["E_v_over_plain_coarse"] = res[k]["E_v"] / plain["E_v"]
+        out_var[name] = res
+        log(f"{name}: prior {prior:.4f}, BF16 E_v {res['dnnmg_bf16']['E_v']}, "
+            f"failed {res['dnnmg_bf16']['failed']}")
     return {"workload": f"channel nz={nz} nested ({levels} refinement of nz={nz >> levels}) with a seeded "
                         f"cylinder: {geos[0]['patches']} coarse hex, targets from level L+2 "
-                        f"({64 * geos[0]['patches']} hex) injected onto L+1; {scheme} dt={dt}, {steps} steps "
-                        f"per geometry from rest; BF16 network {lay}",
+                        f"({64 * geos[0]['patches']} hex, Dirichlet values the prolongated coarse data) "
+                        f"injected onto L+1; backward Euler dt={dt}, {steps} steps per geometry from rest",
             "geometries": geos, "samples": n, "train_samples": n_train, "validation_samples": n_val,
             "batch": batch, "epochs": epochs, "optimizer": "AdamW lr 1e-3, weight decay 1e-5",
-            "train_loss_first_last": [hist[0], hist[-1]], "validation_loss_best": min(vh),
-            "validation_best_epoch": int(np.argmin(vh)),
-            "seconds": {"data": round(t_data, 1), "train": round(t_train, 1), "held_out": round(t_eval, 1),
+            "method": variants[0][0],
+            "seconds": {"data": round(t_data, 1), "train": round(t_train, 1),
                         "total": round(time.perf_counter() - t0, 1)},
-            "held_out": out_eval}
+            "held_out": {"seed": seed, "D": round(float(D), 5), "Re": round(float(re[n_geometries]), 2),
+                         "steps": eval_steps, "plain_coarse": plain, "variants": out_var}}
 
 
 def main():

@@ -573,6 +573,17 @@ dnnmg_status dnnmg_standardize(const void* A_dev, int32_t dtype, int64_t rows, i
 dnnmg_status dnnmg_gather_rows(const void* src_dev, int64_t n_src, int64_t row_bytes, const int64_t* idx_dev,
                                int64_t n, void* dst_dev, void* cuda_stream);
 
+/* dnnmg_add_noise: A[i][j] += sigma z_ij for c0 <= j < c1 (in place), z_ij
+ * standard normal from a counter-based generator: SplitMix64 of (seed, i,
+ * j), two uniforms, the Box-Muller transform; the same seed gives the same
+ * bits.  Training-time input noise (the paper has no counterpart): inputs
+ * perturbed while targets stay the reference's teach the network not to
+ * amplify errors that the time loop feeds back into its inputs.  Computed
+ * in float (double for double data), rounded once to the dtype.  EINVAL
+ * for c0 > c1, c1 > ld or sigma < 0. */
+dnnmg_status dnnmg_add_noise(void* A_dev, int32_t dtype, int64_t rows, int32_t c0, int32_t c1, int64_t ld,
+                             double sigma, uint64_t seed, void* cuda_stream);
+
 /* Measured peak of the SIMT fused multiply-add pipe on the current device
  * (the paper has no counterpart: a roofline denominator for the kernels
  * bound by FP32 or FP64 arithmetic).  Every thread of blocks_per_sm x (SM

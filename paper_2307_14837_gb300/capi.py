@@ -450,6 +450,8 @@ _SIGS.update({
     "dnnmg_standardize": ([_VP, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64, _VP, _VP, _VP, _VP],
                           ctypes.c_int),
     "dnnmg_gather_rows": ([_VP, ctypes.c_int64, ctypes.c_int64, _VP, ctypes.c_int64, _VP, _VP], ctypes.c_int),
+    "dnnmg_add_noise": ([_VP, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
+                         ctypes.c_double, ctypes.c_uint64, _VP], ctypes.c_int),
     "dnnmg_adamw": ([ctypes.c_int64, _VP, _VP, _VP, _VP, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                      ctypes.c_double, ctypes.c_double, ctypes.c_int32, _VP], ctypes.c_int),
 })
@@ -551,6 +553,13 @@ def dnnmg_gather_rows(src, idx, dst, stream=None):
     assert dst.stride(0) * dst.element_size() == row_bytes and dst.shape[0] >= idx.shape[0]
     _check(None, load().dnnmg_gather_rows(_ptr(src), int(src.shape[0]), int(row_bytes), _ptr(idx), int(idx.shape[0]),
                                           _ptr(dst), getattr(stream, "cuda_stream", stream)))
+
+
+def dnnmg_add_noise(A, c0, c1, sigma, seed, stream=None):
+    """A[:, c0:c1] += sigma * (seeded standard normal), in place."""
+    _check(None, load().dnnmg_add_noise(_ptr(A), _dtype_code(A), int(A.shape[0]), int(c0), int(c1),
+                                        int(A.stride(0)), float(sigma), int(seed) & ((1 << 64) - 1),
+                                        getattr(stream, "cuda_stream", stream)))
 
 
 def dnnmg_adamw(w, g, m, v, lr, beta1, beta2, eps, weight_decay, step, stream=None):

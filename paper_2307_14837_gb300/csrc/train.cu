@@ -237,6 +237,36 @@ __global__ void __launch_bounds__(256) gather_rows_kernel(int64_t n, int64_t n_s
     dst[e] = (r >= 0 && r < n_src) ? src[r * q + w] : W{};
 }
 
+// SplitMix64 finaliser (Steele, Lea and Flood, "Fast splittable
+// pseudorandom number generators", 2014) as a counter-based generator
+__device__ __forceinline__ uint64_t splitmix64(uint64_t z) {
+    z += 0x9e3779b97f4a7c15ull;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+// A[i][j] += sigma z_ij for c0 <= j < c1, z_ij standard normal by the
+// Box-Muller transform of two uniforms drawn from (seed, i, j)
+template <typename T>
+__global__ void __launch_bounds__(256) add_noise_kernel(int64_t rows, int c0, int w, int64_t ld, float sigma,
+                                                        uint64_t seed, T* A) {
+    const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (e >= rows * w) return;
+    const int64_t i = e / w;
+    const int j = c0 + int(e - i * w);
+    const uint64_t key = splitmix64(seed ^ splitmix64(uint64_t(i) * 0x100000001b3ull + uint64_t(j)));
+    const uint64_t k2 = splitmix64(key);
+    const float u1 = (float((key >> 40) + 1)) * (1.0f / 16777217.0f);   // (0, 1]
+    const float u2 = float(k2 >> 40) * (1.0f / 16777216.0f);            // [0, 1)
+    const float z = sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+    T* a = A + i * ld + j;
+    if constexpr (std::is_same<T, double>::value)
+        *a = *a + double(sigma) * double(z);
+    else
+        *a = fromf<T>(tof(*a) + sigma * z);
+}
+
 template <typename T>
 dnnmg_status column_stats_t(const T* A, int64_t rows, int cols, int64_t ld, double* mean, double* sd,
                             cudaStream_t s) {
@@ -549,6 +579,29 @@ dnnmg_status dnnmg_gather_rows(const void* src_dev, int64_t n_src, int64_t row_b
     } else {
         gather_rows_kernel<uint8_t><<<nb(n * row_bytes, 256), 256, 0, s>>>(
             n, n_src, row_bytes, idx_dev, static_cast<const uint8_t*>(src_dev), static_cast<uint8_t*>(dst_dev));
+    }
+    return cudaGetLastError() == cudaSuccess ? DNNMG_OK : DNNMG_ECUDA;
+}
+
+dnnmg_status dnnmg_add_noise(void* A_dev, int32_t dtype, int64_t rows, int32_t c0, int32_t c1, int64_t ld,
+                             double sigma, uint64_t seed, void* cuda_stream) {
+    if (!A_dev || rows < 0 || c0 < 0 || c1 < c0 || c1 > ld || !(sigma >= 0.0)) return DNNMG_EINVAL;
+    if (rows == 0 || c1 == c0 || sigma == 0.0) return DNNMG_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    const int w = c1 - c0;
+    const unsigned g = nb(rows * w, 256);
+    switch (dtype) {
+        case DNNMG_FP64:
+            add_noise_kernel<<<g, 256, 0, s>>>(rows, c0, w, ld, float(sigma), seed, static_cast<double*>(A_dev));
+            break;
+        case DNNMG_FP32:
+            add_noise_kernel<<<g, 256, 0, s>>>(rows, c0, w, ld, float(sigma), seed, static_cast<float*>(A_dev));
+            break;
+        case DNNMG_BF16:
+            add_noise_kernel<<<g, 256, 0, s>>>(rows, c0, w, ld, float(sigma), seed,
+                                               static_cast<__nv_bfloat16*>(A_dev));
+            break;
+        default: return DNNMG_EINVAL;
     }
     return cudaGetLastError() == cudaSuccess ? DNNMG_OK : DNNMG_ECUDA;
 }

@@ -148,8 +148,18 @@ class _MSE(torch.autograd.Function):
         return dY * g, None
 
 
-def _rest_state(p, mesh, fine):
-    """Field at rest with the Dirichlet data of the fine (or coarse) nodes."""
+def _rest_state(p, mesh, fine, prolongated_from=None):
+    """Field at rest with the Dirichlet data of the fine (or coarse) nodes;
+    with ``prolongated_from`` (a coarse field), the fine Dirichlet values
+    are its prolongation instead of the boundary data."""
+    if fine and prolongated_from is not None:
+        xf = torch.empty((p.n_fine, 4), dtype=torch.float64, device=p.device)
+        capi.dnnmg_prolongate(p.ctx, prolongated_from, xf)
+        kind = p.mesh_data(capi.FINE_KIND)
+        mask = torch.as_tensor((kind == 1) | (kind == 2), device=p.device)
+        x = torch.zeros_like(xf)
+        x[mask, 0:3] = xf[mask, 0:3]
+        return x
     if fine:
         kind, xyz = p.mesh_data(capi.FINE_KIND), p.mesh_data(capi.FINE_XYZ)
     else:
@@ -161,7 +171,7 @@ def _rest_state(p, mesh, fine):
 
 
 def make_samples(mesh, nu, dt, theta, n_steps, x_dtype=torch.bfloat16, solver=None, features=12, ref_levels=1,
-                 ref_solver=None, keep_steps=True):
+                 ref_solver=None, keep_steps=True, fine_boundary="exact"):
     """(X, T) training pairs from a fine simulation started at rest with the
     mesh's Dirichlet data.  X [n_steps * N_c][256] in x_dtype (216 +
     features used columns), T [n_steps * N_c][81] fp32, both written by
@@ -174,7 +184,12 @@ def make_samples(mesh, nu, dt, theta, n_steps, x_dtype=torch.bfloat16, solver=No
     Sec. 6.4): v_n is the solve on level L+2 (the fine level of a J = 2
     context, its own right-hand side from its previous state), injected
     onto level L+1 (its first n_fine(L+1) nodes), and F_n =
-    Rhs_{L+1}(injected v_{n-1})."""
+    Rhs_{L+1}(injected v_{n-1}).
+
+    fine_boundary = "prolongated": the reference's Dirichlet values are the
+    prolongation of the coarse Dirichlet data (the values the DNN-MG loop
+    has there, where its correction is zero) instead of the boundary data
+    evaluated at the fine nodes."""
     if ref_levels not in (1, 2):
         raise ValueError("ref_levels must be 1 or 2")
     prec = "bf16" if x_dtype == torch.bfloat16 else "fp32"
@@ -184,7 +199,8 @@ def make_samples(mesh, nu, dt, theta, n_steps, x_dtype=torch.bfloat16, solver=No
     dev = f64.device
     nv, nf, nc = f64.n_coarse, f64.n_fine, f64.n_patches
     xc = _rest_state(f64, mesh, fine=False)
-    vr = _rest_state(ref, mesh, fine=True)                # reference state on its own level
+    vr = _rest_state(ref, mesh, fine=True,                # reference state on its own level
+                     prolongated_from=xc if fine_boundary == "prolongated" else None)
     F = torch.empty((nf, 4), dtype=torch.float64, device=dev)
     Fr = F if ref_levels == 1 else torch.empty((ref.n_fine, 4), dtype=torch.float64, device=dev)
     bL = torch.empty((nv, 4), dtype=torch.float64, device=dev)
@@ -323,13 +339,16 @@ def normalize(X, norm, T=None):
 
 
 def train(net, X, T, epochs=100, batch=4096, lr=1e-3, weight_decay=1e-5, seed=0, log=None, val=None,
-          val_hist=None):
+          val_hist=None, noise=None):
     """AdamW on the l2 loss; batches are multiples of 64 (the tail of an epoch
     is dropped), gathered from X and T by libdnnmg (dnnmg_gather_rows) in a
     seeded random order.  Returns the loss history (one value per epoch,
     mean over its batches).  With ``val`` = (Xv, Tv) the validation loss is
     taken after every epoch (appended to ``val_hist`` when given) and the
-    parameters of the epoch with the lowest one are kept (Sec. 6.4)."""
+    parameters of the epoch with the lowest one are kept (Sec. 6.4).  With
+    ``noise`` = (c0, c1, sigma), every batch's input columns c0..c1-1 get
+    seeded Gaussian noise of deviation sigma (dnnmg_add_noise) while its
+    targets stay the reference's."""
     opt = AdamW(net.params(), lr=lr, weight_decay=weight_decay)
     n = X.shape[0]
     batch = min(batch, n) // 64 * 64
@@ -346,6 +365,9 @@ def train(net, X, T, epochs=100, batch=4096, lr=1e-3, weight_decay=1e-5, seed=0,
             idx = perm[i:i + batch]
             capi.dnnmg_gather_rows(X, idx, Xb, stream=st)
             capi.dnnmg_gather_rows(T, idx, Tb, stream=st)
+            if noise is not None:
+                capi.dnnmg_add_noise(Xb, noise[0], noise[1], noise[2], seed=(seed << 32) + ep * 65536 + i // batch,
+                                     stream=st)
             Y = net(Xb)
             loss = mse_loss(Y, Tb)
             opt.zero_grad()

@@ -209,3 +209,44 @@ def test_refined_reference_samples_match_oracle():
         t_ref = (v2[:nf] - transfer.prolongate(h1, xc))[:, 0:3][h1.patch_map].reshape(nc, 81)
         t_got = Tg[n * nc:(n + 1) * nc].double().cpu().numpy()
         assert np.abs(t_got - t_ref).max() <= 1e-6 * np.abs(t_ref).max()
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
+def test_add_noise_statistics_and_determinism(dtype):
+    rows, ld, c0, c1, sigma = 20000, 256, 108, 216, 0.25
+    A = torch.zeros((rows, ld), dtype=dtype, device="cuda")
+    capi.dnnmg_add_noise(A, c0, c1, sigma, seed=7)
+    z = A[:, c0:c1].double()
+    assert torch.all(A[:, :c0] == 0) and torch.all(A[:, c1:] == 0)
+    n = z.numel()
+    assert abs(float(z.mean())) < 5 * sigma / n ** 0.5
+    assert abs(float(z.std()) / sigma - 1.0) < 0.01
+    # a standard normal's fourth moment is 3 (the Box-Muller output, not a uniform)
+    assert abs(float(((z / sigma) ** 4).mean()) - 3.0) < 0.05
+    B = torch.zeros_like(A)
+    capi.dnnmg_add_noise(B, c0, c1, sigma, seed=7)
+    assert torch.equal(A, B)
+    capi.dnnmg_add_noise(B, c0, c1, sigma, seed=8)
+    assert not torch.equal(A, B)
+    # the draws of different entries are uncorrelated
+    cc = float((z[:, 0] * z[:, 1]).mean() / sigma ** 2)
+    assert abs(cc) < 5 / rows ** 0.5
+
+
+def test_prolongated_fine_boundary_gives_zero_targets_on_dirichlet_nodes():
+    # with the reference's Dirichlet values taken from the prolongated
+    # coarse data, the targets vanish on the fine Dirichlet nodes (where the
+    # DNN-MG correction is zero), and the interior still carries a correction
+    from paper_2307_14837_gb300 import train as T
+    m = I.cavity_mesh(4, levels=1, jitter=0.1, seed=6)
+    X, Tg, st = T.make_samples(m, NU, DT, 1.0, 2, ref_levels=2, fine_boundary="prolongated")
+    p = PatchPath(m, NU, DT, 1.0, "fp64")
+    kind = p.mesh_data(capi.FINE_KIND)
+    pm = p.mesh_data(capi.PATCH_MAP)
+    p.close()
+    dir_pn = ((kind == 1) | (kind == 2))[pm]                 # [nc][27] Dirichlet patch nodes
+    t = Tg.reshape(2, -1, 27, 3).double().cpu().numpy()
+    scale = np.abs(t).max()
+    assert scale > 0
+    assert np.abs(t[:, dir_pn]).max() <= 1e-6 * scale
+    assert np.abs(t[:, ~dir_pn]).max() > 1e-3 * scale
