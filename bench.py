@@ -829,17 +829,11 @@ class OracleSample:
 
 
 TRAIN_NZ, TRAIN_LEVELS = 4, 1
-BIG = (228, 1024, 1024, 1024, 1024, 81)
-# (name, widths, deviation of the training noise on the residual columns
-# Q(r) in standardised units); the first noisy one is the method, the others
-# are reported beside it
-TRAIN_VARIANTS = (("w1024x4_noise0.1", BIG, 0.1), ("w1024x4", BIG, 0.0), ("w1024x4_noise0.3", BIG, 0.3),
-                  ("w512x3_noise0.1", (228, 512, 512, 512, 81), 0.1))
 
 
 def train_at_scale(n_geometries=8, steps=128, eval_steps=64, epochs=150, batch=65536, nz=TRAIN_NZ,
-                   levels=TRAIN_LEVELS, dt=0.01, theta=1.0, variants=TRAIN_VARIANTS, val_fraction=0.05, seed0=100,
-                   ref_gmres_rtol=None, save_net=None):
+                   levels=TRAIN_LEVELS, dt=0.01, theta=1.0, widths=(228, 1024, 1024, 1024, 1024, 81),
+                   horizon=4, val_fraction=0.05, seed0=100, ref_gmres_rtol=None, save_net=None):
     """The learned part at scale (Sec. 6.4): training data from the
     project's own solver on n_geometries seeded channel obstacles (cylinder
     diameter and centre from the seed) at Re ~ U[100, 300] (nu = D / Re,
@@ -848,16 +842,18 @@ def train_at_scale(n_geometries=8, steps=128, eval_steps=64, epochs=150, batch=6
     reference two refinements up (level L+2, Newton-GMRES-multigrid over
     L+2, L+1, L and L-1, its Dirichlet values the prolongated coarse data)
     injected onto level L+1, backward Euler dt = 0.01 from rest with the
-    full inflow, `steps` steps per geometry.  Then, per variant (widths,
-    training noise on the residual columns), BF16 training (AdamW lr 1e-3,
-    weight decay 1e-5, batch 65,536, `epochs` epochs), the parameters of
-    the epoch with the lowest loss on a held-back random val_fraction of
-    the samples kept.  On an unseen geometry (seed seed0 + n_geometries,
-    its own Re draw): each network's relative error on that geometry's
-    samples (no feedback), and e_v and E_v of the plain coarse scheme and of
-    DNN-MG (BF16; FP64 too for the first variant) against the level-(L+2)
-    reference over eval_steps steps; a run whose solve fails reports the
-    step.  save_net: a path for the first variant's network (.npz)."""
+    full inflow, `steps` steps per geometry.  BF16 training (AdamW lr 1e-3,
+    weight decay 1e-5, batch 65,536, `epochs` epochs; the parameters of the
+    epoch with the lowest loss on a held-back random val_fraction of the
+    samples kept) in two rounds: network A on the reference pairs; then
+    DNN-MG with A, restarted from the reference every `horizon` steps on
+    every training geometry, gives pairs from the loop's own states
+    (train.rollout_samples), and network B is trained on both sets.  On an
+    unseen geometry (seed seed0 + n_geometries, its own Re draw): each
+    network's relative error on that geometry's reference pairs, and e_v
+    and E_v of the plain coarse scheme and of DNN-MG (BF16; FP64 too for B)
+    against the level-(L+2) reference over eval_steps steps; a run whose
+    solve fails reports the step.  save_net: a path for network B (.npz)."""
     import numpy as np
     import torch
 
@@ -873,48 +869,48 @@ def train_at_scale(n_geometries=8, steps=128, eval_steps=64, epochs=150, batch=6
     re = 100.0 + 200.0 * I.splitmix_uniform(9000 + seed0, n_geometries + 1)
     log = lambda msg: print(f"[train-scale] {msg}, {time.perf_counter() - t0:.1f} s",  # noqa: E731
                             file=sys.stderr, flush=True)
-    geos = []
+    geos, runs = [], []
     Xs, Ts = [], []
     for k in range(n_geometries):
         seed = seed0 + k
         m = I.channel_mesh(nz, seed=seed, levels=levels)
         D = I.channel_geometry(seed)[0]
         nu = D / re[k]
-        X, Tg, _ = T.make_samples(m, nu, dt, theta, steps, solver=coarse_solver(), ref_levels=2,
-                                  ref_solver=ref_solver(), keep_steps=False, fine_boundary="prolongated")
+        X, Tg, st = T.make_samples(m, nu, dt, theta, steps, solver=coarse_solver(), ref_levels=2,
+                                   ref_solver=ref_solver(), fine_boundary="prolongated")
         Xs.append(X)
         Ts.append(Tg)
+        runs.append((m, nu, st))
         geos.append({"seed": seed, "D": round(float(D), 5), "Re": round(float(re[k]), 2), "nu": float(nu),
                      "patches": int(m["cells"].shape[0])})
         log(f"geometry {k}: Re {re[k]:.1f}, {X.shape[0]} samples")
     X, Tg = torch.cat(Xs), torch.cat(Ts)
+    n_ref = int(X.shape[0])
     del Xs, Ts
     torch.cuda.synchronize()
     t_data = time.perf_counter() - t0
-    # validation rows: a seeded random subset
-    n = X.shape[0]
-    perm = torch.randperm(n, generator=torch.Generator(device="cpu").manual_seed(seed0)).to(X.device)
-    n_val = int(val_fraction * n)
-    vi, ti = perm[:n_val], perm[n_val:]
-    Xv = torch.empty((n_val, X.shape[1]), dtype=X.dtype, device=X.device)
-    Tv = torch.empty((n_val, 81), dtype=Tg.dtype, device=X.device)
-    Xt = torch.empty((n - n_val, X.shape[1]), dtype=X.dtype, device=X.device)
-    Tt = torch.empty((n - n_val, 81), dtype=Tg.dtype, device=X.device)
-    for src, idx, dst in ((X, vi, Xv), (Tg, vi, Tv), (X, ti, Xt), (Tg, ti, Tt)):
-        capi.dnnmg_gather_rows(src, idx, dst, stream=torch.cuda.current_stream())
-    del X, Tg
-    norm = T.fit_normalization(Xt, Tt)
-    Xn, Tn = T.normalize(Xt, norm, Tt)
-    Xvn, Tvn = T.normalize(Xv, norm, Tv)
-    n_train = Xn.shape[0]
-    del Xt, Tt, Xv, Tv
+    norm = T.fit_normalization(X, Tg)
 
-    # the unseen geometry: its reference trajectory and samples
+    def split(X, Tg, seed):
+        """standardised training and validation rows (a seeded random subset)"""
+        n = X.shape[0]
+        perm = torch.randperm(n, generator=torch.Generator(device="cpu").manual_seed(seed)).to(X.device)
+        n_val = int(val_fraction * n)
+        out = []
+        for idx in (perm[n_val:], perm[:n_val]):
+            Xa = torch.empty((idx.shape[0], X.shape[1]), dtype=X.dtype, device=X.device)
+            Ta = torch.empty((idx.shape[0], 81), dtype=Tg.dtype, device=X.device)
+            capi.dnnmg_gather_rows(X, idx, Xa, stream=torch.cuda.current_stream())
+            capi.dnnmg_gather_rows(Tg, idx, Ta, stream=torch.cuda.current_stream())
+            out.append(T.normalize(Xa, norm, Ta))
+        return out
+
+    # the unseen geometry: its reference trajectory and pairs
     seed = seed0 + n_geometries
-    m = I.channel_mesh(nz, seed=seed, levels=levels)
-    D = I.channel_geometry(seed)[0]
-    nu = D / re[n_geometries]
-    Xh, Th, held = T.make_samples(m, nu, dt, theta, eval_steps, solver=coarse_solver(), ref_levels=2,
+    mh = I.channel_mesh(nz, seed=seed, levels=levels)
+    Dh = I.channel_geometry(seed)[0]
+    nuh = Dh / re[n_geometries]
+    Xh, Th, held = T.make_samples(mh, nuh, dt, theta, eval_steps, solver=coarse_solver(), ref_levels=2,
                                   ref_solver=ref_solver(), fine_boundary="prolongated")
     Xhn = T.normalize(Xh, norm)
     ref = [s_["v_fine"][:, 0:3].cpu().numpy() for s_ in held]
@@ -923,7 +919,7 @@ def train_at_scale(n_geometries=8, steps=128, eval_steps=64, epochs=150, batch=6
     def run_loop(netw, prec):
         vel = []
         try:
-            T.trajectory_errors(m, nu, dt, theta, held, network=netw, solver=coarse_solver(), precision=prec,
+            T.trajectory_errors(mh, nuh, dt, theta, held, network=netw, solver=coarse_solver(), precision=prec,
                                 velocities=vel)
             failed = None
         except capi.DnnmgError as e:
@@ -934,48 +930,67 @@ def train_at_scale(n_geometries=8, steps=128, eval_steps=64, epochs=150, batch=6
 
     plain = run_loop(None, "fp64")
     log(f"plain coarse E_v {plain['E_v']}")
-    out_var = {}
     t_train = 0.0
-    for vi_, (name, widths, sigma) in enumerate(variants):
+
+    def fit(parts, name):
+        nonlocal t_train
+        (Xn, Tn), (Xvn, Tvn) = parts
         net = T.PatchNet(widths, precision="bf16", max_batch=batch, seed=0)
         vh = []
         t1 = time.perf_counter()
         hist = T.train(net, Xn, Tn, epochs=epochs, batch=batch, lr=1e-3, weight_decay=1e-5, val=(Xvn, Tvn),
-                       val_hist=vh, noise=(108, 216, sigma) if sigma > 0 else None)
+                       val_hist=vh)
         torch.cuda.synchronize()
         t_train += time.perf_counter() - t1
         network = (widths, *net.export(norm))
         Yh = net.predict(Xhn) * norm[2]
         net.close()
         prior = float(torch.linalg.norm(Yh - Th) / torch.linalg.norm(Th))
-        del Yh
-        if vi_ == 0 and save_net:
-            np.savez(save_net, widths=np.array(widths), norm_mu=norm[0], norm_sigma=norm[1], t_scale=norm[2],
-                     **{f"W{i}": w.astype(np.float32) for i, w in enumerate(network[1])},
-                     **{f"shift{i}": b for i, b in enumerate(network[3])})
-        res = {"widths": "-".join(map(str, widths)), "noise_sigma": sigma,
+        res = {"train_samples": int(Xn.shape[0]), "validation_samples": int(Xvn.shape[0]),
                "train_loss_first_last": [hist[0], hist[-1]], "validation_loss_best": min(vh),
-               "validation_best_epoch": int(np.argmin(vh)), "network_relative_error_exact_inputs": prior,
-               "dnnmg_bf16": run_loop(network, "bf16")}
-        if vi_ == 0:
-            res["dnnmg_fp64"] = run_loop(network, "fp64")
+               "validation_best_epoch": int(np.argmin(vh)), "network_relative_error_exact_inputs": prior}
+        log(f"{name}: trained, prior {prior:.4f}")
+        return network, res
+
+    netA, resA = fit(split(X, Tg, seed0), "A")
+    resA["dnnmg_bf16"] = run_loop(netA, "bf16")
+    log(f"A: BF16 E_v {resA['dnnmg_bf16']['E_v']}, failed {resA['dnnmg_bf16']['failed']}")
+    # round 2: the loop's own states with network A on every training geometry
+    Xr, Tr = [], []
+    for m, nu, st in runs:
+        a, b = T.rollout_samples(m, nu, dt, theta, st, netA, horizon=horizon, solver=coarse_solver())
+        Xr.append(a)
+        Tr.append(b)
+    del runs
+    X2, T2 = torch.cat([X] + Xr), torch.cat([Tg] + Tr)
+    n_roll = X2.shape[0] - X.shape[0]
+    del Xr, Tr, X, Tg
+    log(f"rollouts: {n_roll} samples")
+    netB, resB = fit(split(X2, T2, seed0 + 1), "B")
+    del X2, T2
+    resB["dnnmg_bf16"] = run_loop(netB, "bf16")
+    resB["dnnmg_fp64"] = run_loop(netB, "fp64")
+    for r in (resA, resB):
         for k in ("dnnmg_bf16", "dnnmg_fp64"):
-            if k in res and res[k]["failed"] is None:
-                res[k]["E_v_over_plain_coarse"] = res[k]["E_v"] / plain["E_v"]
-        out_var[name] = res
-        log(f"{name}: prior {prior:.4f}, BF16 E_v {res['dnnmg_bf16']['E_v']}, "
-            f"failed {res['dnnmg_bf16']['failed']}")
+            if k in r and r[k]["failed"] is None:
+                r[k]["E_v_over_plain_coarse"] = r[k]["E_v"] / plain["E_v"]
+    log(f"B: BF16 E_v {resB['dnnmg_bf16']['E_v']}, failed {resB['dnnmg_bf16']['failed']}")
+    if save_net:
+        np.savez(save_net, widths=np.array(widths), norm_mu=norm[0], norm_sigma=norm[1], t_scale=norm[2],
+                 **{f"W{i}": w.astype(np.float32) for i, w in enumerate(netB[1])},
+                 **{f"shift{i}": b for i, b in enumerate(netB[3])})
     return {"workload": f"channel nz={nz} nested ({levels} refinement of nz={nz >> levels}) with a seeded "
                         f"cylinder: {geos[0]['patches']} coarse hex, targets from level L+2 "
                         f"({64 * geos[0]['patches']} hex, Dirichlet values the prolongated coarse data) "
-                        f"injected onto L+1; backward Euler dt={dt}, {steps} steps per geometry from rest",
-            "geometries": geos, "samples": n, "train_samples": n_train, "validation_samples": n_val,
-            "batch": batch, "epochs": epochs, "optimizer": "AdamW lr 1e-3, weight decay 1e-5",
-            "method": variants[0][0],
+                        f"injected onto L+1; backward Euler dt={dt}, {steps} steps per geometry from rest; "
+                        f"BF16 network {'-'.join(map(str, widths))}",
+            "geometries": geos, "reference_samples": n_ref,
+            "rollout_samples": n_roll, "rollout_horizon": horizon, "batch": batch, "epochs": epochs,
+            "optimizer": "AdamW lr 1e-3, weight decay 1e-5",
             "seconds": {"data": round(t_data, 1), "train": round(t_train, 1),
                         "total": round(time.perf_counter() - t0, 1)},
-            "held_out": {"seed": seed, "D": round(float(D), 5), "Re": round(float(re[n_geometries]), 2),
-                         "steps": eval_steps, "plain_coarse": plain, "variants": out_var}}
+            "held_out": {"seed": seed, "D": round(float(Dh), 5), "Re": round(float(re[n_geometries]), 2),
+                         "steps": eval_steps, "plain_coarse": plain, "network_A": resA, "network_B": resB}}
 
 
 def main():

@@ -228,6 +228,49 @@ def make_samples(mesh, nu, dt, theta, n_steps, x_dtype=torch.bfloat16, solver=No
     return X, T, steps
 
 
+def rollout_samples(mesh, nu, dt, theta, steps, network, horizon=8, solver=None, precision="bf16", features=12):
+    """Training pairs from the states the DNN-MG loop itself visits (the
+    dataset aggregation of Ross, Gordon and Bagnell, 2011): from the
+    reference state of every `horizon`-th step of ``steps`` (from
+    make_samples) the loop runs `horizon` steps with ``network``; each
+    step's input rows are the loop's own (its coarse state and the residual
+    of its right-hand side), its targets the correction that takes the
+    loop's prolongated coarse state to the reference velocity,
+    Q(v_ref,n - P x_n).  Returns (X, T) as make_samples does."""
+    p = PatchPath(mesh, nu, dt, theta, precision, features=features)    # the loop and its input rows
+    f64 = PatchPath(mesh, nu, dt, theta, "fp64")                          # reference rhs and targets
+    widths, Ws, ss, ts = network
+    p.set_network(widths, Ws, ss, ts)
+    dev, nv, nc = p.device, p.n_coarse, p.n_patches
+    Xs, Ts = [], []
+    bL = torch.empty((nv, 4), dtype=torch.float64, device=dev)
+    try:
+        for s0 in range(0, len(steps) - 1, horizon):
+            x = steps[s0]["x_coarse"].clone()
+            Fd = torch.empty_like(steps[s0]["v_fine"])
+            capi.dnnmg_level_rhs(f64.ctx, capi.LEVEL_FINE, steps[s0]["v_fine"], Fd)   # Rhs_{L+1}(v_ref)
+            capi.dnnmg_restrict(f64.ctx, Fd, bL)
+            bf = Fd.to(p.dtype).contiguous()
+            bc = bL.clone()
+            for n in range(s0 + 1, min(s0 + 1 + horizon, len(steps))):
+                Fn = bf.clone()                                  # the rhs this step solves with
+                try:
+                    capi.dnnmg_time_step(p.ctx, 1, x, bc, bf, solver)
+                except capi.DnnmgError:
+                    break                                        # a diverged rollout ends its samples
+                xl = x.to(p.dtype)
+                X = torch.empty((nc, p.sizes["n_in_padded"]), dtype=p.x_dtype, device=dev)
+                capi.dnnmg_local_restrict(p.ctx, xl, p.residual(xl, Fn), X)
+                T = torch.empty((nc, 81), dtype=torch.float32, device=dev)
+                capi.dnnmg_patch_targets(f64.ctx, x, steps[n]["v_fine"], T)
+                Xs.append(X)
+                Ts.append(T)
+    finally:
+        p.close()
+        f64.close()
+    return torch.cat(Xs), torch.cat(Ts)
+
+
 def velocity_errors(vel, ref):
     """The error measures of Sec. 6.5-6.6 of velocity snapshots ``vel``
     against ``ref`` (lists of [n][3] arrays, one per time step):
