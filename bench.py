@@ -831,9 +831,9 @@ class OracleSample:
 TRAIN_NZ, TRAIN_LEVELS = 4, 1
 
 
-def train_at_scale(n_geometries=8, steps=128, eval_steps=64, epochs=150, batch=65536, nz=TRAIN_NZ,
+def train_at_scale(n_geometries=8, steps=96, eval_steps=64, epochs=150, batch=65536, nz=TRAIN_NZ,
                    levels=TRAIN_LEVELS, dt=0.01, theta=1.0, widths=(228, 1024, 1024, 1024, 1024, 81),
-                   horizon=4, val_fraction=0.05, seed0=100, ref_gmres_rtol=None, save_net=None):
+                   horizons=(4, 8, 16), val_fraction=0.05, seed0=100, ref_gmres_rtol=None, save_net=None):
     """The learned part at scale (Sec. 6.4): training data from the
     project's own solver on n_geometries seeded channel obstacles (cylinder
     diameter and centre from the seed) at Re ~ U[100, 300] (nu = D / Re,
@@ -845,15 +845,16 @@ def train_at_scale(n_geometries=8, steps=128, eval_steps=64, epochs=150, batch=6
     full inflow, `steps` steps per geometry.  BF16 training (AdamW lr 1e-3,
     weight decay 1e-5, batch 65,536, `epochs` epochs; the parameters of the
     epoch with the lowest loss on a held-back random val_fraction of the
-    samples kept) in two rounds: network A on the reference pairs; then
-    DNN-MG with A, restarted from the reference every `horizon` steps on
-    every training geometry, gives pairs from the loop's own states
-    (train.rollout_samples), and network B is trained on both sets.  On an
-    unseen geometry (seed seed0 + n_geometries, its own Re draw): each
-    network's relative error on that geometry's reference pairs, and e_v
-    and E_v of the plain coarse scheme and of DNN-MG (BF16; FP64 too for B)
-    against the level-(L+2) reference over eval_steps steps; a run whose
-    solve fails reports the step.  save_net: a path for network B (.npz)."""
+    samples kept) in rounds: round 0 on the reference pairs; after round r,
+    DNN-MG with its network, restarted from the reference every
+    horizons[r] steps on every training geometry, adds pairs from the
+    loop's own states (train.rollout_samples) to the set, and round r + 1
+    trains a fresh network on the whole set.  On an unseen geometry (seed
+    seed0 + n_geometries, its own Re draw): each round's network's relative
+    error on that geometry's reference pairs, and e_v and E_v of the plain
+    coarse scheme and of DNN-MG (BF16; FP64 too for the last round) against
+    the level-(L+2) reference over eval_steps steps; a run whose solve
+    fails reports the step.  save_net: a path for the last network (.npz)."""
     import numpy as np
     import torch
 
@@ -952,45 +953,50 @@ def train_at_scale(n_geometries=8, steps=128, eval_steps=64, epochs=150, batch=6
         log(f"{name}: trained, prior {prior:.4f}")
         return network, res
 
-    netA, resA = fit(split(X, Tg, seed0), "A")
-    resA["dnnmg_bf16"] = run_loop(netA, "bf16")
-    log(f"A: BF16 E_v {resA['dnnmg_bf16']['E_v']}, failed {resA['dnnmg_bf16']['failed']}")
-    # round 2: the loop's own states with network A on every training geometry
-    Xr, Tr = [], []
-    for m, nu, st in runs:
-        a, b = T.rollout_samples(m, nu, dt, theta, st, netA, horizon=horizon, solver=coarse_solver())
-        Xr.append(a)
-        Tr.append(b)
-    del runs
-    X2, T2 = torch.cat([X] + Xr), torch.cat([Tg] + Tr)
-    n_roll = X2.shape[0] - X.shape[0]
-    del Xr, Tr, X, Tg
-    log(f"rollouts: {n_roll} samples")
-    netB, resB = fit(split(X2, T2, seed0 + 1), "B")
-    del X2, T2
-    resB["dnnmg_bf16"] = run_loop(netB, "bf16")
-    resB["dnnmg_fp64"] = run_loop(netB, "fp64")
-    for r in (resA, resB):
+    rounds = []
+    Xall, Tall = [X], [Tg]
+    del X, Tg
+    n_roll = 0
+    for r in range(len(horizons) + 1):
+        Xc, Tc = torch.cat(Xall), torch.cat(Tall)
+        net_r, res = fit(split(Xc, Tc, seed0 + r), f"round {r}")
+        del Xc, Tc
+        res["dnnmg_bf16"] = run_loop(net_r, "bf16")
+        if r == len(horizons):
+            res["dnnmg_fp64"] = run_loop(net_r, "fp64")
         for k in ("dnnmg_bf16", "dnnmg_fp64"):
-            if k in r and r[k]["failed"] is None:
-                r[k]["E_v_over_plain_coarse"] = r[k]["E_v"] / plain["E_v"]
-    log(f"B: BF16 E_v {resB['dnnmg_bf16']['E_v']}, failed {resB['dnnmg_bf16']['failed']}")
+            if k in res and res[k]["failed"] is None:
+                res[k]["E_v_over_plain_coarse"] = res[k]["E_v"] / plain["E_v"]
+        e = res["dnnmg_bf16"]["e_v"]
+        below = next((i for i, v in enumerate(e) if v >= plain["e_v"][i]), len(e))
+        res["dnnmg_bf16"]["steps_below_plain_coarse"] = below
+        log(f"round {r}: BF16 E_v {res['dnnmg_bf16']['E_v']}, failed {res['dnnmg_bf16']['failed']}, "
+            f"below plain for {below} steps")
+        rounds.append(res)
+        if r < len(horizons):
+            for m, nu, st in runs:
+                a, b = T.rollout_samples(m, nu, dt, theta, st, net_r, horizon=horizons[r], solver=coarse_solver())
+                Xall.append(a)
+                Tall.append(b)
+                n_roll += int(a.shape[0])
+            log(f"rollouts after round {r}: {n_roll} samples in all")
+    del runs, Xall, Tall
     if save_net:
         np.savez(save_net, widths=np.array(widths), norm_mu=norm[0], norm_sigma=norm[1], t_scale=norm[2],
-                 **{f"W{i}": w.astype(np.float32) for i, w in enumerate(netB[1])},
-                 **{f"shift{i}": b for i, b in enumerate(netB[3])})
+                 **{f"W{i}": w.astype(np.float32) for i, w in enumerate(net_r[1])},
+                 **{f"shift{i}": b for i, b in enumerate(net_r[3])})
     return {"workload": f"channel nz={nz} nested ({levels} refinement of nz={nz >> levels}) with a seeded "
                         f"cylinder: {geos[0]['patches']} coarse hex, targets from level L+2 "
                         f"({64 * geos[0]['patches']} hex, Dirichlet values the prolongated coarse data) "
                         f"injected onto L+1; backward Euler dt={dt}, {steps} steps per geometry from rest; "
                         f"BF16 network {'-'.join(map(str, widths))}",
             "geometries": geos, "reference_samples": n_ref,
-            "rollout_samples": n_roll, "rollout_horizon": horizon, "batch": batch, "epochs": epochs,
+            "rollout_samples": n_roll, "rollout_horizons": list(horizons), "batch": batch, "epochs": epochs,
             "optimizer": "AdamW lr 1e-3, weight decay 1e-5",
             "seconds": {"data": round(t_data, 1), "train": round(t_train, 1),
                         "total": round(time.perf_counter() - t0, 1)},
             "held_out": {"seed": seed, "D": round(float(Dh), 5), "Re": round(float(re[n_geometries]), 2),
-                         "steps": eval_steps, "plain_coarse": plain, "network_A": resA, "network_B": resB}}
+                         "steps": eval_steps, "plain_coarse": plain, "rounds": rounds}}
 
 
 def main():
@@ -1013,7 +1019,7 @@ def main():
     ap.add_argument("--train-scale", action="store_true",
                     help="run only the learned part at scale (8 seeded channel obstacles, level L+2 targets, "
                          "held-out geometry) and print its JSON line")
-    ap.add_argument("--train-steps", type=int, default=128, help="time steps per training geometry")
+    ap.add_argument("--train-steps", type=int, default=96, help="time steps per training geometry")
     ap.add_argument("--train-epochs", type=int, default=150)
     ap.add_argument("--train-ref-gmres-rtol", type=float, default=None,
                     help="GMRES tolerance per Newton step of the level-(L+2) reference solves")
