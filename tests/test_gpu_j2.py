@@ -64,8 +64,7 @@ def test_j2_zero_network_equals_plain_scheme():
     a, b = xa.cpu().numpy(), xb.cpu().numpy()
     assert np.abs(a - b).max() <= 1e-10 * np.abs(b).max()
     assert np.abs(b[:, 0:3]).max() > 0.1
-    # the fine-level solver is built for J = 1 only
-    with pytest.raises(capi.DnnmgError) as e:
-        capi.dnnmg_level_info(p.ctx, capi.LEVEL_FINE)
-    assert e.value.status == -8
+    # the fine level of a J = 2 context is level L+2 (16^3 cells), grouped
+    # by the level-(L+1) cells
+    assert capi.dnnmg_level_info(p.ctx, capi.LEVEL_FINE) == (17 ** 3, True)
     p.close()
