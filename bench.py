@@ -999,6 +999,55 @@ def train_at_scale(n_geometries=8, steps=96, eval_steps=64, epochs=150, batch=65
                          "steps": eval_steps, "plain_coarse": plain, "rounds": rounds}}
 
 
+def eval_saved_network(path, seeds, eval_steps=64, nz=TRAIN_NZ, levels=TRAIN_LEVELS, dt=0.01, theta=1.0):
+    """A network saved by --train-scale --save-net on further unseen
+    geometries: for each seed, the channel of that seed with Re drawn from
+    U[100, 300] (its own SplitMix64 stream), the level-(L+2) reference with
+    prolongated Dirichlet data, and e_v / E_v of the plain coarse scheme and
+    of DNN-MG (BF16) over eval_steps steps, as in train_at_scale."""
+    import numpy as np
+
+    from paper_2307_14837_gb300 import capi, inputs as I
+    from paper_2307_14837_gb300 import train as T
+
+    z = np.load(path)
+    widths = tuple(int(w) for w in z["widths"])
+    L = len(widths) - 1
+    network = (widths, [z[f"W{i}"].astype(np.float64) for i in range(L)], [np.ones(w) for w in widths[1:]],
+               [z[f"shift{i}"] for i in range(L)])
+    ref_solver = lambda: capi.dnnmg_solver_defaults(  # noqa: E731
+        mg_levels=levels + 2, mg_pre=4, mg_post=4, mg_omega=0.8, newton_rtol=1e-9, newton_atol=1e-10,
+        gmres_rtol=GMRES_FORCING, mg_bf16=1)
+    coarse_solver = lambda: capi.dnnmg_solver_defaults(  # noqa: E731
+        mg_levels=levels, newton_rtol=1e-9, newton_atol=1e-10, gmres_rtol=GMRES_FORCING)
+    out = {"network": "-".join(map(str, widths)), "steps": eval_steps, "geometries": []}
+    for seed in seeds:
+        m = I.channel_mesh(nz, seed=seed, levels=levels)
+        D = I.channel_geometry(seed)[0]
+        re = float(100.0 + 200.0 * I.splitmix_uniform(9100 + seed, 1)[0])
+        nu = D / re
+        _, _, held = T.make_samples(m, nu, dt, theta, eval_steps, solver=coarse_solver(), ref_levels=2,
+                                    ref_solver=ref_solver(), keep_steps=True, fine_boundary="prolongated")
+        ref = [s_["v_fine"][:, 0:3].cpu().numpy() for s_ in held]
+        res = {"seed": seed, "D": round(float(D), 5), "Re": round(re, 2)}
+        for name, netw in (("plain_coarse", None), ("dnnmg_bf16", network)):
+            vel = []
+            try:
+                T.trajectory_errors(m, nu, dt, theta, held, network=netw, solver=coarse_solver(),
+                                    precision="bf16" if netw else "fp64", velocities=vel)
+                failed = None
+            except capi.DnnmgError as e:
+                failed = {"step": len(vel) + 1, "status": e.status}
+            e = T.velocity_errors(vel, ref[:len(vel)]) if vel else {"e_v": [], "E_v": None}
+            res[name] = {"E_v": e["E_v"], "e_v_first_last": [e["e_v"][0], e["e_v"][-1]] if vel else None,
+                         "failed": failed}
+        if res["dnnmg_bf16"]["failed"] is None:
+            res["E_v_dnnmg_over_plain_coarse"] = res["dnnmg_bf16"]["E_v"] / res["plain_coarse"]["E_v"]
+        out["geometries"].append(res)
+        print(f"[eval-net] seed {seed}: {res}", file=sys.stderr, flush=True)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1024,6 +1073,9 @@ def main():
     ap.add_argument("--train-ref-gmres-rtol", type=float, default=None,
                     help="GMRES tolerance per Newton step of the level-(L+2) reference solves")
     ap.add_argument("--save-net", default=None, help="write the trained network (.npz) to this path")
+    ap.add_argument("--eval-net", default=None,
+                    help="evaluate a network saved by --save-net on the geometries of --eval-seeds")
+    ap.add_argument("--eval-seeds", default="109,110")
     ap.add_argument("--whole-steps-only", type=int, default=0, metavar="K",
                     help="print only the whole-time-step measurement (K timed steps) as one JSON line")
     ap.add_argument("--nz", type=int, default=NZ,
@@ -1063,6 +1115,14 @@ def main():
     if args.serving:
         if rank == 0:
             run_serving(args)
+        return
+
+    if args.eval_net:
+        if rank == 0:
+            import torch
+            torch.cuda.set_device(0)
+            seeds = [int(v) for v in args.eval_seeds.split(",")]
+            print(json.dumps({"eval_saved_network": eval_saved_network(args.eval_net, seeds)}))
         return
 
     if args.train_scale:
