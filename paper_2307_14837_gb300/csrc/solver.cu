@@ -912,40 +912,60 @@ __global__ void __launch_bounds__(256) bsr_spmv_bf16_kernel(int64_t n, const int
     if (lane < 4) y[4 * i + rr] = r ? r[4 * i + rr] - acc : acc;
 }
 
-// Group block of the global matrix inverted in place in shared memory by
-// Gauss-Jordan elimination with partial pivoting (rows swapped, the column
-// order restored at the end), stored column-major in Ainv so that applying
-// it is a coalesced dense product.  Thread (ty, tx) of a 16 x 16 layout
-// updates rows ty + 16 a and columns tx + 16 b at every step.  A zero pivot
-// leaves its row at zero (the inverse then has a zero component there, as a
-// triangular solve with that convention would).
+// Group block of the global matrix inverted by Gauss-Jordan elimination
+// with partial pivoting (rows swapped, the column order restored at the
+// end), stored column-major in Ainv so that applying it is a coalesced dense
+// product.  Thread (ty, tx) of a 16 x 16 layout keeps rows ty + 16 a and
+// columns tx + 16 b of the matrix in registers for the whole elimination;
+// at step k only column k (for the pivot and the multipliers) and the two
+// exchanged rows go through shared memory.  A zero pivot leaves its row at
+// zero (the inverse then has a zero component there, as a triangular solve
+// with that convention would).
 template <typename T, int NPG, typename TO>
 __global__ void __launch_bounds__(256) vanka_factor_kernel(int64_t ng, const int32_t* __restrict__ grp_blk,
                                                            const T* __restrict__ A, TO* __restrict__ Ainv) {
     constexpr int NL = 4 * NPG;
     constexpr int RB = (NL + 15) / 16;   // rows (and columns) per thread
     extern __shared__ __align__(16) unsigned char vf_smem[];
-    T* M = reinterpret_cast<T*>(vf_smem);   // NL x NL, row-major
-    __shared__ T s_f[NL];
+    T* M = reinterpret_cast<T*>(vf_smem);   // NL x NL, row-major: the result, at the end
+    __shared__ T s_col[NL];                 // column k before the row exchange
+    __shared__ T s_rowk[NL];                // the new row k (old row p)
+    __shared__ T s_rowp[NL];                // the new row p (old row k)
     __shared__ int s_piv[NL];
-    __shared__ int s_col[NL];
+    __shared__ int s_perm[NL];
     const int64_t g = blockIdx.x;
     const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
-    for (int e = tid; e < NL * NL; e += blockDim.x) {
-        const int i = e / NL, j = e % NL;
-        const int32_t b = grp_blk[(g * NPG + i / 4) * NPG + j / 4];
-        M[e] = A[16 * int64_t(b) + 4 * (i % 4) + (j % 4)];
-    }
-    __syncthreads();
+    T R[RB][RB];
+#pragma unroll
+    for (int a = 0; a < RB; ++a)
+#pragma unroll
+        for (int b = 0; b < RB; ++b) {
+            const int i = ty + 16 * a, j = tx + 16 * b;
+            R[a][b] = T(0);
+            if (i < NL && j < NL) {
+                const int32_t blk = grp_blk[(g * NPG + i / 4) * NPG + j / 4];
+                R[a][b] = A[16 * int64_t(blk) + 4 * (i % 4) + (j % 4)];
+            }
+        }
     for (int k = 0; k < NL; ++k) {
+        const int kb = k >> 4;
+        if (tx == (k & 15)) {
+#pragma unroll
+            for (int b = 0; b < RB; ++b)
+                if (b == kb)
+#pragma unroll
+                    for (int a = 0; a < RB; ++a)
+                        if (ty + 16 * a < NL) s_col[ty + 16 * a] = R[a][b];
+        }
+        __syncthreads();
         if (tid < 32) {
             // pivot: largest |M[i][k]|, i >= k, smallest i on ties (warp argmax)
             T bv = T(-1);
             int bi = k;
             for (int i = k + tid; i < NL; i += 32) {
-                const T a = fabs(M[i * NL + k]);
-                if (a > bv) {
-                    bv = a;
+                const T v = fabs(s_col[i]);
+                if (v > bv) {
+                    bv = v;
                     bi = i;
                 }
             }
@@ -960,52 +980,73 @@ __global__ void __launch_bounds__(256) vanka_factor_kernel(int64_t ng, const int
             if (tid == 0) s_piv[k] = bi;
         }
         __syncthreads();
-        const int pr = s_piv[k];
-        if (pr != k)
-            for (int j = tid; j < NL; j += blockDim.x) {
-                const T t = M[k * NL + j];
-                M[k * NL + j] = M[pr * NL + j];
-                M[pr * NL + j] = t;
+        const int p = s_piv[k];
+        // the owners of rows p and k publish them (exchanged)
+        if (ty == (p & 15) || ty == (k & 15)) {
+#pragma unroll
+            for (int a = 0; a < RB; ++a) {
+                const int i = ty + 16 * a;
+                if (i != p && i != k) continue;
+#pragma unroll
+                for (int b = 0; b < RB; ++b) {
+                    const int j = tx + 16 * b;
+                    if (j >= NL) continue;
+                    if (i == p) s_rowk[j] = R[a][b];
+                    if (i == k) s_rowp[j] = R[a][b];
+                }
             }
+        }
         __syncthreads();
-        // row k / pivot (the pivot's own slot becomes 1 / pivot); column k kept
-        const T d = M[k * NL + k];
+        const T d = s_col[p];
         const T inv = d != T(0) ? T(1) / d : T(0);
-        for (int i = tid; i < NL; i += blockDim.x) s_f[i] = i == k ? T(0) : M[i * NL + k];
-        __syncthreads();
-        for (int j = tid; j < NL; j += blockDim.x) M[k * NL + j] = (j == k ? T(1) : M[k * NL + j]) * inv;
-        __syncthreads();
-        // every other row: row_i -= f_i row_k, with column k starting from 0
+        T nr[RB];   // the normalised pivot row at this thread's columns
+#pragma unroll
+        for (int b = 0; b < RB; ++b) {
+            const int j = tx + 16 * b;
+            nr[b] = j < NL ? (j == k ? T(1) : s_rowk[j]) * inv : T(0);
+        }
 #pragma unroll
         for (int a = 0; a < RB; ++a) {
             const int i = ty + 16 * a;
-            if (i >= NL || i == k) continue;
-            const T f = s_f[i];
+            if (i >= NL) continue;
+            if (i == k) {
+#pragma unroll
+                for (int b = 0; b < RB; ++b) R[a][b] = nr[b];
+                continue;
+            }
+            const T f = i == p ? s_col[k] : s_col[i];
 #pragma unroll
             for (int b = 0; b < RB; ++b) {
                 const int j = tx + 16 * b;
                 if (j >= NL) continue;
-                const T m = j == k ? T(0) : M[i * NL + j];
-                M[i * NL + j] = m - f * M[k * NL + j];
+                const T src = i == p ? s_rowp[j] : R[a][b];
+                R[a][b] = (j == k ? T(0) : src) - f * nr[b];
             }
         }
-        __syncthreads();
+        __syncthreads();   // s_col and the rows are rewritten at the next step
     }
+#pragma unroll
+    for (int a = 0; a < RB; ++a)
+#pragma unroll
+        for (int b = 0; b < RB; ++b) {
+            const int i = ty + 16 * a, j = tx + 16 * b;
+            if (i < NL && j < NL) M[i * NL + j] = R[a][b];
+        }
     // the row swaps of the elimination become column swaps of the inverse,
-    // undone in reverse order: column c of the inverse is column s_col[c]
+    // undone in reverse order: column c of the inverse is column s_perm[c]
     if (tid == 0) {
-        for (int c = 0; c < NL; ++c) s_col[c] = c;
+        for (int c = 0; c < NL; ++c) s_perm[c] = c;
         for (int k = NL - 1; k >= 0; --k) {
-            const int t = s_col[k];
-            s_col[k] = s_col[s_piv[k]];
-            s_col[s_piv[k]] = t;
+            const int t = s_perm[k];
+            s_perm[k] = s_perm[s_piv[k]];
+            s_perm[s_piv[k]] = t;
         }
     }
     __syncthreads();
     // column-major: Ainv[g][j * NL + i] = (A^{-1})_{ij} (rounded once to TO)
     for (int e = tid; e < NL * NL; e += blockDim.x) {
         const int j = e / NL, i = e % NL;
-        Ainv[g * NL * NL + e] = TO(M[i * NL + s_col[j]]);
+        Ainv[g * NL * NL + e] = TO(M[i * NL + s_perm[j]]);
     }
 }
 
