@@ -74,3 +74,24 @@ def test_noalloc_limit_matches_header():
     src = open(os.path.join(ROOT, "include", "dnnmg.h")).read()
     m = re.search(r"#define\s+DNNMG_NOALLOC_MAX_PATCHES\s+(\d+)", src)
     assert m and int(m.group(1)) == capi.NOALLOC_MAX_PATCHES
+
+
+def test_training_data_calls_reject_bad_arguments_without_a_gpu(lib):
+    # argument checks come before any CUDA call: EINVAL (-1) on the CPU
+    L = capi.load()
+    fake = 4096                                   # never dereferenced on these paths
+    FP32, BF16 = capi.FP32, capi.BF16
+    assert L.dnnmg_column_stats(None, FP32, 10, 4, 4, fake, fake, None) == -1
+    assert L.dnnmg_column_stats(fake, FP32, 1, 4, 4, fake, fake, None) == -1     # rows < 2
+    assert L.dnnmg_column_stats(fake, FP32, 10, 8, 4, fake, fake, None) == -1    # ld < cols
+    assert L.dnnmg_column_stats(fake, 7, 10, 4, 4, fake, fake, None) == -1       # unknown dtype
+    assert L.dnnmg_standardize(fake, BF16, 10, 0, 4, fake, fake, fake, None) == -1
+    assert L.dnnmg_standardize(fake, BF16, 0, 4, 4, fake, fake, fake, None) == 0  # nothing to do
+    assert L.dnnmg_gather_rows(fake, 10, 0, fake, 5, fake, None) == -1           # row_bytes
+    assert L.dnnmg_gather_rows(fake, 10, 16, fake, 0, fake, None) == 0
+    assert L.dnnmg_add_noise(None, BF16, 10, 0, 4, 8, 0.1, 1, None) == -1
+    assert L.dnnmg_add_noise(fake, BF16, 10, 4, 2, 8, 0.1, 1, None) == -1        # c1 < c0
+    assert L.dnnmg_add_noise(fake, BF16, 10, 0, 9, 8, 0.1, 1, None) == -1        # c1 > ld
+    assert L.dnnmg_add_noise(fake, BF16, 10, 0, 4, 8, -0.1, 1, None) == -1       # sigma < 0
+    assert L.dnnmg_add_noise(fake, BF16, 10, 0, 4, 8, 0.0, 1, None) == 0         # no noise: no launch
+    assert L.dnnmg_patch_targets(None, fake, fake, fake, 81) == -1
